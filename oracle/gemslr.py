@@ -1,0 +1,155 @@
+"""GeMSLR setup (Alg. 1) and standard solve (Alg. 2), FP64, plain and slow.
+
+Level structure (reading of "l_ev levels", Sec. 2.4 and Alg. 2's commented
+last-level branch): levels l = 0 .. nlev-2 are Schur levels, each with its
+B_l (p diagonal blocks, incomplete LU), coupling blocks E_l, F_l and a rank-k
+correction W_l, H_l; the last level is the matrix C_{nlev-2} itself, applied
+by block-Jacobi incomplete LU over its p_last diagonal blocks with the
+off-block entries discarded (Sec. 4.3), and no low-rank term.
+
+Vectors handled by ``apply_perm`` are in the multilevel (permuted) order
+x_hat = P^T x, i.e. x_hat[i] = x[perm[i]]; level l owns the contiguous range
+[level_ptr[l], level_ptr[l+1]) and A_l acts on the tail [level_ptr[l], n).
+"""
+import numpy as np
+import scipy.sparse as sp
+
+from . import ilu as _ilu
+from .lowrank import correction_matrix, krylov_schur
+from .partition import level_blocks
+
+
+def _factor_blocks(B, bp, kind, tau, lfil):
+    """Incomplete LU of every diagonal block of B; block-diagonal L, U."""
+    Ls, Us = [], []
+    nclamp = 0
+    for j in range(len(bp) - 1):
+        a, b = bp[j], bp[j + 1]
+        Bj = B[a:b, a:b]
+        if kind == "ilu0":
+            L, U, c = _ilu.ilu0(Bj)
+        elif kind == "ilut":
+            L, U, c = _ilu.ilut(Bj, tau, lfil)
+        elif kind == "exact":
+            L, U, c = _ilu.ilut(Bj, 0.0, -1)
+        else:
+            raise ValueError(kind)
+        Ls.append(sp.csr_matrix(L, shape=(b - a, b - a)))
+        Us.append(sp.csr_matrix(U, shape=(b - a, b - a)))
+        nclamp += c
+    n = B.shape[0]
+    if n == 0:
+        z = sp.csr_matrix((0, 0))
+        return z, z, nclamp
+    L = sp.block_diag(Ls, format="csr") if Ls else sp.csr_matrix((n, n))
+    U = sp.block_diag(Us, format="csr") if Us else sp.csr_matrix((n, n))
+    L.sort_indices()
+    U.sort_indices()
+    return sp.csr_matrix(L, shape=(n, n)), sp.csr_matrix(U, shape=(n, n)), nclamp
+
+
+class OracleGemslr:
+    """Multilevel GeMSLR preconditioner built by the oracle.
+
+    Parameters
+    ----------
+    A : scipy sparse (n x n)
+    part : dict from ``multilevel_partition``
+    ilu : "ilu0" | "ilut" | "exact" (ILUT with tau = 0 and no fill limit)
+    rank : int or list (per Schur level); 0 disables the correction
+    last_ilu : factor kind of the last-level blocks (defaults to ``ilu``)
+    """
+
+    def __init__(self, A, part, ilu="ilu0", tau=1e-3, lfil=10, rank=8, last_ilu=None,
+                 arnoldi_tol=1e-2, max_cycles=20, lowrank=True):
+        A = sp.csr_matrix(A)
+        self.n = A.shape[0]
+        self.part = part
+        self.perm = np.asarray(part["perm"], dtype=np.int64)
+        self.nlev = len(part["nblk"])
+        Ah = A[self.perm][:, self.perm].tocsr()
+        Ah.sort_indices()
+        self.Ahat = Ah
+        nsch = self.nlev - 1
+        ranks = list(rank) if np.ndim(rank) else [int(rank)] * nsch
+        self.levels = []
+        self.nclamp = 0
+        for l in range(nsch):
+            s, e, bp = level_blocks(part, l)
+            bp = bp - s
+            B = Ah[s:e, s:e]
+            L, U, c = _factor_blocks(B, bp, ilu, tau, lfil)
+            self.nclamp += c
+            self.levels.append(dict(s=s, e=e, bp=bp, L=L, U=U,
+                                    E=Ah[e:, s:e].tocsr(), F=Ah[s:e, e:].tocsr(),
+                                    W=np.zeros((self.n - e, 0)), H=np.zeros((0, 0)),
+                                    rank=ranks[l], info=None))
+        s, e, bp = level_blocks(part, self.nlev - 1)
+        bp = bp - s
+        C = Ah[s:, s:].tocsr()
+        # block-Jacobi: keep the diagonal blocks only
+        keep = sp.block_diag([C[bp[j]:bp[j + 1], bp[j]:bp[j + 1]] for j in range(len(bp) - 1)],
+                             format="csr") if C.shape[0] else sp.csr_matrix((0, 0))
+        self.last_s = s
+        self.last_bp = bp
+        self.last_C = keep
+        Lc, Uc, c = _factor_blocks(keep, bp, last_ilu or ilu, tau, lfil)
+        self.nclamp += c
+        self.last_L, self.last_U = Lc, Uc
+        if lowrank:
+            # bottom-up (Sec. 4.2): level l needs the apply of every level > l
+            for l in range(nsch - 1, -1, -1):
+                self.build_lowrank(l, arnoldi_tol, max_cycles)
+
+    # ---- pieces of Alg. 2 -------------------------------------------------
+    def solve_level(self, r, l):
+        """pGeMSLRSolve(r, l) on the tail vector r (length n - level_ptr[l])."""
+        if l == self.nlev - 1:
+            return _ilu.lu_solve(self.last_L, self.last_U, r)
+        lv = self.levels[l]
+        d = lv["e"] - lv["s"]
+        b1, b2 = r[:d], r[d:]
+        z1 = _ilu.lu_solve(lv["L"], lv["U"], b1)                 # z1 = U^-1 L^-1 b1
+        z2 = b2 - lv["E"] @ z1                                   # z2 = b2 - E z1
+        W, H = lv["W"], lv["H"]
+        u2 = W @ (H @ (W.T @ z2)) if W.shape[1] else np.zeros_like(z2)
+        y2 = self.solve_level(u2 + z2, l + 1)                    # y2 = Solve(u2 + z2, l+1)
+        y1 = z1 - _ilu.lu_solve(lv["L"], lv["U"], lv["F"] @ y2)  # y1 = z1 - U^-1 L^-1 F y2
+        return np.concatenate([y1, y2])
+
+    def apply_perm(self, r_hat):
+        """M^{-1} in the multilevel ordering."""
+        return self.solve_level(np.asarray(r_hat, dtype=np.float64), 0)
+
+    def apply(self, r):
+        """M^{-1} r in the original ordering: P (M_hat^{-1} (P^T r))."""
+        y = self.apply_perm(np.asarray(r, dtype=np.float64)[self.perm])
+        out = np.empty_like(y)
+        out[self.perm] = y
+        return out
+
+    def g_hat(self, l, z):
+        """G_hat_l z = E_l U_l^-1 L_l^-1 F_l C_l^-1 z with C_l^-1 the apply of levels > l."""
+        lv = self.levels[l]
+        y = self.solve_level(z, l + 1)
+        return lv["E"] @ _ilu.lu_solve(lv["L"], lv["U"], lv["F"] @ y)
+
+    def build_lowrank(self, l, tol=1e-2, max_cycles=20):
+        lv = self.levels[l]
+        s = self.n - lv["e"]
+        W, Tk, info = krylov_schur(lambda z: self.g_hat(l, z), s, lv["rank"], 1000 + l,
+                                   tol=tol, max_cycles=max_cycles)
+        lv["W"] = W
+        lv["T"] = Tk
+        lv["H"] = correction_matrix(Tk)
+        lv["info"] = info
+
+    # ---- export -------------------------------------------------------------
+    def factors(self):
+        """Everything the solve phase reads, in the multilevel ordering."""
+        out = dict(n=self.n, perm=self.perm.astype(np.int32), nlev=self.nlev, levels=[])
+        for lv in self.levels:
+            out["levels"].append(dict(s=lv["s"], e=lv["e"], bp=lv["bp"], L=lv["L"], U=lv["U"],
+                                      E=lv["E"], F=lv["F"], W=lv["W"], H=lv["H"]))
+        out["last"] = dict(s=self.last_s, bp=self.last_bp, L=self.last_L, U=self.last_U)
+        return out
