@@ -1,0 +1,230 @@
+/*
+ * gemslr.h -- C ABI of the GB300 GeMSLR-preconditioned FGMRES solve phase.
+ *
+ * Method: Xu, Kalantzis, Li, Xi, Dillon, Saad, "parGeMSLR: A Parallel
+ * Multilevel Schur Complement Low-Rank Preconditioning and Solution Package
+ * for General Sparse Matrices" (arXiv 2205.03224).  The problem is A x = b
+ * with A large, sparse, possibly non-symmetric (Sec. 1), solved by right-
+ * preconditioned restarted FGMRES (Sec. 4.1, Sec. 5) whose preconditioner
+ * M^{-1} is the multilevel Schur-complement low-rank (GeMSLR) operator of
+ * Alg. 2 built by Alg. 1 over the multilevel vertex-separator reordering of
+ * Alg. 3.
+ *
+ * Conventions for every entry point:
+ *  - Host arrays passed in are read during the call only and stay owned by
+ *    the caller; the library copies what it keeps.
+ *  - Device arrays ("_dev") are caller-owned CUDA device memory on the
+ *    current device, FP64, used only on the given stream (NULL = default
+ *    stream).  Multi-RHS arrays are column-major with leading dimension n.
+ *  - Every call returns a gemslr_status; on failure a thread-local message is
+ *    available from gemslr_last_error().  No C++ exception crosses the ABI.
+ *  - Handles are not thread-safe: one host thread at a time per handle.
+ *  - Levels: nlev counts the Schur levels l = 0..nlev-2 (each with B_l, E_l,
+ *    F_l and a rank-k_l correction) plus the last level, the matrix
+ *    C_{nlev-2}, which is applied by block-Jacobi incomplete LU of its
+ *    diagonal blocks (Sec. 4.3) and has no low-rank term.
+ */
+#ifndef GEMSLR_H
+#define GEMSLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GEMSLR_MAX_LEVELS 16
+
+typedef struct gemslr_ctx *gemslr_handle;   /* opaque, owned by the library */
+
+typedef enum {
+    GEMSLR_OK = 0,
+    GEMSLR_ERR_ARG = 1,           /* bad argument (NULL, size, option)            */
+    GEMSLR_ERR_PARTITION = 2,     /* partition invalid or blocks of B_l coupled    */
+    GEMSLR_ERR_ZERO_PIVOT = 3,    /* pivot clamped while options.strict_pivots set */
+    GEMSLR_ERR_NOT_CONVERGED = 4, /* FGMRES hit maxit (the paper's "F")           */
+    GEMSLR_ERR_NAN = 5,           /* NaN/Inf in b or during the iteration          */
+    GEMSLR_ERR_TIMEOUT = 6,       /* a bounded device wait expired                 */
+    GEMSLR_ERR_CUDA = 7,          /* CUDA runtime error                            */
+    GEMSLR_ERR_NOMEM = 8,         /* host or device allocation failed              */
+    GEMSLR_ERR_UNSUPPORTED = 9    /* valid request this build does not implement   */
+} gemslr_status;
+
+/* Host CSR matrix, 0-based, columns ascending within a row. */
+typedef struct {
+    int64_t n;                /* rows = columns                                   */
+    const int64_t *rowptr;    /* n + 1                                            */
+    const int32_t *colind;    /* rowptr[n]                                        */
+    const double *val;        /* rowptr[n]                                        */
+} gemslr_csr;
+
+/*
+ * Multilevel partition (Alg. 3): perm lists the original index of every
+ * unknown in the multilevel order (new -> old).  Level l owns the contiguous
+ * range [level_ptr[l], level_ptr[l+1]); its blocks are given by
+ * block_ptr[o_l .. o_l + nblk[l]] relative to level_ptr[l], where
+ * o_l = sum_{i<l} (nblk[i] + 1).  For Schur levels the blocks must be
+ * uncoupled in |A| + |A^T| (the vertex-separator property, Sec. 3); the
+ * last level's blocks are the block-Jacobi blocks (Sec. 4.3).
+ */
+typedef struct {
+    int32_t nlev;
+    const int32_t *perm;       /* n                        */
+    const int64_t *level_ptr;  /* nlev + 1                 */
+    const int32_t *nblk;       /* nlev                     */
+    const int64_t *block_ptr;  /* sum(nblk) + nlev         */
+} gemslr_partition;
+
+/* Precision of the preconditioner application (FGMRES is FP64 in both). */
+enum { GEMSLR_PREC_FP64 = 0, GEMSLR_PREC_MIXED = 1 };
+/* Incomplete factorisation of the diagonal blocks. */
+enum { GEMSLR_ILU0 = 0, GEMSLR_ILUT = 1 };
+
+typedef struct {
+    int32_t ilu_kind;             /* GEMSLR_ILU0 or GEMSLR_ILUT                     */
+    double ilut_tau;              /* ILUT drop tolerance (relative to ||a_i||_2)    */
+    int32_t ilut_lfil;            /* ILUT fill per row in L and in U (<0: no cap)   */
+    int32_t rank[GEMSLR_MAX_LEVELS]; /* k_l per Schur level (0 = no correction)     */
+    int32_t precision;            /* GEMSLR_PREC_FP64 or GEMSLR_PREC_MIXED          */
+    double arnoldi_tol;           /* Ritz accuracy for the low-rank term (1e-2)     */
+    int32_t arnoldi_max_cycles;   /* thick-restart cycles (20)                      */
+    int32_t strict_pivots;        /* nonzero: a clamped pivot fails the setup      */
+} gemslr_options;
+
+/* Fill *opt with the defaults: ILUT(1e-3, 10), rank 0, FP64, 1e-2, 20 cycles. */
+void gemslr_default_options(gemslr_options *opt);
+
+/*
+ * Geometric multilevel partition (Alg. 3 with a p-way vertex separator from
+ * recursive coordinate bisection; the last level ordered by reverse
+ * Cuthill-McKee and cut into p_last chunks, Sec. 4.3).  coords: n x 3 int32
+ * grid coordinates, row-major.  p must be a power of two.  Output arrays are
+ * caller-allocated: perm (n), level_ptr (nlev+1), nblk (nlev),
+ * block_ptr ((nlev-1)*(p+1) + p_last + 1).
+ */
+gemslr_status gemslr_partition_geometric(const gemslr_csr *A, const int32_t *coords,
+                                         int32_t nlev, int32_t p, int32_t p_last,
+                                         int32_t *perm, int64_t *level_ptr, int32_t *nblk,
+                                         int64_t *block_ptr);
+
+/*
+ * Setup (Alg. 1): permute A, factor every diagonal block of every B_l and of
+ * the last level, then bottom-up (Sec. 4.2) compute the rank-k_l correction
+ * W_l [(I - R_l)^{-1} - I] W_l^T from thick-restart Arnoldi on
+ * G_l = E_l (U_l^{-1} L_l^{-1}) F_l C_l^{-1} (Sec. 2.3), with C_l^{-1} the
+ * GPU application of the levels below.  Uses the current CUDA device.
+ * Errors: ARG, PARTITION (blocks coupled), ZERO_PIVOT (strict_pivots),
+ * CUDA, NOMEM.  On success *out owns all device memory it uses.
+ */
+gemslr_status gemslr_setup(const gemslr_csr *A, const gemslr_partition *part,
+                           const gemslr_options *opt, gemslr_handle *out);
+
+/* One CSR piece of the hierarchy in the multilevel order (host, 0-based). */
+typedef struct {
+    int64_t nrows, ncols;
+    const int64_t *rowptr;
+    const int32_t *colind;
+    const double *val;
+} gemslr_mat;
+
+/*
+ * Factors of one Schur level l, in level-local numbering:
+ *  L: d_l x d_l strictly lower (unit diagonal implied), block diagonal;
+ *  U: d_l x d_l upper including its diagonal, block diagonal;
+ *  E: s_l x d_l (rows: the tail [level_ptr[l+1], n) minus level_ptr[l+1]);
+ *  F: d_l x s_l;
+ *  W: s_l x k column-major, H = (I - R_k)^{-1} - I: k x k column-major.
+ */
+typedef struct {
+    gemslr_mat L, U, E, F;
+    int32_t k;
+    const double *W;
+    const double *H;
+} gemslr_level_factors;
+
+typedef struct {
+    int32_t nlev;
+    const gemslr_level_factors *levels;   /* nlev - 1 Schur levels              */
+    gemslr_mat last_L, last_U;            /* last level, block diagonal         */
+} gemslr_factors;
+
+/*
+ * Build a handle from factors computed elsewhere (checkpoint/resume, or a
+ * reference computation): nothing is factored, the permuted A is still
+ * formed for the FGMRES products.  Same errors as gemslr_setup.
+ */
+gemslr_status gemslr_setup_from_factors(const gemslr_csr *A, const gemslr_partition *part,
+                                        const gemslr_factors *f, const gemslr_options *opt,
+                                        gemslr_handle *out);
+
+/*
+ * Sizes of the handle's factors (for gemslr_export_factors buffers):
+ * counts[0] = nlev; then per Schur level l, 9 entries starting at 1 + 9*l:
+ * nnz(L), nnz(U), nnz(E), nnz(F), k, d_l, s_l, level_ptr[l], level_ptr[l+1];
+ * then nnz(last_L), nnz(last_U), size of the last level.  ncounts must be at
+ * least 4 + 9*(nlev-1).
+ */
+gemslr_status gemslr_factor_sizes(gemslr_handle h, int64_t *counts, int64_t ncounts);
+
+/*
+ * Copy the factors out (host).  The caller fills the pointer fields of every
+ * gemslr_mat / W / H in *f with buffers of the sizes reported by
+ * gemslr_factor_sizes (rowptr nrows+1, colind/val nnz, W s*k, H k*k); the
+ * library writes into them.
+ */
+gemslr_status gemslr_export_factors(gemslr_handle h, gemslr_factors *f);
+
+/*
+ * z = M^{-1} r (Alg. 2) for nrhs right-hand sides in the ORIGINAL ordering:
+ * z = P M_hat^{-1} P^T r.  r_dev, z_dev: n x nrhs column-major device arrays
+ * (may not alias).  Asynchronous on `stream`.
+ */
+gemslr_status gemslr_apply(gemslr_handle h, const double *r_dev, double *z_dev, int32_t nrhs,
+                           void *stream);
+
+typedef struct {
+    int32_t restart;     /* FGMRES cycle length m                               */
+    int32_t maxit;       /* total inner iterations (1,000 in the paper)         */
+    double rtol;         /* stop when ||b - A x|| <= rtol ||b|| (true residual) */
+} gemslr_solve_opts;
+
+typedef struct {
+    int32_t iters;            /* inner iterations taken                         */
+    int32_t restarts;         /* completed cycles that did not converge        */
+    int32_t converged;        /* 1 if the true residual met rtol                */
+    int32_t reorth;           /* iterations that needed a second orthogonalisation */
+    double rel_res_est;       /* |g_{j+1}| / ||b|| at exit                      */
+    double rel_res_true;      /* ||b - A x|| / ||b|| at exit                    */
+    double t_total_ms;        /* wall time of the solve call                    */
+} gemslr_solve_info;
+
+/*
+ * Solve A x = b by restarted right-preconditioned FGMRES(m) with x_0 = 0 and
+ * M^{-1} from the handle.  b_dev, x_dev: n x nrhs column-major device arrays in
+ * the original ordering; info: nrhs entries (host).  Synchronises `stream`.
+ * Returns NOT_CONVERGED (with info filled) when maxit is reached, NAN when b
+ * or the iteration is not finite.
+ */
+gemslr_status gemslr_fgmres_solve(gemslr_handle h, const double *b_dev, double *x_dev,
+                                  int32_t nrhs, const gemslr_solve_opts *opts,
+                                  gemslr_solve_info *info, void *stream);
+
+/*
+ * Statistics: out[0..] = n, nlev, nclamped pivots, nnz(A), nnz of all
+ * factors, algorithmic bytes per M^{-1} application, setup ms, device bytes,
+ * then per level: d_l, s_l, k_l, nnz(L_l)+nnz(U_l), L wavefronts, U wavefronts.
+ * nout: capacity of out (8 + 6*nlev suffices).
+ */
+gemslr_status gemslr_get_stats(gemslr_handle h, double *out, int32_t nout);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *gemslr_last_error(void);
+
+/* Free the handle and its device memory (NULL is accepted). */
+void gemslr_destroy(gemslr_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEMSLR_H */

@@ -1,0 +1,179 @@
+"""Python front end of the C ABI (argument marshalling only)."""
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _stream(torch):
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def partition_geometric(A, coords, nlev, p, p_last=None):
+    """Multilevel partition (Alg. 3) computed by the library; returns a dict of arrays."""
+    lib = L.load()
+    keep = []
+    csr = L.csr_struct(A, keep)
+    n = csr.n
+    p_last = p if p_last is None else p_last
+    coords = np.ascontiguousarray(coords, dtype=np.int32).reshape(n, 3)
+    perm = np.zeros(n, dtype=np.int32)
+    level_ptr = np.zeros(nlev + 1, dtype=np.int64)
+    nblk = np.zeros(nlev, dtype=np.int32)
+    block_ptr = np.zeros((nlev - 1) * (p + 1) + p_last + 1, dtype=np.int64)
+    L.check(lib.gemslr_partition_geometric(ctypes.byref(csr), L.ptr(coords), nlev, p, p_last, L.ptr(perm),
+                                           L.ptr(level_ptr), L.ptr(nblk), L.ptr(block_ptr)))
+    return dict(perm=perm, level_ptr=level_ptr, nblk=nblk, block_ptr=block_ptr)
+
+
+def options(ilu="ilut", tau=1e-3, lfil=10, rank=0, precision="fp64", arnoldi_tol=1e-2, max_cycles=20,
+            strict_pivots=False):
+    o = L.Options()
+    L.load().gemslr_default_options(ctypes.byref(o))
+    o.ilu_kind = {"ilu0": 0, "ilut": 1}[ilu]
+    o.ilut_tau = tau
+    o.ilut_lfil = lfil
+    ranks = list(rank) if np.ndim(rank) else [int(rank)] * L.MAX_LEVELS
+    for i in range(L.MAX_LEVELS):
+        o.rank[i] = ranks[i] if i < len(ranks) else 0
+    o.precision = {"fp64": 0, "mixed": 1}[precision]
+    o.arnoldi_tol = arnoldi_tol
+    o.arnoldi_max_cycles = max_cycles
+    o.strict_pivots = 1 if strict_pivots else 0
+    return o
+
+
+class Gemslr:
+    """Handle of a GeMSLR preconditioner living on the current CUDA device."""
+
+    def __init__(self, A, part, _handle=None, **opts):
+        self._lib = L.load()
+        self.n = int(len(part["perm"]))
+        self.nlev = int(len(part["nblk"]))
+        if _handle is not None:
+            self._h = _handle
+            return
+        keep = []
+        csr = L.csr_struct(A, keep)
+        prt = L.partition_struct(part, keep)
+        o = options(**opts)
+        h = ctypes.c_void_p()
+        L.check(self._lib.gemslr_setup(ctypes.byref(csr), ctypes.byref(prt), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_factors(cls, A, part, fac, **opts):
+        """Handle built from given factors (dict as produced by ``oracle``'s factors())."""
+        lib = L.load()
+        keep = []
+        csr = L.csr_struct(A, keep)
+        prt = L.partition_struct(part, keep)
+        lv = fac["levels"]
+        arr = (L.LevelFactors * max(len(lv), 1))()
+        for i, f in enumerate(lv):
+            W = np.asfortranarray(f["W"], dtype=np.float64)
+            H = np.asfortranarray(f["H"], dtype=np.float64)
+            keep.extend([W, H])
+            arr[i] = L.LevelFactors(L.mat_struct(f["L"], keep), L.mat_struct(f["U"], keep),
+                                    L.mat_struct(f["E"], keep), L.mat_struct(f["F"], keep),
+                                    W.shape[1], L.ptr(W) if W.size else None, L.ptr(H) if H.size else None)
+        fs = L.Factors(len(lv) + 1, arr, L.mat_struct(fac["last"]["L"], keep), L.mat_struct(fac["last"]["U"], keep))
+        o = options(**opts)
+        h = ctypes.c_void_p()
+        L.check(lib.gemslr_setup_from_factors(ctypes.byref(csr), ctypes.byref(prt), ctypes.byref(fs),
+                                              ctypes.byref(o), ctypes.byref(h)))
+        return cls(A, part, _handle=h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gemslr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, r):
+        """z = M^{-1} r for a CUDA float64 tensor r of shape (n,) or (n, nrhs) column-major."""
+        import torch
+        r = r.contiguous() if r.dim() == 1 else r.t().contiguous().t()
+        z = torch.empty_like(r)
+        nrhs = 1 if r.dim() == 1 else r.shape[1]
+        L.check(self._lib.gemslr_apply(self._h, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                       nrhs, _stream(torch)))
+        return z
+
+    def solve(self, b, restart=50, rtol=1e-8, maxit=1000, check=True):
+        """FGMRES(restart) on A x = b; returns (x, [info dict per right-hand side])."""
+        import torch
+        b = b.contiguous() if b.dim() == 1 else b.t().contiguous().t()
+        x = torch.empty_like(b)
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+        so = L.SolveOpts(restart, maxit, rtol)
+        info = (L.SolveInfo * nrhs)()
+        st = self._lib.gemslr_fgmres_solve(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                           nrhs, ctypes.byref(so), info, _stream(torch))
+        infos = [dict(iters=i.iters, restarts=i.restarts, converged=bool(i.converged), reorth=i.reorth,
+                      rel_res_est=i.rel_res_est, rel_res_true=i.rel_res_true, t_total_ms=i.t_total_ms,
+                      status=L.STATUS.get(st, st)) for i in info]
+        if check and st not in (0, 4):
+            L.check(st)
+        return x, infos
+
+    def stats(self):
+        out = np.zeros(8 + 6 * self.nlev)
+        L.check(self._lib.gemslr_get_stats(self._h, L.ptr(out), len(out)))
+        lev = [dict(d=int(out[8 + 6 * l]), s=int(out[9 + 6 * l]), k=int(out[10 + 6 * l]),
+                    nnz_lu=int(out[11 + 6 * l]), wavefronts_L=int(out[12 + 6 * l]),
+                    wavefronts_U=int(out[13 + 6 * l])) for l in range(self.nlev)]
+        return dict(n=int(out[0]), nlev=int(out[1]), nclamp=int(out[2]), nnz_A=int(out[3]),
+                    nnz_factors=int(out[4]), bytes_per_apply=float(out[5]), setup_ms=float(out[6]),
+                    device_bytes=int(out[7]), levels=lev)
+
+    def export_factors(self):
+        """Copy the factors to host (dict with the layout of ``from_factors``)."""
+        import scipy.sparse as sp
+        nl = self.nlev
+        counts = np.zeros(4 + 9 * (nl - 1), dtype=np.int64)
+        L.check(self._lib.gemslr_factor_sizes(self._h, L.ptr(counts), len(counts)))
+        keep = []
+
+        def mk(nrows, ncols, nnz):
+            rp = np.zeros(nrows + 1, dtype=np.int64)
+            ci = np.zeros(max(nnz, 1), dtype=np.int32)
+            v = np.zeros(max(nnz, 1), dtype=np.float64)
+            keep.append((rp, ci, v, nrows, ncols, nnz))
+            return L.Mat(nrows, ncols, L.ptr(rp), L.ptr(ci), L.ptr(v)), len(keep) - 1
+
+        arr = (L.LevelFactors * max(nl - 1, 1))()
+        meta = []
+        for l in range(nl - 1):
+            c = counts[1 + 9 * l: 10 + 9 * l]
+            nL, nU, nE, nF, k, d, s = [int(t) for t in c[:7]]
+            mL, iL = mk(d, d, nL)
+            mU, iU = mk(d, d, nU)
+            mE, iE = mk(s, d, nE)
+            mF, iF = mk(d, s, nF)
+            W = np.zeros((s, max(k, 1)), dtype=np.float64, order="F")
+            H = np.zeros((max(k, 1), max(k, 1)), dtype=np.float64, order="F")
+            arr[l] = L.LevelFactors(mL, mU, mE, mF, k, L.ptr(W), L.ptr(H))
+            meta.append((iL, iU, iE, iF, W, H, k, int(c[7]), int(c[8])))
+        c = counts[1 + 9 * (nl - 1):]
+        nLl, nUl, sl = int(c[0]), int(c[1]), int(c[2])
+        mLl, iLl = mk(sl, sl, nLl)
+        mUl, iUl = mk(sl, sl, nUl)
+        fs = L.Factors(nl, arr, mLl, mUl)
+        L.check(self._lib.gemslr_export_factors(self._h, ctypes.byref(fs)))
+
+        def tocsr(i):
+            rp, ci, v, nr, nc, nnz = keep[i]
+            return sp.csr_matrix((v[:nnz], ci[:nnz], rp), shape=(nr, nc))
+
+        levels = []
+        for (iL, iU, iE, iF, W, H, k, s0, e0) in meta:
+            levels.append(dict(s=s0, e=e0, L=tocsr(iL), U=tocsr(iU), E=tocsr(iE), F=tocsr(iF),
+                               W=np.array(W[:, :k]), H=np.array(H[:k, :k])))
+        return dict(levels=levels, last=dict(L=tocsr(iLl), U=tocsr(iUl)))

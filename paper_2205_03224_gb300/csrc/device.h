@@ -1,0 +1,109 @@
+// Device-side state of a GeMSLR handle and the launch wrappers of kernels.cu.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace gemslr {
+
+void cuda_check(cudaError_t e, const char *what);
+#define GEMSLR_CUDA(x) ::gemslr::cuda_check((x), #x)
+
+// ---- launchers (kernels.cu) --------------------------------------------------
+template <typename VT, typename WT>
+void launch_trsv(const LevelView<VT, WT> &lv, int mode, int smem_rows, const double *in, VT *work,
+                 double *out_final, VT *scratch, cudaStream_t st);
+template <typename VT, typename WT> void set_trsv_smem_limit(int bytes);
+template <typename VT, typename WT>
+void launch_couple(const LevelView<VT, WT> &lv, const double *in, VT *work, VT *partial, unsigned *counter,
+                   VT *u, cudaStream_t st);
+template <typename VT, typename WT>
+void launch_lowrank(const LevelView<VT, WT> &lv, VT *work, const VT *u, cudaStream_t st);
+void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t st);
+void launch_scatter(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t st);
+void launch_zero(int64_t n, double *x, cudaStream_t st);
+void launch_zero_f(int64_t n, float *x, cudaStream_t st);
+void launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *x,
+                 const double *b, double *y, int lanes, cudaStream_t st);
+void launch_gs_dots(int64_t len, const double *V, int64_t ldv, const double *w, double *partial, unsigned *counter,
+                    KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, int grid, cudaStream_t st);
+void launch_gs_sub(int64_t len, double *V, int64_t ldv, double *w, double *partial, unsigned *counter,
+                   KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *h2buf, int grid,
+                   cudaStream_t st);
+void launch_gs_sub2(int64_t len, double *V, int64_t ldv, const double *w, const double *h2, KrylovCtl *ctl,
+                    cudaStream_t st);
+void launch_gs_next(KrylovCtl *ctl, cudaStream_t st);
+void launch_norm2(int64_t len, const double *x, double *partial, unsigned *counter, double *out, int grid,
+                  cudaStream_t st);
+void launch_scale_by_norm(int64_t len, const double *x, const double *n2, double *v, cudaStream_t st);
+void launch_cycle_start(KrylovCtl *ctl, double *g, const double *n2, cudaStream_t st);
+void launch_lsq(const KrylovCtl *ctl, const double *H, const double *g, double *y, cudaStream_t st);
+void launch_update_x(int64_t len, const double *Z, int64_t ldz, const KrylovCtl *ctl, const double *y, double *x,
+                     cudaStream_t st);
+void launch_basis_rotate(int64_t len, const double *V, int64_t ldv, int mm, const double *Q, int kk, double *out,
+                         cudaStream_t st);
+
+// ---- device memory arena ------------------------------------------------------------
+class Arena {
+  public:
+    ~Arena();
+    void *alloc(size_t bytes);
+    template <typename T> T *upload(const std::vector<T> &v) {
+        T *p = (T *)alloc(v.size() * sizeof(T));
+        if (!v.empty()) GEMSLR_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return p;
+    }
+    size_t bytes() const { return total_; }
+
+  private:
+    std::vector<void *> ptrs_;
+    size_t total_ = 0;
+};
+
+// One level in device memory (value type VT, low-rank storage WT).
+template <typename VT, typename WT>
+struct DevLevel {
+    LevelView<VT, WT> view{};
+    int smem_rows = 0;          // dynamic shared memory rows of the trsv kernel (0 = global)
+    int nwf_L = 0, nwf_U = 0;   // wavefront counts (max over blocks)
+    int64_t nnz_tri = 0;
+};
+
+template <typename VT, typename WT>
+struct DevHierarchy {
+    std::vector<DevLevel<VT, WT>> lev;   // Schur levels
+    DevLevel<VT, WT> last;
+    VT *work = nullptr;                  // n, M^{-1} work vector (mixed precision)
+    VT *scratch = nullptr;               // max d_l, trsv up-sweep without shared memory
+    VT *partial = nullptr;               // couple-kernel partial sums
+    unsigned *counter = nullptr;
+    VT *u = nullptr;                     // kMaxRank
+};
+
+// Build the device copy of a host hierarchy.
+template <typename VT, typename WT>
+void upload_hierarchy(const Hierarchy &h, Arena &arena, DevHierarchy<VT, WT> &d, int smem_limit_bytes);
+
+// Attach the low-rank term of a host level to its device level.
+template <typename VT, typename WT>
+void set_lowrank(DevLevel<VT, WT> &d, const HostLevel &hl, Arena &a);
+
+// Apply levels >= from (Alg. 2 recursion entered at level `from`).  With
+// `in` non-null the right-hand side is read from it (FP64, multilevel
+// order); otherwise from the tail of `work` starting at level `from`.
+// out_final (optional) receives the FP64 result of every level.
+template <typename VT, typename WT>
+void apply_levels(DevHierarchy<VT, WT> &d, int from, const double *in, VT *work, double *out_final,
+                  cudaStream_t st);
+
+// z = M^{-1} r in the multilevel order.  `in` FP64 (length n), `out` FP64.
+// start_level > 0 applies the sub-hierarchy of levels >= start_level to the
+// tail held in d.work (used by the Arnoldi operator), with in/out ignored.
+template <typename VT, typename WT>
+void apply_hierarchy(DevHierarchy<VT, WT> &d, int64_t n, const double *in, double *out, cudaStream_t st);
+
+}  // namespace gemslr

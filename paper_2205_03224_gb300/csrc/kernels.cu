@@ -1,0 +1,570 @@
+// CUDA kernels of the GeMSLR solve phase for sm_103a.
+//
+// Preconditioner application (Alg. 2), per Schur level l:
+//   k_trsv   (down)  z1 = U^-1 L^-1 b1          one CTA per diagonal block of B_l,
+//                    level-scheduled substitutions on a shared-memory copy of
+//                    the block's vector (Sec. 4.2: the p block solves are
+//                    independent);
+//   k_couple         z2 = b2 - E_l z1 and the partial sums of W_l^T z2; the last
+//                    CTA to finish reduces them in a fixed order and forms
+//                    u = H_l (W_l^T z2), H_l = (I - R_l)^-1 - I (eq. gemslr5);
+//   k_lowrank        z2 += W_l u  (the right-hand side u2 + z2 of level l+1);
+//   last level       k_trsv on the block-Jacobi blocks (Sec. 4.3);
+//   k_trsv   (up)    y1 = z1 - U^-1 L^-1 (F_l y2), F_l y2 formed row by row as
+//                    the right-hand side of the forward sweep.
+// FGMRES (Sec. 4.1): CSR SpMV, classical Gram-Schmidt with a second pass when
+// the first one cancels (Daniel-Gragg-Kaufman-Stewart test), Givens update of
+// the Hessenberg least-squares problem, solution update.  Reductions are
+// per-CTA partial sums finished by the last CTA in a fixed order, so results
+// are deterministic run to run.
+#include <cstdio>
+
+#include "device.h"
+
+namespace gemslr {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename VT, typename WT> __device__ __forceinline__ VT wval(WT w) { return (VT)to_f(w); }
+template <> __device__ __forceinline__ double wval<double, double>(double w) { return w; }
+
+// ---- level-scheduled substitutions over one block --------------------------
+template <typename VT>
+__device__ __forceinline__ void sweep(const TriView<VT> &T, int b, VT *xs, const VT *dinv) {
+    const int w0 = T.blk_wf[b], w1 = T.blk_wf[b + 1];
+    for (int w = w0; w < w1; ++w) {
+        const int s0 = T.wf_slot[w];
+        const int cnt = T.wf_slot[w + 1] - s0;
+        const int64_t e0 = T.wf_ent[w];
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            const int row = __ldg(T.slot_row + s0 + t);
+            const int len = __ldg(T.slot_len + s0 + t);
+            const int32_t *cp = T.ent_col + e0 + t;
+            const VT *vp = T.ent_val + e0 + t;
+            VT acc = xs[row];
+            for (int q = 0; q < len; ++q) {
+                const int64_t o = (int64_t)q * cnt;
+                acc -= __ldg(vp + o) * xs[__ldg(cp + o)];
+            }
+            if (dinv) acc *= dinv[row];
+            xs[row] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// MODE 0: down sweep / last level: rhs from `in` (FP64 user vector, when
+//         non-null) or from `work`; result to work (and out_final).
+// MODE 1: up sweep: rhs = F y2 from work's tail; work[rows] -= result.
+template <typename VT, typename WT, int MODE, bool SMEM>
+__global__ void __launch_bounds__(kTrsvThreads)
+k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict__ work,
+       double *__restrict__ out_final, VT *__restrict__ scratch) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int b = blockIdx.x;
+    const int64_t r0 = lv.blk_row[b];
+    const int nr = (int)(lv.blk_row[b + 1] - r0);
+    if (nr == 0) return;
+    VT *mine = work + lv.s + r0;                       // this block's rows of the work vector
+    VT *xs = SMEM ? reinterpret_cast<VT *>(smem_raw) : (MODE == 1 ? scratch + r0 : mine);
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+        if (MODE == 1) {
+            VT acc = 0;
+            const int64_t g = r0 + i;
+            for (int64_t p = lv.F_rp[g]; p < lv.F_rp[g + 1]; ++p) acc += lv.F_v[p] * work[lv.F_ci[p]];
+            xs[i] = acc;
+        } else if (in) {
+            xs[i] = (VT)in[lv.s + r0 + i];
+        } else if (SMEM) {
+            xs[i] = mine[i];
+        }
+    }
+    __syncthreads();
+    sweep<VT>(lv.L, b, xs, nullptr);
+    sweep<VT>(lv.U, b, xs, lv.dinv + r0);
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+        VT y = xs[i];
+        if (MODE == 1) y = mine[i] - y;
+        if (SMEM || MODE == 1) mine[i] = y;
+        if (out_final) out_final[lv.s + r0 + i] = (double)y;
+    }
+}
+
+// z2 = b2 - E z1 on rows [row0, row1) of the tail, then partial W^T z2.
+template <typename VT, typename WT>
+__global__ void __launch_bounds__(kCoupleRows)
+k_couple(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict__ work,
+         VT *__restrict__ partial, unsigned *__restrict__ counter, VT *__restrict__ u_out) {
+    __shared__ VT zs[kCoupleRows];
+    __shared__ VT ts[kMaxRank];
+    __shared__ int last;
+    const int64_t i0 = (int64_t)blockIdx.x * kCoupleRows;
+    const int64_t i1 = min(i0 + (int64_t)kCoupleRows, lv.stail);
+    const int64_t i = i0 + threadIdx.x;
+    if (i < i1) {
+        VT z = in ? (VT)in[lv.e + i] : work[lv.e + i];
+        for (int64_t p = lv.E_rp[i]; p < lv.E_rp[i + 1]; ++p) z -= lv.E_v[p] * work[lv.s + lv.E_ci[p]];
+        work[lv.e + i] = z;
+        zs[threadIdx.x] = z;
+    }
+    const int k = lv.k;
+    if (k == 0) return;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int c = warp; c < k; c += nwarp) {
+        VT acc = 0;
+        const WT *wc = lv.W + (int64_t)c * lv.stail;
+        for (int64_t r = i0 + lane; r < i1; r += 32) acc += wval<VT, WT>(wc[r]) * zs[r - i0];
+        acc = warp_sum(acc);
+        if (lane == 0) partial[(int64_t)blockIdx.x * k + c] = acc;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        VT acc = 0;
+        for (unsigned bb = 0; bb < gridDim.x; ++bb) acc += __ldcg(partial + (int64_t)bb * k + c);
+        ts[c] = acc;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        VT acc = 0;
+        for (int d = 0; d < k; ++d) acc += lv.H[c + (int64_t)d * k] * ts[d];
+        u_out[c] = acc;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// work[e + i] += sum_c W[i, c] u[c]
+template <typename VT, typename WT>
+__global__ void __launch_bounds__(256)
+k_lowrank(const LevelView<VT, WT> lv, VT *__restrict__ work, const VT *__restrict__ u) {
+    __shared__ VT us[kMaxRank];
+    const int k = lv.k;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) us[c] = u[c];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lv.stail;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        VT acc = 0;
+        for (int c = 0; c < k; ++c) acc += wval<VT, WT>(lv.W[(int64_t)c * lv.stail + i]) * us[c];
+        work[lv.e + i] += acc;
+    }
+}
+
+// ---- vectors ----------------------------------------------------------------
+__global__ void k_gather(int64_t n, const int32_t *__restrict__ perm, const double *__restrict__ src,
+                         double *__restrict__ dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[perm[i]];
+}
+__global__ void k_scatter(int64_t n, const int32_t *__restrict__ perm, const double *__restrict__ src,
+                          double *__restrict__ dst) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[perm[i]] = src[i];
+}
+template <typename VT>
+__global__ void k_set(int64_t n, VT *__restrict__ x, VT v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+// y = A x (sub == 0) or y = b - A x (sub == 1); `lanes` threads per row.
+template <int LANES>
+__global__ void __launch_bounds__(256)
+k_spmv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+       const double *__restrict__ v, const double *__restrict__ x, const double *__restrict__ b,
+       double *__restrict__ y) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = tid / LANES;
+    const int sub = threadIdx.x % LANES;
+    double acc = 0.0;
+    if (row < n)
+        for (int64_t p = rp[row] + sub; p < rp[row + 1]; p += LANES) acc += __ldg(v + p) * __ldg(x + __ldg(ci + p));
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, LANES);
+    if (row < n && sub == 0) y[row] = b ? b[row] - acc : acc;
+}
+
+// ---- Gram-Schmidt passes -------------------------------------------------------
+// Every pass streams the rows [i0, i1) of one CTA once.  ncols <= kMaxCols.
+
+
+__device__ __forceinline__ bool finish_block(unsigned *counter) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// Column sums of the per-CTA partials [grid][ncols+1] into out[0..ncols] (fixed order).
+__device__ void reduce_partials(const double *partial, int ncols1, double *out) {
+    for (int c = threadIdx.x; c < ncols1; c += blockDim.x) {
+        double acc = 0.0;
+        for (unsigned bb = 0; bb < gridDim.x; ++bb) acc += __ldcg(partial + (int64_t)bb * ncols1 + c);
+        out[c] = acc;
+    }
+    __syncthreads();
+}
+
+// Block partial sums of V[:, c] . w for c < ncols and of w . w (slot ncols).
+__device__ void block_dots(int64_t len, const double *__restrict__ V, int64_t ldv, int ncols,
+                           const double *__restrict__ w, int64_t i0, int64_t i1, double *partial) {
+    __shared__ double red[kReduceThreads / 32];
+    for (int c = 0; c <= ncols; ++c) {
+        const double *vc = c < ncols ? V + (int64_t)c * ldv : w;
+        double acc = 0.0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += vc[i] * w[i];
+        acc = warp_sum(acc);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+            partial[(int64_t)blockIdx.x * (ncols + 1) + c] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Givens update of column j of the (m+1) x m Hessenberg matrix H (FGMRES).
+__device__ void givens_step(KrylovCtl *ctl, double *H, double *cs, double *sn, double *g) {
+    const int j = ctl->j, m1 = ctl->m + 1;
+    double *h = H + (int64_t)j * m1;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+    }
+    const double den = hypot(h[j], h[j + 1]);
+    const double c = den == 0.0 ? 1.0 : h[j] / den;
+    const double s = den == 0.0 ? 0.0 : h[j + 1] / den;
+    cs[j] = c;
+    sn[j] = s;
+    h[j] = den;
+    h[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    const double r = fabs(g[j + 1]);
+    ctl->resid = r;
+    ctl->iters += 1;
+    ctl->jdone = j + 1;
+    const bool bad = !isfinite(r) || !isfinite(den);
+    if (bad) ctl->nonfinite = 1;
+    if (r <= ctl->tol_abs || ctl->breakdown || bad || ctl->iters >= ctl->maxit || j + 1 >= ctl->m)
+        ctl->stop = 1;
+}
+
+// After h (ncols values) and ||w||^2 are known: record h in column j of H,
+// decide on a second pass and, if none, the norm of the projected vector.
+__device__ void after_first_pass(KrylovCtl *ctl, const double *red, int ncols, double *H, double *cs,
+                                 double *sn, double *g) {
+    const int j = ctl->j, m1 = ctl->m + 1;
+    double hh = 0.0;
+    for (int c = 0; c < ncols; ++c) { H[(int64_t)j * m1 + c] = red[c]; hh += red[c] * red[c]; }
+    const double ww = red[ncols];
+    ctl->wnorm2 = ww;
+    const double rest = ww - hh;      // ||w - V h||^2 by Pythagoras
+    const bool again = ctl->force_reorth || !(rest > 0.5 * ww);
+    ctl->reorth = again ? 1 : 0;
+    if (again) { ctl->nreorth += 1; return; }
+    const double beta = sqrt(rest);
+    ctl->beta = beta;
+    ctl->breakdown = beta <= 1e-14 * sqrt(ww) ? 1 : 0;
+    H[(int64_t)j * m1 + j + 1] = beta;
+    if (ctl->givens) givens_step(ctl, H, cs, sn, g);
+}
+
+}  // namespace
+
+// Pass 1: partial dots; finisher stores h, decides on reorthogonalisation.
+// A step is only launched while its cycle is active (ctl->stop == 0).
+__global__ void __launch_bounds__(kReduceThreads)
+k_gs_dots(int64_t len, const double *__restrict__ V, int64_t ldv, const double *__restrict__ w,
+          double *partial, unsigned *counter, KrylovCtl *ctl, double *H, double *cs, double *sn, double *g) {
+    if (ctl->stop) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->reorth = 0;
+        return;
+    }
+    const int ncols = ctl->j + 1;
+    const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
+    block_dots(len, V, ldv, ncols, w, i0, i1, partial);
+    if (!finish_block(counter)) return;
+    __shared__ double red[kMaxCols + 1];
+    reduce_partials(partial, ncols + 1, red);
+    if (threadIdx.x == 0) {
+        after_first_pass(ctl, red, ncols, H, cs, sn, g);
+        *counter = 0u;
+    }
+}
+
+// Pass 2: w -= V h.  Without reorthogonalisation the result is scaled into
+// V[:, j+1] (unless the step ended the cycle); otherwise w is kept, the
+// second-pass coefficients h2 are reduced into h2buf and added to H.
+__global__ void __launch_bounds__(kReduceThreads)
+k_gs_sub(int64_t len, double *__restrict__ V, int64_t ldv, double *__restrict__ w, double *partial,
+         unsigned *counter, KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *h2buf) {
+    const int again = ctl->reorth;
+    if (!again && (ctl->stop || ctl->breakdown)) return;
+    __shared__ double hs[kMaxCols];
+    const int j = ctl->j, ncols = j + 1, m1 = ctl->m + 1;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = H[(int64_t)j * m1 + c];
+    __syncthreads();
+    const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
+    const double inv = again ? 0.0 : 1.0 / ctl->beta;
+    double *vn = V + (int64_t)(j + 1) * ldv;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        double x = w[i];
+        for (int c = 0; c < ncols; ++c) x -= V[(int64_t)c * ldv + i] * hs[c];
+        if (again) w[i] = x;
+        else vn[i] = x * inv;
+    }
+    if (!again) return;
+    __syncthreads();
+    block_dots(len, V, ldv, ncols, w, i0, i1, partial);
+    if (!finish_block(counter)) return;
+    __shared__ double red[kMaxCols + 1];
+    reduce_partials(partial, ncols + 1, red);
+    if (threadIdx.x == 0) {
+        double hh = 0.0;
+        for (int c = 0; c < ncols; ++c) {
+            H[(int64_t)j * m1 + c] += red[c];
+            h2buf[c] = red[c];
+            hh += red[c] * red[c];
+        }
+        const double rest = red[ncols] - hh;
+        const double beta = sqrt(rest > 0.0 ? rest : 0.0);
+        ctl->beta = beta;
+        ctl->breakdown = beta <= 1e-14 * sqrt(ctl->wnorm2) ? 1 : 0;
+        H[(int64_t)j * m1 + j + 1] = beta;
+        if (ctl->givens) givens_step(ctl, H, cs, sn, g);
+        *counter = 0u;
+    }
+}
+
+// Pass 3 (only after a second Gram-Schmidt pass): V[:, j+1] = (w - V h2) / beta.
+__global__ void __launch_bounds__(kReduceThreads)
+k_gs_sub2(int64_t len, double *__restrict__ V, int64_t ldv, const double *__restrict__ w,
+          const double *__restrict__ h2, KrylovCtl *ctl) {
+    if (!ctl->reorth || ctl->stop || ctl->breakdown) return;
+    __shared__ double hs[kMaxCols];
+    const int j = ctl->j, ncols = j + 1;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = __ldcg(h2 + c);
+    __syncthreads();
+    const double inv = 1.0 / ctl->beta;
+    double *vn = V + (int64_t)(j + 1) * ldv;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        double x = w[i];
+        for (int c = 0; c < ncols; ++c) x -= V[(int64_t)c * ldv + i] * hs[c];
+        vn[i] = x * inv;
+    }
+}
+
+// Advance to the next column (one thread).
+__global__ void k_gs_next(KrylovCtl *ctl) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && !ctl->stop) ctl->j += 1;
+}
+
+// ||x||^2 into *out (partials + finisher).
+__global__ void __launch_bounds__(kReduceThreads)
+k_norm2(int64_t len, const double *__restrict__ x, double *partial, unsigned *counter, double *out) {
+    const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
+    block_dots(len, x, 0, 0, x, i0, i1, partial);
+    if (!finish_block(counter)) return;
+    __shared__ double red[1];
+    reduce_partials(partial, 1, red);
+    if (threadIdx.x == 0) { *out = red[0]; *counter = 0u; }
+}
+
+// v = x * (1 / sqrt(*n2))
+__global__ void k_scale_by_norm(int64_t len, const double *__restrict__ x, const double *n2, double *__restrict__ v) {
+    const double inv = 1.0 / sqrt(*n2);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = x[i] * inv;
+}
+
+// Start of an FGMRES cycle: g = (beta, 0, ...), j = 0 (one thread).
+__global__ void k_cycle_start(KrylovCtl *ctl, double *g, const double *n2) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = 0; i <= ctl->m; ++i) g[i] = 0.0;
+    g[0] = sqrt(*n2);
+    ctl->j = 0;
+    ctl->stop = 0;
+    ctl->breakdown = 0;
+    ctl->reorth = 0;
+    ctl->jdone = 0;
+}
+
+// y = R^{-1} g (back substitution on the rotated Hessenberg), one thread.
+__global__ void k_lsq(const KrylovCtl *ctl, const double *H, const double *g, double *y) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int jd = ctl->jdone, m1 = ctl->m + 1;
+    for (int i = jd - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int t = i + 1; t < jd; ++t) s -= H[(int64_t)t * m1 + i] * y[t];
+        y[i] = s / H[(int64_t)i * m1 + i];
+    }
+}
+
+// x += Z[:, :jdone] y
+__global__ void k_update_x(int64_t len, const double *__restrict__ Z, int64_t ldz, const KrylovCtl *ctl,
+                           const double *__restrict__ y, double *__restrict__ x) {
+    __shared__ double ys[kMaxCols];
+    const int jd = ctl->jdone;
+    for (int c = threadIdx.x; c < jd; c += blockDim.x) ys[c] = y[c];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = x[i];
+        for (int c = 0; c < jd; ++c) acc += Z[(int64_t)c * ldz + i] * ys[c];
+        x[i] = acc;
+    }
+}
+
+// out[:, c] = V[:, :mm] Q[:, c] for c < kk (thick restart of the Arnoldi basis).
+__global__ void k_basis_rotate(int64_t len, const double *__restrict__ V, int64_t ldv, int mm,
+                               const double *__restrict__ Q, int kk, double *__restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int c = 0; c < kk; ++c) {
+            double acc = 0.0;
+            for (int d = 0; d < mm; ++d) acc += V[(int64_t)d * ldv + i] * Q[d + (int64_t)c * mm];
+            out[(int64_t)c * ldv + i] = acc;
+        }
+    }
+}
+
+// ---- host launchers -----------------------------------------------------------------
+static int grid_for(int64_t n, int threads, int cap) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    return (int)(g > cap ? cap : g);
+}
+
+template <typename VT, typename WT>
+void launch_trsv(const LevelView<VT, WT> &lv, int mode, int smem_rows, const double *in, VT *work,
+                 double *out_final, VT *scratch, cudaStream_t st) {
+    if (lv.nblk == 0) return;
+    const bool smem = smem_rows > 0;
+    const size_t bytes = smem ? (size_t)smem_rows * sizeof(VT) : 0;
+    if (mode == 0) {
+        if (smem) k_trsv<VT, WT, 0, true><<<lv.nblk, kTrsvThreads, bytes, st>>>(lv, in, work, out_final, scratch);
+        else k_trsv<VT, WT, 0, false><<<lv.nblk, kTrsvThreads, 0, st>>>(lv, in, work, out_final, scratch);
+    } else {
+        if (smem) k_trsv<VT, WT, 1, true><<<lv.nblk, kTrsvThreads, bytes, st>>>(lv, in, work, out_final, scratch);
+        else k_trsv<VT, WT, 1, false><<<lv.nblk, kTrsvThreads, 0, st>>>(lv, in, work, out_final, scratch);
+    }
+}
+
+template <typename VT, typename WT>
+void set_trsv_smem_limit(int bytes) {
+    cudaFuncSetAttribute(k_trsv<VT, WT, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_trsv<VT, WT, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <typename VT, typename WT>
+void launch_couple(const LevelView<VT, WT> &lv, const double *in, VT *work, VT *partial, unsigned *counter,
+                   VT *u, cudaStream_t st) {
+    if (lv.stail == 0) return;
+    const int grid = (int)((lv.stail + kCoupleRows - 1) / kCoupleRows);
+    k_couple<VT, WT><<<grid, kCoupleRows, 0, st>>>(lv, in, work, partial, counter, u);
+}
+
+template <typename VT, typename WT>
+void launch_lowrank(const LevelView<VT, WT> &lv, VT *work, const VT *u, cudaStream_t st) {
+    if (lv.k == 0 || lv.stail == 0) return;
+    k_lowrank<VT, WT><<<grid_for(lv.stail, 256, 1216), 256, 0, st>>>(lv, work, u);
+}
+
+template void launch_trsv<double, double>(const LevelView<double, double> &, int, int, const double *, double *,
+                                          double *, double *, cudaStream_t);
+template void launch_trsv<float, __nv_bfloat16>(const LevelView<float, __nv_bfloat16> &, int, int, const double *,
+                                                float *, double *, float *, cudaStream_t);
+template void set_trsv_smem_limit<double, double>(int);
+template void set_trsv_smem_limit<float, __nv_bfloat16>(int);
+template void launch_couple<double, double>(const LevelView<double, double> &, const double *, double *, double *,
+                                            unsigned *, double *, cudaStream_t);
+template void launch_couple<float, __nv_bfloat16>(const LevelView<float, __nv_bfloat16> &, const double *, float *,
+                                                  float *, unsigned *, float *, cudaStream_t);
+template void launch_lowrank<double, double>(const LevelView<double, double> &, double *, const double *, cudaStream_t);
+template void launch_lowrank<float, __nv_bfloat16>(const LevelView<float, __nv_bfloat16> &, float *, const float *,
+                                                   cudaStream_t);
+
+void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t st) {
+    if (n > 0) k_gather<<<grid_for(n, 256, 4864), 256, 0, st>>>(n, perm, src, dst);
+}
+void launch_scatter(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t st) {
+    if (n > 0) k_scatter<<<grid_for(n, 256, 4864), 256, 0, st>>>(n, perm, src, dst);
+}
+void launch_zero(int64_t n, double *x, cudaStream_t st) {
+    if (n > 0) k_set<double><<<grid_for(n, 256, 4864), 256, 0, st>>>(n, x, 0.0);
+}
+void launch_zero_f(int64_t n, float *x, cudaStream_t st) {
+    if (n > 0) k_set<float><<<grid_for(n, 256, 4864), 256, 0, st>>>(n, x, 0.0f);
+}
+void launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *x,
+                 const double *b, double *y, int lanes, cudaStream_t st) {
+    if (n == 0) return;
+    const int64_t threads = n * lanes;
+    const int grid = (int)((threads + 255) / 256);
+    switch (lanes) {
+        case 2: k_spmv<2><<<grid, 256, 0, st>>>(n, rp, ci, v, x, b, y); break;
+        case 4: k_spmv<4><<<grid, 256, 0, st>>>(n, rp, ci, v, x, b, y); break;
+        case 16: k_spmv<16><<<grid, 256, 0, st>>>(n, rp, ci, v, x, b, y); break;
+        default: k_spmv<8><<<grid, 256, 0, st>>>(n, rp, ci, v, x, b, y); break;
+    }
+}
+void launch_gs_dots(int64_t len, const double *V, int64_t ldv, const double *w, double *partial, unsigned *counter,
+                    KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, int grid, cudaStream_t st) {
+    k_gs_dots<<<grid, kReduceThreads, 0, st>>>(len, V, ldv, w, partial, counter, ctl, H, cs, sn, g);
+}
+void launch_gs_sub(int64_t len, double *V, int64_t ldv, double *w, double *partial, unsigned *counter,
+                   KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *h2buf, int grid,
+                   cudaStream_t st) {
+    k_gs_sub<<<grid, kReduceThreads, 0, st>>>(len, V, ldv, w, partial, counter, ctl, H, cs, sn, g, h2buf);
+}
+void launch_gs_sub2(int64_t len, double *V, int64_t ldv, const double *w, const double *h2, KrylovCtl *ctl,
+                    cudaStream_t st) {
+    k_gs_sub2<<<grid_for(len, 256, 1216), 256, 0, st>>>(len, V, ldv, w, h2, ctl);
+}
+void launch_gs_next(KrylovCtl *ctl, cudaStream_t st) { k_gs_next<<<1, 32, 0, st>>>(ctl); }
+void launch_norm2(int64_t len, const double *x, double *partial, unsigned *counter, double *out, int grid,
+                  cudaStream_t st) {
+    k_norm2<<<grid, kReduceThreads, 0, st>>>(len, x, partial, counter, out);
+}
+void launch_scale_by_norm(int64_t len, const double *x, const double *n2, double *v, cudaStream_t st) {
+    if (len > 0) k_scale_by_norm<<<grid_for(len, 256, 4864), 256, 0, st>>>(len, x, n2, v);
+}
+void launch_cycle_start(KrylovCtl *ctl, double *g, const double *n2, cudaStream_t st) {
+    k_cycle_start<<<1, 32, 0, st>>>(ctl, g, n2);
+}
+void launch_lsq(const KrylovCtl *ctl, const double *H, const double *g, double *y, cudaStream_t st) {
+    k_lsq<<<1, 32, 0, st>>>(ctl, H, g, y);
+}
+void launch_update_x(int64_t len, const double *Z, int64_t ldz, const KrylovCtl *ctl, const double *y, double *x,
+                     cudaStream_t st) {
+    if (len > 0) k_update_x<<<grid_for(len, 256, 4864), 256, 0, st>>>(len, Z, ldz, ctl, y, x);
+}
+void launch_basis_rotate(int64_t len, const double *V, int64_t ldv, int mm, const double *Q, int kk, double *out,
+                         cudaStream_t st) {
+    if (len > 0) k_basis_rotate<<<grid_for(len, 256, 4864), 256, 0, st>>>(len, V, ldv, mm, Q, kk, out);
+}
+
+}  // namespace gemslr

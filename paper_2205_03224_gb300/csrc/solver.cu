@@ -1,0 +1,617 @@
+// GeMSLR handle, low-rank setup (Alg. 1 / Sec. 2.3), FGMRES (Sec. 4.1) and the C ABI.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <memory>
+
+#include "device.h"
+
+using namespace gemslr;
+
+struct gemslr_ctx {
+    Hierarchy host;
+    gemslr_options opt{};
+    Arena arena;
+    DevHierarchy<double, double> d64;
+    DevHierarchy<float, __nv_bfloat16> d32;
+    bool mixed = false;
+    // permuted A for the Krylov products
+    int64_t *A_rp = nullptr;
+    int32_t *A_ci = nullptr;
+    double *A_v = nullptr;
+    int spmv_lanes = 8;
+    int32_t *perm = nullptr;
+    double *zeros = nullptr;       // n zeros (Arnoldi operator)
+    // Krylov workspace
+    int m_alloc = 0;
+    double *V = nullptr, *Z = nullptr, *w = nullptr, *xh = nullptr, *bh = nullptr, *r = nullptr;
+    double *Hs = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *h2 = nullptr;
+    double *partial = nullptr, *n2 = nullptr;
+    unsigned *counter = nullptr;
+    KrylovCtl *ctl = nullptr;
+    KrylovCtl *ctl_host = nullptr;      // pinned
+    double *n2_host = nullptr;          // pinned
+    int red_grid = 0;
+    double setup_ms = 0.0;
+    ~gemslr_ctx() {
+        if (ctl_host) cudaFreeHost(ctl_host);
+        if (n2_host) cudaFreeHost(n2_host);
+    }
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+gemslr_status guard(const std::function<void()> &fn);
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+int smem_optin() {
+    int dev = 0, b = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return b;
+}
+
+void ensure_krylov(gemslr_ctx *h, int m) {
+    const int64_t n = std::max<int64_t>(h->host.n, 1);
+    if (!h->ctl) {
+        h->xh = (double *)h->arena.alloc(8 * n);
+        h->bh = (double *)h->arena.alloc(8 * n);
+        h->r = (double *)h->arena.alloc(8 * n);
+        h->w = (double *)h->arena.alloc(8 * n);
+        h->red_grid = 4 * sm_count();
+        h->partial = (double *)h->arena.alloc(8 * (size_t)h->red_grid * (kMaxCols + 1));
+        h->counter = (unsigned *)h->arena.alloc(16);
+        GEMSLR_CUDA(cudaMemset(h->counter, 0, 16));
+        h->n2 = (double *)h->arena.alloc(8 * 4);
+        h->ctl = (KrylovCtl *)h->arena.alloc(sizeof(KrylovCtl));
+        h->h2 = (double *)h->arena.alloc(8 * kMaxCols);
+        GEMSLR_CUDA(cudaMallocHost(&h->ctl_host, sizeof(KrylovCtl)));
+        GEMSLR_CUDA(cudaMallocHost(&h->n2_host, 8 * 4));
+    }
+    if (m > h->m_alloc) {
+        if (m + 1 > kMaxCols) fail(GEMSLR_ERR_ARG, "restart length too large");
+        h->V = (double *)h->arena.alloc(8 * (size_t)n * (m + 1));
+        h->Z = (double *)h->arena.alloc(8 * (size_t)n * m);
+        h->Hs = (double *)h->arena.alloc(8 * (size_t)(m + 1) * m);
+        h->cs = (double *)h->arena.alloc(8 * (size_t)(m + 1));
+        h->sn = (double *)h->arena.alloc(8 * (size_t)(m + 1));
+        h->g = (double *)h->arena.alloc(8 * (size_t)(m + 2));
+        h->y = (double *)h->arena.alloc(8 * (size_t)(m + 1));
+        h->m_alloc = m;
+    }
+}
+
+// M^{-1} on a multilevel-ordered FP64 vector (device).
+void apply_perm(gemslr_ctx *h, const double *in, double *out, cudaStream_t st) {
+    if (h->mixed) apply_hierarchy<float, __nv_bfloat16>(h->d32, h->host.n, in, out, st);
+    else apply_hierarchy<double, double>(h->d64, h->host.n, in, out, st);
+}
+
+// G_hat_l z = E_l U_l^-1 L_l^-1 F_l C_l^-1 z for z of length n - e_l (device, FP64 hierarchy).
+void g_hat(gemslr_ctx *h, int l, const double *z, double *out, cudaStream_t st) {
+    DevHierarchy<double, double> &d = h->d64;
+    const HostLevel &hl = h->host.lev[l];
+    const int64_t s = h->host.n - hl.e, dl = hl.e - hl.s;
+    double *X = d.work;
+    GEMSLR_CUDA(cudaMemcpyAsync(X + hl.e, z, 8 * s, cudaMemcpyDeviceToDevice, st));
+    apply_levels<double, double>(d, l + 1, nullptr, X, nullptr, st);         // y = C_l^-1 z (tail)
+    GEMSLR_CUDA(cudaMemsetAsync(X + hl.s, 0, 8 * dl, st));
+    launch_trsv<double, double>(d.lev[l].view, 1, d.lev[l].smem_rows, nullptr, X, nullptr, d.scratch, st);
+    LevelView<double, double> v0 = d.lev[l].view;                            // -(LU)^-1 F y in level rows
+    v0.k = 0;
+    launch_couple<double, double>(v0, h->zeros, X, d.partial, d.counter, d.u, st);   // tail = E (LU)^-1 F y
+    GEMSLR_CUDA(cudaMemcpyAsync(out, X + hl.e, 8 * s, cudaMemcpyDeviceToDevice, st));
+}
+
+void read_ctl(gemslr_ctx *h, cudaStream_t st) {
+    GEMSLR_CUDA(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(KrylovCtl), cudaMemcpyDeviceToHost, st));
+    GEMSLR_CUDA(cudaStreamSynchronize(st));
+}
+
+void write_ctl(gemslr_ctx *h, cudaStream_t st) {
+    GEMSLR_CUDA(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(KrylovCtl), cudaMemcpyHostToDevice, st));
+}
+
+double read_scalar(gemslr_ctx *h, const double *dev, cudaStream_t st) {
+    GEMSLR_CUDA(cudaMemcpyAsync(h->n2_host, dev, 8, cudaMemcpyDeviceToHost, st));
+    GEMSLR_CUDA(cudaStreamSynchronize(st));
+    return h->n2_host[0];
+}
+
+// splitmix64 uniform doubles in [-1, 1) (the seeded Arnoldi start vector).
+std::vector<double> start_vector(uint64_t seed, int64_t s) {
+    std::vector<double> v(s);
+    uint64_t state = seed;
+    for (int64_t i = 0; i < s; ++i) {
+        state += 0x9E3779B97F4A7C15ull;
+        uint64_t z = state;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        v[i] = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+    }
+    return v;
+}
+
+// Low-rank correction of level l by thick-restart (Krylov-Schur) Arnoldi on
+// G_hat_l with classical Gram-Schmidt and one forced re-orthogonalisation.
+// Cycle m = 2k; the wanted subspace is kept on restart; converged when
+// ||beta * Q[m-1, :k]||_2 <= tol * min |theta_i| (every Ritz value to ~two
+// digits, Sec. 5 set-up); s_l <= m: dense G_hat and its full Schur form.
+void build_lowrank(gemslr_ctx *h, int l, cudaStream_t st) {
+    HostLevel &hl = h->host.lev[l];
+    const int64_t s = h->host.n - hl.e;
+    int k = std::max(0, hl.rank_req);
+    hl.k = 0;
+    hl.W.clear();
+    hl.H.clear();
+    if (k == 0 || s == 0) return;
+    const int m = 2 * k;
+    std::vector<double> Q, Tk, tre, tim;
+    if (s <= m) {
+        std::vector<double> G((size_t)s * s), e(s, 0.0);
+        double *ed = (double *)h->arena.alloc(8 * s), *gd = (double *)h->arena.alloc(8 * s);
+        for (int64_t i = 0; i < s; ++i) {
+            e.assign(s, 0.0);
+            e[i] = 1.0;
+            GEMSLR_CUDA(cudaMemcpyAsync(ed, e.data(), 8 * s, cudaMemcpyHostToDevice, st));
+            g_hat(h, l, ed, gd, st);
+            GEMSLR_CUDA(cudaMemcpyAsync(G.data() + (size_t)i * s, gd, 8 * s, cudaMemcpyDeviceToHost, st));
+            GEMSLR_CUDA(cudaStreamSynchronize(st));
+        }
+        const int keff = schur_wanted(G, (int)s, k, Q, Tk, tre, tim);
+        hl.k = keff;
+        hl.W.assign(Q.begin(), Q.begin() + (size_t)s * keff);
+        hl.H = correction_matrix(Tk, keff);
+        return;
+    }
+    if (m + 1 > kMaxCols) fail(GEMSLR_ERR_ARG, "rank too large for the Arnoldi workspace");
+    double *V = (double *)h->arena.alloc(8 * (size_t)s * (m + 1));
+    double *W2 = (double *)h->arena.alloc(8 * (size_t)s * (k + 2));
+    double *w = (double *)h->arena.alloc(8 * (size_t)s);
+    double *Hd = (double *)h->arena.alloc(8 * (size_t)(m + 1) * m);
+    double *Qd = (double *)h->arena.alloc(8 * (size_t)m * (k + 2));
+    std::vector<double> v1 = start_vector(1000 + (uint64_t)l, s);
+    double nv = 0.0;
+    for (double x : v1) nv += x * x;
+    nv = std::sqrt(nv);
+    for (double &x : v1) x /= nv;
+    GEMSLR_CUDA(cudaMemcpyAsync(V, v1.data(), 8 * s, cudaMemcpyHostToDevice, st));
+    std::vector<double> Hb((size_t)(m + 1) * m, 0.0);
+    GEMSLR_CUDA(cudaMemsetAsync(Hd, 0, 8 * (size_t)(m + 1) * m, st));
+    const double tol = h->opt.arnoldi_tol > 0 ? h->opt.arnoldi_tol : 1e-2;
+    const int maxc = h->opt.arnoldi_max_cycles > 0 ? h->opt.arnoldi_max_cycles : 20;
+    int p = 0;
+    for (int cycle = 0; cycle < maxc; ++cycle) {
+        KrylovCtl c{};
+        c.j = p;
+        c.m = m;
+        c.givens = 0;
+        c.force_reorth = 1;
+        c.maxit = 1 << 30;
+        *h->ctl_host = c;
+        write_ctl(h, st);
+        int mm = m;
+        bool broke = false;
+        double beta = 0.0;
+        for (int j = p; j < m; ++j) {
+            g_hat(h, l, V + (size_t)j * s, w, st);
+            launch_gs_dots(s, V, s, w, h->partial, h->counter, h->ctl, Hd, nullptr, nullptr, nullptr, h->red_grid, st);
+            launch_gs_sub(s, V, s, w, h->partial, h->counter, h->ctl, Hd, nullptr, nullptr, nullptr, h->h2,
+                          h->red_grid, st);
+            launch_gs_sub2(s, V, s, w, h->h2, h->ctl, st);
+            launch_gs_next(h->ctl, st);
+            read_ctl(h, st);
+            beta = h->ctl_host->beta;
+            if (h->ctl_host->breakdown) { mm = j + 1; broke = true; beta = 0.0; break; }
+        }
+        GEMSLR_CUDA(cudaMemcpyAsync(Hb.data(), Hd, 8 * Hb.size(), cudaMemcpyDeviceToHost, st));
+        GEMSLR_CUDA(cudaStreamSynchronize(st));
+        std::vector<double> Hm((size_t)mm * mm);
+        for (int j = 0; j < mm; ++j)
+            for (int i = 0; i < mm; ++i) Hm[i + (size_t)j * mm] = Hb[i + (size_t)j * (m + 1)];
+        const int keff = schur_wanted(Hm, mm, k, Q, Tk, tre, tim);
+        double res = 0.0, tmin = INFINITY;
+        for (int t = 0; t < keff; ++t) {
+            const double q = beta * Q[(mm - 1) + (size_t)t * mm];
+            res += q * q;
+            tmin = std::min(tmin, std::hypot(tre[t], tim[t]));
+        }
+        res = std::sqrt(res);
+        const bool ok = broke || res <= tol * tmin;
+        GEMSLR_CUDA(cudaMemcpyAsync(Qd, Q.data(), 8 * (size_t)mm * keff, cudaMemcpyHostToDevice, st));
+        launch_basis_rotate(s, V, s, mm, Qd, keff, W2, st);
+        if (ok || cycle == maxc - 1) {
+            hl.k = keff;
+            hl.W.resize((size_t)s * keff);
+            GEMSLR_CUDA(cudaMemcpyAsync(hl.W.data(), W2, 8 * (size_t)s * keff, cudaMemcpyDeviceToHost, st));
+            GEMSLR_CUDA(cudaStreamSynchronize(st));
+            hl.H = correction_matrix(Tk, keff);
+            return;
+        }
+        // thick restart: V[:, :keff] = V Q, V[:, keff] = v_{m+1}
+        GEMSLR_CUDA(cudaMemcpyAsync(V + (size_t)keff * s, V + (size_t)mm * s, 8 * s, cudaMemcpyDeviceToDevice, st));
+        GEMSLR_CUDA(cudaMemcpyAsync(V, W2, 8 * (size_t)s * keff, cudaMemcpyDeviceToDevice, st));
+        std::fill(Hb.begin(), Hb.end(), 0.0);
+        for (int b = 0; b < keff; ++b) {
+            for (int a = 0; a < keff; ++a) Hb[a + (size_t)b * (m + 1)] = Tk[a + (size_t)b * keff];
+            Hb[keff + (size_t)b * (m + 1)] = beta * Q[(mm - 1) + (size_t)b * mm];
+        }
+        GEMSLR_CUDA(cudaMemcpyAsync(Hd, Hb.data(), 8 * Hb.size(), cudaMemcpyHostToDevice, st));
+        p = keff;
+    }
+}
+
+void finish_setup(gemslr_ctx *h, bool compute_lowrank) {
+    cudaStream_t st = nullptr;
+    const int64_t n = h->host.n;
+    const Csr &A = h->host.Ahat;
+    h->A_rp = h->arena.upload(A.rp);
+    h->A_ci = h->arena.upload(A.ci);
+    h->A_v = h->arena.upload(A.v);
+    const double avg = n ? (double)A.nnz() / n : 0.0;
+    h->spmv_lanes = avg <= 3 ? 2 : (avg <= 8 ? 4 : (avg <= 24 ? 8 : 16));
+    h->perm = h->arena.upload(h->host.perm);
+    h->zeros = (double *)h->arena.alloc(8 * std::max<int64_t>(n, 1));
+    GEMSLR_CUDA(cudaMemset(h->zeros, 0, 8 * std::max<int64_t>(n, 1)));
+    const int limit = std::min(smem_optin(), 200 * 1024);
+    upload_hierarchy<double, double>(h->host, h->arena, h->d64, limit);
+    ensure_krylov(h, 8);
+    if (compute_lowrank) {
+        for (int l = (int)h->host.lev.size() - 1; l >= 0; --l) {   // bottom-up (Sec. 4.2)
+            build_lowrank(h, l, st);
+            set_lowrank<double, double>(h->d64.lev[l], h->host.lev[l], h->arena);
+        }
+    }
+    if (h->opt.precision == GEMSLR_PREC_MIXED) {
+        upload_hierarchy<float, __nv_bfloat16>(h->host, h->arena, h->d32, limit);
+        h->mixed = true;
+    }
+    GEMSLR_CUDA(cudaDeviceSynchronize());
+}
+
+gemslr_status guard(const std::function<void()> &fn) {
+    try {
+        fn();
+        return GEMSLR_OK;
+    } catch (const Error &e) {
+        g_last_error = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        g_last_error = "host allocation failed";
+        return GEMSLR_ERR_NOMEM;
+    } catch (const std::exception &e) {
+        g_last_error = e.what();
+        return GEMSLR_ERR_ARG;
+    }
+}
+
+gemslr_options normalized(const gemslr_options *opt) {
+    gemslr_options o;
+    gemslr_default_options(&o);
+    if (opt) o = *opt;
+    if (o.ilu_kind != GEMSLR_ILU0 && o.ilu_kind != GEMSLR_ILUT) fail(GEMSLR_ERR_ARG, "unknown ilu_kind");
+    if (o.precision != GEMSLR_PREC_FP64 && o.precision != GEMSLR_PREC_MIXED) fail(GEMSLR_ERR_ARG, "unknown precision");
+    if (o.ilut_tau < 0) fail(GEMSLR_ERR_ARG, "ilut_tau must be >= 0");
+    for (int l = 0; l < GEMSLR_MAX_LEVELS; ++l)
+        if (o.rank[l] < 0 || 2 * o.rank[l] + 1 > kMaxCols || o.rank[l] + 2 > kMaxRank)
+            fail(GEMSLR_ERR_ARG, "rank out of range (0..63)");
+    return o;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gemslr_default_options(gemslr_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->ilu_kind = GEMSLR_ILUT;
+    opt->ilut_tau = 1e-3;
+    opt->ilut_lfil = 10;
+    opt->precision = GEMSLR_PREC_FP64;
+    opt->arnoldi_tol = 1e-2;
+    opt->arnoldi_max_cycles = 20;
+}
+
+const char *gemslr_last_error(void) { return g_last_error.c_str(); }
+
+gemslr_status gemslr_partition_geometric(const gemslr_csr *A, const int32_t *coords, int32_t nlev, int32_t p,
+                                         int32_t p_last, int32_t *perm, int64_t *level_ptr, int32_t *nblk,
+                                         int64_t *block_ptr) {
+    return guard([&] {
+        if (!perm || !level_ptr || !nblk || !block_ptr) fail(GEMSLR_ERR_ARG, "NULL output array");
+        Csr M = csr_from_abi(A);
+        std::vector<int32_t> pv, nb;
+        std::vector<int64_t> lp, bp;
+        partition_geometric(M, coords, nlev, p, p_last, pv, lp, nb, bp);
+        std::copy(pv.begin(), pv.end(), perm);
+        std::copy(lp.begin(), lp.end(), level_ptr);
+        std::copy(nb.begin(), nb.end(), nblk);
+        std::copy(bp.begin(), bp.end(), block_ptr);
+    });
+}
+
+gemslr_status gemslr_setup(const gemslr_csr *A, const gemslr_partition *part, const gemslr_options *opt,
+                           gemslr_handle *out) {
+    if (out) *out = nullptr;
+    return guard([&] {
+        if (!out) fail(GEMSLR_ERR_ARG, "out is NULL");
+        auto t0 = std::chrono::steady_clock::now();
+        std::unique_ptr<gemslr_ctx> h(new gemslr_ctx());
+        h->opt = normalized(opt);
+        Csr M = csr_from_abi(A);
+        build_levels(M, part, &h->opt, h->host);
+        finish_setup(h.get(), true);
+        h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        *out = h.release();
+    });
+}
+
+gemslr_status gemslr_setup_from_factors(const gemslr_csr *A, const gemslr_partition *part, const gemslr_factors *f,
+                                        const gemslr_options *opt, gemslr_handle *out) {
+    if (out) *out = nullptr;
+    return guard([&] {
+        if (!out || !f) fail(GEMSLR_ERR_ARG, "NULL argument");
+        auto t0 = std::chrono::steady_clock::now();
+        std::unique_ptr<gemslr_ctx> h(new gemslr_ctx());
+        h->opt = normalized(opt);
+        Csr M = csr_from_abi(A);
+        // slice levels from the partition but take every factor from f
+        gemslr_options o = h->opt;
+        o.ilu_kind = GEMSLR_ILU0;       // cheap placeholder factorisation, replaced below
+        for (int l = 0; l < GEMSLR_MAX_LEVELS; ++l) o.rank[l] = 0;
+        build_levels(M, part, &o, h->host);
+        Hierarchy &H = h->host;
+        if (f->nlev != H.nlev || !f->levels) fail(GEMSLR_ERR_ARG, "factor level count mismatch");
+        for (int l = 0; l < H.nlev - 1; ++l) {
+            const gemslr_level_factors &lf = f->levels[l];
+            HostLevel &hl = H.lev[l];
+            const int64_t d = hl.e - hl.s, s = H.n - hl.e;
+            hl.L = csr_from_mat(lf.L);
+            hl.U = csr_from_mat(lf.U);
+            hl.E = csr_from_mat(lf.E);
+            hl.F = csr_from_mat(lf.F);
+            if (hl.L.nrows != d || hl.U.nrows != d || hl.E.nrows != s || hl.E.ncols != d || hl.F.nrows != d ||
+                hl.F.ncols != s)
+                fail(GEMSLR_ERR_ARG, "factor shapes do not match the partition at level " + std::to_string(l));
+            if (lf.k < 0 || lf.k + 2 > kMaxRank) fail(GEMSLR_ERR_ARG, "rank out of range");
+            hl.k = lf.k;
+            if (lf.k > 0) {
+                if (!lf.W || !lf.H) fail(GEMSLR_ERR_ARG, "W/H missing");
+                hl.W.assign(lf.W, lf.W + (size_t)s * lf.k);
+                hl.H.assign(lf.H, lf.H + (size_t)lf.k * lf.k);
+            }
+        }
+        H.last.L = csr_from_mat(f->last_L);
+        H.last.U = csr_from_mat(f->last_U);
+        if (H.last.L.nrows != H.n - H.last.s || H.last.U.nrows != H.n - H.last.s)
+            fail(GEMSLR_ERR_ARG, "last-level factor shape mismatch");
+        finish_setup(h.get(), false);
+        for (size_t l = 0; l < H.lev.size(); ++l) set_lowrank<double, double>(h->d64.lev[l], H.lev[l], h->arena);
+        if (h->mixed) {
+            // rebuild the mixed hierarchy now that W/H are attached
+            h->d32 = DevHierarchy<float, __nv_bfloat16>();
+            upload_hierarchy<float, __nv_bfloat16>(H, h->arena, h->d32, std::min(smem_optin(), 200 * 1024));
+        }
+        GEMSLR_CUDA(cudaDeviceSynchronize());
+        h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        *out = h.release();
+    });
+}
+
+gemslr_status gemslr_factor_sizes(gemslr_handle h, int64_t *counts, int64_t ncounts) {
+    return guard([&] {
+        if (!h || !counts) fail(GEMSLR_ERR_ARG, "NULL argument");
+        const Hierarchy &H = h->host;
+        if (ncounts < 4 + 9 * (int64_t)H.lev.size()) fail(GEMSLR_ERR_ARG, "counts too small");
+        counts[0] = H.nlev;
+        for (size_t l = 0; l < H.lev.size(); ++l) {
+            const HostLevel &hl = H.lev[l];
+            int64_t *c = counts + 1 + 9 * l;
+            c[0] = hl.L.nnz(); c[1] = hl.U.nnz(); c[2] = hl.E.nnz(); c[3] = hl.F.nnz(); c[4] = hl.k;
+            c[5] = hl.e - hl.s; c[6] = H.n - hl.e; c[7] = hl.s; c[8] = hl.e;
+        }
+        int64_t *c = counts + 1 + 9 * H.lev.size();
+        c[0] = H.last.L.nnz(); c[1] = H.last.U.nnz(); c[2] = H.n - H.last.s;
+    });
+}
+
+static void put_mat(const Csr &M, const gemslr_mat &dst) {
+    if (!dst.rowptr || (M.nnz() > 0 && (!dst.colind || !dst.val))) fail(GEMSLR_ERR_ARG, "NULL export buffer");
+    std::copy(M.rp.begin(), M.rp.end(), const_cast<int64_t *>(dst.rowptr));
+    std::copy(M.ci.begin(), M.ci.end(), const_cast<int32_t *>(dst.colind));
+    std::copy(M.v.begin(), M.v.end(), const_cast<double *>(dst.val));
+}
+
+gemslr_status gemslr_export_factors(gemslr_handle h, gemslr_factors *f) {
+    return guard([&] {
+        if (!h || !f || !f->levels) fail(GEMSLR_ERR_ARG, "NULL argument");
+        const Hierarchy &H = h->host;
+        if (f->nlev != H.nlev) fail(GEMSLR_ERR_ARG, "nlev mismatch");
+        for (size_t l = 0; l < H.lev.size(); ++l) {
+            const HostLevel &hl = H.lev[l];
+            const gemslr_level_factors &lf = f->levels[l];
+            put_mat(hl.L, lf.L);
+            put_mat(hl.U, lf.U);
+            put_mat(hl.E, lf.E);
+            put_mat(hl.F, lf.F);
+            const_cast<gemslr_level_factors &>(lf).k = hl.k;
+            if (hl.k > 0) {
+                if (!lf.W || !lf.H) fail(GEMSLR_ERR_ARG, "NULL W/H buffer");
+                std::copy(hl.W.begin(), hl.W.end(), const_cast<double *>(lf.W));
+                std::copy(hl.H.begin(), hl.H.end(), const_cast<double *>(lf.H));
+            }
+        }
+        put_mat(H.last.L, f->last_L);
+        put_mat(H.last.U, f->last_U);
+    });
+}
+
+gemslr_status gemslr_apply(gemslr_handle h, const double *r_dev, double *z_dev, int32_t nrhs, void *stream) {
+    return guard([&] {
+        if (!h || nrhs < 0 || (nrhs > 0 && (!r_dev || !z_dev))) fail(GEMSLR_ERR_ARG, "invalid argument");
+        if (r_dev == z_dev && nrhs > 0) fail(GEMSLR_ERR_ARG, "r and z must not alias");
+        cudaStream_t st = (cudaStream_t)stream;
+        const int64_t n = h->host.n;
+        ensure_krylov(h, 8);
+        for (int c = 0; c < nrhs; ++c) {
+            launch_gather(n, h->perm, r_dev + (size_t)c * n, h->bh, st);
+            apply_perm(h, h->bh, h->xh, st);
+            launch_scatter(n, h->perm, h->xh, z_dev + (size_t)c * n, st);
+        }
+        GEMSLR_CUDA(cudaGetLastError());
+    });
+}
+
+gemslr_status gemslr_fgmres_solve(gemslr_handle h, const double *b_dev, double *x_dev, int32_t nrhs,
+                                  const gemslr_solve_opts *opts, gemslr_solve_info *info, void *stream) {
+    gemslr_status worst = GEMSLR_OK;
+    gemslr_status st_ = guard([&] {
+        if (!h || !opts || !info || nrhs < 0 || (nrhs > 0 && (!b_dev || !x_dev)))
+            fail(GEMSLR_ERR_ARG, "invalid argument");
+        if (opts->restart < 1 || opts->maxit < 1 || !(opts->rtol > 0)) fail(GEMSLR_ERR_ARG, "invalid solve options");
+        cudaStream_t st = (cudaStream_t)stream;
+        const int64_t n = h->host.n;
+        const int m = opts->restart;
+        ensure_krylov(h, m);
+        for (int c = 0; c < nrhs; ++c) {
+            auto t0 = std::chrono::steady_clock::now();
+            gemslr_solve_info &inf = info[c];
+            std::memset(&inf, 0, sizeof(inf));
+            launch_gather(n, h->perm, b_dev + (size_t)c * n, h->bh, st);
+            launch_norm2(n, h->bh, h->partial, h->counter, h->n2, h->red_grid, st);
+            const double bn2 = read_scalar(h, h->n2, st);
+            const double bnorm = std::sqrt(bn2);
+            launch_zero(n, h->xh, st);
+            if (!std::isfinite(bnorm)) {
+                if (worst == GEMSLR_OK) worst = GEMSLR_ERR_NAN;
+                g_last_error = "right-hand side is not finite";
+                launch_scatter(n, h->perm, h->xh, x_dev + (size_t)c * n, st);
+                continue;
+            }
+            if (bnorm == 0.0) {
+                inf.converged = 1;
+                launch_scatter(n, h->perm, h->xh, x_dev + (size_t)c * n, st);
+                continue;
+            }
+            KrylovCtl cc{};
+            cc.m = m;
+            cc.givens = 1;
+            cc.force_reorth = 0;
+            cc.maxit = opts->maxit;
+            cc.tol_abs = opts->rtol * bnorm;
+            *h->ctl_host = cc;
+            write_ctl(h, st);
+            GEMSLR_CUDA(cudaMemcpyAsync(h->r, h->bh, 8 * n, cudaMemcpyDeviceToDevice, st));
+            GEMSLR_CUDA(cudaMemcpyAsync(h->n2 + 1, h->n2, 8, cudaMemcpyDeviceToDevice, st));   // ||r||^2
+            bool converged = false, bad = false;
+            int iters = 0;
+            double rel_true = 1.0;
+            while (true) {
+                launch_cycle_start(h->ctl, h->g, h->n2 + 1, st);
+                launch_scale_by_norm(n, h->r, h->n2 + 1, h->V, st);
+                for (int j = 0; j < m; ++j) {
+                    double *vj = h->V + (size_t)j * n, *zj = h->Z + (size_t)j * n;
+                    apply_perm(h, vj, zj, st);
+                    launch_spmv(n, h->A_rp, h->A_ci, h->A_v, zj, nullptr, h->w, h->spmv_lanes, st);
+                    launch_gs_dots(n, h->V, n, h->w, h->partial, h->counter, h->ctl, h->Hs, h->cs, h->sn, h->g,
+                                   h->red_grid, st);
+                    launch_gs_sub(n, h->V, n, h->w, h->partial, h->counter, h->ctl, h->Hs, h->cs, h->sn, h->g, h->h2,
+                                  h->red_grid, st);
+                    launch_gs_sub2(n, h->V, n, h->w, h->h2, h->ctl, st);
+                    launch_gs_next(h->ctl, st);
+                    read_ctl(h, st);
+                    if (h->ctl_host->stop) break;
+                }
+                launch_lsq(h->ctl, h->Hs, h->g, h->y, st);
+                launch_update_x(n, h->Z, n, h->ctl, h->y, h->xh, st);
+                launch_spmv(n, h->A_rp, h->A_ci, h->A_v, h->xh, h->bh, h->r, h->spmv_lanes, st);
+                launch_norm2(n, h->r, h->partial, h->counter, h->n2 + 1, h->red_grid, st);
+                const double rn = std::sqrt(read_scalar(h, h->n2 + 1, st));
+                read_ctl(h, st);
+                iters = h->ctl_host->iters;
+                rel_true = rn / bnorm;
+                inf.rel_res_est = h->ctl_host->resid / bnorm;
+                if (!std::isfinite(rn) || h->ctl_host->nonfinite) { bad = true; break; }
+                if (rn <= opts->rtol * bnorm) { converged = true; break; }
+                if (iters >= opts->maxit) break;
+                inf.restarts += 1;
+            }
+            launch_scatter(n, h->perm, h->xh, x_dev + (size_t)c * n, st);
+            GEMSLR_CUDA(cudaStreamSynchronize(st));
+            inf.iters = iters;
+            inf.converged = converged ? 1 : 0;
+            inf.reorth = h->ctl_host->nreorth;
+            inf.rel_res_true = rel_true;
+            inf.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (bad) {
+                if (worst == GEMSLR_OK) worst = GEMSLR_ERR_NAN;
+                g_last_error = "FGMRES produced a non-finite value";
+            } else if (!converged && worst == GEMSLR_OK) {
+                worst = GEMSLR_ERR_NOT_CONVERGED;
+                g_last_error = "FGMRES reached maxit";
+            }
+        }
+    });
+    return st_ != GEMSLR_OK ? st_ : worst;
+}
+
+gemslr_status gemslr_get_stats(gemslr_handle h, double *out, int32_t nout) {
+    return guard([&] {
+        if (!h || !out) fail(GEMSLR_ERR_ARG, "NULL argument");
+        const Hierarchy &H = h->host;
+        const int need = 8 + 6 * H.nlev;
+        if (nout < need) fail(GEMSLR_ERR_ARG, "stats buffer too small");
+        std::fill(out, out + nout, 0.0);
+        int64_t nnzf = 0;
+        for (auto &l : H.lev) nnzf += l.L.nnz() + l.U.nnz();
+        nnzf += H.last.L.nnz() + H.last.U.nnz();
+        out[0] = (double)H.n;
+        out[1] = H.nlev;
+        out[2] = (double)H.nclamp;
+        out[3] = (double)H.Ahat.nnz();
+        out[4] = (double)nnzf;
+        // algorithmic bytes of one application (values, indices, vectors, W)
+        const double sv = h->mixed ? 4.0 : 8.0, sw = h->mixed ? 2.0 : 8.0, si = 4.0;
+        double bytes = 0.0;
+        for (auto &l : H.lev) {
+            const double d = (double)(l.e - l.s), s = (double)(H.n - l.e);
+            bytes += 2.0 * (l.L.nnz() + l.U.nnz()) * (sv + si);        // two substitutions
+            bytes += (l.E.nnz() + l.F.nnz()) * (sv + si);
+            bytes += 2.0 * s * l.k * sw;                               // W^T z and W u
+            bytes += (8.0 * d + 6.0 * s) * sv;
+        }
+        bytes += (H.last.L.nnz() + H.last.U.nnz()) * (sv + si) + 2.0 * (H.n - H.last.s) * sv;
+        bytes += 2.0 * H.n * 8.0;
+        out[5] = bytes;
+        out[6] = h->setup_ms;
+        out[7] = (double)h->arena.bytes();
+        for (int l = 0; l < H.nlev; ++l) {
+            double *o = out + 8 + 6 * l;
+            if (l + 1 < H.nlev) {
+                const HostLevel &hl = H.lev[l];
+                const auto &dl = h->d64.lev[l];
+                o[0] = (double)(hl.e - hl.s); o[1] = (double)(H.n - hl.e); o[2] = hl.k;
+                o[3] = (double)(hl.L.nnz() + hl.U.nnz()); o[4] = dl.nwf_L; o[5] = dl.nwf_U;
+            } else {
+                o[0] = (double)(H.n - H.last.s);
+                o[3] = (double)(H.last.L.nnz() + H.last.U.nnz());
+                o[4] = h->d64.last.nwf_L; o[5] = h->d64.last.nwf_U;
+            }
+        }
+    });
+}
+
+void gemslr_destroy(gemslr_handle h) { delete h; }
+
+}  // extern "C"

@@ -1,0 +1,44 @@
+"""Shared builders for the tests (oracle hierarchies on seeded problems)."""
+import functools
+
+import numpy as np
+
+import gemslr_inputs as gi
+from oracle import OracleGemslr, multilevel_partition
+
+CASES = {
+    # name: (dims, beta, sigma, nlev, p, ilu, tau, lfil, rank)
+    "c1": ((32, 32), 0.0, 0.0, 2, 4, "ilu0", 0.0, 0, 8),
+    "small3d": ((13, 11, 9), 0.4, 0.0, 3, 8, "ilut", 1e-2, 5, 5),
+    "shifted": ((12, 12, 12), 0.0, 0.05, 4, 8, "ilut", 1e-3, 10, 6),
+    "rank0": ((10, 9, 8), 0.2, 0.0, 3, 4, "ilu0", 0.0, 0, 0),
+    "tinyparts": ((6, 5, 4), 0.3, 0.0, 3, 16, "ilu0", 0.0, 0, 3),
+    "bigblock": ((240, 240), 0.5, 0.0, 2, 2, "ilu0", 0.0, 0, 4),
+    "c2": ((64, 64, 64), 0.1, 0.0, 4, 64, "ilut", 1e-3, 10, 32),
+}
+
+
+@functools.lru_cache(maxsize=None)
+def problem(name):
+    dims, beta, sigma, nlev, p, ilu, tau, lfil, rank = CASES[name]
+    A, xyz = gi.grid_operator(dims, beta=beta, sigma=sigma)
+    part = multilevel_partition(A.to_scipy(), xyz, nlev, p)
+    return A, xyz, part
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_hierarchy(name):
+    dims, beta, sigma, nlev, p, ilu, tau, lfil, rank = CASES[name]
+    A, xyz, part = problem(name)
+    return OracleGemslr(A.to_scipy(), part, ilu=ilu, tau=tau, lfil=lfil, rank=rank)
+
+
+def lib_opts(name):
+    dims, beta, sigma, nlev, p, ilu, tau, lfil, rank = CASES[name]
+    return dict(ilu=ilu, tau=tau, lfil=lfil, rank=rank)
+
+
+def rel_err(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
