@@ -149,7 +149,7 @@ def test_arnoldi_relation_and_ritz_values_T8():
     Gd = np.column_stack([op(np.eye(s)[:, i]) for i in range(s)])
     R = Gd @ W - W @ Tk
     theta = block_eigs(Tk)
-    assert np.all(np.linalg.norm(R, axis=0) <= 1.01e-2 * np.abs(theta) + 1e-12)
+    assert np.linalg.norm(R, 2) <= 1.01e-2 * np.min(np.abs(theta)) + 1e-12
     # Ritz values agree with the wanted eigenvalues of the dense G_hat to two digits
     ev = np.linalg.eigvals(Gd)
     order = np.lexsort((-np.abs(ev), -correction_score(ev)))
