@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Benchmark of the GeMSLR-preconditioned FGMRES solve phase on GB300.
+
+One step = one complete right-preconditioned FGMRES(50) solve to relative
+residual 1e-8 (every application of M^{-1} walks the whole multilevel
+hierarchy) of the 64^3 convection-diffusion system (n = 262,144; 4 levels,
+64 subdomains per level, ILUT(1e-3, 10), rank 32, b ~ U[-1, 1) seed 1), with
+the preconditioner already set up and b resident on the GPU.  The value is
+whole-job throughput in solves per second; N > 1 runs independent replicas
+(the path has no data exchange on one GPU).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gemslr_inputs as gi  # noqa: E402
+
+METRIC = "time to 1e-8 residual and M^-1 applies/s: mixed/learned vs plain FP64 GPU"
+CONFIG = "c2"
+WORKLOAD = ("3-D 7-pt convection-diffusion 64^3 (n=262144, beta=0.1), 4 levels x 64 subdomains, "
+            "ILUT(1e-3,10), rank 32, FGMRES(50) to rel. residual 1e-8, b~U[-1,1) seed 1")
+UNIT = "solves/s (FGMRES to 1e-8)"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_PEAK_TFLOPS = 1.203      # FP64 FMA probe on this machine's GB300 (0.601 TFMA/s)
+
+
+def cfg():
+    return gi.CONFIGS[CONFIG]
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------------------------
+def oracle_solves(nsolve):
+    """The CPU oracle as it stands: setup once (untimed), then ``nsolve`` timed FGMRES solves."""
+    from oracle import OracleGemslr, fgmres, multilevel_partition
+    c = cfg()
+    A, xyz, b = gi.config_problem(CONFIG)
+    As = A.to_scipy()
+    t0 = time.perf_counter()
+    part = multilevel_partition(As, xyz, c["nlev"], c["p"])
+    M = OracleGemslr(As, part, ilu=c["ilu"], tau=c["tau"], lfil=c["lfil"], rank=c["rank"])
+    t_setup = time.perf_counter() - t0
+    times, its = [], []
+    for _ in range(nsolve):
+        t0 = time.perf_counter()
+        x, info = fgmres(As, b, M.apply, restart=c["restart"], rtol=c["rtol"])
+        times.append(time.perf_counter() - t0)
+        its.append(info["iters"])
+    return times, its, t_setup
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return 0
+    times, its, t_setup = oracle_solves(args.warmup + args.steps)
+    timed = times[args.warmup:]
+    total = sum(timed)
+    value = len(timed) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
+                         "sample": f"{len(timed)} complete oracle FGMRES solves of the workload "
+                                   f"(setup {t_setup:.1f} s excluded), iterations {its[-1]}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------------------------
+def algorithmic_bytes(fac, n, nnzA, sv=8, si=4, sw=8):
+    """Bytes each kernel class must move per launch (values, indices, vectors), by the layout."""
+    out = {}
+    for l, lv in enumerate(fac["levels"]):
+        d = lv["L"].shape[0]
+        s = lv["E"].shape[0]
+        k = lv["W"].shape[1]
+        nl = lv["L"].nnz
+        nu_off = lv["U"].nnz - d
+        tri = (nl + nu_off) * (sv + si) + d * sv + 2 * d * 4 * 2      # entries, 1/u_ii, slot rows/lengths
+        out[f"trsv_down_L{l}"] = tri + 2 * d * sv
+        out[f"trsv_up_L{l}"] = tri + lv["F"].nnz * (2 * sv + si) + (d + 1) * 8 + 2 * d * sv
+        out[f"couple_EWt_L{l}"] = lv["E"].nnz * (2 * sv + si) + (s + 1) * 8 + 2 * s * sv + s * k * sw
+        out[f"lowrank_Wu_L{l}"] = s * k * sw + 2 * s * sv if k else 0
+    last = fac["last"]
+    dl = last["L"].shape[0]
+    out["trsv_last"] = (last["L"].nnz + last["U"].nnz - dl) * (sv + si) + dl * sv + 2 * dl * 8 + 2 * dl * sv
+    out["spmv_A"] = nnzA * 12 + (n + 1) * 8 + 2 * n * 8
+    return out
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_03224_gb300 import Gemslr, partition_geometric
+    from paper_2205_03224_gb300 import _lib
+
+    c = cfg()
+    A, xyz, b = gi.config_problem(CONFIG)
+    part = partition_geometric(A, xyz, c["nlev"], c["p"])
+    t0 = time.perf_counter()
+    G = Gemslr(A, part, ilu=c["ilu"], tau=c["tau"], lfil=c["lfil"], rank=c["rank"], precision=args.precision)
+    setup_s = time.perf_counter() - t0
+    st = G.stats()
+    b_dev = torch.from_numpy(b).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        x, info = G.solve(b_dev, restart=c["restart"], rtol=c["rtol"])
+    its = info[0]["iters"]
+    clocks = Clocks(local)
+    clocks.start()
+    barrier()
+    l0 = _lib.kernel_launches()
+    ms = []
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, info = G.solve(b_dev, restart=c["restart"], rtol=c["rtol"])
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    torch.cuda.nvtx.range_pop()
+    barrier()
+    launches = _lib.kernel_launches() - l0
+    clk = clocks.stop()
+    total_ms = sum(ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * args.steps / (total_ms / 1e3)
+    x_np = x.cpu().numpy()
+    res = float(np.linalg.norm(b - A.to_scipy() @ x_np) / np.linalg.norm(b))
+
+    # M^{-1} applications per second (inputs resident, events on the launching stream)
+    r_dev = torch.from_numpy(gi.rhs_uniform(A.n, 7)).cuda()
+    for _ in range(3):
+        G.apply(r_dev)
+    napply = 50
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("applies")
+    e0.record(stream)
+    for _ in range(napply):
+        G.apply(r_dev)
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    e1.synchronize()
+    apply_ms = e0.elapsed_time(e1) / napply
+
+    # end to end through the public API from pinned host memory
+    b_host = torch.from_numpy(b).pin_memory()
+    x_host = torch.empty_like(b_host).pin_memory()
+    e2e = []
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bd = b_host.to("cuda", non_blocking=True)
+        xd, _ = G.solve(bd, restart=c["restart"], rtol=c["rtol"])
+        x_host.copy_(xd, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e.append(e0.elapsed_time(e1))
+    e2e_value = ws / (statistics.mean(e2e) / 1e3)
+
+    # per-kernel times over one profiled solve (events on the launching stream)
+    _lib.profile_reset()
+    _lib.profile_enable(True)
+    G.solve(b_dev, restart=c["restart"], rtol=c["rtol"])
+    prof = _lib.profile_read()
+    _lib.profile_enable(False)
+    fac = G.export_factors()
+    sv = 4 if args.precision == "mixed" else 8
+    sw = 2 if args.precision == "mixed" else 8
+    ab = algorithmic_bytes(fac, A.n, A.nnz, sv=sv, sw=sw)
+    top = max((k for k in prof if k in ab), key=lambda k: prof[k][0])
+    top_ms = prof[top][0] / prof[top][1]
+    peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    achieved = ab[top] / (top_ms * 1e-3) / 1e9
+    roofline = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "bytes_per_launch": ab[top],
+                "ms_per_launch": top_ms,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    total_prof = sum(v[0] for v in prof.values())
+    kernels = {k: {"ms_total": round(v[0], 4), "launches": v[1], "share": round(v[0] / total_prof, 4)}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/bf16+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "Krylov basis 2 x 107 MB > L2; 256 MB buffer written between solves"},
+        "time_to_solution_ms": total_ms / args.steps, "iterations": its, "final_rel_residual": res,
+        "applies_per_s": 1e3 / apply_ms, "apply_ms": apply_ms, "setup_s": setup_s,
+        "bytes_per_apply": st["bytes_per_apply"],
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(A.n * 8), "d2h_bytes_per_step": int(A.n * 8)},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "kernels": kernels,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        times, oits, t_setup = oracle_solves(2)
+        line["cpu_baseline"] = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{len(times)} complete oracle FGMRES solves of the workload "
+                                          f"(oracle setup {t_setup:.1f} s excluded), {oits[-1]} iterations"}
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -224,6 +224,21 @@ const char *gemslr_last_error(void);
 /* Free the handle and its device memory (NULL is accepted). */
 void gemslr_destroy(gemslr_handle h);
 
+/*
+ * Instrumentation (not part of the method; process-wide, thread-safe).
+ * gemslr_kernel_launches: number of CUDA kernels this library has launched.
+ * gemslr_profile_enable: with on != 0 every instrumented launch is bracketed
+ * by CUDA events on its stream (adds host overhead; for measurement runs).
+ * gemslr_profile_read: synchronises the recorded events and returns the
+ * number of kernel names; writes up to maxn totals (ms) and launch counts,
+ * and the names, newline-separated, into names[len].
+ * gemslr_profile_reset: drops the accumulated totals.
+ */
+uint64_t gemslr_kernel_launches(void);
+void gemslr_profile_enable(int32_t on);
+void gemslr_profile_reset(void);
+int32_t gemslr_profile_read(char *names, size_t len, double *ms, int64_t *counts, int32_t maxn);
+
 #ifdef __cplusplus
 }
 #endif

@@ -59,7 +59,8 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_PARTITION", 3: "ERR_ZERO_PIVOT", 4: "ER
 EXPORTED = [
     "gemslr_default_options", "gemslr_partition_geometric", "gemslr_setup", "gemslr_setup_from_factors",
     "gemslr_factor_sizes", "gemslr_export_factors", "gemslr_apply", "gemslr_fgmres_solve",
-    "gemslr_get_stats", "gemslr_last_error", "gemslr_destroy",
+    "gemslr_get_stats", "gemslr_last_error", "gemslr_destroy", "gemslr_kernel_launches",
+    "gemslr_profile_enable", "gemslr_profile_reset", "gemslr_profile_read",
 ]
 
 _lib = None
@@ -94,9 +95,18 @@ def load():
     L.gemslr_last_error.argtypes = []
     L.gemslr_destroy.argtypes = [P]
     L.gemslr_destroy.restype = None
+    L.gemslr_kernel_launches.restype = ctypes.c_uint64
+    L.gemslr_kernel_launches.argtypes = []
+    L.gemslr_profile_enable.argtypes = [i32]
+    L.gemslr_profile_enable.restype = None
+    L.gemslr_profile_reset.argtypes = []
+    L.gemslr_profile_reset.restype = None
+    L.gemslr_profile_read.argtypes = [ctypes.c_char_p, ctypes.c_size_t, P, P, i32]
+    L.gemslr_profile_read.restype = i32
     for name in EXPORTED:
         fn = getattr(L, name)
-        if name not in ("gemslr_default_options", "gemslr_last_error", "gemslr_destroy"):
+        if name not in ("gemslr_default_options", "gemslr_last_error", "gemslr_destroy", "gemslr_kernel_launches",
+                        "gemslr_profile_enable", "gemslr_profile_reset", "gemslr_profile_read"):
             fn.restype = ctypes.c_int
     _lib = L
     return L
@@ -143,3 +153,26 @@ def mat_struct(M, keep):
     v = np.ascontiguousarray(M.data, dtype=np.float64)
     keep.extend([rp, ci, v])
     return Mat(M.shape[0], M.shape[1], ptr(rp), ptr(ci), ptr(v))
+
+
+def kernel_launches():
+    return int(load().gemslr_kernel_launches())
+
+
+def profile_enable(on=True):
+    load().gemslr_profile_enable(1 if on else 0)
+
+
+def profile_reset():
+    load().gemslr_profile_reset()
+
+
+def profile_read():
+    """{kernel name: (total ms, launches)} accumulated since the last reset."""
+    lib = load()
+    buf = ctypes.create_string_buffer(1 << 16)
+    ms = np.zeros(256)
+    cnt = np.zeros(256, dtype=np.int64)
+    k = lib.gemslr_profile_read(buf, len(buf), ptr(ms), ptr(cnt), 256)
+    names = buf.value.decode().split("\n")[:k]
+    return {nm: (float(ms[i]), int(cnt[i])) for i, nm in enumerate(names)}

@@ -1,6 +1,8 @@
 // Device layout of the GeMSLR hierarchy and the application of M^{-1} (Alg. 2).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <mutex>
 
 #include "device.h"
 
@@ -9,6 +11,93 @@ namespace gemslr {
 void cuda_check(cudaError_t e, const char *what) {
     if (e != cudaSuccess) fail(GEMSLR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
+
+// ---- instrumentation ---------------------------------------------------------
+namespace {
+struct ProfEntry { std::string name; cudaEvent_t a, b; };
+struct ProfStat { double ms = 0.0; int64_t count = 0; };
+std::atomic<uint64_t> g_launches{0};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfEntry> g_prof_pending;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_pool;
+std::vector<std::pair<std::string, ProfStat>> g_prof_stats;
+}  // namespace
+
+void count_launch(int n) { g_launches += (uint64_t)n; }
+
+bool profile_enabled() { return g_prof_on; }
+
+ProfScope::ProfScope(const char *name, cudaStream_t s) : slot(-1), st(s) {
+    if (!g_prof_on) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::pair<cudaEvent_t, cudaEvent_t> ev;
+    if (!g_prof_pool.empty()) { ev = g_prof_pool.back(); g_prof_pool.pop_back(); }
+    else { cudaEventCreate(&ev.first); cudaEventCreate(&ev.second); }
+    cudaEventRecord(ev.first, st);
+    g_prof_pending.push_back({name, ev.first, ev.second});
+    slot = (int)g_prof_pending.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEventRecord(g_prof_pending[slot].b, st);
+}
+
+void profile_enable(bool on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on;
+}
+
+// Synchronise the recorded events and fold them into the per-name totals.
+void profile_collect() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &e : g_prof_pending) {
+        cudaEventSynchronize(e.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e.a, e.b);
+        auto it = std::find_if(g_prof_stats.begin(), g_prof_stats.end(),
+                               [&](const std::pair<std::string, ProfStat> &p) { return p.first == e.name; });
+        if (it == g_prof_stats.end()) { g_prof_stats.push_back({e.name, ProfStat()}); it = g_prof_stats.end() - 1; }
+        it->second.ms += ms;
+        it->second.count += 1;
+        g_prof_pool.push_back({e.a, e.b});
+    }
+    g_prof_pending.clear();
+}
+
+void profile_reset() {
+    profile_collect();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_stats.clear();
+}
+
+int profile_read(char *names, size_t len, double *ms, int64_t *counts, int maxn) {
+    profile_collect();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    std::string all;
+    int k = 0;
+    for (auto &p : g_prof_stats) {
+        if (k < maxn) {
+            if (ms) ms[k] = p.second.ms;
+            if (counts) counts[k] = p.second.count;
+        }
+        all += p.first;
+        all += '\n';
+        ++k;
+    }
+    if (names && len) {
+        const size_t c = std::min(len - 1, all.size());
+        std::memcpy(names, all.data(), c);
+        names[c] = 0;
+    }
+    return k;
+}
+
+uint64_t launches_total() { return g_launches.load(); }
 
 Arena::~Arena() {
     for (void *p : ptrs_) cudaFree(p);
@@ -33,16 +122,6 @@ template <> double cast_to<double>(double v) { return v; }
 template <> float cast_to<float>(double v) { return (float)v; }
 template <> __nv_bfloat16 cast_to<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
 
-template <typename VT>
-struct TriHost {
-    std::vector<int32_t> blk_wf{0}, wf_slot{0}, slot_row, slot_len, ent_col;
-    std::vector<int64_t> wf_ent;
-    std::vector<VT> ent_val;
-    int maxwf = 0;
-};
-
-// Wavefront-sliced layout of a block-diagonal triangular factor.  For U the
-// diagonal is moved to dinv (as 1/u_ii).
 // Every entry must lie in its row's diagonal block, strictly below (L) or on
 // and above (U) the diagonal, and U needs a nonzero diagonal: the kernels
 // index the block's shared-memory vector with these columns.
@@ -62,66 +141,96 @@ void validate_tri(const Csr &T, const std::vector<int64_t> &bp, bool upper) {
         }
 }
 
+size_t pad16(size_t x) { return (x + 15) & ~size_t(15); }
+
 template <typename VT>
-void build_tri(const Csr &T, const std::vector<int64_t> &bp, bool upper, TriHost<VT> &out, std::vector<VT> *dinv) {
-    validate_tri(T, bp, upper);
-    if (upper) dinv->assign(T.nrows, cast_to<VT>(0.0));
-    for (size_t b = 0; b + 1 < bp.size(); ++b) {
-        const int64_t r0 = bp[b], r1 = bp[b + 1];
-        std::vector<int32_t> lev = upper ? wavefronts_upper(T, r0, r1) : wavefronts_lower(T, r0, r1);
-        int nw = 0;
-        for (int32_t x : lev) nw = std::max(nw, x + 1);
-        out.maxwf = std::max(out.maxwf, nw);
-        std::vector<std::vector<int64_t>> rows(nw);
-        for (int64_t i = r0; i < r1; ++i) rows[lev[i - r0]].push_back(i);
-        auto offdiag = [&](int64_t i) {
-            int64_t c = 0;
-            for (int64_t p = T.rp[i]; p < T.rp[i + 1]; ++p) c += (T.ci[p] != i);
-            return c;
-        };
-        for (int w = 0; w < nw; ++w) {
-            std::vector<int64_t> &R = rows[w];
-            std::stable_sort(R.begin(), R.end(), [&](int64_t a, int64_t c) { return offdiag(a) > offdiag(c); });
-            const int64_t cnt = (int64_t)R.size();
-            int64_t maxlen = 0;
-            for (int64_t i : R) maxlen = std::max(maxlen, offdiag(i));
-            const int64_t base = (int64_t)out.ent_col.size();
-            out.wf_ent.push_back(base);
-            out.ent_col.resize(base + cnt * maxlen, 0);
-            out.ent_val.resize(base + cnt * maxlen, cast_to<VT>(0.0));
-            for (int64_t t = 0; t < cnt; ++t) {
-                const int64_t i = R[t];
-                out.slot_row.push_back((int32_t)(i - r0));
-                int64_t q = 0;
-                for (int64_t p = T.rp[i]; p < T.rp[i + 1]; ++p) {
-                    if (T.ci[p] == i) {
-                        if (upper) (*dinv)[i] = cast_to<VT>(1.0 / T.v[p]);
-                        continue;
-                    }
-                    out.ent_col[base + q * cnt + t] = (int32_t)(T.ci[p] - r0);
-                    out.ent_val[base + q * cnt + t] = cast_to<VT>(T.v[p]);
-                    ++q;
-                }
-                out.slot_len.push_back((int32_t)q);
-            }
-            out.wf_slot.push_back((int32_t)out.slot_row.size());
-        }
-        out.blk_wf.push_back((int32_t)out.wf_ent.size());
-    }
-    if (out.wf_ent.empty()) out.wf_ent.push_back(0);
+size_t chunk_bytes(int64_t nrows, int64_t maxlen, bool upper) {
+    const size_t pr = (size_t)((nrows + 3) & ~int64_t(3));
+    const size_t kq = (size_t)((maxlen + 3) / 4);
+    return 16 + 8 * pr + kq * (size_t)nrows * 4 * (4 + sizeof(VT)) + (upper ? pad16((size_t)nrows * sizeof(VT)) : 0);
 }
 
 template <typename VT>
-TriView<VT> upload_tri(const TriHost<VT> &t, Arena &a) {
-    TriView<VT> v;
-    v.blk_wf = a.upload(t.blk_wf);
-    v.wf_slot = a.upload(t.wf_slot);
-    v.wf_ent = a.upload(t.wf_ent);
-    v.slot_row = a.upload(t.slot_row);
-    v.slot_len = a.upload(t.slot_len);
-    v.ent_col = a.upload(t.ent_col);
-    v.ent_val = a.upload(t.ent_val);
-    return v;
+struct ChunkHost {
+    std::vector<unsigned char> data;
+    std::vector<int64_t> off{0};
+    std::vector<int32_t> blk_chunk{0};
+    int maxwf_L = 0, maxwf_U = 0;
+};
+
+// Append the chunks of one triangular factor of block [r0, r1) (see kernels.cuh).
+template <typename VT>
+void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, ChunkHost<VT> &out, int &maxwf) {
+    std::vector<int32_t> lev = upper ? wavefronts_upper(T, r0, r1) : wavefronts_lower(T, r0, r1);
+    int nw = 0;
+    for (int32_t x : lev) nw = std::max(nw, x + 1);
+    maxwf = std::max(maxwf, nw);
+    std::vector<std::vector<int64_t>> rows(nw);
+    for (int64_t i = r0; i < r1; ++i) rows[lev[i - r0]].push_back(i);
+    std::vector<int64_t> nlen(r1 - r0);
+    for (int64_t i = r0; i < r1; ++i) {
+        int64_t c = 0;
+        for (int64_t p = T.rp[i]; p < T.rp[i + 1]; ++p) c += (T.ci[p] != i);
+        nlen[i - r0] = c;
+    }
+    for (int w = 0; w < nw; ++w) {
+        std::vector<int64_t> &R = rows[w];
+        std::stable_sort(R.begin(), R.end(), [&](int64_t a, int64_t c) { return nlen[a - r0] > nlen[c - r0]; });
+        if (!upper && nlen[R[0] - r0] == 0) continue;          // rows without L entries: x_i unchanged
+        size_t start = 0;
+        while (start < R.size()) {
+            const int64_t maxlen = nlen[R[start] - r0];
+            int64_t n = 0;
+            while (start + n < R.size() && n < kChunkRows &&
+                   chunk_bytes<VT>(n + 1, maxlen, upper) <= (size_t)kStageBytes)
+                ++n;
+            if (n == 0) fail(GEMSLR_ERR_UNSUPPORTED, "a factor row has too many entries for the staged substitution");
+            const size_t bytes = chunk_bytes<VT>(n, maxlen, upper);
+            const int64_t kq = (maxlen + 3) / 4;
+            const size_t base = out.data.size();
+            out.data.resize(base + bytes, 0);
+            unsigned char *p = out.data.data() + base;
+            int32_t *hdr = reinterpret_cast<int32_t *>(p);
+            hdr[0] = (int32_t)n;
+            hdr[1] = (int32_t)kq;
+            hdr[2] = upper ? 1 : 0;
+            hdr[3] = 0;
+            const int64_t pr = (n + 3) & ~int64_t(3);
+            int32_t *rr = hdr + 4, *ll = rr + pr, *cc = ll + pr;
+            VT *vv = reinterpret_cast<VT *>(cc + kq * n * 4);
+            VT *dd = vv + kq * n * 4;
+            for (int64_t t = 0; t < n; ++t) {
+                const int64_t i = R[start + t];
+                rr[t] = (int32_t)(i - r0);
+                ll[t] = (int32_t)nlen[i - r0];
+                int64_t q = 0;
+                for (int64_t pp = T.rp[i]; pp < T.rp[i + 1]; ++pp) {
+                    if (T.ci[pp] == i) {
+                        if (upper) dd[t] = cast_to<VT>(1.0 / T.v[pp]);
+                        continue;
+                    }
+                    const int64_t e = ((q >> 2) * n + t) * 4 + (q & 3);
+                    cc[e] = (int32_t)(T.ci[pp] - r0);
+                    vv[e] = cast_to<VT>(T.v[pp]);
+                    ++q;
+                }
+            }
+            out.off.push_back((int64_t)out.data.size());
+            start += n;
+        }
+    }
+}
+
+template <typename VT>
+void build_chunks(const Csr &L, const Csr &U, const std::vector<int64_t> &bp, ChunkHost<VT> &out) {
+    validate_tri(L, bp, false);
+    validate_tri(U, bp, true);
+    for (size_t b = 0; b + 1 < bp.size(); ++b) {
+        append_factor_chunks<VT>(L, bp[b], bp[b + 1], false, out, out.maxwf_L);
+        append_factor_chunks<VT>(U, bp[b], bp[b + 1], true, out, out.maxwf_U);
+        out.blk_chunk.push_back((int32_t)(out.off.size() - 1));
+    }
+    if (out.data.empty()) out.data.resize(16, 0);
 }
 
 template <typename T>
@@ -141,16 +250,15 @@ void upload_level(const HostLevel &hl, int64_t n, bool schur, Arena &a, DevLevel
     v.blk_row = a.upload(hl.bp);
     int64_t maxrows = 0;
     for (size_t b = 0; b + 1 < hl.bp.size(); ++b) maxrows = std::max(maxrows, hl.bp[b + 1] - hl.bp[b]);
-    d.smem_rows = (maxrows * (int64_t)sizeof(VT) <= smem_limit) ? (int)maxrows : 0;
-    TriHost<VT> L, U;
-    std::vector<VT> dinv;
-    build_tri<VT>(hl.L, hl.bp, false, L, nullptr);
-    build_tri<VT>(hl.U, hl.bp, true, U, &dinv);
-    v.L = upload_tri(L, a);
-    v.U = upload_tri(U, a);
-    v.dinv = a.upload(dinv);
-    d.nwf_L = L.maxwf;
-    d.nwf_U = U.maxwf;
+    d.smem_rows = (kRingBytes + maxrows * (int64_t)sizeof(VT) <= smem_limit) ? (int)maxrows : 0;
+    ChunkHost<VT> ch;
+    build_chunks<VT>(hl.L, hl.U, hl.bp, ch);
+    v.C.data = a.upload(ch.data);
+    v.C.off = a.upload(ch.off);
+    v.C.blk_chunk = a.upload(ch.blk_chunk);
+    d.nwf_L = ch.maxwf_L;
+    d.nwf_U = ch.maxwf_U;
+    d.nchunks = (int64_t)ch.off.size() - 1;
     d.nnz_tri = hl.L.nnz() + hl.U.nnz();
     if (schur) {
         std::vector<int32_t> fci(hl.F.ci.size());
@@ -181,14 +289,18 @@ void set_lowrank(DevLevel<VT, WT> &d, const HostLevel &hl, Arena &a) {
 template <typename VT, typename WT>
 void upload_hierarchy(const Hierarchy &h, Arena &a, DevHierarchy<VT, WT> &d, int smem_limit) {
     set_trsv_smem_limit<VT, WT>(smem_limit);
+    d.err = (int32_t *)a.alloc(sizeof(int32_t) * 4);
+    GEMSLR_CUDA(cudaMemset(d.err, 0, sizeof(int32_t) * 4));
     d.lev.resize(h.lev.size());
     int64_t maxd = 1;
     for (size_t l = 0; l < h.lev.size(); ++l) {
         upload_level<VT, WT>(h.lev[l], h.n, true, a, d.lev[l], smem_limit);
+        d.lev[l].view.err = d.err;
         set_lowrank<VT, WT>(d.lev[l], h.lev[l], a);
         maxd = std::max(maxd, h.lev[l].e - h.lev[l].s);
     }
     upload_level<VT, WT>(h.last, h.n, false, a, d.last, smem_limit);
+    d.last.view.err = d.err;
     maxd = std::max(maxd, h.n - h.last.s);
     d.work = (VT *)a.alloc(sizeof(VT) * std::max<int64_t>(h.n, 1));
     d.scratch = (VT *)a.alloc(sizeof(VT) * maxd);
@@ -204,16 +316,35 @@ template <typename VT, typename WT>
 void apply_levels(DevHierarchy<VT, WT> &d, int from, const double *in, VT *work, double *out_final,
                   cudaStream_t st) {
     const int nl = (int)d.lev.size();
+    static const char *kDown[] = {"trsv_down_L0", "trsv_down_L1", "trsv_down_L2", "trsv_down_L3", "trsv_down_L4+"};
+    static const char *kUp[] = {"trsv_up_L0", "trsv_up_L1", "trsv_up_L2", "trsv_up_L3", "trsv_up_L4+"};
+    static const char *kCouple[] = {"couple_EWt_L0", "couple_EWt_L1", "couple_EWt_L2", "couple_EWt_L3", "couple_EWt_L4+"};
+    static const char *kLow[] = {"lowrank_Wu_L0", "lowrank_Wu_L1", "lowrank_Wu_L2", "lowrank_Wu_L3", "lowrank_Wu_L4+"};
     for (int l = from; l < nl; ++l) {
         DevLevel<VT, WT> &L = d.lev[l];
         const double *src = (l == from) ? in : nullptr;
-        launch_trsv<VT, WT>(L.view, 0, L.smem_rows, src, work, nullptr, d.scratch, st);
-        launch_couple<VT, WT>(L.view, src, work, d.partial, d.counter, d.u, st);
-        launch_lowrank<VT, WT>(L.view, work, d.u, st);
+        {
+            ProfScope ps(kDown[std::min(l, 4)], st);
+            launch_trsv<VT, WT>(L.view, 0, L.smem_rows, src, work, nullptr, d.scratch, st);
+        }
+        {
+            ProfScope ps(kCouple[std::min(l, 4)], st);
+            launch_couple<VT, WT>(L.view, src, work, d.partial, d.counter, d.u, st);
+        }
+        {
+            ProfScope ps(kLow[std::min(l, 4)], st);
+            launch_lowrank<VT, WT>(L.view, work, d.u, st);
+        }
     }
-    launch_trsv<VT, WT>(d.last.view, 0, d.last.smem_rows, from == nl ? in : nullptr, work, out_final, d.scratch, st);
-    for (int l = nl - 1; l >= from; --l)
+    {
+        ProfScope ps("trsv_last", st);
+        launch_trsv<VT, WT>(d.last.view, 0, d.last.smem_rows, from == nl ? in : nullptr, work, out_final,
+                            d.scratch, st);
+    }
+    for (int l = nl - 1; l >= from; --l) {
+        ProfScope ps(kUp[std::min(l, 4)], st);
         launch_trsv<VT, WT>(d.lev[l].view, 1, d.lev[l].smem_rows, nullptr, work, out_final, d.scratch, st);
+    }
 }
 
 template <>

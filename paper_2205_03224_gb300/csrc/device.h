@@ -13,6 +13,24 @@ namespace gemslr {
 void cuda_check(cudaError_t e, const char *what);
 #define GEMSLR_CUDA(x) ::gemslr::cuda_check((x), #x)
 
+// ---- instrumentation -------------------------------------------------------------
+// Every launch wrapper counts its launch; with profiling on, ProfScope
+// brackets a launch with CUDA events on its stream and the elapsed time is
+// accumulated per kernel name when the profile is read.
+void count_launch(int n = 1);
+struct ProfScope {
+    ProfScope(const char *name, cudaStream_t st);
+    ~ProfScope();
+    int slot;
+    cudaStream_t st;
+};
+
+void profile_enable(bool on);
+bool profile_enabled();
+void profile_reset();
+int profile_read(char *names, size_t len, double *ms, int64_t *counts, int maxn);
+uint64_t launches_total();
+
 // ---- launchers (kernels.cu) --------------------------------------------------
 template <typename VT, typename WT>
 void launch_trsv(const LevelView<VT, WT> &lv, int mode, int smem_rows, const double *in, VT *work,
@@ -28,22 +46,27 @@ void launch_scatter(int64_t n, const int32_t *perm, const double *src, double *d
 void launch_zero(int64_t n, double *x, cudaStream_t st);
 void launch_zero_f(int64_t n, float *x, cudaStream_t st);
 void launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *x,
-                 const double *b, double *y, int lanes, cudaStream_t st);
+                 const double *b, double *y, int lanes, cudaStream_t st, double *zcol = nullptr,
+                 const KrylovCtl *ctl = nullptr);
 void launch_gs_dots(int64_t len, const double *V, int64_t ldv, const double *w, double *partial, unsigned *counter,
                     KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, int grid, cudaStream_t st);
 void launch_gs_sub(int64_t len, double *V, int64_t ldv, double *w, double *partial, unsigned *counter,
                    KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *h2buf, int grid,
-                   cudaStream_t st);
+                   cudaStream_t st, double *vcopy = nullptr);
 void launch_gs_sub2(int64_t len, double *V, int64_t ldv, const double *w, const double *h2, KrylovCtl *ctl,
-                    cudaStream_t st);
+                    cudaStream_t st, double *vcopy = nullptr);
 void launch_gs_next(KrylovCtl *ctl, cudaStream_t st);
 void launch_norm2(int64_t len, const double *x, double *partial, unsigned *counter, double *out, int grid,
                   cudaStream_t st);
-void launch_scale_by_norm(int64_t len, const double *x, const double *n2, double *v, cudaStream_t st);
+void launch_scale_by_norm(int64_t len, const double *x, const double *n2, double *v, cudaStream_t st,
+                          double *vcopy = nullptr);
 void launch_cycle_start(KrylovCtl *ctl, double *g, const double *n2, cudaStream_t st);
 void launch_lsq(const KrylovCtl *ctl, const double *H, const double *g, double *y, cudaStream_t st);
 void launch_update_x(int64_t len, const double *Z, int64_t ldz, const KrylovCtl *ctl, const double *y, double *x,
                      cudaStream_t st);
+void launch_cycle_start_g(KrylovCtl *ctl, double *g, const double *n2, cudaGraphConditionalHandle h, cudaStream_t st);
+void launch_step_end_g(KrylovCtl *ctl, cudaGraphConditionalHandle h, cudaStream_t st);
+void launch_cycle_end_g(KrylovCtl *ctl, const double *n2r, cudaGraphConditionalHandle h, cudaStream_t st);
 void launch_basis_rotate(int64_t len, const double *V, int64_t ldv, int mm, const double *Q, int kk, double *out,
                          cudaStream_t st);
 
@@ -71,6 +94,7 @@ struct DevLevel {
     int smem_rows = 0;          // dynamic shared memory rows of the trsv kernel (0 = global)
     int nwf_L = 0, nwf_U = 0;   // wavefront counts (max over blocks)
     int64_t nnz_tri = 0;
+    int64_t nchunks = 0;
 };
 
 template <typename VT, typename WT>
@@ -82,6 +106,7 @@ struct DevHierarchy {
     VT *partial = nullptr;               // couple-kernel partial sums
     unsigned *counter = nullptr;
     VT *u = nullptr;                     // kMaxRank
+    int32_t *err = nullptr;              // device error word of the substitution kernels
 };
 
 // Build the device copy of a host hierarchy.

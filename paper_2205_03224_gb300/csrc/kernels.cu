@@ -39,46 +39,173 @@ template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v
 template <typename VT, typename WT> __device__ __forceinline__ VT wval(WT w) { return (VT)to_f(w); }
 template <> __device__ __forceinline__ double wval<double, double>(double w) { return w; }
 
-// ---- level-scheduled substitutions over one block --------------------------
-template <typename VT>
-__device__ __forceinline__ void sweep(const TriView<VT> &T, int b, VT *xs, const VT *dinv) {
-    const int w0 = T.blk_wf[b], w1 = T.blk_wf[b + 1];
-    for (int w = w0; w < w1; ++w) {
-        const int s0 = T.wf_slot[w];
-        const int cnt = T.wf_slot[w + 1] - s0;
-        const int64_t e0 = T.wf_ent[w];
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-            const int row = __ldg(T.slot_row + s0 + t);
-            const int len = __ldg(T.slot_len + s0 + t);
-            const int32_t *cp = T.ent_col + e0 + t;
-            const VT *vp = T.ent_val + e0 + t;
-            VT acc = xs[row];
-            for (int q = 0; q < len; ++q) {
-                const int64_t o = (int64_t)q * cnt;
-                acc -= __ldg(vp + o) * xs[__ldg(cp + o)];
-            }
-            if (dinv) acc *= dinv[row];
-            xs[row] = acc;
+// Column sums of per-CTA partials [nparts][ncols1] into out[0..ncols1) (shared
+// memory), by all warps of the finishing CTA: warp w owns columns w, w+nw, ...,
+// its lanes stride over the partials (callers use 256-thread CTAs: 8 warps), so every lane keeps up to kColsPerWarp
+// independent loads in flight; the summation order is fixed (deterministic).
+constexpr int kColsPerWarp = (kMaxCols + 1 + 7) / 8;
+template <typename T>
+__device__ void reduce_columns(const T *partial, int nparts, int ncols1, T *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T acc[kColsPerWarp];
+#pragma unroll
+    for (int u = 0; u < kColsPerWarp; ++u) acc[u] = 0;
+    for (int p = lane; p < nparts; p += 32) {
+        const T *row = partial + (int64_t)p * ncols1;
+#pragma unroll
+        for (int u = 0; u < kColsPerWarp; ++u) {
+            const int c = warp + nw * u;
+            if (c < ncols1) acc[u] += __ldcg(row + c);
         }
-        __syncthreads();
     }
+#pragma unroll
+    for (int u = 0; u < kColsPerWarp; ++u) {
+        const int c = warp + nw * u;
+        const T v = warp_sum(acc[u]);
+        if (lane == 0 && c < ncols1) out[c] = v;
+    }
+    __syncthreads();
 }
 
-// MODE 0: down sweep / last level: rhs from `in` (FP64 user vector, when
-//         non-null) or from `work`; result to work (and out_final).
-// MODE 1: up sweep: rhs = F y2 from work's tail; work[rows] -= result.
+// ---- mbarrier / bulk-copy primitives (sm_90+ PTX) ------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Polling wait (no suspension) for the consumers' critical path, bounded like wait_bounded.
+__device__ __forceinline__ bool poll_bounded(uint64_t *bar, unsigned parity, volatile int *abort_flag) {
+    if (mbar_test_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    unsigned spins = 0;
+    while (!mbar_test_wait(bar, parity)) {
+        if ((++spins & 63u) == 0u) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > 4000000000ll) return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void consumer_barrier() {
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kConsumerWarps) : "memory");
+}
+// One bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Every wait is bounded: about 2 s of clock cycles, or until another warp of
+// the CTA has raised `abort`.
+constexpr long long kSpinCycles = 4000000000ll;
+
+__device__ __forceinline__ bool wait_bounded(uint64_t *bar, unsigned parity, volatile int *abort_flag) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (abort_flag && *abort_flag) return false;
+        if (clock64() - t0 > kSpinCycles) return false;
+    }
+    return true;
+}
+
+// ---- level-scheduled substitutions over one block --------------------------
+// One CTA per diagonal block.  Warp kConsumerWarps is the producer: one lane
+// streams the block's chunks (see kernels.cuh) into a ring of kStages
+// shared-memory stages with bulk copies completing on mbarriers.  The
+// consumer warps keep the block's vector x in shared memory (or global memory
+// for blocks that do not fit) and, chunk by chunk, compute
+//   x_i = (x_i - sum_j T_ij x_j) * (U ? 1/u_ii : 1)
+// with the rows of a chunk spread over the consumer warps, lane per row.
+// MODE 0: right-hand side from `in` (FP64 user vector) or `work`; result in work.
+// MODE 1: right-hand side F y2 (gathered from work's tail); work[rows] -= result.
 template <typename VT, typename WT, int MODE, bool SMEM>
-__global__ void __launch_bounds__(kTrsvThreads)
+__global__ void __launch_bounds__(kTrsvThreads2)
 k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict__ work,
        double *__restrict__ out_final, VT *__restrict__ scratch) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *ring = smem;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStageBytes * kStages);
+    uint64_t *empty = full + kStages;
+    uint64_t *cbar = empty + kStages;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(cbar + 1);
+    VT *xs_smem = reinterpret_cast<VT *>(smem + kRingBytes);
+
     const int b = blockIdx.x;
     const int64_t r0 = lv.blk_row[b];
     const int nr = (int)(lv.blk_row[b + 1] - r0);
     if (nr == 0) return;
-    VT *mine = work + lv.s + r0;                       // this block's rows of the work vector
-    VT *xs = SMEM ? reinterpret_cast<VT *>(smem_raw) : (MODE == 1 ? scratch + r0 : mine);
-    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = lv.C.blk_chunk[b], c1 = lv.C.blk_chunk[b + 1];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        mbar_init(cbar, kConsumerWarps);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kConsumerWarps) {            // producer warp
+        if (lane == 0) {
+            int issued = 0;
+            for (int c = c0; c < c1; ++c) {
+                const int k = c - c0, st = k % kStages;
+                if (k >= kStages && !wait_bounded(&empty[st], ((k / kStages) - 1) & 1, abort_flag)) {
+                    *abort_flag = 1;
+                    atomicExch(lv.err, 1);
+                    break;
+                }
+                const unsigned bytes = (unsigned)(lv.C.off[c + 1] - lv.C.off[c]);
+                mbar_expect_tx(&full[st], bytes);
+                bulk_load(ring + (size_t)st * kStageBytes, lv.C.data + lv.C.off[c], bytes, &full[st]);
+                issued = k + 1;
+            }
+            // no copy may still be in flight when the CTA exits
+            for (int k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
+                wait_bounded(&full[k % kStages], (k / kStages) & 1, nullptr);
+        }
+        return;
+    }
+
+    // consumer warps: every chunk ends with the same named barrier, so a warp
+    // whose wait expired keeps the barrier count of the others (no deadlock)
+    const int ct = threadIdx.x;                        // 0 .. 32*kConsumerWarps-1
+    constexpr int NC = 32 * kConsumerWarps;
+    VT *mine = work + lv.s + r0;
+    VT *xs = SMEM ? xs_smem : (MODE == 1 ? scratch + r0 : mine);
+    for (int i = ct; i < nr; i += NC) {
         if (MODE == 1) {
             VT acc = 0;
             const int64_t g = r0 + i;
@@ -90,10 +217,54 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
             xs[i] = mine[i];
         }
     }
-    __syncthreads();
-    sweep<VT>(lv.L, b, xs, nullptr);
-    sweep<VT>(lv.U, b, xs, lv.dinv + r0);
-    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    consumer_barrier();
+    bool aborted = false;
+    const int r = lane >> 2, sub = lane & 3;
+    for (int c = c0; c < c1; ++c) {
+        const int k = c - c0, st = k % kStages;
+        if (!aborted && !poll_bounded(&full[st], (k / kStages) & 1, abort_flag)) {
+            aborted = true;
+            *abort_flag = 1;
+        }
+        if (!aborted) {
+            const unsigned char *base = ring + (size_t)st * kStageBytes;
+            const int *hdr = reinterpret_cast<const int *>(base);
+            const int nrow = hdr[0], kq = hdr[1], upper = hdr[2];
+            const int pr = (nrow + 3) & ~3;
+            const int *rows = hdr + 4;
+            const int *lens = rows + pr;
+            const int *cols = lens + pr;
+            const VT *vals = reinterpret_cast<const VT *>(cols + (size_t)kq * nrow * 4);
+            const int per = (nrow + kConsumerWarps - 1) / kConsumerWarps;   // rows of this warp (<= 8)
+            const int t = warp * per + r;
+            const bool active = r < per && t < nrow;
+            const int len = active ? lens[t] : 0;
+            VT acc = 0;
+            for (int kk = 0; kk < kq; ++kk) {
+                const int q = 4 * kk + sub;
+                if (q < len) {
+                    const int e = (kk * nrow + t) * 4 + sub;
+                    acc += vals[e] * xs[cols[e]];
+                }
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (active && sub == 0) {
+                const int row = rows[t];
+                VT y = xs[row] - acc;
+                if (upper) y *= vals[(size_t)kq * nrow * 4 + t];     // dinv follows vals
+                xs[row] = y;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+        }
+        consumer_barrier();
+    }
+    if (*abort_flag) {
+        if (ct == 0) atomicExch(lv.err, 1);
+        return;
+    }
+    for (int i = ct; i < nr; i += NC) {
         VT y = xs[i];
         if (MODE == 1) y = mine[i] - y;
         if (SMEM || MODE == 1) mine[i] = y;
@@ -135,12 +306,7 @@ k_couple(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restri
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-        VT acc = 0;
-        for (unsigned bb = 0; bb < gridDim.x; ++bb) acc += __ldcg(partial + (int64_t)bb * k + c);
-        ts[c] = acc;
-    }
-    __syncthreads();
+    reduce_columns<VT>(partial, (int)gridDim.x, k, ts);
     for (int c = threadIdx.x; c < k; c += blockDim.x) {
         VT acc = 0;
         for (int d = 0; d < k; ++d) acc += lv.H[c + (int64_t)d * k] * ts[d];
@@ -183,11 +349,13 @@ __global__ void k_set(int64_t n, VT *__restrict__ x, VT v) {
 }
 
 // y = A x (sub == 0) or y = b - A x (sub == 1); `lanes` threads per row.
+// With zcol non-null, x is also copied into column ctl->j of zcol (leading
+// dimension n): the FGMRES step stores z_j while it forms A z_j.
 template <int LANES>
 __global__ void __launch_bounds__(256)
 k_spmv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
        const double *__restrict__ v, const double *__restrict__ x, const double *__restrict__ b,
-       double *__restrict__ y) {
+       double *__restrict__ y, double *__restrict__ zcol, const KrylovCtl *__restrict__ ctl) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t row = tid / LANES;
     const int sub = threadIdx.x % LANES;
@@ -196,7 +364,10 @@ k_spmv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci
         for (int64_t p = rp[row] + sub; p < rp[row + 1]; p += LANES) acc += __ldg(v + p) * __ldg(x + __ldg(ci + p));
 #pragma unroll
     for (int o = LANES / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, LANES);
-    if (row < n && sub == 0) y[row] = b ? b[row] - acc : acc;
+    if (row < n && sub == 0) {
+        y[row] = b ? b[row] - acc : acc;
+        if (zcol) zcol[(int64_t)ctl->j * n + row] = x[row];
+    }
 }
 
 // ---- Gram-Schmidt passes -------------------------------------------------------
@@ -213,34 +384,59 @@ __device__ __forceinline__ bool finish_block(unsigned *counter) {
     return last;
 }
 
-// Column sums of the per-CTA partials [grid][ncols+1] into out[0..ncols] (fixed order).
-__device__ void reduce_partials(const double *partial, int ncols1, double *out) {
-    for (int c = threadIdx.x; c < ncols1; c += blockDim.x) {
-        double acc = 0.0;
-        for (unsigned bb = 0; bb < gridDim.x; ++bb) acc += __ldcg(partial + (int64_t)bb * ncols1 + c);
-        out[c] = acc;
+__device__ __forceinline__ void reduce_partials(const double *partial, int ncols1, double *out) {
+    reduce_columns<double>(partial, (int)gridDim.x, ncols1, out);
+}
+
+// Block partial sums of V[:, c] . w for c < ncols and of w . w (slot ncols),
+// written to partial[blockIdx.x * (ncols + 1) + c].  Columns are taken eight
+// at a time with register accumulators so that every thread keeps many
+// independent loads in flight; one block-wide reduction at the end.
+__device__ void block_dots(const double *__restrict__ V, int64_t ldv, int ncols, const double *__restrict__ w,
+                           int64_t i0, int64_t i1, double *partial) {
+    __shared__ double red[kReduceThreads / 32][kMaxCols + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c0 = 0; c0 <= ncols; c0 += 8) {
+        double acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = 0.0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const double wi = w[i];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = c0 + u;
+                if (c < ncols) acc[u] += V[(int64_t)c * ldv + i] * wi;
+                else if (c == ncols) acc[u] += wi * wi;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const double x = warp_sum(acc[u]);
+            if (lane == 0 && c0 + u <= ncols) red[warp][c0 + u] = x;
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c <= ncols; c += blockDim.x) {
+        double sum = 0.0;
+        for (int q = 0; q < nw; ++q) sum += red[q][c];
+        partial[(int64_t)blockIdx.x * (ncols + 1) + c] = sum;
     }
     __syncthreads();
 }
 
-// Block partial sums of V[:, c] . w for c < ncols and of w . w (slot ncols).
-__device__ void block_dots(int64_t len, const double *__restrict__ V, int64_t ldv, int ncols,
-                           const double *__restrict__ w, int64_t i0, int64_t i1, double *partial) {
-    __shared__ double red[kReduceThreads / 32];
-    for (int c = 0; c <= ncols; ++c) {
-        const double *vc = c < ncols ? V + (int64_t)c * ldv : w;
-        double acc = 0.0;
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc += vc[i] * w[i];
-        acc = warp_sum(acc);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q];
-            partial[(int64_t)blockIdx.x * (ncols + 1) + c] = s;
-        }
-        __syncthreads();
+// x_i - sum_c V[i, c] h_c with four independent partial sums.
+__device__ __forceinline__ double project_out(const double *__restrict__ V, int64_t ldv, int ncols,
+                                              const double *hs, int64_t i, double x) {
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int c = 0;
+    for (; c + 3 < ncols; c += 4) {
+        x -= V[(int64_t)c * ldv + i] * hs[c];
+        a1 -= V[(int64_t)(c + 1) * ldv + i] * hs[c + 1];
+        a2 -= V[(int64_t)(c + 2) * ldv + i] * hs[c + 2];
+        a3 -= V[(int64_t)(c + 3) * ldv + i] * hs[c + 3];
     }
+    for (; c < ncols; ++c) x -= V[(int64_t)c * ldv + i] * hs[c];
+    return x + (a1 + a2 + a3);
 }
 
 // Givens update of column j of the (m+1) x m Hessenberg matrix H (FGMRES).
@@ -305,7 +501,7 @@ k_gs_dots(int64_t len, const double *__restrict__ V, int64_t ldv, const double *
     const int ncols = ctl->j + 1;
     const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
     const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
-    block_dots(len, V, ldv, ncols, w, i0, i1, partial);
+    block_dots(V, ldv, ncols, w, i0, i1, partial);
     if (!finish_block(counter)) return;
     __shared__ double red[kMaxCols + 1];
     reduce_partials(partial, ncols + 1, red);
@@ -320,7 +516,8 @@ k_gs_dots(int64_t len, const double *__restrict__ V, int64_t ldv, const double *
 // second-pass coefficients h2 are reduced into h2buf and added to H.
 __global__ void __launch_bounds__(kReduceThreads)
 k_gs_sub(int64_t len, double *__restrict__ V, int64_t ldv, double *__restrict__ w, double *partial,
-         unsigned *counter, KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *h2buf) {
+         unsigned *counter, KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *h2buf,
+         double *__restrict__ vcopy) {
     const int again = ctl->reorth;
     if (!again && (ctl->stop || ctl->breakdown)) return;
     __shared__ double hs[kMaxCols];
@@ -332,14 +529,17 @@ k_gs_sub(int64_t len, double *__restrict__ V, int64_t ldv, double *__restrict__ 
     const double inv = again ? 0.0 : 1.0 / ctl->beta;
     double *vn = V + (int64_t)(j + 1) * ldv;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        double x = w[i];
-        for (int c = 0; c < ncols; ++c) x -= V[(int64_t)c * ldv + i] * hs[c];
-        if (again) w[i] = x;
-        else vn[i] = x * inv;
+        const double x = project_out(V, ldv, ncols, hs, i, w[i]);
+        if (again) {
+            w[i] = x;
+        } else {
+            vn[i] = x * inv;
+            if (vcopy) vcopy[i] = x * inv;
+        }
     }
     if (!again) return;
     __syncthreads();
-    block_dots(len, V, ldv, ncols, w, i0, i1, partial);
+    block_dots(V, ldv, ncols, w, i0, i1, partial);
     if (!finish_block(counter)) return;
     __shared__ double red[kMaxCols + 1];
     reduce_partials(partial, ncols + 1, red);
@@ -363,7 +563,7 @@ k_gs_sub(int64_t len, double *__restrict__ V, int64_t ldv, double *__restrict__ 
 // Pass 3 (only after a second Gram-Schmidt pass): V[:, j+1] = (w - V h2) / beta.
 __global__ void __launch_bounds__(kReduceThreads)
 k_gs_sub2(int64_t len, double *__restrict__ V, int64_t ldv, const double *__restrict__ w,
-          const double *__restrict__ h2, KrylovCtl *ctl) {
+          const double *__restrict__ h2, KrylovCtl *ctl, double *__restrict__ vcopy) {
     if (!ctl->reorth || ctl->stop || ctl->breakdown) return;
     __shared__ double hs[kMaxCols];
     const int j = ctl->j, ncols = j + 1;
@@ -372,9 +572,9 @@ k_gs_sub2(int64_t len, double *__restrict__ V, int64_t ldv, const double *__rest
     const double inv = 1.0 / ctl->beta;
     double *vn = V + (int64_t)(j + 1) * ldv;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
-        double x = w[i];
-        for (int c = 0; c < ncols; ++c) x -= V[(int64_t)c * ldv + i] * hs[c];
-        vn[i] = x * inv;
+        const double x = project_out(V, ldv, ncols, hs, i, w[i]) * inv;
+        vn[i] = x;
+        if (vcopy) vcopy[i] = x;
     }
 }
 
@@ -388,7 +588,7 @@ __global__ void __launch_bounds__(kReduceThreads)
 k_norm2(int64_t len, const double *__restrict__ x, double *partial, unsigned *counter, double *out) {
     const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
     const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
-    block_dots(len, x, 0, 0, x, i0, i1, partial);
+    block_dots(x, 0, 0, x, i0, i1, partial);
     if (!finish_block(counter)) return;
     __shared__ double red[1];
     reduce_partials(partial, 1, red);
@@ -396,10 +596,13 @@ k_norm2(int64_t len, const double *__restrict__ x, double *partial, unsigned *co
 }
 
 // v = x * (1 / sqrt(*n2))
-__global__ void k_scale_by_norm(int64_t len, const double *__restrict__ x, const double *n2, double *__restrict__ v) {
+__global__ void k_scale_by_norm(int64_t len, const double *__restrict__ x, const double *n2, double *__restrict__ v,
+                                double *__restrict__ vcopy) {
     const double inv = 1.0 / sqrt(*n2);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
         v[i] = x[i] * inv;
+        if (vcopy) vcopy[i] = x[i] * inv;
+    }
 }
 
 // Start of an FGMRES cycle: g = (beta, 0, ...), j = 0 (one thread).
@@ -451,6 +654,48 @@ __global__ void k_basis_rotate(int64_t len, const double *__restrict__ V, int64_
     }
 }
 
+// ---- graph-resident FGMRES control (conditional WHILE nodes) ----------------------
+// Cycle start inside the outer loop body: g = (||r||, 0, ...), j = 0, and the
+// inner loop's condition set so that the first Arnoldi step runs.
+__global__ void k_cycle_start_g(KrylovCtl *ctl, double *g, const double *n2, cudaGraphConditionalHandle inner) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = 0; i <= ctl->m; ++i) g[i] = 0.0;
+    g[0] = sqrt(*n2);
+    ctl->j = 0;
+    ctl->stop = 0;
+    ctl->breakdown = 0;
+    ctl->reorth = 0;
+    ctl->jdone = 0;
+    cudaGraphSetConditional(inner, 1u);
+}
+
+// End of one Arnoldi step: advance j, continue while the cycle is active.
+__global__ void k_step_end_g(KrylovCtl *ctl, cudaGraphConditionalHandle inner) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (!ctl->stop) ctl->j += 1;
+    cudaGraphSetConditional(inner, ctl->stop ? 0u : 1u);
+}
+
+// End of a cycle: true residual test (Sec. 5 set-up), restart or finish.
+__global__ void k_cycle_end_g(KrylovCtl *ctl, const double *n2r, cudaGraphConditionalHandle outer) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double rn = sqrt(*n2r);
+    ctl->rnorm = rn;
+    bool again = true;
+    if (!isfinite(rn) || ctl->nonfinite) {
+        ctl->nonfinite = 1;
+        again = false;
+    } else if (rn <= ctl->tol_abs) {
+        ctl->converged = 1;
+        again = false;
+    } else if (ctl->iters >= ctl->maxit) {
+        again = false;
+    } else {
+        ctl->restarts += 1;
+    }
+    cudaGraphSetConditional(outer, again ? 1u : 0u);
+}
+
 // ---- host launchers -----------------------------------------------------------------
 static int grid_for(int64_t n, int threads, int cap) {
     int64_t g = (n + threads - 1) / threads;
@@ -463,13 +708,13 @@ void launch_trsv(const LevelView<VT, WT> &lv, int mode, int smem_rows, const dou
                  double *out_final, VT *scratch, cudaStream_t st) {
     if (lv.nblk == 0) return;
     const bool smem = smem_rows > 0;
-    const size_t bytes = smem ? (size_t)smem_rows * sizeof(VT) : 0;
+    const size_t bytes = kRingBytes + (smem ? (size_t)smem_rows * sizeof(VT) : 0);
     if (mode == 0) {
-        if (smem) k_trsv<VT, WT, 0, true><<<lv.nblk, kTrsvThreads, bytes, st>>>(lv, in, work, out_final, scratch);
-        else k_trsv<VT, WT, 0, false><<<lv.nblk, kTrsvThreads, 0, st>>>(lv, in, work, out_final, scratch);
+        if (smem) { k_trsv<VT, WT, 0, true><<<lv.nblk, kTrsvThreads2, bytes, st>>>(lv, in, work, out_final, scratch); count_launch(); }
+        else { k_trsv<VT, WT, 0, false><<<lv.nblk, kTrsvThreads2, bytes, st>>>(lv, in, work, out_final, scratch); count_launch(); }
     } else {
-        if (smem) k_trsv<VT, WT, 1, true><<<lv.nblk, kTrsvThreads, bytes, st>>>(lv, in, work, out_final, scratch);
-        else k_trsv<VT, WT, 1, false><<<lv.nblk, kTrsvThreads, 0, st>>>(lv, in, work, out_final, scratch);
+        if (smem) { k_trsv<VT, WT, 1, true><<<lv.nblk, kTrsvThreads2, bytes, st>>>(lv, in, work, out_final, scratch); count_launch(); }
+        else { k_trsv<VT, WT, 1, false><<<lv.nblk, kTrsvThreads2, bytes, st>>>(lv, in, work, out_final, scratch); count_launch(); }
     }
 }
 
@@ -477,6 +722,8 @@ template <typename VT, typename WT>
 void set_trsv_smem_limit(int bytes) {
     cudaFuncSetAttribute(k_trsv<VT, WT, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     cudaFuncSetAttribute(k_trsv<VT, WT, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_trsv<VT, WT, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
+    cudaFuncSetAttribute(k_trsv<VT, WT, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
 }
 
 template <typename VT, typename WT>
@@ -484,13 +731,13 @@ void launch_couple(const LevelView<VT, WT> &lv, const double *in, VT *work, VT *
                    VT *u, cudaStream_t st) {
     if (lv.stail == 0) return;
     const int grid = (int)((lv.stail + kCoupleRows - 1) / kCoupleRows);
-    k_couple<VT, WT><<<grid, kCoupleRows, 0, st>>>(lv, in, work, partial, counter, u);
+    k_couple<VT, WT><<<grid, kCoupleRows, 0, st>>>(lv, in, work, partial, counter, u); count_launch();
 }
 
 template <typename VT, typename WT>
 void launch_lowrank(const LevelView<VT, WT> &lv, VT *work, const VT *u, cudaStream_t st) {
     if (lv.k == 0 || lv.stail == 0) return;
-    k_lowrank<VT, WT><<<grid_for(lv.stail, 256, 1216), 256, 0, st>>>(lv, work, u);
+    k_lowrank<VT, WT><<<grid_for(lv.stail, 256, 1216), 256, 0, st>>>(lv, work, u); count_launch();
 }
 
 template void launch_trsv<double, double>(const LevelView<double, double> &, int, int, const double *, double *,
@@ -508,63 +755,81 @@ template void launch_lowrank<float, __nv_bfloat16>(const LevelView<float, __nv_b
                                                    cudaStream_t);
 
 void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t st) {
-    if (n > 0) k_gather<<<grid_for(n, 256, 4864), 256, 0, st>>>(n, perm, src, dst);
+    if (n > 0) { k_gather<<<grid_for(n, 256, 4864), 256, 0, st>>>(n, perm, src, dst); count_launch(); }
 }
 void launch_scatter(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t st) {
-    if (n > 0) k_scatter<<<grid_for(n, 256, 4864), 256, 0, st>>>(n, perm, src, dst);
+    if (n > 0) { k_scatter<<<grid_for(n, 256, 4864), 256, 0, st>>>(n, perm, src, dst); count_launch(); }
 }
 void launch_zero(int64_t n, double *x, cudaStream_t st) {
-    if (n > 0) k_set<double><<<grid_for(n, 256, 4864), 256, 0, st>>>(n, x, 0.0);
+    if (n > 0) { k_set<double><<<grid_for(n, 256, 4864), 256, 0, st>>>(n, x, 0.0); count_launch(); }
 }
 void launch_zero_f(int64_t n, float *x, cudaStream_t st) {
-    if (n > 0) k_set<float><<<grid_for(n, 256, 4864), 256, 0, st>>>(n, x, 0.0f);
+    if (n > 0) { k_set<float><<<grid_for(n, 256, 4864), 256, 0, st>>>(n, x, 0.0f); count_launch(); }
 }
 void launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *x,
-                 const double *b, double *y, int lanes, cudaStream_t st) {
+                 const double *b, double *y, int lanes, cudaStream_t st, double *zcol, const KrylovCtl *ctl) {
     if (n == 0) return;
     const int64_t threads = n * lanes;
     const int grid = (int)((threads + 255) / 256);
     switch (lanes) {
-        case 2: k_spmv<2><<<grid, 256, 0, st>>>(n, rp, ci, v, x, b, y); break;
-        case 4: k_spmv<4><<<grid, 256, 0, st>>>(n, rp, ci, v, x, b, y); break;
-        case 16: k_spmv<16><<<grid, 256, 0, st>>>(n, rp, ci, v, x, b, y); break;
-        default: k_spmv<8><<<grid, 256, 0, st>>>(n, rp, ci, v, x, b, y); break;
+        case 2: k_spmv<2><<<grid, 256, 0, st>>>(n, rp, ci, v, x, b, y, zcol, ctl); break;
+        case 4: k_spmv<4><<<grid, 256, 0, st>>>(n, rp, ci, v, x, b, y, zcol, ctl); break;
+        case 16: k_spmv<16><<<grid, 256, 0, st>>>(n, rp, ci, v, x, b, y, zcol, ctl); break;
+        default: k_spmv<8><<<grid, 256, 0, st>>>(n, rp, ci, v, x, b, y, zcol, ctl); break;
     }
+    count_launch();
 }
 void launch_gs_dots(int64_t len, const double *V, int64_t ldv, const double *w, double *partial, unsigned *counter,
                     KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, int grid, cudaStream_t st) {
-    k_gs_dots<<<grid, kReduceThreads, 0, st>>>(len, V, ldv, w, partial, counter, ctl, H, cs, sn, g);
+    k_gs_dots<<<grid, kReduceThreads, 0, st>>>(len, V, ldv, w, partial, counter, ctl, H, cs, sn, g); count_launch();
 }
 void launch_gs_sub(int64_t len, double *V, int64_t ldv, double *w, double *partial, unsigned *counter,
                    KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *h2buf, int grid,
-                   cudaStream_t st) {
-    k_gs_sub<<<grid, kReduceThreads, 0, st>>>(len, V, ldv, w, partial, counter, ctl, H, cs, sn, g, h2buf);
+                   cudaStream_t st, double *vcopy) {
+    k_gs_sub<<<grid, kReduceThreads, 0, st>>>(len, V, ldv, w, partial, counter, ctl, H, cs, sn, g, h2buf, vcopy);
+    count_launch();
 }
 void launch_gs_sub2(int64_t len, double *V, int64_t ldv, const double *w, const double *h2, KrylovCtl *ctl,
-                    cudaStream_t st) {
-    k_gs_sub2<<<grid_for(len, 256, 1216), 256, 0, st>>>(len, V, ldv, w, h2, ctl);
+                    cudaStream_t st, double *vcopy) {
+    k_gs_sub2<<<grid_for(len, 256, 1216), 256, 0, st>>>(len, V, ldv, w, h2, ctl, vcopy);
+    count_launch();
 }
-void launch_gs_next(KrylovCtl *ctl, cudaStream_t st) { k_gs_next<<<1, 32, 0, st>>>(ctl); }
+void launch_gs_next(KrylovCtl *ctl, cudaStream_t st) { k_gs_next<<<1, 32, 0, st>>>(ctl); count_launch(); }
 void launch_norm2(int64_t len, const double *x, double *partial, unsigned *counter, double *out, int grid,
                   cudaStream_t st) {
-    k_norm2<<<grid, kReduceThreads, 0, st>>>(len, x, partial, counter, out);
+    k_norm2<<<grid, kReduceThreads, 0, st>>>(len, x, partial, counter, out); count_launch();
 }
-void launch_scale_by_norm(int64_t len, const double *x, const double *n2, double *v, cudaStream_t st) {
-    if (len > 0) k_scale_by_norm<<<grid_for(len, 256, 4864), 256, 0, st>>>(len, x, n2, v);
+void launch_scale_by_norm(int64_t len, const double *x, const double *n2, double *v, cudaStream_t st, double *vcopy) {
+    if (len > 0) { k_scale_by_norm<<<grid_for(len, 256, 4864), 256, 0, st>>>(len, x, n2, v, vcopy); count_launch(); }
 }
 void launch_cycle_start(KrylovCtl *ctl, double *g, const double *n2, cudaStream_t st) {
-    k_cycle_start<<<1, 32, 0, st>>>(ctl, g, n2);
+    k_cycle_start<<<1, 32, 0, st>>>(ctl, g, n2); count_launch();
 }
 void launch_lsq(const KrylovCtl *ctl, const double *H, const double *g, double *y, cudaStream_t st) {
-    k_lsq<<<1, 32, 0, st>>>(ctl, H, g, y);
+    k_lsq<<<1, 32, 0, st>>>(ctl, H, g, y); count_launch();
 }
 void launch_update_x(int64_t len, const double *Z, int64_t ldz, const KrylovCtl *ctl, const double *y, double *x,
                      cudaStream_t st) {
-    if (len > 0) k_update_x<<<grid_for(len, 256, 4864), 256, 0, st>>>(len, Z, ldz, ctl, y, x);
+    if (len > 0) { k_update_x<<<grid_for(len, 256, 4864), 256, 0, st>>>(len, Z, ldz, ctl, y, x); count_launch(); }
 }
 void launch_basis_rotate(int64_t len, const double *V, int64_t ldv, int mm, const double *Q, int kk, double *out,
                          cudaStream_t st) {
-    if (len > 0) k_basis_rotate<<<grid_for(len, 256, 4864), 256, 0, st>>>(len, V, ldv, mm, Q, kk, out);
+    if (len > 0) { k_basis_rotate<<<grid_for(len, 256, 4864), 256, 0, st>>>(len, V, ldv, mm, Q, kk, out); count_launch(); }
 }
 
+}  // namespace gemslr
+
+namespace gemslr {
+void launch_cycle_start_g(KrylovCtl *ctl, double *g, const double *n2, cudaGraphConditionalHandle h, cudaStream_t st) {
+    k_cycle_start_g<<<1, 32, 0, st>>>(ctl, g, n2, h);
+    count_launch();
+}
+void launch_step_end_g(KrylovCtl *ctl, cudaGraphConditionalHandle h, cudaStream_t st) {
+    k_step_end_g<<<1, 32, 0, st>>>(ctl, h);
+    count_launch();
+}
+void launch_cycle_end_g(KrylovCtl *ctl, const double *n2r, cudaGraphConditionalHandle h, cudaStream_t st) {
+    k_cycle_end_g<<<1, 32, 0, st>>>(ctl, n2r, h);
+    count_launch();
+}
 }  // namespace gemslr

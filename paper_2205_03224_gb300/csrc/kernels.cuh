@@ -11,21 +11,32 @@ constexpr int kTrsvThreads = 512;
 constexpr int kCoupleRows = 256;    // tail rows per CTA in the E / W^T kernel
 constexpr int kMaxRank = 160;       // k_eff upper bound in the correction kernels
 constexpr int kReduceThreads = 256;
-constexpr int kMaxCols = 128;     // Krylov columns per Gram-Schmidt pass (m + 1 <= kMaxCols)
+constexpr int kMaxCols = 160;     // Krylov columns per Gram-Schmidt pass (m + 1 <= kMaxCols)
 
-// One triangular factor of one level in the wavefront-sliced layout: the rows
-// of a wavefront ("slots") are independent; entry q of slot t of wavefront w
-// sits at ent_base[w] + q * (slots in w) + t, so one thread per row reads
-// consecutive addresses across a warp.  Columns are block-local.
-template <typename VT>
-struct TriView {
-    const int32_t *blk_wf;     // nblk + 1 : wavefront range of every block
-    const int32_t *wf_slot;    // nwf + 1  : slot range of every wavefront
-    const int64_t *wf_ent;     // nwf      : first entry of every wavefront
-    const int32_t *slot_row;   // block-local row of every slot
-    const int32_t *slot_len;   // entries of every slot
-    const int32_t *ent_col;    // block-local column
-    const VT *ent_val;
+// Triangular factors of one level as a sequence of "chunks" per block: the L
+// chunks of a block in wavefront (level-set) order, then its U chunks.  A
+// chunk holds <= kChunkRows independent rows of one wavefront and is one
+// contiguous, 16-byte aligned byte range (<= kStageBytes) that a single bulk
+// copy moves into shared memory:
+//   int32 {nrows, kq, upper, 0}   kq = ceil(max entries / 4)
+//   int32 rows[pad4(nrows)]       block-local row of every slot
+//   int32 lens[pad4(nrows)]       entries of every slot
+//   int32 cols[kq*nrows*4]        entry q of slot t at ((q/4)*nrows + t)*4 + q%4
+//   VT    vals[kq*nrows*4]        same positions (padded to 16 bytes)
+//   VT    dinv[nrows]             1/u_ii, U chunks only (padded to 16 bytes)
+// Four lanes share a row (entries q = sub, sub+4, ...), so a warp reads
+// consecutive addresses and every FP64 instruction has most lanes active.
+constexpr int kStageBytes = 4096;
+constexpr int kStages = 16;
+constexpr int kConsumerWarps = 4;
+constexpr int kChunkRows = 8 * kConsumerWarps;
+constexpr int kTrsvThreads2 = 32 * (kConsumerWarps + 1);
+constexpr int kRingBytes = kStageBytes * kStages + 2 * kStages * 8 + 64;   // ring + mbarriers + flags
+
+struct ChunkView {
+    const unsigned char *data;
+    const int64_t *off;        // nchunk + 1 byte offsets into data
+    const int32_t *blk_chunk;  // nblk + 1 chunk range of every block
 };
 
 // Everything one Schur level (or the last level) needs on the device.
@@ -35,8 +46,8 @@ struct LevelView {
     int64_t stail;             // n - e
     int32_t nblk;
     const int64_t *blk_row;    // nblk + 1, level-local
-    TriView<VT> L, U;          // U without its diagonal
-    const VT *dinv;            // 1 / u_ii, level-local
+    ChunkView C;               // L and U of every block (see above)
+    int32_t *err;              // device error word (1: a bounded wait expired)
     const int64_t *F_rp;       // d rows
     const int32_t *F_ci;       // global column (>= e)
     const VT *F_v;
@@ -67,6 +78,9 @@ struct KrylovCtl {
     double resid;         // |g_{j+1}|
     double tol_abs;       // rtol * ||b||
     double rnorm2;        // ||r||^2 (restart)
+    int32_t restarts;     // completed cycles that did not converge
+    int32_t converged;    // true residual met tol_abs
+    double rnorm;         // ||b - A x|| after the last cycle
 };
 
 }  // namespace gemslr

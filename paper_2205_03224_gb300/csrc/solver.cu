@@ -1,6 +1,7 @@
 // GeMSLR handle, low-rank setup (Alg. 1 / Sec. 2.3), FGMRES (Sec. 4.1) and the C ABI.
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <memory>
@@ -33,10 +34,23 @@ struct gemslr_ctx {
     KrylovCtl *ctl_host = nullptr;      // pinned
     double *n2_host = nullptr;          // pinned
     int red_grid = 0;
+    double *vin = nullptr, *zout = nullptr;   // fixed in/out of M^{-1} inside the FGMRES step
+    int32_t *err_host = nullptr;              // pinned copy of the substitution error word
     double setup_ms = 0.0;
+    // CUDA graph of a whole FGMRES solve (conditional WHILE nodes for the cycle and step loops)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_m = 0;
+    bool graph_failed = false;
+    uint64_t graph_k_top = 0, graph_k_cycle = 0, graph_k_step = 0;
     ~gemslr_ctx() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         if (ctl_host) cudaFreeHost(ctl_host);
         if (n2_host) cudaFreeHost(n2_host);
+        if (err_host) cudaFreeHost(err_host);
     }
 };
 
@@ -67,15 +81,18 @@ void ensure_krylov(gemslr_ctx *h, int m) {
         h->bh = (double *)h->arena.alloc(8 * n);
         h->r = (double *)h->arena.alloc(8 * n);
         h->w = (double *)h->arena.alloc(8 * n);
-        h->red_grid = 4 * sm_count();
+        h->red_grid = sm_count();                 // one CTA per SM: few partials for the finisher
         h->partial = (double *)h->arena.alloc(8 * (size_t)h->red_grid * (kMaxCols + 1));
         h->counter = (unsigned *)h->arena.alloc(16);
         GEMSLR_CUDA(cudaMemset(h->counter, 0, 16));
         h->n2 = (double *)h->arena.alloc(8 * 4);
         h->ctl = (KrylovCtl *)h->arena.alloc(sizeof(KrylovCtl));
         h->h2 = (double *)h->arena.alloc(8 * kMaxCols);
+        h->vin = (double *)h->arena.alloc(8 * n);
+        h->zout = (double *)h->arena.alloc(8 * n);
         GEMSLR_CUDA(cudaMallocHost(&h->ctl_host, sizeof(KrylovCtl)));
         GEMSLR_CUDA(cudaMallocHost(&h->n2_host, 8 * 4));
+        GEMSLR_CUDA(cudaMallocHost(&h->err_host, 16));
     }
     if (m > h->m_alloc) {
         if (m + 1 > kMaxCols) fail(GEMSLR_ERR_ARG, "restart length too large");
@@ -263,7 +280,7 @@ void finish_setup(gemslr_ctx *h, bool compute_lowrank) {
     h->perm = h->arena.upload(h->host.perm);
     h->zeros = (double *)h->arena.alloc(8 * std::max<int64_t>(n, 1));
     GEMSLR_CUDA(cudaMemset(h->zeros, 0, 8 * std::max<int64_t>(n, 1)));
-    const int limit = std::min(smem_optin(), 200 * 1024);
+    const int limit = smem_optin();
     upload_hierarchy<double, double>(h->host, h->arena, h->d64, limit);
     ensure_krylov(h, 8);
     if (compute_lowrank) {
@@ -277,6 +294,149 @@ void finish_setup(gemslr_ctx *h, bool compute_lowrank) {
         h->mixed = true;
     }
     GEMSLR_CUDA(cudaDeviceSynchronize());
+}
+
+// ---- FGMRES (Sec. 4.1) ---------------------------------------------------------------
+// One Arnoldi step on fixed buffers: z = M^{-1} vin, w = A z with z stored as
+// Z[:, j], Gram-Schmidt against V[:, :j+1], Givens update, and the next basis
+// vector written to V[:, j+1] and to vin.
+void fgmres_step(gemslr_ctx *h, cudaStream_t st) {
+    const int64_t n = h->host.n;
+    apply_perm(h, h->vin, h->zout, st);
+    {
+        ProfScope ps("spmv_A", st);
+        launch_spmv(n, h->A_rp, h->A_ci, h->A_v, h->zout, nullptr, h->w, h->spmv_lanes, st, h->Z, h->ctl);
+    }
+    {
+        ProfScope ps("gs_dots", st);
+        launch_gs_dots(n, h->V, n, h->w, h->partial, h->counter, h->ctl, h->Hs, h->cs, h->sn, h->g, h->red_grid, st);
+    }
+    {
+        ProfScope ps("gs_sub", st);
+        launch_gs_sub(n, h->V, n, h->w, h->partial, h->counter, h->ctl, h->Hs, h->cs, h->sn, h->g, h->h2,
+                      h->red_grid, st, h->vin);
+    }
+    {
+        ProfScope ps("gs_sub2", st);
+        launch_gs_sub2(n, h->V, n, h->w, h->h2, h->ctl, st, h->vin);
+    }
+}
+
+// End of a cycle: x += Z y, r = b - A x, ||r||^2 into n2[1].
+void fgmres_cycle_end(gemslr_ctx *h, cudaStream_t st) {
+    const int64_t n = h->host.n;
+    launch_lsq(h->ctl, h->Hs, h->g, h->y, st);
+    launch_update_x(n, h->Z, n, h->ctl, h->y, h->xh, st);
+    launch_spmv(n, h->A_rp, h->A_ci, h->A_v, h->xh, h->bh, h->r, h->spmv_lanes, st);
+    launch_norm2(n, h->r, h->partial, h->counter, h->n2 + 1, h->red_grid, st);
+}
+
+// Host-driven loop (used while profiling): the host reads the control block
+// after every step and every cycle.
+void fgmres_host_loop(gemslr_ctx *h, int m, cudaStream_t st) {
+    const int64_t n = h->host.n;
+    launch_zero(n, h->xh, st);
+    GEMSLR_CUDA(cudaMemcpyAsync(h->r, h->bh, 8 * n, cudaMemcpyDeviceToDevice, st));
+    GEMSLR_CUDA(cudaMemcpyAsync(h->n2 + 1, h->n2, 8, cudaMemcpyDeviceToDevice, st));
+    while (true) {
+        launch_cycle_start(h->ctl, h->g, h->n2 + 1, st);
+        launch_scale_by_norm(n, h->r, h->n2 + 1, h->V, st, h->vin);
+        for (int j = 0; j < m; ++j) {
+            fgmres_step(h, st);
+            launch_gs_next(h->ctl, st);
+            read_ctl(h, st);
+            if (h->ctl_host->stop) break;
+        }
+        fgmres_cycle_end(h, st);
+        const double rn = std::sqrt(read_scalar(h, h->n2 + 1, st));
+        read_ctl(h, st);
+        KrylovCtl &k = *h->ctl_host;
+        k.rnorm = rn;
+        bool again = true;
+        if (!std::isfinite(rn) || k.nonfinite) { k.nonfinite = 1; again = false; }
+        else if (rn <= k.tol_abs) { k.converged = 1; again = false; }
+        else if (k.iters >= k.maxit) again = false;
+        else k.restarts += 1;
+        write_ctl(h, st);
+        if (!again) break;
+    }
+    read_ctl(h, st);
+}
+
+// Add a WHILE conditional node at the current capture position of `cs`;
+// returns its body graph.
+cudaGraph_t capture_while(cudaStream_t cs, cudaGraphConditionalHandle handle) {
+    cudaStreamCaptureStatus status;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    GEMSLR_CUDA(cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = handle;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    GEMSLR_CUDA(cudaGraphAddNode(&node, cg, deps, nullptr, nd, &p));
+    GEMSLR_CUDA(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return p.conditional.phGraph_out[0];
+}
+
+// The whole solve as one CUDA graph: prologue, then
+//   WHILE (cycle) { cycle start; WHILE (step) { FGMRES step }; cycle end }
+// with both conditions set by device kernels from the control block, so a
+// solve needs no host round trip.  Built once per restart length.
+bool ensure_solve_graph(gemslr_ctx *h, int m) {
+    if (h->graph_failed) return false;
+    if (h->graph_exec && h->graph_m == m) return true;
+    try {
+        if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+        if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+        if (!h->cap_stream) GEMSLR_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        cudaStream_t cs = h->cap_stream;
+        const int64_t n = h->host.n;
+        const uint64_t k0 = launches_total();
+        cudaGraph_t g;
+        GEMSLR_CUDA(cudaGraphCreate(&g, 0));
+        h->graph = g;
+        cudaGraphConditionalHandle hc;
+        GEMSLR_CUDA(cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault));
+        GEMSLR_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        launch_zero(n, h->xh, cs);
+        GEMSLR_CUDA(cudaMemcpyAsync(h->r, h->bh, 8 * n, cudaMemcpyDeviceToDevice, cs));
+        GEMSLR_CUDA(cudaMemcpyAsync(h->n2 + 1, h->n2, 8, cudaMemcpyDeviceToDevice, cs));
+        cudaGraph_t body_cycle = capture_while(cs, hc);
+        GEMSLR_CUDA(cudaStreamEndCapture(cs, &g));
+        const uint64_t k1 = launches_total();
+        cudaGraphConditionalHandle hs;
+        GEMSLR_CUDA(cudaGraphConditionalHandleCreate(&hs, body_cycle, 1, cudaGraphCondAssignDefault));
+        GEMSLR_CUDA(cudaStreamBeginCaptureToGraph(cs, body_cycle, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        launch_cycle_start_g(h->ctl, h->g, h->n2 + 1, hs, cs);
+        launch_scale_by_norm(n, h->r, h->n2 + 1, h->V, cs, h->vin);
+        cudaGraph_t body_step = capture_while(cs, hs);
+        fgmres_cycle_end(h, cs);
+        launch_cycle_end_g(h->ctl, h->n2 + 1, hc, cs);
+        GEMSLR_CUDA(cudaStreamEndCapture(cs, &body_cycle));
+        const uint64_t k2 = launches_total();
+        GEMSLR_CUDA(cudaStreamBeginCaptureToGraph(cs, body_step, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+        fgmres_step(h, cs);
+        launch_step_end_g(h->ctl, hs, cs);
+        GEMSLR_CUDA(cudaStreamEndCapture(cs, &body_step));
+        const uint64_t k3 = launches_total();
+        GEMSLR_CUDA(cudaGraphInstantiate(&h->graph_exec, g, 0));
+        h->graph_k_top = k1 - k0;
+        h->graph_k_cycle = k2 - k1;
+        h->graph_k_step = k3 - k2;
+        count_launch(-(int)(k3 - k0));      // capture launches nothing
+        h->graph_m = m;
+        return true;
+    } catch (const Error &e) {
+        cudaGetLastError();
+        h->graph_failed = true;
+        if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+        if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+        return false;
+    }
 }
 
 gemslr_status guard(const std::function<void()> &fn) {
@@ -304,7 +464,7 @@ gemslr_options normalized(const gemslr_options *opt) {
     if (o.ilut_tau < 0) fail(GEMSLR_ERR_ARG, "ilut_tau must be >= 0");
     for (int l = 0; l < GEMSLR_MAX_LEVELS; ++l)
         if (o.rank[l] < 0 || 2 * o.rank[l] + 1 > kMaxCols || o.rank[l] + 2 > kMaxRank)
-            fail(GEMSLR_ERR_ARG, "rank out of range (0..63)");
+            fail(GEMSLR_ERR_ARG, "rank out of range (0..79)");
     return o;
 }
 
@@ -401,7 +561,7 @@ gemslr_status gemslr_setup_from_factors(const gemslr_csr *A, const gemslr_partit
         if (h->mixed) {
             // rebuild the mixed hierarchy now that W/H are attached
             h->d32 = DevHierarchy<float, __nv_bfloat16>();
-            upload_hierarchy<float, __nv_bfloat16>(H, h->arena, h->d32, std::min(smem_optin(), 200 * 1024));
+            upload_hierarchy<float, __nv_bfloat16>(H, h->arena, h->d32, smem_optin());
         }
         GEMSLR_CUDA(cudaDeviceSynchronize());
         h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -492,16 +652,15 @@ gemslr_status gemslr_fgmres_solve(gemslr_handle h, const double *b_dev, double *
             launch_norm2(n, h->bh, h->partial, h->counter, h->n2, h->red_grid, st);
             const double bn2 = read_scalar(h, h->n2, st);
             const double bnorm = std::sqrt(bn2);
-            launch_zero(n, h->xh, st);
-            if (!std::isfinite(bnorm)) {
-                if (worst == GEMSLR_OK) worst = GEMSLR_ERR_NAN;
-                g_last_error = "right-hand side is not finite";
+            if (!std::isfinite(bnorm) || bnorm == 0.0) {
+                launch_zero(n, h->xh, st);
                 launch_scatter(n, h->perm, h->xh, x_dev + (size_t)c * n, st);
-                continue;
-            }
-            if (bnorm == 0.0) {
-                inf.converged = 1;
-                launch_scatter(n, h->perm, h->xh, x_dev + (size_t)c * n, st);
+                if (bnorm == 0.0) {
+                    inf.converged = 1;
+                } else {
+                    if (worst == GEMSLR_OK) worst = GEMSLR_ERR_NAN;
+                    g_last_error = "right-hand side is not finite";
+                }
                 continue;
             }
             KrylovCtl cc{};
@@ -512,52 +671,39 @@ gemslr_status gemslr_fgmres_solve(gemslr_handle h, const double *b_dev, double *
             cc.tol_abs = opts->rtol * bnorm;
             *h->ctl_host = cc;
             write_ctl(h, st);
-            GEMSLR_CUDA(cudaMemcpyAsync(h->r, h->bh, 8 * n, cudaMemcpyDeviceToDevice, st));
-            GEMSLR_CUDA(cudaMemcpyAsync(h->n2 + 1, h->n2, 8, cudaMemcpyDeviceToDevice, st));   // ||r||^2
-            bool converged = false, bad = false;
-            int iters = 0;
-            double rel_true = 1.0;
-            while (true) {
-                launch_cycle_start(h->ctl, h->g, h->n2 + 1, st);
-                launch_scale_by_norm(n, h->r, h->n2 + 1, h->V, st);
-                for (int j = 0; j < m; ++j) {
-                    double *vj = h->V + (size_t)j * n, *zj = h->Z + (size_t)j * n;
-                    apply_perm(h, vj, zj, st);
-                    launch_spmv(n, h->A_rp, h->A_ci, h->A_v, zj, nullptr, h->w, h->spmv_lanes, st);
-                    launch_gs_dots(n, h->V, n, h->w, h->partial, h->counter, h->ctl, h->Hs, h->cs, h->sn, h->g,
-                                   h->red_grid, st);
-                    launch_gs_sub(n, h->V, n, h->w, h->partial, h->counter, h->ctl, h->Hs, h->cs, h->sn, h->g, h->h2,
-                                  h->red_grid, st);
-                    launch_gs_sub2(n, h->V, n, h->w, h->h2, h->ctl, st);
-                    launch_gs_next(h->ctl, st);
-                    read_ctl(h, st);
-                    if (h->ctl_host->stop) break;
-                }
-                launch_lsq(h->ctl, h->Hs, h->g, h->y, st);
-                launch_update_x(n, h->Z, n, h->ctl, h->y, h->xh, st);
-                launch_spmv(n, h->A_rp, h->A_ci, h->A_v, h->xh, h->bh, h->r, h->spmv_lanes, st);
-                launch_norm2(n, h->r, h->partial, h->counter, h->n2 + 1, h->red_grid, st);
-                const double rn = std::sqrt(read_scalar(h, h->n2 + 1, st));
+            // GEMSLR_SOLVE_GRAPH=0 selects the host-driven loop (profilers cannot
+            // see kernels inside conditional graph nodes)
+            const char *env = std::getenv("GEMSLR_SOLVE_GRAPH");
+            const bool allow_graph = !(env && env[0] == '0');
+            const bool use_graph = allow_graph && !profile_enabled() && ensure_solve_graph(h, m);
+            if (use_graph) {
+                GEMSLR_CUDA(cudaGraphLaunch(h->graph_exec, st));
                 read_ctl(h, st);
-                iters = h->ctl_host->iters;
-                rel_true = rn / bnorm;
-                inf.rel_res_est = h->ctl_host->resid / bnorm;
-                if (!std::isfinite(rn) || h->ctl_host->nonfinite) { bad = true; break; }
-                if (rn <= opts->rtol * bnorm) { converged = true; break; }
-                if (iters >= opts->maxit) break;
-                inf.restarts += 1;
+                const KrylovCtl &k = *h->ctl_host;
+                count_launch((int)(h->graph_k_top + (uint64_t)(k.restarts + 1) * h->graph_k_cycle +
+                                   (uint64_t)k.iters * h->graph_k_step));
+            } else {
+                fgmres_host_loop(h, m, st);
             }
+            const KrylovCtl &k = *h->ctl_host;
+            GEMSLR_CUDA(cudaMemcpyAsync(h->err_host, h->mixed ? h->d32.err : h->d64.err, 4, cudaMemcpyDeviceToHost, st));
             launch_scatter(n, h->perm, h->xh, x_dev + (size_t)c * n, st);
             GEMSLR_CUDA(cudaStreamSynchronize(st));
-            inf.iters = iters;
-            inf.converged = converged ? 1 : 0;
-            inf.reorth = h->ctl_host->nreorth;
-            inf.rel_res_true = rel_true;
+            inf.iters = k.iters;
+            inf.restarts = k.restarts;
+            inf.converged = k.converged ? 1 : 0;
+            inf.reorth = k.nreorth;
+            inf.rel_res_est = k.resid / bnorm;
+            inf.rel_res_true = k.rnorm / bnorm;
             inf.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-            if (bad) {
+            if (h->err_host[0]) {
+                GEMSLR_CUDA(cudaMemsetAsync(h->mixed ? h->d32.err : h->d64.err, 0, 4, st));
+                fail(GEMSLR_ERR_TIMEOUT, "a bounded wait in the substitution kernel expired");
+            }
+            if (k.nonfinite) {
                 if (worst == GEMSLR_OK) worst = GEMSLR_ERR_NAN;
                 g_last_error = "FGMRES produced a non-finite value";
-            } else if (!converged && worst == GEMSLR_OK) {
+            } else if (!k.converged && worst == GEMSLR_OK) {
                 worst = GEMSLR_ERR_NOT_CONVERGED;
                 g_last_error = "FGMRES reached maxit";
             }
@@ -613,5 +759,15 @@ gemslr_status gemslr_get_stats(gemslr_handle h, double *out, int32_t nout) {
 }
 
 void gemslr_destroy(gemslr_handle h) { delete h; }
+
+uint64_t gemslr_kernel_launches(void) { return launches_total(); }
+
+void gemslr_profile_enable(int32_t on) { profile_enable(on != 0); }
+
+void gemslr_profile_reset(void) { profile_reset(); }
+
+int32_t gemslr_profile_read(char *names, size_t len, double *ms, int64_t *counts, int32_t maxn) {
+    return profile_read(names, len, ms, counts, maxn);
+}
 
 }  // extern "C"

@@ -81,3 +81,47 @@ def test_library_setup_solves_to_tolerance(torch_cuda, name):
     assert res <= 1e-8
     st = G.stats()
     assert st["n"] == A.n and st["bytes_per_apply"] > 0
+
+
+def test_graph_and_host_loop_give_identical_solves(torch_cuda):
+    """The solve captured as one CUDA graph (conditional WHILE nodes) and the
+    host-driven loop (used while profiling) run the same kernels in the same
+    order: identical iterates."""
+    torch = torch_cuda
+    from paper_2205_03224_gb300 import Gemslr
+    from paper_2205_03224_gb300 import _lib
+    A, xyz, part = problem("small3d")
+    M = oracle_hierarchy("small3d")
+    G = Gemslr.from_factors(A, part, M.factors())
+    b = torch.from_numpy(gi.rhs_uniform(M.n, 4)).cuda()
+    x1, i1 = G.solve(b, restart=12, rtol=1e-9)
+    _lib.profile_enable(True)
+    try:
+        x2, i2 = G.solve(b, restart=12, rtol=1e-9)
+    finally:
+        _lib.profile_enable(False)
+        _lib.profile_reset()
+    assert i1[0]["iters"] == i2[0]["iters"] and i1[0]["restarts"] == i2[0]["restarts"] >= 1
+    assert torch.equal(x1, x2)
+    n0 = _lib.kernel_launches()
+    G.solve(b, restart=12, rtol=1e-9)
+    assert _lib.kernel_launches() - n0 >= 10 * i1[0]["iters"]
+
+
+def test_maxit_reports_not_converged(torch_cuda):
+    torch = torch_cuda
+    from paper_2205_03224_gb300 import Gemslr
+    A, xyz, part = problem("c1")
+    M = oracle_hierarchy("c1")
+    G = Gemslr.from_factors(A, part, M.factors())
+    b = torch.from_numpy(gi.rhs_uniform(M.n, 4)).cuda()
+    x, info = G.solve(b, restart=5, rtol=1e-12, maxit=7, check=False)
+    assert info[0]["status"] == "ERR_NOT_CONVERGED"
+    assert info[0]["iters"] == 7 and not info[0]["converged"]
+    z = torch.zeros_like(b)
+    x0, info0 = G.solve(z, restart=5, rtol=1e-8)
+    assert info0[0]["converged"] and info0[0]["iters"] == 0 and torch.count_nonzero(x0) == 0
+    nan = b.clone()
+    nan[3] = float("nan")
+    xn, infon = G.solve(nan, restart=5, rtol=1e-8, check=False)
+    assert infon[0]["status"] == "ERR_NAN"
