@@ -144,10 +144,15 @@ void validate_tri(const Csr &T, const std::vector<int64_t> &bp, bool upper) {
 size_t pad16(size_t x) { return (x + 15) & ~size_t(15); }
 
 template <typename VT>
+int64_t chunk_slots(int64_t maxlen) {
+    return LanesPerRow<VT>::value == 1 ? maxlen : 4 * ((maxlen + 3) / 4);
+}
+
+template <typename VT>
 size_t chunk_bytes(int64_t nrows, int64_t maxlen, bool upper) {
     const size_t pr = (size_t)((nrows + 3) & ~int64_t(3));
-    const size_t kq = (size_t)((maxlen + 3) / 4);
-    return 16 + 8 * pr + kq * (size_t)nrows * 4 * (4 + sizeof(VT)) + (upper ? pad16((size_t)nrows * sizeof(VT)) : 0);
+    const size_t ne = (size_t)(chunk_slots<VT>(maxlen) * nrows);
+    return 16 + 8 * pr + pad16(ne * 4) + pad16(ne * sizeof(VT)) + (upper ? pad16((size_t)nrows * sizeof(VT)) : 0);
 }
 
 template <typename VT>
@@ -186,19 +191,19 @@ void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, Chun
                 ++n;
             if (n == 0) fail(GEMSLR_ERR_UNSUPPORTED, "a factor row has too many entries for the staged substitution");
             const size_t bytes = chunk_bytes<VT>(n, maxlen, upper);
-            const int64_t kq = (maxlen + 3) / 4;
+            const int64_t S = chunk_slots<VT>(maxlen);
             const size_t base = out.data.size();
             out.data.resize(base + bytes, 0);
             unsigned char *p = out.data.data() + base;
             int32_t *hdr = reinterpret_cast<int32_t *>(p);
             hdr[0] = (int32_t)n;
-            hdr[1] = (int32_t)kq;
+            hdr[1] = (int32_t)S;
             hdr[2] = upper ? 1 : 0;
-            hdr[3] = 0;
+            hdr[3] = (int32_t)maxlen;
             const int64_t pr = (n + 3) & ~int64_t(3);
             int32_t *rr = hdr + 4, *ll = rr + pr, *cc = ll + pr;
-            VT *vv = reinterpret_cast<VT *>(cc + kq * n * 4);
-            VT *dd = vv + kq * n * 4;
+            VT *vv = reinterpret_cast<VT *>(reinterpret_cast<unsigned char *>(cc) + pad16((size_t)(S * n) * 4));
+            VT *dd = reinterpret_cast<VT *>(reinterpret_cast<unsigned char *>(vv) + pad16((size_t)(S * n) * sizeof(VT)));
             for (int64_t t = 0; t < n; ++t) {
                 const int64_t i = R[start + t];
                 rr[t] = (int32_t)(i - r0);
@@ -209,7 +214,7 @@ void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, Chun
                         if (upper) dd[t] = cast_to<VT>(1.0 / T.v[pp]);
                         continue;
                     }
-                    const int64_t e = ((q >> 2) * n + t) * 4 + (q & 3);
+                    const int64_t e = LanesPerRow<VT>::value == 1 ? q * n + t : ((q >> 2) * n + t) * 4 + (q & 3);
                     cc[e] = (int32_t)(T.ci[pp] - r0);
                     vv[e] = cast_to<VT>(T.v[pp]);
                     ++q;

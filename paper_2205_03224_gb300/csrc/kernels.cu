@@ -20,17 +20,11 @@
 #include <cstdio>
 
 #include "device.h"
+#include "ptx.cuh"
 
 namespace gemslr {
 
 namespace {
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 template <typename T> __device__ __forceinline__ float to_f(T v);
 template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
@@ -39,104 +33,6 @@ template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v
 template <typename VT, typename WT> __device__ __forceinline__ VT wval(WT w) { return (VT)to_f(w); }
 template <> __device__ __forceinline__ double wval<double, double>(double w) { return w; }
 
-// Column sums of per-CTA partials [nparts][ncols1] into out[0..ncols1) (shared
-// memory), by all warps of the finishing CTA: warp w owns columns w, w+nw, ...,
-// its lanes stride over the partials (callers use 256-thread CTAs: 8 warps), so every lane keeps up to kColsPerWarp
-// independent loads in flight; the summation order is fixed (deterministic).
-constexpr int kColsPerWarp = (kMaxCols + 1 + 7) / 8;
-template <typename T>
-__device__ void reduce_columns(const T *partial, int nparts, int ncols1, T *out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    T acc[kColsPerWarp];
-#pragma unroll
-    for (int u = 0; u < kColsPerWarp; ++u) acc[u] = 0;
-    for (int p = lane; p < nparts; p += 32) {
-        const T *row = partial + (int64_t)p * ncols1;
-#pragma unroll
-        for (int u = 0; u < kColsPerWarp; ++u) {
-            const int c = warp + nw * u;
-            if (c < ncols1) acc[u] += __ldcg(row + c);
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < kColsPerWarp; ++u) {
-        const int c = warp + nw * u;
-        const T v = warp_sum(acc[u]);
-        if (lane == 0 && c < ncols1) out[c] = v;
-    }
-    __syncthreads();
-}
-
-// ---- mbarrier / bulk-copy primitives (sm_90+ PTX) ------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, unsigned parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Polling wait (no suspension) for the consumers' critical path, bounded like wait_bounded.
-__device__ __forceinline__ bool poll_bounded(uint64_t *bar, unsigned parity, volatile int *abort_flag) {
-    if (mbar_test_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    unsigned spins = 0;
-    while (!mbar_test_wait(bar, parity)) {
-        if ((++spins & 63u) == 0u) {
-            if (*abort_flag) return false;
-            if (clock64() - t0 > 4000000000ll) return false;
-        }
-    }
-    return true;
-}
-__device__ __forceinline__ void consumer_barrier() {
-    asm volatile("bar.sync 1, %0;" ::"n"(32 * kConsumerWarps) : "memory");
-}
-// One bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-// Every wait is bounded: about 2 s of clock cycles, or until another warp of
-// the CTA has raised `abort`.
-constexpr long long kSpinCycles = 4000000000ll;
-
-__device__ __forceinline__ bool wait_bounded(uint64_t *bar, unsigned parity, volatile int *abort_flag) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (abort_flag && *abort_flag) return false;
-        if (clock64() - t0 > kSpinCycles) return false;
-    }
-    return true;
-}
 
 // ---- level-scheduled substitutions over one block --------------------------
 // One CTA per diagonal block.  Warp kConsumerWarps is the producer: one lane
@@ -169,7 +65,8 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kConsumerWarps);
+            // FP32 chunks are released by one consumer warp, FP64 chunks by all of them
+            mbar_init(&empty[s], LanesPerRow<VT>::value == 1 ? 1 : kConsumerWarps);
         }
         mbar_init(cbar, kConsumerWarps);
         *abort_flag = 0;
@@ -218,48 +115,60 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
         }
     }
     consumer_barrier();
-    bool aborted = false;
-    const int r = lane >> 2, sub = lane & 3;
-    for (int c = c0; c < c1; ++c) {
-        const int k = c - c0, st = k % kStages;
-        if (!aborted && !poll_bounded(&full[st], (k / kStages) & 1, abort_flag)) {
-            aborted = true;
-            *abort_flag = 1;
-        }
-        if (!aborted) {
-            const unsigned char *base = ring + (size_t)st * kStageBytes;
-            const int *hdr = reinterpret_cast<const int *>(base);
-            const int nrow = hdr[0], kq = hdr[1], upper = hdr[2];
-            const int pr = (nrow + 3) & ~3;
-            const int *rows = hdr + 4;
-            const int *lens = rows + pr;
-            const int *cols = lens + pr;
-            const VT *vals = reinterpret_cast<const VT *>(cols + (size_t)kq * nrow * 4);
-            const int per = (nrow + kConsumerWarps - 1) / kConsumerWarps;   // rows of this warp (<= 8)
-            const int t = warp * per + r;
-            const bool active = r < per && t < nrow;
-            const int len = active ? lens[t] : 0;
-            VT acc = 0;
-            for (int kk = 0; kk < kq; ++kk) {
-                const int q = 4 * kk + sub;
-                if (q < len) {
-                    const int e = (kk * nrow + t) * 4 + sub;
-                    acc += vals[e] * xs[cols[e]];
+    if constexpr (LanesPerRow<VT>::value == 1) {
+        // FP32: consumer warp 0 walks every chunk, one lane per row, and loads
+        // the next chunk's rows, lengths, columns and values into registers
+        // while the current chunk's x gathers are in flight; rows of one
+        // chunk are ordered after the previous chunk by __syncwarp alone.
+        if (warp == 0) consume_chunks_lane_per_row<VT>(ring, full, empty, abort_flag, c1 - c0, xs, lane);
+    } else {
+        bool aborted = false;
+        const int r = lane >> 2, sub = lane & 3;
+        for (int c = c0; c < c1; ++c) {
+            const int k = c - c0, st = k % kStages;
+            if (!aborted && !poll_bounded(&full[st], (k / kStages) & 1, abort_flag)) {
+                aborted = true;
+                *abort_flag = 1;
+            }
+            if (!aborted) {
+                const unsigned char *base = ring + (size_t)st * kStageBytes;
+                const int *hdr = reinterpret_cast<const int *>(base);
+                const int nrow = hdr[0], S = hdr[1], upper = hdr[2];
+                const int pr = (nrow + 3) & ~3;
+                const int *rows = hdr + 4;
+                const int *lens = rows + pr;
+                const int *cols = lens + pr;
+                const VT *vals = reinterpret_cast<const VT *>(cols + (size_t)S * nrow);
+                const int per = (nrow + kConsumerWarps - 1) / kConsumerWarps;   // rows of this warp (<= 8)
+                if (warp * per < nrow) {                                       // idle warps skip the FP64 work
+                    const int t = warp * per + r;
+                    const bool active = r < per && t < nrow;
+                    const int len = active ? lens[t] : 0;
+                    const int kq = S >> 2;
+                    VT acc = 0;
+                    for (int kk = 0; kk < kq; ++kk) {
+                        const int q = 4 * kk + sub;
+                        if (q < len) {
+                            const int e = (kk * nrow + t) * 4 + sub;
+                            acc += vals[e] * xs[cols[e]];
+                        }
+                    }
+                    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                    if (active && sub == 0) {
+                        const int row = rows[t];
+                        VT y = xs[row] - acc;
+                        if (upper) y *= vals[(size_t)S * nrow + t];     // dinv follows vals
+                        xs[row] = y;
+                    }
                 }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[st]);
             }
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            if (active && sub == 0) {
-                const int row = rows[t];
-                VT y = xs[row] - acc;
-                if (upper) y *= vals[(size_t)kq * nrow * 4 + t];     // dinv follows vals
-                xs[row] = y;
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[st]);
+            consumer_barrier();
         }
-        consumer_barrier();
     }
+    consumer_barrier();
     if (*abort_flag) {
         if (ct == 0) atomicExch(lv.err, 1);
         return;

@@ -18,20 +18,24 @@ constexpr int kMaxCols = 160;     // Krylov columns per Gram-Schmidt pass (m + 1
 // chunk holds <= kChunkRows independent rows of one wavefront and is one
 // contiguous, 16-byte aligned byte range (<= kStageBytes) that a single bulk
 // copy moves into shared memory:
-//   int32 {nrows, kq, upper, 0}   kq = ceil(max entries / 4)
-//   int32 rows[pad4(nrows)]       block-local row of every slot
-//   int32 lens[pad4(nrows)]       entries of every slot
-//   int32 cols[kq*nrows*4]        entry q of slot t at ((q/4)*nrows + t)*4 + q%4
-//   VT    vals[kq*nrows*4]        same positions (padded to 16 bytes)
-//   VT    dinv[nrows]             1/u_ii, U chunks only (padded to 16 bytes)
-// Four lanes share a row (entries q = sub, sub+4, ...), so a warp reads
-// consecutive addresses and every FP64 instruction has most lanes active.
+//   int32 {nrows, S, upper, maxlen}   S = entry slots per row
+//   int32 rows[pad4(nrows)]           block-local row of every slot
+//   int32 lens[pad4(nrows)]           entries of every slot
+//   int32 cols[pad4(S*nrows)]         block-local columns
+//   VT    vals[S*nrows] padded to 16 bytes
+//   VT    dinv[nrows]  padded to 16 bytes (U chunks: 1/u_ii)
+// Entry q of row slot t sits at
+//   FP32 (one lane per row, S = maxlen):          q*nrows + t
+//   FP64 (four lanes per row, S = 4*ceil(maxlen/4)): ((q/4)*nrows + t)*4 + q%4
+// so a warp always reads consecutive addresses.
 constexpr int kStageBytes = 4096;
 constexpr int kStages = 16;
 constexpr int kConsumerWarps = 4;
-constexpr int kChunkRows = 8 * kConsumerWarps;
+constexpr int kChunkRows = 32;
 constexpr int kTrsvThreads2 = 32 * (kConsumerWarps + 1);
 constexpr int kRingBytes = kStageBytes * kStages + 2 * kStages * 8 + 64;   // ring + mbarriers + flags
+template <typename VT> struct LanesPerRow { static constexpr int value = 4; };
+template <> struct LanesPerRow<float> { static constexpr int value = 1; };
 
 struct ChunkView {
     const unsigned char *data;
