@@ -225,6 +225,38 @@ const char *gemslr_last_error(void);
 void gemslr_destroy(gemslr_handle h);
 
 /*
+ * Batched solve phase: many independent systems (each with its own CSR,
+ * multilevel partition and setup, Alg. 1) handled together with up to
+ * GEMSLR_BATCH_RHS right-hand sides each.  Every stage of M^{-1} (Alg. 2) is
+ * one launch over all systems; FGMRES runs for every (system, rhs) pair in
+ * lock step, the whole solve being one CUDA graph.  The preconditioner is
+ * applied in FP32 (W in BF16, FP32 accumulation); Krylov vectors, the
+ * least-squares problems and residuals are FP64.  All systems need the same
+ * nlev; ranks up to 64.
+ *
+ * Vector layout of r/z/b/x: the systems one after another, system s a
+ * column-major n_s x nrhs block in its original ordering.
+ * gemslr_setup_batch: A and part are arrays of nsys entries; opt applies to all.
+ * gemslr_batch_apply: z = M_s^{-1} r for every system and rhs (captured graph).
+ * gemslr_batch_fgmres_solve: info has nsys * nrhs entries (system-major).
+ * gemslr_batch_stats: out[0..7] = nsys, total rows, factor nonzeros, bytes of one
+ * application (approximate), setup ms, autotuning ms, tuned rows per CTA of the
+ * coupling kernels and of the Krylov kernels.
+ */
+#define GEMSLR_BATCH_RHS 8
+typedef struct gemslr_batch_ctx *gemslr_batch;
+gemslr_status gemslr_setup_batch(int32_t nsys, const gemslr_csr *A, const gemslr_partition *part,
+                                 const gemslr_options *opt, gemslr_batch *out);
+gemslr_status gemslr_batch_apply(gemslr_batch b, const double *r_dev, double *z_dev, int32_t nrhs,
+                                 void *stream);
+gemslr_status gemslr_batch_fgmres_solve(gemslr_batch b, const double *b_dev, double *x_dev, int32_t nrhs,
+                                        const gemslr_solve_opts *opts, gemslr_solve_info *info,
+                                        void *stream);
+gemslr_status gemslr_batch_stats(gemslr_batch b, double *out, int32_t nout);
+const char *gemslr_batch_last_error(void);
+void gemslr_batch_destroy(gemslr_batch b);
+
+/*
  * Instrumentation (not part of the method; process-wide, thread-safe).
  * gemslr_kernel_launches: number of CUDA kernels this library has launched.
  * gemslr_profile_enable: with on != 0 every instrumented launch is bracketed

@@ -61,6 +61,8 @@ EXPORTED = [
     "gemslr_factor_sizes", "gemslr_export_factors", "gemslr_apply", "gemslr_fgmres_solve",
     "gemslr_get_stats", "gemslr_last_error", "gemslr_destroy", "gemslr_kernel_launches",
     "gemslr_profile_enable", "gemslr_profile_reset", "gemslr_profile_read",
+    "gemslr_setup_batch", "gemslr_batch_apply", "gemslr_batch_fgmres_solve", "gemslr_batch_stats",
+    "gemslr_batch_last_error", "gemslr_batch_destroy",
 ]
 
 _lib = None
@@ -103,18 +105,30 @@ def load():
     L.gemslr_profile_reset.restype = None
     L.gemslr_profile_read.argtypes = [ctypes.c_char_p, ctypes.c_size_t, P, P, i32]
     L.gemslr_profile_read.restype = i32
+    L.gemslr_setup_batch.argtypes = [i32, ctypes.POINTER(CSR), ctypes.POINTER(Partition), ctypes.POINTER(Options),
+                                     ctypes.POINTER(P)]
+    L.gemslr_batch_apply.argtypes = [P, P, P, i32, P]
+    L.gemslr_batch_fgmres_solve.argtypes = [P, P, P, i32, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), P]
+    L.gemslr_batch_stats.argtypes = [P, P, i32]
+    L.gemslr_batch_last_error.restype = ctypes.c_char_p
+    L.gemslr_batch_last_error.argtypes = []
+    L.gemslr_batch_destroy.argtypes = [P]
+    L.gemslr_batch_destroy.restype = None
     for name in EXPORTED:
         fn = getattr(L, name)
         if name not in ("gemslr_default_options", "gemslr_last_error", "gemslr_destroy", "gemslr_kernel_launches",
-                        "gemslr_profile_enable", "gemslr_profile_reset", "gemslr_profile_read"):
+                        "gemslr_profile_enable", "gemslr_profile_reset", "gemslr_profile_read",
+                        "gemslr_batch_last_error", "gemslr_batch_destroy"):
             fn.restype = ctypes.c_int
     _lib = L
     return L
 
 
-def check(status):
+def check(status, batch=False):
     if status != 0:
-        raise GemslrError(status, load().gemslr_last_error().decode())
+        lib = load()
+        msg = lib.gemslr_batch_last_error() if batch else lib.gemslr_last_error()
+        raise GemslrError(status, msg.decode())
 
 
 def ptr(a):

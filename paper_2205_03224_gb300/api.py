@@ -177,3 +177,62 @@ class Gemslr:
             levels.append(dict(s=s0, e=e0, L=tocsr(iL), U=tocsr(iU), E=tocsr(iE), F=tocsr(iF),
                                W=np.array(W[:, :k]), H=np.array(H[:k, :k])))
         return dict(levels=levels, last=dict(L=tocsr(iLl), U=tocsr(iUl)))
+
+
+class GemslrBatch:
+    """Many independent systems solved together (up to 8 right-hand sides each)."""
+
+    MAX_RHS = 8
+
+    def __init__(self, As, parts, **opts):
+        self._lib = L.load()
+        keep = []
+        n = len(As)
+        csrs = (L.CSR * n)(*[L.csr_struct(A, keep) for A in As])
+        prts = (L.Partition * n)(*[L.partition_struct(p, keep) for p in parts])
+        o = options(**opts)
+        h = ctypes.c_void_p()
+        L.check(self._lib.gemslr_setup_batch(n, csrs, prts, ctypes.byref(o), ctypes.byref(h)), batch=True)
+        self._h = h
+        self.sizes = [int(c.n) for c in csrs]
+        self.nsys = n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gemslr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, r, nrhs):
+        """z = M_s^{-1} r for the concatenated column-major blocks of every system."""
+        import torch
+        r = r.contiguous()
+        z = torch.empty_like(r)
+        L.check(self._lib.gemslr_batch_apply(self._h, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                             nrhs, _stream(torch)), batch=True)
+        return z
+
+    def solve(self, b, nrhs, restart=50, rtol=1e-8, maxit=1000, check=True):
+        import torch
+        b = b.contiguous()
+        x = torch.empty_like(b)
+        so = L.SolveOpts(restart, maxit, rtol)
+        info = (L.SolveInfo * (self.nsys * nrhs))()
+        st = self._lib.gemslr_batch_fgmres_solve(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                                 nrhs, ctypes.byref(so), info, _stream(torch))
+        infos = [dict(iters=i.iters, restarts=i.restarts, converged=bool(i.converged),
+                      rel_res_true=i.rel_res_true, t_total_ms=i.t_total_ms, status=L.STATUS.get(st, st)) for i in info]
+        if check and st not in (0, 4):
+            L.check(st, batch=True)
+        return x, infos
+
+    def stats(self):
+        out = np.zeros(8)
+        L.check(self._lib.gemslr_batch_stats(self._h, L.ptr(out), 8), batch=True)
+        return dict(nsys=int(out[0]), rows=int(out[1]), nnz_factors=int(out[2]), bytes_per_apply=float(out[3]),
+                    setup_ms=float(out[4]), tune_ms=float(out[5]), rows_couple=int(out[6]), rows_krylov=int(out[7]))

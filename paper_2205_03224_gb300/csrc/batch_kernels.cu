@@ -1,0 +1,681 @@
+// Batched kernels: many independent GeMSLR systems, kBatchRhs right-hand
+// sides each, one launch per stage of M^{-1} (Alg. 2) over every system, and
+// FGMRES (Sec. 4.1) run for every (system, rhs) pair in lock step.
+// Preconditioner in FP32 (W in BF16, FP32 accumulation), Krylov in FP64.
+#include "batch.cuh"
+#include "device.h"
+#include "ptx.cuh"
+
+namespace gemslr {
+
+namespace {
+constexpr int R8 = kBatchRhs;
+
+__device__ __forceinline__ bool last_of(unsigned *counter, unsigned n) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == n - 1);
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+}  // namespace
+
+// ---- M^{-1} stages -------------------------------------------------------------------
+// Level-scheduled substitutions, one CTA per block of any system; the lanes of
+// a warp are 4 rows x 8 right-hand sides.  MODE 0: right-hand side from `in`
+// (FP64) or `work`.  MODE 1: right-hand side F y2, then work[rows] -= result.
+template <int MODE, bool SMEM>
+__global__ void __launch_bounds__(kTrsvThreads2)
+k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ work, double *__restrict__ out_final,
+        float *__restrict__ scratch) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *ring = smem;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStageBytes * kStages);
+    uint64_t *empty = full + kStages;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + kStages + 1);
+    float *xs_smem = reinterpret_cast<float *>(smem + kRingBytes);
+    const int b = blockIdx.x;
+    const int64_t r0 = lv.blk_r0[b];
+    const int nr = lv.blk_nr[b];
+    if (nr == 0) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = lv.C.blk_chunk[b], c1 = lv.C.blk_chunk[b + 1];
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerWarps);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == kConsumerWarps) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int c = c0; c < c1; ++c) {
+                const int k = c - c0, st = k % kStages;
+                if (k >= kStages && !wait_bounded(&empty[st], ((k / kStages) - 1) & 1, abort_flag)) {
+                    *abort_flag = 1;
+                    atomicExch(lv.err, 1);
+                    break;
+                }
+                const unsigned bytes = (unsigned)(lv.C.off[c + 1] - lv.C.off[c]);
+                mbar_expect_tx(&full[st], bytes);
+                bulk_load(ring + (size_t)st * kStageBytes, lv.C.data + lv.C.off[c], bytes, &full[st]);
+                issued = k + 1;
+            }
+            for (int k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
+                wait_bounded(&full[k % kStages], (k / kStages) & 1, nullptr);
+        }
+        return;
+    }
+    const int ct = threadIdx.x;
+    constexpr int NC = 32 * kConsumerWarps;
+    float *mine = work + r0 * R8;
+    float *xs = SMEM ? xs_smem : (MODE == 1 ? scratch + lv.blk_f0[b] * R8 : mine);
+    const int64_t f0 = lv.blk_f0[b];
+    for (int idx = ct; idx < nr * R8; idx += NC) {
+        const int i = idx / R8, r = idx % R8;
+        if (MODE == 1) {
+            float acc = 0.f;
+            for (int64_t p = lv.F_rp[f0 + i]; p < lv.F_rp[f0 + i + 1]; ++p) acc += lv.F_v[p] * work[(int64_t)lv.F_ci[p] * R8 + r];
+            xs[idx] = acc;
+        } else if (in) {
+            xs[idx] = (float)in[(r0 + i) * R8 + r];
+        } else if (SMEM) {
+            xs[idx] = mine[idx];
+        }
+    }
+    consumer_barrier();
+    bool aborted = false;
+    const int rr = lane >> 3, r = lane & 7;
+    for (int c = c0; c < c1; ++c) {
+        const int k = c - c0, st = k % kStages;
+        if (!aborted && !poll_bounded(&full[st], (k / kStages) & 1, abort_flag)) {
+            aborted = true;
+            *abort_flag = 1;
+        }
+        if (!aborted) {
+            const int *hdr = reinterpret_cast<const int *>(ring + (size_t)st * kStageBytes);
+            const int nrow = hdr[0], S = hdr[1], upper = hdr[2];
+            const int pr = (nrow + 3) & ~3;
+            const int *rows = hdr + 4;
+            const int *lens = rows + pr;
+            const int *cols = lens + pr;
+            const int ne = S * nrow;
+            const float *vals = reinterpret_cast<const float *>(cols + ((ne + 3) & ~3));
+            const float *dinv = vals + ((ne + 3) & ~3);
+            const int per = (nrow + kConsumerWarps - 1) / kConsumerWarps;   // <= 4 rows per warp
+            const int t = warp * per + rr;
+            if (rr < per && t < nrow) {
+                const int row = rows[t], len = lens[t];
+                float a0 = 0.f, a1 = 0.f;
+                int q = 0;
+                for (; q + 1 < len; q += 2) {
+                    a0 += vals[q * nrow + t] * xs[cols[q * nrow + t] * R8 + r];
+                    a1 += vals[(q + 1) * nrow + t] * xs[cols[(q + 1) * nrow + t] * R8 + r];
+                }
+                if (q < len) a0 += vals[q * nrow + t] * xs[cols[q * nrow + t] * R8 + r];
+                float y = xs[row * R8 + r] - (a0 + a1);
+                if (upper) y *= dinv[t];
+                xs[row * R8 + r] = y;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+        }
+        consumer_barrier();
+    }
+    consumer_barrier();
+    if (*abort_flag) {
+        if (ct == 0) atomicExch(lv.err, 1);
+        return;
+    }
+    for (int idx = ct; idx < nr * R8; idx += NC) {
+        float y = xs[idx];
+        if (MODE == 1) y = mine[idx] - y;
+        if (SMEM || MODE == 1) mine[idx] = y;
+        if (out_final) out_final[r0 * R8 + idx] = (double)y;
+    }
+}
+
+// z2 = b2 - E z1 on the CTA's tail rows, partial W_s^T z2, and (last CTA of
+// the system) u_s = H_s (W_s^T z2).
+__global__ void __launch_bounds__(kBatchThreads)
+k_bcouple(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ work) {
+    __shared__ float zs[256 * R8];
+    __shared__ float ts[kBatchMaxRank * R8];
+    const int c = blockIdx.x, s = lv.cta_seg[c];
+    const int64_t i0 = lv.cta_i0[c], len = lv.seg_len[s];
+    const int rows = (int)min((int64_t)lv.rows_cta, len - i0);
+    const int64_t g0 = lv.seg_r0[s] + i0, e0 = lv.seg_e0[s] + i0;
+    for (int idx = threadIdx.x; idx < rows * R8; idx += blockDim.x) {
+        const int i = idx / R8, r = idx % R8;
+        const int64_t g = g0 + i;
+        float z = in ? (float)in[g * R8 + r] : work[g * R8 + r];
+        for (int64_t p = lv.E_rp[e0 + i]; p < lv.E_rp[e0 + i + 1]; ++p) z -= lv.E_v[p] * work[(int64_t)lv.E_ci[p] * R8 + r];
+        work[g * R8 + r] = z;
+        zs[idx] = z;
+    }
+    const int k = lv.seg_k[s];
+    if (k == 0) return;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int r = lane & 7, ig = lane >> 3;
+    const __nv_bfloat16 *Ws = lv.W + lv.seg_w0[s];
+    for (int cc = warp; cc < k; cc += nw) {
+        float acc = 0.f;
+        const __nv_bfloat16 *wc = Ws + (int64_t)cc * len + i0;
+        for (int i = ig; i < rows; i += 4) acc += __bfloat162float(wc[i]) * zs[i * R8 + r];
+        acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+        if (ig == 0) lv.partial[((int64_t)c * kBatchMaxRank + cc) * R8 + r] = acc;
+    }
+    const int ca = lv.seg_cta0[s], cb = lv.seg_cta0[s + 1];
+    if (!last_of(&lv.seg_counter[s], (unsigned)(cb - ca))) return;
+    for (int idx = threadIdx.x; idx < k * R8; idx += blockDim.x) {
+        const int cc = idx / R8, rr = idx % R8;
+        float acc = 0.f;
+        for (int q = ca; q < cb; ++q) acc += __ldcg(lv.partial + ((int64_t)q * kBatchMaxRank + cc) * R8 + rr);
+        ts[idx] = acc;
+    }
+    __syncthreads();
+    const float *Hs = lv.H + lv.seg_h0[s];
+    for (int idx = threadIdx.x; idx < k * R8; idx += blockDim.x) {
+        const int cc = idx / R8, rr = idx % R8;
+        float acc = 0.f;
+        for (int d = 0; d < k; ++d) acc += Hs[cc + (int64_t)d * k] * ts[d * R8 + rr];
+        lv.u[((int64_t)s * kBatchMaxRank + cc) * R8 + rr] = acc;
+    }
+    if (threadIdx.x == 0) lv.seg_counter[s] = 0u;
+}
+
+// work[tail] += W_s u_s
+__global__ void __launch_bounds__(kBatchThreads)
+k_blowrank(const BatchLevel lv, float *__restrict__ work) {
+    __shared__ float us[kBatchMaxRank * R8];
+    const int c = blockIdx.x, s = lv.cta_seg[c];
+    const int k = lv.seg_k[s];
+    if (k == 0) return;
+    const int64_t i0 = lv.cta_i0[c], len = lv.seg_len[s];
+    const int rows = (int)min((int64_t)lv.rows_cta, len - i0);
+    for (int idx = threadIdx.x; idx < k * R8; idx += blockDim.x) us[idx] = lv.u[(int64_t)s * kBatchMaxRank * R8 + idx];
+    __syncthreads();
+    const __nv_bfloat16 *Ws = lv.W + lv.seg_w0[s];
+    const int64_t g0 = lv.seg_r0[s] + i0;
+    for (int idx = threadIdx.x; idx < rows * R8; idx += blockDim.x) {
+        const int i = idx / R8, r = idx % R8;
+        float acc = 0.f;
+        for (int cc = 0; cc < k; ++cc) acc += __bfloat162float(Ws[(int64_t)cc * len + i0 + i]) * us[cc * R8 + r];
+        work[(g0 + i) * R8 + r] += acc;
+    }
+}
+
+// ---- Krylov kernels (FP64, per (system, rhs) pair) ---------------------------------
+// y = A x or y = b - A x over the batch (block-diagonal A, batch columns);
+// zcol: copy x into column *j of zcol (leading dimension ld).
+__global__ void __launch_bounds__(256)
+k_bspmv(int64_t nrows, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
+        const double *__restrict__ x, const double *__restrict__ b, double *__restrict__ y, double *__restrict__ zcol,
+        const int32_t *__restrict__ jp, int64_t ld) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nrows * R8) return;
+    const int64_t g = idx / R8;
+    const int r = (int)(idx % R8);
+    double acc = 0.0;
+    for (int64_t p = rp[g]; p < rp[g + 1]; ++p) acc += v[p] * x[(int64_t)ci[p] * R8 + r];
+    y[idx] = b ? b[idx] - acc : acc;
+    if (zcol) zcol[(int64_t)(*jp) * ld + idx] = x[idx];
+}
+
+namespace {
+// Per-CTA partial dot products of columns 0..ncols-1 of V (and of w itself
+// when with_norm) with w over rows [r0, r1), for the 8 right-hand sides.
+// Threads: r = tid & 7, row group = tid >> 3 (32 groups); 4 columns at a time.
+__device__ void bdots_block(const double *__restrict__ V, int64_t ldv, int ncols, bool with_norm,
+                            const double *__restrict__ w, int64_t r0, int64_t r1, double *partial_cta) {
+    __shared__ double red[8][4][R8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int r = threadIdx.x & 7, grp = threadIdx.x >> 3;
+    const int ntot = ncols + (with_norm ? 1 : 0);
+    for (int c0 = 0; c0 < ntot; c0 += 4) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int64_t g = r0 + grp; g < r1; g += 32) {
+            const double wi = w[g * R8 + r];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + u;
+                if (c < ncols) acc[u] += V[(int64_t)c * ldv + g * R8 + r] * wi;
+                else if (c < ntot) acc[u] += wi * wi;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            double x = acc[u];
+            x += __shfl_xor_sync(0xffffffffu, x, 8);
+            x += __shfl_xor_sync(0xffffffffu, x, 16);
+            if (lane < 8) red[warp][u][r] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x < 4 * R8) {
+            const int u = threadIdx.x / R8, rr = threadIdx.x % R8, c = c0 + u;
+            if (c < ntot) {
+                double sum = 0.0;
+                for (int q = 0; q < nw; ++q) sum += red[q][u][rr];
+                partial_cta[c * R8 + rr] = sum;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Sum the partials of system s's CTAs: out[c * 8 + r].
+__device__ void bdots_finish(const double *partial, int ca, int cb, int ntot, double *out) {
+    for (int idx = threadIdx.x; idx < ntot * R8; idx += blockDim.x) {
+        double sum = 0.0;
+        for (int q = ca; q < cb; ++q) sum += __ldcg(partial + (int64_t)q * (kMaxCols + 1) * R8 + idx);
+        out[idx] = sum;
+    }
+    __syncthreads();
+}
+
+// Givens update of column j of pair p's Hessenberg matrix (as in the single-system solver).
+__device__ void bgivens(const BatchKrylov &K, int p, int j) {
+    const int m = K.m, m1 = m + 1;
+    double *h = K.H + (int64_t)p * m1 * m + (int64_t)j * m1;
+    double *cs = K.cs + (int64_t)p * (m + 2), *sn = K.sn + (int64_t)p * (m + 2), *g = K.g + (int64_t)p * (m + 2);
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+    }
+    const double den = hypot(h[j], h[j + 1]);
+    const double c = den == 0.0 ? 1.0 : h[j] / den, s = den == 0.0 ? 0.0 : h[j + 1] / den;
+    cs[j] = c;
+    sn[j] = s;
+    const double brk = h[j + 1];
+    h[j] = den;
+    h[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    const double rsd = fabs(g[j + 1]);
+    K.resid[p] = rsd;
+    K.jdone[p] = j + 1;
+    const bool bad = !isfinite(rsd) || !isfinite(den);
+    if (bad) K.bad[p] = 1;
+    const bool breakdown = brk <= 1e-14 * sqrt(K.wn2[p]);
+    if (rsd <= K.tol[p] || breakdown || bad || *K.iters + j + 1 >= *K.maxit || j + 1 >= m) K.run[p] = 0;
+}
+}  // namespace
+
+// Gram-Schmidt pass 1 (pass == 1): h1 = V^T w.  Pass 2: w -= V h1, then
+// h2 = V^T w and ||w||^2; the finisher adds h2, forms beta by Pythagoras and
+// updates the pair's Givens rotations.
+__global__ void __launch_bounds__(256)
+k_bgs(int pass, const BatchSegs S, BatchKrylov K, double *__restrict__ V, int64_t ldv, double *__restrict__ w) {
+    __shared__ double hs[R8][kMaxCols];
+    __shared__ double out[(kMaxCols + 1) * R8];
+    const int c = blockIdx.x, s = S.cta_sys[c];
+    const int64_t r0 = S.cta_r0[c], r1 = S.cta_r1[c];
+    const int j = *K.j, ncols = j + 1;
+    if (pass == 2) {
+        for (int idx = threadIdx.x; idx < R8 * ncols; idx += blockDim.x) {
+            const int rr = idx / ncols, cc = idx % ncols;
+            hs[rr][cc] = K.hbuf[(int64_t)(s * R8 + rr) * kMaxCols + cc];
+        }
+        __syncthreads();
+        for (int64_t idx = r0 * R8 + threadIdx.x; idx < r1 * R8; idx += blockDim.x) {
+            const int rr = (int)(idx % R8);
+            double x = w[idx];
+            for (int cc = 0; cc < ncols; ++cc) x -= V[(int64_t)cc * ldv + idx] * hs[rr][cc];
+            w[idx] = x;
+        }
+        __syncthreads();
+    }
+    bdots_block(V, ldv, ncols, pass == 2, w, r0, r1, K.partial + (int64_t)c * (kMaxCols + 1) * R8);
+    const int ca = S.sys_cta0[s], cb = S.sys_cta0[s + 1];
+    if (!last_of(&S.sys_counter[s], (unsigned)(cb - ca))) return;
+    const int ntot = ncols + (pass == 2 ? 1 : 0);
+    bdots_finish(K.partial, ca, cb, ntot, out);
+    if (threadIdx.x < R8) {
+        const int rr = threadIdx.x, p = s * R8 + rr;
+        const int m1 = K.m + 1;
+        double *hcol = K.H + (int64_t)p * m1 * K.m + (int64_t)j * m1;
+        if (K.run[p]) {
+            if (pass == 1) {
+                for (int cc = 0; cc < ncols; ++cc) {
+                    hcol[cc] = out[cc * R8 + rr];
+                    K.hbuf[(int64_t)p * kMaxCols + cc] = out[cc * R8 + rr];
+                }
+            } else {
+                double hh = 0.0;
+                for (int cc = 0; cc < ncols; ++cc) {
+                    const double h2 = out[cc * R8 + rr];
+                    hcol[cc] += h2;
+                    K.hbuf[(int64_t)p * kMaxCols + cc] = h2;
+                    hh += h2 * h2;
+                }
+                const double rest = out[ncols * R8 + rr] - hh;
+                const double beta = sqrt(rest > 0.0 ? rest : 0.0);
+                double htot = 0.0;
+                for (int cc = 0; cc < ncols; ++cc) htot += hcol[cc] * hcol[cc];
+                K.wn2[p] = htot + beta * beta;          // ||A z_j||^2 by Pythagoras
+                K.beta[p] = beta;
+                hcol[j + 1] = beta;
+                bgivens(K, p, j);
+            }
+        } else if (pass == 2) {
+            for (int cc = 0; cc < ncols; ++cc) K.hbuf[(int64_t)p * kMaxCols + cc] = 0.0;
+            K.beta[p] = 0.0;
+        }
+    }
+    if (threadIdx.x == 0) S.sys_counter[s] = 0u;
+}
+
+// w -= V h2; V[:, j+1] = w / beta for pairs still running (0 otherwise); vin = same.
+__global__ void __launch_bounds__(256)
+k_bgs_final(const BatchSegs S, BatchKrylov K, double *__restrict__ V, int64_t ldv, const double *__restrict__ w,
+            double *__restrict__ vin) {
+    __shared__ double hs[R8][kMaxCols];
+    __shared__ double inv[R8];
+    const int c = blockIdx.x, s = S.cta_sys[c];
+    const int64_t r0 = S.cta_r0[c], r1 = S.cta_r1[c];
+    const int j = *K.j, ncols = j + 1;
+    for (int idx = threadIdx.x; idx < R8 * ncols; idx += blockDim.x) {
+        const int rr = idx / ncols, cc = idx % ncols;
+        hs[rr][cc] = K.hbuf[(int64_t)(s * R8 + rr) * kMaxCols + cc];
+    }
+    if (threadIdx.x < R8) {
+        const int p = s * R8 + threadIdx.x;
+        inv[threadIdx.x] = (K.run[p] && K.beta[p] > 0.0) ? 1.0 / K.beta[p] : 0.0;
+    }
+    __syncthreads();
+    double *vn = V + (int64_t)(j + 1) * ldv;
+    for (int64_t idx = r0 * R8 + threadIdx.x; idx < r1 * R8; idx += blockDim.x) {
+        const int rr = (int)(idx % R8);
+        double x = w[idx];
+        for (int cc = 0; cc < ncols; ++cc) x -= V[(int64_t)cc * ldv + idx] * hs[rr][cc];
+        const double v = x * inv[rr];
+        vn[idx] = v;
+        vin[idx] = v;
+    }
+}
+
+// ||x_p||^2 for every pair into out[p].
+__global__ void __launch_bounds__(256)
+k_bnorm2(const BatchSegs S, double *partial, const double *__restrict__ x, double *out) {
+    __shared__ double o[R8 * (kMaxCols + 1)];
+    const int c = blockIdx.x, s = S.cta_sys[c];
+    bdots_block(nullptr, 0, 0, true, x, S.cta_r0[c], S.cta_r1[c], partial + (int64_t)c * (kMaxCols + 1) * R8);
+    const int ca = S.sys_cta0[s], cb = S.sys_cta0[s + 1];
+    if (!last_of(&S.sys_counter[s], (unsigned)(cb - ca))) return;
+    bdots_finish(partial, ca, cb, 1, o);
+    if (threadIdx.x < R8) out[s * R8 + threadIdx.x] = o[threadIdx.x];
+    if (threadIdx.x == 0) S.sys_counter[s] = 0u;
+}
+
+// Before the first cycle: pair tolerances and states from ||b_p||^2 (in rn2).
+__global__ void k_binit(BatchKrylov K, double rtol, int maxit) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < K.npair; p += gridDim.x * blockDim.x) {
+        const double bn2 = K.rn2[p];
+        const bool fin = isfinite(bn2);
+        K.tol[p] = rtol * sqrt(fin ? bn2 : 0.0);
+        K.active[p] = (fin && bn2 > 0.0) ? 1 : 0;
+        K.conv[p] = (fin && bn2 == 0.0) ? 1 : 0;
+        K.bad[p] = fin ? 0 : 1;
+        K.its[p] = 0;
+        K.restarts[p] = 0;
+        K.run[p] = 0;
+        K.jdone[p] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *K.iters = 0;
+        *K.maxit = maxit;
+        *K.j = 0;
+    }
+}
+
+// Cycle start: g_p = (||r_p||, 0, ...), pairs still active run; V[:,0] = r_p / ||r_p||.
+__global__ void k_bcycle_start(BatchKrylov K, cudaGraphConditionalHandle inner, int use_cond) {
+    __shared__ int anyrun;
+    if (threadIdx.x == 0) anyrun = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < K.npair; p += blockDim.x) {
+        double *g = K.g + (int64_t)p * (K.m + 2);
+        for (int i = 0; i <= K.m; ++i) g[i] = 0.0;
+        g[0] = sqrt(K.rn2[p]);
+        K.run[p] = K.active[p];
+        K.jdone[p] = 0;
+        if (K.active[p]) anyrun = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *K.j = 0;
+        K.any[0] = anyrun;
+        if (use_cond) cudaGraphSetConditional(inner, anyrun ? 1u : 0u);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_bscale(const BatchSegs S, BatchKrylov K, const double *__restrict__ r, double *__restrict__ V,
+         double *__restrict__ vin) {
+    const int c = blockIdx.x, s = S.cta_sys[c];
+    __shared__ double inv[R8];
+    if (threadIdx.x < R8) {
+        const int p = s * R8 + threadIdx.x;
+        inv[threadIdx.x] = K.active[p] ? 1.0 / sqrt(K.rn2[p]) : 0.0;
+    }
+    __syncthreads();
+    for (int64_t idx = S.cta_r0[c] * R8 + threadIdx.x; idx < S.cta_r1[c] * R8; idx += blockDim.x) {
+        const double v = r[idx] * inv[idx % R8];
+        V[idx] = v;
+        vin[idx] = v;
+    }
+}
+
+// End of a step: next column while any pair is still running.
+__global__ void k_bstep_end(BatchKrylov K, cudaGraphConditionalHandle inner, int use_cond) {
+    __shared__ int anyrun;
+    if (threadIdx.x == 0) anyrun = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < K.npair; p += blockDim.x)
+        if (K.run[p]) anyrun = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (anyrun) *K.j += 1;
+        K.any[0] = anyrun;
+        if (use_cond) cudaGraphSetConditional(inner, anyrun ? 1u : 0u);
+    }
+}
+
+// y_p = R_p^{-1} g_p (one thread per pair).
+__global__ void k_blsq(BatchKrylov K) {
+    const int m = K.m, m1 = m + 1;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < K.npair; p += gridDim.x * blockDim.x) {
+        const int jd = K.active[p] ? K.jdone[p] : 0;
+        const double *H = K.H + (int64_t)p * m1 * m;
+        const double *g = K.g + (int64_t)p * (m + 2);
+        double *y = K.y + (int64_t)p * (m + 2);
+        for (int i = jd - 1; i >= 0; --i) {
+            double sum = g[i];
+            for (int t = i + 1; t < jd; ++t) sum -= H[(int64_t)t * m1 + i] * y[t];
+            y[i] = sum / H[(int64_t)i * m1 + i];
+        }
+        for (int i = jd; i <= m; ++i) y[i] = 0.0;
+    }
+}
+
+// x_p += Z_p y_p
+__global__ void __launch_bounds__(256)
+k_bupdate_x(const BatchSegs S, BatchKrylov K, const double *__restrict__ Z, int64_t ldz, double *__restrict__ x) {
+    __shared__ double ys[R8][kMaxCols];
+    __shared__ int jd[R8];
+    const int c = blockIdx.x, s = S.cta_sys[c];
+    if (threadIdx.x < R8) {
+        const int p = s * R8 + threadIdx.x;
+        jd[threadIdx.x] = K.active[p] ? K.jdone[p] : 0;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < R8 * K.m; idx += blockDim.x) {
+        const int rr = idx / K.m, cc = idx % K.m;
+        ys[rr][cc] = K.y[(int64_t)(s * R8 + rr) * (K.m + 2) + cc];
+    }
+    __syncthreads();
+    for (int64_t idx = S.cta_r0[c] * R8 + threadIdx.x; idx < S.cta_r1[c] * R8; idx += blockDim.x) {
+        const int rr = (int)(idx % R8);
+        double acc = x[idx];
+        for (int cc = 0; cc < jd[rr]; ++cc) acc += Z[(int64_t)cc * ldz + idx] * ys[rr][cc];
+        x[idx] = acc;
+    }
+}
+
+// End of a cycle: true residual test per pair (rn2 holds ||b - A x||^2).
+__global__ void k_bcycle_end(BatchKrylov K, cudaGraphConditionalHandle outer, int use_cond) {
+    __shared__ int anyact, jmax;
+    if (threadIdx.x == 0) { anyact = 0; jmax = 0; }
+    __syncthreads();
+    for (int p = threadIdx.x; p < K.npair; p += blockDim.x) {
+        if (!K.active[p]) continue;
+        atomicMax(&jmax, K.jdone[p]);
+        K.its[p] += K.jdone[p];
+        const double rn = sqrt(K.rn2[p]);
+        if (!isfinite(rn) || K.bad[p]) {
+            K.bad[p] = 1;
+            K.active[p] = 0;
+        } else if (rn <= K.tol[p]) {
+            K.conv[p] = 1;
+            K.active[p] = 0;
+        } else {
+            K.restarts[p] += 1;
+            anyact = 1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *K.iters += jmax;
+        const int again = anyact && *K.iters < *K.maxit;
+        K.any[1] = again;
+        if (use_cond) cudaGraphSetConditional(outer, again ? 1u : 0u);
+    }
+}
+
+// Gather / scatter between the user layout (system s: n_s x nrhs, column-major)
+// and the batch layout (permuted rows, 8 interleaved rhs).
+__global__ void k_bgather(int64_t nrows, const int32_t *__restrict__ sys_of, const int64_t *__restrict__ perm_g,
+                          const int64_t *__restrict__ usr_off, const int64_t *__restrict__ nsz, int nrhs,
+                          const double *__restrict__ src, double *__restrict__ dst) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nrows * R8) return;
+    const int64_t g = idx / R8;
+    const int r = (int)(idx % R8);
+    const int s = sys_of[g];
+    dst[idx] = r < nrhs ? src[usr_off[s] + (int64_t)r * nsz[s] + perm_g[g]] : 0.0;
+}
+__global__ void k_bscatter(int64_t nrows, const int32_t *__restrict__ sys_of, const int64_t *__restrict__ perm_g,
+                           const int64_t *__restrict__ usr_off, const int64_t *__restrict__ nsz, int nrhs,
+                           const double *__restrict__ src, double *__restrict__ dst) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nrows * R8) return;
+    const int64_t g = idx / R8;
+    const int r = (int)(idx % R8);
+    if (r >= nrhs) return;
+    const int s = sys_of[g];
+    dst[usr_off[s] + (int64_t)r * nsz[s] + perm_g[g]] = src[idx];
+}
+
+// ---- launchers ----------------------------------------------------------------------------
+void launch_btrsv(const BatchLevel &lv, int mode, bool smem, size_t smem_bytes, const double *in, float *work,
+                  double *out_final, float *scratch, cudaStream_t st) {
+    if (lv.nblk == 0) return;
+    if (mode == 0) {
+        if (smem) k_btrsv<0, true><<<lv.nblk, kTrsvThreads2, smem_bytes, st>>>(lv, in, work, out_final, scratch);
+        else k_btrsv<0, false><<<lv.nblk, kTrsvThreads2, kRingBytes, st>>>(lv, in, work, out_final, scratch);
+    } else {
+        if (smem) k_btrsv<1, true><<<lv.nblk, kTrsvThreads2, smem_bytes, st>>>(lv, in, work, out_final, scratch);
+        else k_btrsv<1, false><<<lv.nblk, kTrsvThreads2, kRingBytes, st>>>(lv, in, work, out_final, scratch);
+    }
+    count_launch();
+}
+void set_btrsv_smem_limit(int bytes) {
+    cudaFuncSetAttribute(k_btrsv<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_btrsv<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_btrsv<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
+    cudaFuncSetAttribute(k_btrsv<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
+}
+void launch_bcouple(const BatchLevel &lv, const double *in, float *work, cudaStream_t st) {
+    if (lv.ncta == 0) return;
+    k_bcouple<<<lv.ncta, kBatchThreads, 0, st>>>(lv, in, work);
+    count_launch();
+}
+void launch_blowrank(const BatchLevel &lv, float *work, cudaStream_t st) {
+    if (lv.ncta == 0) return;
+    k_blowrank<<<lv.ncta, kBatchThreads, 0, st>>>(lv, work);
+    count_launch();
+}
+void launch_bspmv(int64_t nrows, const int64_t *rp, const int32_t *ci, const double *v, const double *x,
+                  const double *b, double *y, double *zcol, const int32_t *jp, int64_t ld, cudaStream_t st) {
+    const int64_t n = nrows * R8;
+    if (n == 0) return;
+    k_bspmv<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nrows, rp, ci, v, x, b, y, zcol, jp, ld);
+    count_launch();
+}
+void launch_bgs(int pass, const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, double *w,
+                cudaStream_t st) {
+    k_bgs<<<S.ncta, 256, 0, st>>>(pass, S, K, V, ldv, w);
+    count_launch();
+}
+void launch_bgs_final(const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, const double *w, double *vin,
+                      cudaStream_t st) {
+    k_bgs_final<<<S.ncta, 256, 0, st>>>(S, K, V, ldv, w, vin);
+    count_launch();
+}
+void launch_bnorm2(const BatchSegs &S, double *partial, const double *x, double *out, cudaStream_t st) {
+    k_bnorm2<<<S.ncta, 256, 0, st>>>(S, partial, x, out);
+    count_launch();
+}
+void launch_binit(const BatchKrylov &K, double rtol, int maxit, cudaStream_t st) {
+    k_binit<<<(K.npair + 255) / 256, 256, 0, st>>>(K, rtol, maxit);
+    count_launch();
+}
+void launch_bcycle_start(const BatchKrylov &K, cudaGraphConditionalHandle h, int use_cond, cudaStream_t st) {
+    k_bcycle_start<<<1, 1024, 0, st>>>(K, h, use_cond);
+    count_launch();
+}
+void launch_bscale(const BatchSegs &S, const BatchKrylov &K, const double *r, double *V, double *vin, cudaStream_t st) {
+    k_bscale<<<S.ncta, 256, 0, st>>>(S, K, r, V, vin);
+    count_launch();
+}
+void launch_bstep_end(const BatchKrylov &K, cudaGraphConditionalHandle h, int use_cond, cudaStream_t st) {
+    k_bstep_end<<<1, 1024, 0, st>>>(K, h, use_cond);
+    count_launch();
+}
+void launch_blsq(const BatchKrylov &K, cudaStream_t st) {
+    k_blsq<<<(K.npair + 127) / 128, 128, 0, st>>>(K);
+    count_launch();
+}
+void launch_bupdate_x(const BatchSegs &S, const BatchKrylov &K, const double *Z, int64_t ldz, double *x,
+                      cudaStream_t st) {
+    k_bupdate_x<<<S.ncta, 256, 0, st>>>(S, K, Z, ldz, x);
+    count_launch();
+}
+void launch_bcycle_end(const BatchKrylov &K, cudaGraphConditionalHandle h, int use_cond, cudaStream_t st) {
+    k_bcycle_end<<<1, 1024, 0, st>>>(K, h, use_cond);
+    count_launch();
+}
+void launch_bgather(int64_t nrows, const int32_t *sys_of, const int64_t *perm_g, const int64_t *usr_off,
+                    const int64_t *nsz, int nrhs, const double *src, double *dst, cudaStream_t st) {
+    const int64_t n = nrows * R8;
+    if (n == 0) return;
+    k_bgather<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nrows, sys_of, perm_g, usr_off, nsz, nrhs, src, dst);
+    count_launch();
+}
+void launch_bscatter(int64_t nrows, const int32_t *sys_of, const int64_t *perm_g, const int64_t *usr_off,
+                     const int64_t *nsz, int nrhs, const double *src, double *dst, cudaStream_t st) {
+    const int64_t n = nrows * R8;
+    if (n == 0) return;
+    k_bscatter<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nrows, sys_of, perm_g, usr_off, nsz, nrhs, src, dst);
+    count_launch();
+}
+
+}  // namespace gemslr

@@ -117,10 +117,6 @@ void *Arena::alloc(size_t bytes) {
 
 namespace {
 
-template <typename T> T cast_to(double v);
-template <> double cast_to<double>(double v) { return v; }
-template <> float cast_to<float>(double v) { return (float)v; }
-template <> __nv_bfloat16 cast_to<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
 
 // Every entry must lie in its row's diagonal block, strictly below (L) or on
 // and above (U) the diagonal, and U needs a nonzero diagonal: the kernels
@@ -143,6 +139,8 @@ void validate_tri(const Csr &T, const std::vector<int64_t> &bp, bool upper) {
 
 size_t pad16(size_t x) { return (x + 15) & ~size_t(15); }
 
+}  // namespace
+
 template <typename VT>
 int64_t chunk_slots(int64_t maxlen) {
     return LanesPerRow<VT>::value == 1 ? maxlen : 4 * ((maxlen + 3) / 4);
@@ -155,17 +153,10 @@ size_t chunk_bytes(int64_t nrows, int64_t maxlen, bool upper) {
     return 16 + 8 * pr + pad16(ne * 4) + pad16(ne * sizeof(VT)) + (upper ? pad16((size_t)nrows * sizeof(VT)) : 0);
 }
 
-template <typename VT>
-struct ChunkHost {
-    std::vector<unsigned char> data;
-    std::vector<int64_t> off{0};
-    std::vector<int32_t> blk_chunk{0};
-    int maxwf_L = 0, maxwf_U = 0;
-};
-
 // Append the chunks of one triangular factor of block [r0, r1) (see kernels.cuh).
 template <typename VT>
-void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, ChunkHost<VT> &out, int &maxwf) {
+void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, ChunkHost<VT> &out, int &maxwf,
+                          int max_rows) {
     std::vector<int32_t> lev = upper ? wavefronts_upper(T, r0, r1) : wavefronts_lower(T, r0, r1);
     int nw = 0;
     for (int32_t x : lev) nw = std::max(nw, x + 1);
@@ -186,7 +177,7 @@ void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, Chun
         while (start < R.size()) {
             const int64_t maxlen = nlen[R[start] - r0];
             int64_t n = 0;
-            while (start + n < R.size() && n < kChunkRows &&
+            while (start + n < R.size() && n < max_rows &&
                    chunk_bytes<VT>(n + 1, maxlen, upper) <= (size_t)kStageBytes)
                 ++n;
             if (n == 0) fail(GEMSLR_ERR_UNSUPPORTED, "a factor row has too many entries for the staged substitution");
@@ -227,23 +218,23 @@ void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, Chun
 }
 
 template <typename VT>
-void build_chunks(const Csr &L, const Csr &U, const std::vector<int64_t> &bp, ChunkHost<VT> &out) {
+void build_chunks(const Csr &L, const Csr &U, const std::vector<int64_t> &bp, ChunkHost<VT> &out, int max_rows) {
     validate_tri(L, bp, false);
     validate_tri(U, bp, true);
     for (size_t b = 0; b + 1 < bp.size(); ++b) {
-        append_factor_chunks<VT>(L, bp[b], bp[b + 1], false, out, out.maxwf_L);
-        append_factor_chunks<VT>(U, bp[b], bp[b + 1], true, out, out.maxwf_U);
+        append_factor_chunks<VT>(L, bp[b], bp[b + 1], false, out, out.maxwf_L, max_rows);
+        append_factor_chunks<VT>(U, bp[b], bp[b + 1], true, out, out.maxwf_U, max_rows);
         out.blk_chunk.push_back((int32_t)(out.off.size() - 1));
     }
     if (out.data.empty()) out.data.resize(16, 0);
 }
 
-template <typename T>
-std::vector<T> convert(const std::vector<double> &x) {
-    std::vector<T> y(x.size());
-    for (size_t i = 0; i < x.size(); ++i) y[i] = cast_to<T>(x[i]);
-    return y;
-}
+
+template void build_chunks<float>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<float> &, int);
+template void build_chunks<double>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<double> &, int);
+
+namespace {
+
 
 template <typename VT, typename WT>
 void upload_level(const HostLevel &hl, int64_t n, bool schur, Arena &a, DevLevel<VT, WT> &d, int smem_limit) {
@@ -257,7 +248,7 @@ void upload_level(const HostLevel &hl, int64_t n, bool schur, Arena &a, DevLevel
     for (size_t b = 0; b + 1 < hl.bp.size(); ++b) maxrows = std::max(maxrows, hl.bp[b + 1] - hl.bp[b]);
     d.smem_rows = (kRingBytes + maxrows * (int64_t)sizeof(VT) <= smem_limit) ? (int)maxrows : 0;
     ChunkHost<VT> ch;
-    build_chunks<VT>(hl.L, hl.U, hl.bp, ch);
+    build_chunks<VT>(hl.L, hl.U, hl.bp, ch, kChunkRows);
     v.C.data = a.upload(ch.data);
     v.C.off = a.upload(ch.off);
     v.C.blk_chunk = a.upload(ch.blk_chunk);

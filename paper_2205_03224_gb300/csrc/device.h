@@ -70,6 +70,30 @@ void launch_cycle_end_g(KrylovCtl *ctl, const double *n2r, cudaGraphConditionalH
 void launch_basis_rotate(int64_t len, const double *V, int64_t ldv, int mm, const double *Q, int kk, double *out,
                          cudaStream_t st);
 
+// ---- host-side conversions and the chunk layout of the substitutions ---------------
+template <typename T> inline T cast_to(double v);
+template <> inline double cast_to<double>(double v) { return v; }
+template <> inline float cast_to<float>(double v) { return (float)v; }
+template <> inline __nv_bfloat16 cast_to<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
+template <typename T> inline std::vector<T> convert(const std::vector<double> &x) {
+    std::vector<T> y(x.size());
+    for (size_t i = 0; i < x.size(); ++i) y[i] = cast_to<T>(x[i]);
+    return y;
+}
+
+template <typename VT>
+struct ChunkHost {
+    std::vector<unsigned char> data;
+    std::vector<int64_t> off{0};
+    std::vector<int32_t> blk_chunk{0};
+    int maxwf_L = 0, maxwf_U = 0;
+};
+
+// Chunks (layout in kernels.cuh) of the block-diagonal factors L, U of one
+// level with at most max_rows row slots per chunk.
+template <typename VT>
+void build_chunks(const Csr &L, const Csr &U, const std::vector<int64_t> &bp, ChunkHost<VT> &out, int max_rows);
+
 // ---- device memory arena ------------------------------------------------------------
 class Arena {
   public:

@@ -363,9 +363,12 @@ void fgmres_host_loop(gemslr_ctx *h, int m, cudaStream_t st) {
     read_ctl(h, st);
 }
 
+}  // namespace
+
+namespace gemslr {
 // Add a WHILE conditional node at the current capture position of `cs`;
 // returns its body graph.
-cudaGraph_t capture_while(cudaStream_t cs, cudaGraphConditionalHandle handle) {
+cudaGraph_t capture_while_node(cudaStream_t cs, cudaGraphConditionalHandle handle) {
     cudaStreamCaptureStatus status;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t *deps = nullptr;
@@ -381,6 +384,9 @@ cudaGraph_t capture_while(cudaStream_t cs, cudaGraphConditionalHandle handle) {
     GEMSLR_CUDA(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
     return p.conditional.phGraph_out[0];
 }
+}  // namespace gemslr
+
+namespace {
 
 // The whole solve as one CUDA graph: prologue, then
 //   WHILE (cycle) { cycle start; WHILE (step) { FGMRES step }; cycle end }
@@ -405,7 +411,7 @@ bool ensure_solve_graph(gemslr_ctx *h, int m) {
         launch_zero(n, h->xh, cs);
         GEMSLR_CUDA(cudaMemcpyAsync(h->r, h->bh, 8 * n, cudaMemcpyDeviceToDevice, cs));
         GEMSLR_CUDA(cudaMemcpyAsync(h->n2 + 1, h->n2, 8, cudaMemcpyDeviceToDevice, cs));
-        cudaGraph_t body_cycle = capture_while(cs, hc);
+        cudaGraph_t body_cycle = capture_while_node(cs, hc);
         GEMSLR_CUDA(cudaStreamEndCapture(cs, &g));
         const uint64_t k1 = launches_total();
         cudaGraphConditionalHandle hs;
@@ -413,7 +419,7 @@ bool ensure_solve_graph(gemslr_ctx *h, int m) {
         GEMSLR_CUDA(cudaStreamBeginCaptureToGraph(cs, body_cycle, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
         launch_cycle_start_g(h->ctl, h->g, h->n2 + 1, hs, cs);
         launch_scale_by_norm(n, h->r, h->n2 + 1, h->V, cs, h->vin);
-        cudaGraph_t body_step = capture_while(cs, hs);
+        cudaGraph_t body_step = capture_while_node(cs, hs);
         fgmres_cycle_end(h, cs);
         launch_cycle_end_g(h->ctl, h->n2 + 1, hc, cs);
         GEMSLR_CUDA(cudaStreamEndCapture(cs, &body_cycle));
@@ -469,6 +475,20 @@ gemslr_options normalized(const gemslr_options *opt) {
 }
 
 }  // namespace
+
+namespace gemslr {
+// Single-system setup (factors and low-rank terms, FP64) kept on the host; the
+// device copy used for the Arnoldi products is released afterwards.
+void setup_single_host(const gemslr_csr *A, const gemslr_partition *part, const gemslr_options *opt, Hierarchy &out) {
+    std::unique_ptr<gemslr_ctx> h(new gemslr_ctx());
+    h->opt = normalized(opt);
+    h->opt.precision = GEMSLR_PREC_FP64;
+    Csr M = csr_from_abi(A);
+    build_levels(M, part, &h->opt, h->host);
+    finish_setup(h.get(), true);
+    out = std::move(h->host);
+}
+}  // namespace gemslr
 
 extern "C" {
 
