@@ -257,6 +257,45 @@ const char *gemslr_batch_last_error(void);
 void gemslr_batch_destroy(gemslr_batch b);
 
 /*
+ * Learned interface correction (an addition; the paper has no counterpart).
+ * At the deepest Schur level l* = nlev-2, after M^{-1}'s recursion has
+ * produced y2 from z2, the stage computes rho = z2 - S_hat y2 with
+ * S_hat = C - E (U^{-1} L^{-1}) F of that level (Sec. 2.4) and adds
+ * (||rho||/d) * net(rho/||rho||), net a 4-layer 27-tap 3-D convolution network
+ * over the level's unknowns (BF16 weights, FP32 accumulation), d the mean
+ * |diagonal| of S_hat.  The application becomes nonlinear, which flexible
+ * GMRES tolerates (Sec. 5 set-up).
+ * gemslr_learned_train: coords (n x 3 grid coordinates, original order) give
+ * the sites; generates npairs (rho, S_hat^{-1} rho) pairs with rho = z - S_hat
+ * M_S^{-1} z (z ~ U[-1,1) from splitmix64(seed ^ 0x5eed), M_S^{-1} the
+ * method's own level-l* application), trains with Adam on the relative
+ * squared error, enables the stage; loss_history (epochs entries, may be
+ * NULL) receives the mean training loss per epoch.
+ * gemslr_learned_enable: switch the stage on or off.
+ * gemslr_learned_info: out[0..3] = sites, channels, d, parameter count.
+ * gemslr_learned_params: get (get != 0) or set the FP32 master parameters,
+ * flattened as W_0, b_0, ..., W_3, b_3 with W_l[t][c_in][c_out] (t = 27 taps,
+ * t = (dz+1)*9 + (dy+1)*3 + (dx+1)); setting refreshes the BF16 copies.
+ * gemslr_learned_loss_grad: mean loss and parameter gradients (same layout)
+ * for nb given scaled inputs x and targets y (nb x sites, row-major).
+ */
+typedef struct {
+    int32_t channels;   /* hidden channels (<= 32)          */
+    int32_t npairs;     /* training pairs                   */
+    int32_t epochs;
+    int32_t batch;
+    double lr;          /* Adam step size                   */
+    uint64_t seed;
+} gemslr_learned_opts;
+gemslr_status gemslr_learned_train(gemslr_handle h, const int32_t *coords, const gemslr_learned_opts *o,
+                                   double *loss_history);
+gemslr_status gemslr_learned_enable(gemslr_handle h, int32_t on);
+gemslr_status gemslr_learned_info(gemslr_handle h, double *out);
+gemslr_status gemslr_learned_params(gemslr_handle h, int32_t get, double *params, int64_t n);
+gemslr_status gemslr_learned_loss_grad(gemslr_handle h, int32_t nb, const double *x, const double *y, double *loss,
+                                       double *grad);
+
+/*
  * Instrumentation (not part of the method; process-wide, thread-safe).
  * gemslr_kernel_launches: number of CUDA kernels this library has launched.
  * gemslr_profile_enable: with on != 0 every instrumented launch is bracketed

@@ -44,6 +44,11 @@ class Factors(ctypes.Structure):
     _fields_ = [("nlev", i32), ("levels", ctypes.POINTER(LevelFactors)), ("last_L", Mat), ("last_U", Mat)]
 
 
+class LearnedOpts(ctypes.Structure):
+    _fields_ = [("channels", i32), ("npairs", i32), ("epochs", i32), ("batch", i32), ("lr", f64),
+                ("seed", ctypes.c_uint64)]
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [("restart", i32), ("maxit", i32), ("rtol", f64)]
 
@@ -63,6 +68,8 @@ EXPORTED = [
     "gemslr_profile_enable", "gemslr_profile_reset", "gemslr_profile_read",
     "gemslr_setup_batch", "gemslr_batch_apply", "gemslr_batch_fgmres_solve", "gemslr_batch_stats",
     "gemslr_batch_last_error", "gemslr_batch_destroy",
+    "gemslr_learned_train", "gemslr_learned_enable", "gemslr_learned_info", "gemslr_learned_params",
+    "gemslr_learned_loss_grad",
 ]
 
 _lib = None
@@ -112,6 +119,11 @@ def load():
     L.gemslr_batch_stats.argtypes = [P, P, i32]
     L.gemslr_batch_last_error.restype = ctypes.c_char_p
     L.gemslr_batch_last_error.argtypes = []
+    L.gemslr_learned_train.argtypes = [P, P, ctypes.POINTER(LearnedOpts), P]
+    L.gemslr_learned_enable.argtypes = [P, i32]
+    L.gemslr_learned_info.argtypes = [P, P]
+    L.gemslr_learned_params.argtypes = [P, i32, P, i64]
+    L.gemslr_learned_loss_grad.argtypes = [P, i32, P, P, P, P]
     L.gemslr_batch_destroy.argtypes = [P]
     L.gemslr_batch_destroy.restype = None
     for name in EXPORTED:

@@ -133,6 +133,40 @@ class Gemslr:
                     nnz_factors=int(out[4]), bytes_per_apply=float(out[5]), setup_ms=float(out[6]),
                     device_bytes=int(out[7]), levels=lev)
 
+    # ---- learned interface correction (an addition to the method) ----
+    def learned_train(self, coords, channels=32, npairs=20000, epochs=10, batch=64, lr=1e-3, seed=4):
+        """Train the level-l* correction network on the method's own pairs; returns the loss per epoch."""
+        coords = np.ascontiguousarray(coords, dtype=np.int32).reshape(-1, 3)
+        o = L.LearnedOpts(channels, npairs, epochs, batch, lr, seed)
+        hist = np.zeros(max(epochs, 1))
+        L.check(self._lib.gemslr_learned_train(self._h, L.ptr(coords), ctypes.byref(o), L.ptr(hist)))
+        return hist[:epochs]
+
+    def learned_enable(self, on=True):
+        L.check(self._lib.gemslr_learned_enable(self._h, 1 if on else 0))
+
+    def learned_info(self):
+        out = np.zeros(4)
+        L.check(self._lib.gemslr_learned_info(self._h, L.ptr(out)))
+        return dict(sites=int(out[0]), channels=int(out[1]), dscale=float(out[2]), nparams=int(out[3]))
+
+    def learned_params(self, params=None):
+        n = self.learned_info()["nparams"]
+        if params is None:
+            out = np.zeros(n)
+            L.check(self._lib.gemslr_learned_params(self._h, 1, L.ptr(out), n))
+            return out
+        params = np.ascontiguousarray(params, dtype=np.float64)
+        L.check(self._lib.gemslr_learned_params(self._h, 0, L.ptr(params), n))
+
+    def learned_loss_grad(self, x, y):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        loss = np.zeros(1)
+        grad = np.zeros(self.learned_info()["nparams"])
+        L.check(self._lib.gemslr_learned_loss_grad(self._h, x.shape[0], L.ptr(x), L.ptr(y), L.ptr(loss), L.ptr(grad)))
+        return float(loss[0]), grad
+
     def export_factors(self):
         """Copy the factors to host (dict with the layout of ``from_factors``)."""
         import scipy.sparse as sp

@@ -316,6 +316,8 @@ void apply_levels(DevHierarchy<VT, WT> &d, int from, const double *in, VT *work,
     static const char *kUp[] = {"trsv_up_L0", "trsv_up_L1", "trsv_up_L2", "trsv_up_L3", "trsv_up_L4+"};
     static const char *kCouple[] = {"couple_EWt_L0", "couple_EWt_L1", "couple_EWt_L2", "couple_EWt_L3", "couple_EWt_L4+"};
     static const char *kLow[] = {"lowrank_Wu_L0", "lowrank_Wu_L1", "lowrank_Wu_L2", "lowrank_Wu_L3", "lowrank_Wu_L4+"};
+    // learned correction at the deepest Schur level (active only when that level is part of this application)
+    const bool learn = d.learned && d.learned->enabled && nl >= 1 && from <= nl - 1;
     for (int l = from; l < nl; ++l) {
         DevLevel<VT, WT> &L = d.lev[l];
         const double *src = (l == from) ? in : nullptr;
@@ -327,6 +329,7 @@ void apply_levels(DevHierarchy<VT, WT> &d, int from, const double *in, VT *work,
             ProfScope ps(kCouple[std::min(l, 4)], st);
             launch_couple<VT, WT>(L.view, src, work, d.partial, d.counter, d.u, st);
         }
+        if (learn && l == nl - 1) learned_save<VT>(*d.learned, L.view.e, work, st);   // z2 of level l*
         {
             ProfScope ps(kLow[std::min(l, 4)], st);
             launch_lowrank<VT, WT>(L.view, work, d.u, st);
@@ -334,8 +337,23 @@ void apply_levels(DevHierarchy<VT, WT> &d, int from, const double *in, VT *work,
     }
     {
         ProfScope ps("trsv_last", st);
-        launch_trsv<VT, WT>(d.last.view, 0, d.last.smem_rows, from == nl ? in : nullptr, work, out_final,
-                            d.scratch, st);
+        launch_trsv<VT, WT>(d.last.view, 0, d.last.smem_rows, from == nl ? in : nullptr, work,
+                            learn ? nullptr : out_final, d.scratch, st);
+    }
+    if (learn) {
+        // S_hat y2 = C y2 - E (LU)^{-1} F y2 on a scratch vector, then y2 += N(rho)
+        ProfScope ps("learned_stage", st);
+        DevLevel<VT, WT> &L = d.lev[nl - 1];
+        LearnedStage<VT> &Ls = *d.learned;
+        const int64_t e = L.view.e, s0 = L.view.s, ntail = L.view.stail;
+        GEMSLR_CUDA(cudaMemcpyAsync(Ls.work2 + e, work + e, sizeof(VT) * ntail, cudaMemcpyDeviceToDevice, st));
+        GEMSLR_CUDA(cudaMemsetAsync(Ls.work2 + s0, 0, sizeof(VT) * (e - s0), st));
+        launch_trsv<VT, WT>(L.view, 1, L.smem_rows, nullptr, Ls.work2, nullptr, d.scratch, st);
+        LevelView<VT, WT> v0 = L.view;
+        v0.k = 0;
+        launch_couple<VT, WT>(v0, Ls.zeros, Ls.work2, d.partial, d.counter, d.u, st);
+        learned_rho_and_update<VT>(Ls, e, work, st);
+        if (out_final) launch_cast_out<VT>(ntail, work + e, out_final + e, st);
     }
     for (int l = nl - 1; l >= from; --l) {
         ProfScope ps(kUp[std::min(l, 4)], st);

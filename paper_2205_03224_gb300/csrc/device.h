@@ -7,6 +7,7 @@
 
 #include "internal.h"
 #include "kernels.cuh"
+#include "learned.cuh"
 
 namespace gemslr {
 
@@ -131,7 +132,23 @@ struct DevHierarchy {
     unsigned *counter = nullptr;
     VT *u = nullptr;                     // kMaxRank
     int32_t *err = nullptr;              // device error word of the substitution kernels
+    LearnedStage<VT> *learned = nullptr; // optional learned correction at the deepest Schur level
 };
+
+// Learned-stage glue (learned.cu).
+template <typename VT> void learned_save(const LearnedStage<VT> &L, int64_t e, const VT *work, cudaStream_t st);
+template <typename VT> void learned_rho_and_update(const LearnedStage<VT> &L, int64_t e, VT *work, cudaStream_t st);
+template <typename VT> void launch_cast_out(int64_t n, const VT *src, double *dst, cudaStream_t st);
+void net_forward(NetDev &net, int N, const float *x0, float *const zs[4], float *const hs[3], cudaStream_t st);
+void net_backward(NetDev &net, int N, const float *x0, float *const zs[4], float *const hs[3], float *dout,
+                  float *gbuf0, float *gbuf1, float *part, int nchunk, cudaStream_t st);
+void net_adam(NetDev &net, float lr, cudaStream_t st);
+void net_sync_bf16(NetDev &net, cudaStream_t st);
+void launch_uniform(uint64_t seed, int64_t count, double *out, cudaStream_t st);
+void launch_dgemm(int M, int N, int K, const double *A, const double *B, double *C, cudaStream_t st);
+void launch_scale_pairs(int S, int count, const double *R, const double *T, double d, float *X, float *Y,
+                        cudaStream_t st);
+void launch_loss(int S, int N, const float *out, const float *tgt, float *dout, float *loss, cudaStream_t st);
 
 // Build the device copy of a host hierarchy.
 template <typename VT, typename WT>

@@ -5,10 +5,20 @@
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <unordered_map>
 
 #include "device.h"
 
 using namespace gemslr;
+
+// Learned interface correction state of a handle (network and in-apply buffers).
+struct LearnedHost {
+    NetDev net;
+    LearnedStage<double> st64;
+    LearnedStage<float> st32;
+    int lstar = -1;
+    int64_t e = 0;
+};
 
 struct gemslr_ctx {
     Hierarchy host;
@@ -44,7 +54,9 @@ struct gemslr_ctx {
     int graph_m = 0;
     bool graph_failed = false;
     uint64_t graph_k_top = 0, graph_k_cycle = 0, graph_k_step = 0;
+    LearnedHost *learned = nullptr;
     ~gemslr_ctx() {
+        delete learned;
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (graph) cudaGraphDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -788,6 +800,405 @@ void gemslr_profile_reset(void) { profile_reset(); }
 
 int32_t gemslr_profile_read(char *names, size_t len, double *ms, int64_t *counts, int32_t maxn) {
     return profile_read(names, len, ms, counts, maxn);
+}
+
+}  // extern "C"
+
+// ---- learned interface correction (not in the paper) ------------------------------------
+namespace {
+
+// Dense S_hat = C - E (LU)^{-1} F of level l (host, FP64) from the host factors.
+std::vector<double> dense_schur(const Hierarchy &H, int l, std::vector<double> &diag) {
+    const HostLevel &hl = H.lev[l];
+    const int64_t d = hl.e - hl.s, S = H.n - hl.e;
+    std::vector<double> X((size_t)d * S, 0.0), col(d);
+    for (int64_t j = 0; j < S; ++j) {
+        std::fill(col.begin(), col.end(), 0.0);
+        for (int64_t i = 0; i < d; ++i)
+            for (int64_t p = hl.F.rp[i]; p < hl.F.rp[i + 1]; ++p)
+                if (hl.F.ci[p] == j) col[i] = hl.F.v[p];
+        for (int64_t i = 0; i < d; ++i) {               // L y = col (unit lower)
+            double s = col[i];
+            for (int64_t p = hl.L.rp[i]; p < hl.L.rp[i + 1]; ++p) s -= hl.L.v[p] * col[hl.L.ci[p]];
+            col[i] = s;
+        }
+        for (int64_t i = d - 1; i >= 0; --i) {          // U x = y
+            double s = col[i], dg = 1.0;
+            for (int64_t p = hl.U.rp[i]; p < hl.U.rp[i + 1]; ++p) {
+                if (hl.U.ci[p] == i) dg = hl.U.v[p];
+                else s -= hl.U.v[p] * col[hl.U.ci[p]];
+            }
+            col[i] = s / dg;
+        }
+        std::copy(col.begin(), col.end(), X.begin() + (size_t)j * d);
+    }
+    std::vector<double> Sh((size_t)S * S, 0.0);       // column-major
+    for (int64_t i = 0; i < S; ++i)
+        for (int64_t p = H.Ahat.rp[hl.e + i]; p < H.Ahat.rp[hl.e + i + 1]; ++p) {
+            const int64_t c = H.Ahat.ci[p] - hl.e;
+            if (c >= 0) Sh[(size_t)c * S + i] += H.Ahat.v[p];
+        }
+    for (int64_t i = 0; i < S; ++i)
+        for (int64_t p = hl.E.rp[i]; p < hl.E.rp[i + 1]; ++p) {
+            const int64_t k = hl.E.ci[p];
+            const double ev = hl.E.v[p];
+            for (int64_t j = 0; j < S; ++j) Sh[(size_t)j * S + i] -= ev * X[(size_t)j * d + k];
+        }
+    diag.resize(S);
+    for (int64_t i = 0; i < S; ++i) diag[i] = Sh[(size_t)i * S + i];
+    return Sh;
+}
+
+// Dense level-l* preconditioner M_S^{-1} = C~^{-1} (I + W H W^T), C~^{-1} the last-level block LU.
+std::vector<double> dense_level_prec(const Hierarchy &H, int l) {
+    const HostLevel &hl = H.lev[l];
+    const HostLevel &la = H.last;
+    const int64_t S = H.n - hl.e;
+    if (l != (int)H.lev.size() - 1 || la.s != hl.e) fail(GEMSLR_ERR_UNSUPPORTED, "learned stage needs the deepest level");
+    std::vector<double> P((size_t)S * S, 0.0), z(S), t;
+    const int k = hl.k;
+    for (int64_t j = 0; j < S; ++j) {
+        std::fill(z.begin(), z.end(), 0.0);
+        z[j] = 1.0;
+        if (k > 0) {
+            t.assign(k, 0.0);
+            std::vector<double> u(k, 0.0);
+            for (int c = 0; c < k; ++c) t[c] = hl.W[(size_t)c * S + j];
+            for (int a = 0; a < k; ++a)
+                for (int c = 0; c < k; ++c) u[a] += hl.H[a + (size_t)c * k] * t[c];
+            for (int64_t i = 0; i < S; ++i)
+                for (int c = 0; c < k; ++c) z[i] += hl.W[(size_t)c * S + i] * u[c];
+        }
+        for (int64_t i = 0; i < S; ++i) {
+            double s = z[i];
+            for (int64_t p = la.L.rp[i]; p < la.L.rp[i + 1]; ++p) s -= la.L.v[p] * z[la.L.ci[p]];
+            z[i] = s;
+        }
+        for (int64_t i = S - 1; i >= 0; --i) {
+            double s = z[i], dg = 1.0;
+            for (int64_t p = la.U.rp[i]; p < la.U.rp[i + 1]; ++p) {
+                if (la.U.ci[p] == i) dg = la.U.v[p];
+                else s -= la.U.v[p] * z[la.U.ci[p]];
+            }
+            z[i] = s / dg;
+        }
+        std::copy(z.begin(), z.end(), P.begin() + (size_t)j * S);
+    }
+    return P;
+}
+
+// In-place inverse of a dense column-major matrix (Gauss-Jordan, partial pivoting).
+void dense_inverse(std::vector<double> &A, int64_t n) {
+    std::vector<double> Inv((size_t)n * n, 0.0);
+    for (int64_t i = 0; i < n; ++i) Inv[(size_t)i * n + i] = 1.0;
+    for (int64_t c = 0; c < n; ++c) {
+        int64_t piv = c;
+        for (int64_t i = c + 1; i < n; ++i)
+            if (std::fabs(A[(size_t)c * n + i]) > std::fabs(A[(size_t)c * n + piv])) piv = i;
+        if (A[(size_t)c * n + piv] == 0.0) fail(GEMSLR_ERR_NOT_CONVERGED, "S_hat is singular");
+        if (piv != c)
+            for (int64_t j = 0; j < n; ++j) {
+                std::swap(A[(size_t)j * n + c], A[(size_t)j * n + piv]);
+                std::swap(Inv[(size_t)j * n + c], Inv[(size_t)j * n + piv]);
+            }
+        const double inv = 1.0 / A[(size_t)c * n + c];
+        for (int64_t j = 0; j < n; ++j) {
+            A[(size_t)j * n + c] *= inv;
+            Inv[(size_t)j * n + c] *= inv;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            if (i == c) continue;
+            const double f = A[(size_t)c * n + i];
+            if (f == 0.0) continue;
+            for (int64_t j = 0; j < n; ++j) {
+                A[(size_t)j * n + i] -= f * A[(size_t)j * n + c];
+                Inv[(size_t)j * n + i] -= f * Inv[(size_t)j * n + c];
+            }
+        }
+    }
+    A.swap(Inv);
+}
+
+std::vector<double> splitmix_uniform01(uint64_t seed, int64_t count) {
+    std::vector<double> v(count);
+    uint64_t state = seed;
+    for (int64_t i = 0; i < count; ++i) {
+        state += 0x9E3779B97F4A7C15ull;
+        uint64_t z = state;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        v[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    }
+    return v;
+}
+
+// Sites of level l*'s tail, neighbour table, weights (seeded He initialisation).
+void learned_init(gemslr_ctx *h, LearnedHost &Lh, const int32_t *coords, int channels, uint64_t seed) {
+    const Hierarchy &H = h->host;
+    if (H.lev.empty()) fail(GEMSLR_ERR_UNSUPPORTED, "learned stage needs a Schur level");
+    if (channels < 1 || channels > 32) fail(GEMSLR_ERR_ARG, "channels must be in 1..32");
+    Lh.lstar = (int)H.lev.size() - 1;
+    Lh.e = H.lev[Lh.lstar].e;
+    const int64_t S = H.n - Lh.e;
+    NetDev &net = Lh.net;
+    net.S = (int)S;
+    net.C = channels;
+    const int dims[5] = {1, channels, channels, channels, 1};
+    std::unordered_map<uint64_t, int32_t> where;
+    auto key = [](int64_t x, int64_t y, int64_t z) {
+        return ((uint64_t)(x + 1) << 42) | ((uint64_t)(y + 1) << 21) | (uint64_t)(z + 1);
+    };
+    std::vector<int64_t> cx(S), cy(S), cz(S);
+    for (int64_t s = 0; s < S; ++s) {
+        const int64_t o = H.perm[Lh.e + s];
+        cx[s] = coords[3 * o];
+        cy[s] = coords[3 * o + 1];
+        cz[s] = coords[3 * o + 2];
+        where[key(cx[s], cy[s], cz[s])] = (int32_t)s;
+    }
+    std::vector<int32_t> nbr((size_t)S * 27, -1);
+    for (int64_t s = 0; s < S; ++s)
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int t = (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+                    auto it = where.find(key(cx[s] + dx, cy[s] + dy, cz[s] + dz));
+                    nbr[(size_t)s * 27 + t] = it == where.end() ? -1 : it->second;
+                }
+    Arena &a = h->arena;
+    net.nbr = a.upload(nbr);
+    net.nparams = 0;
+    for (int l = 0; l < kNetLayers; ++l) {
+        net.cin[l] = dims[l];
+        net.cout[l] = dims[l + 1];
+        const int64_t nw = 27LL * dims[l] * dims[l + 1];
+        std::vector<double> u = splitmix_uniform01(seed * 100 + (uint64_t)l, nw);
+        const double bound = std::sqrt(6.0 / (27.0 * dims[l])) * (l < 3 ? 1.0 : 0.1);
+        std::vector<float> w(nw);
+        for (int64_t i = 0; i < nw; ++i) w[i] = (float)((2.0 * u[i] - 1.0) * bound);
+        net.W[l] = a.upload(w);
+        net.b[l] = (float *)a.alloc(4 * dims[l + 1]);
+        GEMSLR_CUDA(cudaMemset(net.b[l], 0, 4 * dims[l + 1]));
+        net.Wb[l] = (__nv_bfloat16 *)a.alloc(2 * nw);
+        net.gW[l] = (float *)a.alloc(4 * nw);
+        net.gb[l] = (float *)a.alloc(4 * dims[l + 1]);
+        net.mW[l] = (float *)a.alloc(4 * nw);
+        net.vW[l] = (float *)a.alloc(4 * nw);
+        net.mb[l] = (float *)a.alloc(4 * dims[l + 1]);
+        net.vb[l] = (float *)a.alloc(4 * dims[l + 1]);
+        GEMSLR_CUDA(cudaMemset(net.mW[l], 0, 4 * nw));
+        GEMSLR_CUDA(cudaMemset(net.vW[l], 0, 4 * nw));
+        GEMSLR_CUDA(cudaMemset(net.mb[l], 0, 4 * dims[l + 1]));
+        GEMSLR_CUDA(cudaMemset(net.vb[l], 0, 4 * dims[l + 1]));
+        net.nparams += nw + dims[l + 1];
+    }
+    net.adam_t = 0;
+    net_sync_bf16(net, nullptr);
+    // in-apply buffers for both precisions
+    const HostLevel &hl = H.lev[Lh.lstar];
+    Csr C = submatrix(H.Ahat, hl.e, H.n, hl.e, H.n);
+    auto setup_stage = [&](auto &st, auto tag) {
+        using VT = decltype(tag);
+        st.net = &Lh.net;
+        st.zsave = (VT *)a.alloc(sizeof(VT) * S);
+        st.work2 = (VT *)a.alloc(sizeof(VT) * H.n);
+        st.zeros = h->zeros;
+        st.C_rp = a.upload(C.rp);
+        st.C_ci = a.upload(C.ci);
+        st.C_v = a.upload(convert<VT>(C.v));
+        st.act0 = (float *)a.alloc(4 * S);
+        st.act1 = (float *)a.alloc(4 * S * channels);
+        st.act2 = (float *)a.alloc(4 * S * channels);
+        st.rnorm = (float *)a.alloc(16);
+    };
+    setup_stage(Lh.st64, double(0));
+    setup_stage(Lh.st32, float(0));
+    h->d64.learned = &Lh.st64;
+    if (h->mixed) h->d32.learned = &Lh.st32;
+}
+
+// Batch buffers of one training / gradient pass.
+struct PassBufs {
+    int B = 0;
+    float *zs[4], *hs[3], *g0, *g1, *dout, *loss, *part;
+    int nchunk = 0;
+};
+
+PassBufs pass_bufs(gemslr_ctx *h, const NetDev &net, int B) {
+    PassBufs p;
+    p.B = B;
+    Arena &a = h->arena;
+    const int64_t SC = (int64_t)net.S * net.C * B;
+    for (int l = 0; l < 4; ++l) p.zs[l] = (float *)a.alloc(4 * (l < 3 ? SC : (int64_t)net.S * B));
+    for (int l = 0; l < 3; ++l) p.hs[l] = (float *)a.alloc(4 * SC);
+    p.g0 = (float *)a.alloc(4 * SC);
+    p.g1 = (float *)a.alloc(4 * SC);
+    p.dout = (float *)a.alloc(4 * (int64_t)net.S * B);
+    p.loss = (float *)a.alloc(4 * B);
+    p.nchunk = 64;
+    p.part = (float *)a.alloc(4 * (int64_t)p.nchunk * 27 * net.C * net.C);
+    return p;
+}
+
+// Forward, loss and backward on one batch (x0: B x S inputs, y: targets).
+void train_pass(NetDev &net, PassBufs &pb, const float *x0, const float *y, cudaStream_t st) {
+    net_forward(net, pb.B, x0, pb.zs, pb.hs, st);
+    launch_loss(net.S, pb.B, pb.zs[3], y, pb.dout, pb.loss, st);
+    net_backward(net, pb.B, x0, pb.zs, pb.hs, pb.dout, pb.g0, pb.g1, pb.part, pb.nchunk, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+gemslr_status gemslr_learned_train(gemslr_handle h, const int32_t *coords, const gemslr_learned_opts *o,
+                                   double *loss_history) {
+    return guard([&] {
+        if (!h || !coords || !o) fail(GEMSLR_ERR_ARG, "NULL argument");
+        if (o->npairs < 1 || o->epochs < 0 || o->batch < 1 || !(o->lr > 0)) fail(GEMSLR_ERR_ARG, "invalid learned options");
+        if (!h->learned) h->learned = new LearnedHost();
+        LearnedHost &Lh = *h->learned;
+        learned_init(h, Lh, coords, o->channels, o->seed);
+        NetDev &net = Lh.net;
+        const Hierarchy &H = h->host;
+        const int64_t S = net.S;
+        cudaStream_t st = nullptr;
+        // training pairs (rho, S_hat^{-1} rho) from the method's own level-l* application
+        std::vector<double> diag;
+        std::vector<double> Sh = dense_schur(H, Lh.lstar, diag);
+        std::vector<double> P = dense_level_prec(H, Lh.lstar);
+        double dmean = 0.0;
+        for (double v : diag) dmean += std::fabs(v);
+        net.dscale = S > 0 ? dmean / S : 1.0;
+        Arena &a = h->arena;
+        double *dS = a.upload(Sh), *dP = a.upload(P);
+        double *dR = (double *)a.alloc(8 * (size_t)S * S);
+        launch_dgemm((int)S, (int)S, (int)S, dS, dP, dR, st);                    // S_hat P
+        std::vector<double> R((size_t)S * S);
+        GEMSLR_CUDA(cudaMemcpy(R.data(), dR, 8 * R.size(), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < R.size(); ++i) R[i] = -R[i];
+        for (int64_t i = 0; i < S; ++i) R[(size_t)i * S + i] += 1.0;          // I - S_hat P
+        GEMSLR_CUDA(cudaMemcpy(dR, R.data(), 8 * R.size(), cudaMemcpyHostToDevice));
+        dense_inverse(Sh, S);
+        double *dSi = a.upload(Sh);
+        const int64_t N = o->npairs;
+        double *Z = (double *)a.alloc(8 * (size_t)S * N), *RHO = (double *)a.alloc(8 * (size_t)S * N),
+               *T = (double *)a.alloc(8 * (size_t)S * N);
+        launch_uniform(o->seed ^ 0x5eedULL, (int64_t)S * N, Z, st);
+        launch_dgemm((int)S, (int)N, (int)S, dR, Z, RHO, st);
+        launch_dgemm((int)S, (int)N, (int)S, dSi, RHO, T, st);
+        float *X = (float *)a.alloc(4 * (size_t)S * N), *Y = (float *)a.alloc(4 * (size_t)S * N);
+        launch_scale_pairs((int)S, (int)N, RHO, T, net.dscale, X, Y, st);
+        // training: Adam, sequential batches
+        const int B = std::min<int64_t>(o->batch, N);
+        PassBufs pb = pass_bufs(h, net, B);
+        std::vector<float> lossb(B);
+        for (int ep = 0; ep < o->epochs; ++ep) {
+            double acc = 0.0;
+            int64_t cnt = 0;
+            for (int64_t i0 = 0; i0 + B <= N; i0 += B) {
+                train_pass(net, pb, X + i0 * S, Y + i0 * S, st);
+                net_adam(net, (float)o->lr, st);
+                GEMSLR_CUDA(cudaMemcpyAsync(lossb.data(), pb.loss, 4 * B, cudaMemcpyDeviceToHost, st));
+                GEMSLR_CUDA(cudaStreamSynchronize(st));
+                for (float v : lossb) acc += v;
+                cnt += B;
+            }
+            if (loss_history) loss_history[ep] = cnt ? acc / cnt : 0.0;
+        }
+        GEMSLR_CUDA(cudaDeviceSynchronize());
+        Lh.st64.enabled = Lh.st32.enabled = true;
+        if (h->graph_exec) {                 // the captured solve must include the new stage
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+            cudaGraphDestroy(h->graph);
+            h->graph = nullptr;
+        }
+    });
+}
+
+gemslr_status gemslr_learned_enable(gemslr_handle h, int32_t on) {
+    return guard([&] {
+        if (!h || !h->learned) fail(GEMSLR_ERR_ARG, "no learned stage on this handle");
+        h->learned->st64.enabled = h->learned->st32.enabled = on != 0;
+        if (h->graph_exec) {                 // the captured solve depends on the stage: rebuild on next use
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+            cudaGraphDestroy(h->graph);
+            h->graph = nullptr;
+        }
+    });
+}
+
+gemslr_status gemslr_learned_info(gemslr_handle h, double *out) {
+    return guard([&] {
+        if (!h || !h->learned || !out) fail(GEMSLR_ERR_ARG, "no learned stage on this handle");
+        const NetDev &net = h->learned->net;
+        out[0] = net.S;
+        out[1] = net.C;
+        out[2] = net.dscale;
+        out[3] = (double)net.nparams;
+    });
+}
+
+gemslr_status gemslr_learned_params(gemslr_handle h, int32_t get, double *params, int64_t n) {
+    return guard([&] {
+        if (!h || !h->learned || !params) fail(GEMSLR_ERR_ARG, "no learned stage on this handle");
+        NetDev &net = h->learned->net;
+        if (n != net.nparams) fail(GEMSLR_ERR_ARG, "parameter count mismatch");
+        int64_t off = 0;
+        for (int l = 0; l < kNetLayers; ++l) {
+            const int64_t nw = 27LL * net.cin[l] * net.cout[l], nb = net.cout[l];
+            std::vector<float> w(nw), b(nb);
+            if (get) {
+                GEMSLR_CUDA(cudaMemcpy(w.data(), net.W[l], 4 * nw, cudaMemcpyDeviceToHost));
+                GEMSLR_CUDA(cudaMemcpy(b.data(), net.b[l], 4 * nb, cudaMemcpyDeviceToHost));
+                for (int64_t i = 0; i < nw; ++i) params[off + i] = w[i];
+                for (int64_t i = 0; i < nb; ++i) params[off + nw + i] = b[i];
+            } else {
+                for (int64_t i = 0; i < nw; ++i) w[i] = (float)params[off + i];
+                for (int64_t i = 0; i < nb; ++i) b[i] = (float)params[off + nw + i];
+                GEMSLR_CUDA(cudaMemcpy(net.W[l], w.data(), 4 * nw, cudaMemcpyHostToDevice));
+                GEMSLR_CUDA(cudaMemcpy(net.b[l], b.data(), 4 * nb, cudaMemcpyHostToDevice));
+            }
+            off += nw + nb;
+        }
+        if (!get) {
+            net_sync_bf16(net, nullptr);
+            GEMSLR_CUDA(cudaDeviceSynchronize());
+        }
+    });
+}
+
+gemslr_status gemslr_learned_loss_grad(gemslr_handle h, int32_t nb, const double *x, const double *y, double *loss,
+                                       double *grad) {
+    return guard([&] {
+        if (!h || !h->learned || nb < 1 || !x || !y || !loss || !grad) fail(GEMSLR_ERR_ARG, "invalid argument");
+        NetDev &net = h->learned->net;
+        const int64_t S = net.S;
+        std::vector<float> xf((size_t)nb * S), yf((size_t)nb * S);
+        for (size_t i = 0; i < xf.size(); ++i) { xf[i] = (float)x[i]; yf[i] = (float)y[i]; }
+        Arena tmp;
+        float *dx = tmp.upload(xf), *dy = tmp.upload(yf);
+        PassBufs pb = pass_bufs(h, net, nb);
+        train_pass(net, pb, dx, dy, nullptr);
+        std::vector<float> l(nb);
+        GEMSLR_CUDA(cudaMemcpy(l.data(), pb.loss, 4 * nb, cudaMemcpyDeviceToHost));
+        double acc = 0.0;
+        for (float v : l) acc += v;
+        *loss = acc / nb;
+        int64_t off = 0;
+        for (int lyr = 0; lyr < kNetLayers; ++lyr) {
+            const int64_t nw = 27LL * net.cin[lyr] * net.cout[lyr], nbias = net.cout[lyr];
+            std::vector<float> gw(nw), gbv(nbias);
+            GEMSLR_CUDA(cudaMemcpy(gw.data(), net.gW[lyr], 4 * nw, cudaMemcpyDeviceToHost));
+            GEMSLR_CUDA(cudaMemcpy(gbv.data(), net.gb[lyr], 4 * nbias, cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < nw; ++i) grad[off + i] = gw[i];
+            for (int64_t i = 0; i < nbias; ++i) grad[off + nw + i] = gbv[i];
+            off += nw + nbias;
+        }
+    });
 }
 
 }  // extern "C"

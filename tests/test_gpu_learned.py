@@ -1,0 +1,102 @@
+"""Learned interface correction (an addition to the paper's method).
+
+The GPU network (BF16 weights, FP32 accumulation) must reproduce the FP64
+oracle's loss and gradients at the same (BF16-rounded) weights; training
+must reduce the loss; with the stage on, FGMRES must still reach 1e-8."""
+import numpy as np
+import pytest
+
+import gemslr_inputs as gi
+from oracle.learned import init_params, loss_and_grads, site_neighbors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _bf16(a):
+    """Round float64 -> float32 -> bfloat16 (nearest even) -> float64."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _flat(params):
+    return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params])
+
+
+def _unflat(vec, C):
+    dims = [1, C, C, C, 1]
+    out, off = [], 0
+    for l in range(4):
+        nw = 27 * dims[l] * dims[l + 1]
+        W = vec[off:off + nw].reshape(27, dims[l], dims[l + 1])
+        b = vec[off + nw: off + nw + dims[l + 1]]
+        out.append([W.copy(), b.copy()])
+        off += nw + dims[l + 1]
+    return out
+
+
+@pytest.fixture(scope="module")
+def handle(torch_cuda):
+    from paper_2205_03224_gb300 import Gemslr, partition_geometric
+    A, xyz = gi.stencil3d(14, sigma=0.05)
+    part = partition_geometric(A, xyz, 3, 8)
+    G = Gemslr(A, part, ilu="ilut", tau=1e-3, lfil=10, rank=6)
+    return A, xyz, part, G
+
+
+def test_gradients_match_oracle(handle):
+    A, xyz, part, G = handle
+    C = 8
+    G.learned_train(xyz, channels=C, npairs=64, epochs=0, batch=16, seed=7)
+    info = G.learned_info()
+    S = info["sites"]
+    # same seeded initialisation on both sides
+    ref = init_params(channels=C, seed=7)
+    assert np.allclose(G.learned_params(), _flat(ref), rtol=1e-6, atol=1e-7)
+    # sites = the deepest level's unknowns in the multilevel order
+    e = int(part["level_ptr"][-2])
+    nbr = site_neighbors(xyz[part["perm"][e:]])
+    assert nbr.shape[0] == S
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((5, S))
+    y = rng.standard_normal((5, S))
+    loss, grad = G.learned_loss_grad(x, y)
+    pr = [[_bf16(W), b.copy()] for W, b in ref]   # the GPU passes use BF16 copies of the weights
+    xr, yr = np.asarray(x, np.float32).astype(np.float64), np.asarray(y, np.float32).astype(np.float64)
+    lref, gref = loss_and_grads(pr, xr, yr, nbr)
+    gflat = np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in gref])
+    assert abs(loss - lref) <= 1e-4 * abs(lref)
+    assert np.linalg.norm(grad - gflat) <= 1e-3 * np.linalg.norm(gflat)
+
+
+def test_training_reduces_loss_and_solve_converges(torch_cuda, handle):
+    torch = torch_cuda
+    A, xyz, part, G = handle
+    b = torch.from_numpy(gi.rhs_uniform(A.n, 4)).cuda()
+    G.learned_enable(False) if _has_stage(G) else None
+    x0, i0 = G.solve(b, restart=40, rtol=1e-8)
+    hist = G.learned_train(xyz, channels=16, npairs=2048, epochs=6, batch=32, lr=2e-3, seed=4)
+    assert hist[-1] < hist[0]
+    x1, i1 = G.solve(b, restart=40, rtol=1e-8)
+    res = np.linalg.norm(gi.rhs_uniform(A.n, 4) - A.to_scipy() @ x1.cpu().numpy()) / np.linalg.norm(b.cpu().numpy())
+    assert i1[0]["converged"] and res <= 1e-8
+    G.learned_enable(False)
+    x2, i2 = G.solve(b, restart=40, rtol=1e-8)
+    assert i2[0]["iters"] == i0[0]["iters"]        # switching the stage off restores the method
+
+
+def _has_stage(G):
+    try:
+        G.learned_info()
+        return True
+    except Exception:
+        return False
