@@ -257,6 +257,28 @@ const char *gemslr_batch_last_error(void);
 void gemslr_batch_destroy(gemslr_batch b);
 
 /*
+ * Allocation-free M^{-1} (the paper has no counterpart; an interface
+ * addition).  Same result as gemslr_apply with nrhs = 1, for callers that
+ * cannot allocate device memory when they apply the preconditioner: code
+ * running while a stream is captured into a CUDA graph (cudaMalloc is not
+ * allowed during a global-mode capture), callers whose own pool or allocator
+ * owns all device memory, and latency-critical loops that must not enter the
+ * allocator.  gemslr_apply may allocate its permutation buffers on its first
+ * call; this entry point never calls cudaMalloc, cudaFree or any allocating
+ * routine: the permuted copies of r and z live in a fixed device array of
+ * 2 x 2,097,152 doubles (32 MiB) that every GPU loading the library holds
+ * until the process exits.  Limit: n <= 2,097,152, larger handles are
+ * rejected with GEMSLR_ERR_ARG.  The first call on a device looks up the
+ * array's device address (with that device current), so make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents; every call overwrites all n entries it reads, so
+ * nothing needs clearing, but calls that overlap on the GPU (different
+ * streams, or different handles at once) race on it.  Instrumentation
+ * (gemslr_profile_enable) must be off.
+ */
+gemslr_status gemslr_apply_static(gemslr_handle h, const double *r_dev, double *z_dev, void *stream);
+
+/*
  * Learned interface correction (an addition; the paper has no counterpart).
  * At the deepest Schur level l* = nlev-2, after M^{-1}'s recursion has
  * produced y2 from z2, the stage computes rho = z2 - S_hat y2 with

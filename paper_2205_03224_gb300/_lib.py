@@ -69,7 +69,7 @@ EXPORTED = [
     "gemslr_setup_batch", "gemslr_batch_apply", "gemslr_batch_fgmres_solve", "gemslr_batch_stats",
     "gemslr_batch_last_error", "gemslr_batch_destroy",
     "gemslr_learned_train", "gemslr_learned_enable", "gemslr_learned_info", "gemslr_learned_params",
-    "gemslr_learned_loss_grad",
+    "gemslr_learned_loss_grad", "gemslr_apply_static",
 ]
 
 _lib = None
@@ -124,6 +124,7 @@ def load():
     L.gemslr_learned_info.argtypes = [P, P]
     L.gemslr_learned_params.argtypes = [P, i32, P, i64]
     L.gemslr_learned_loss_grad.argtypes = [P, i32, P, P, P, P]
+    L.gemslr_apply_static.argtypes = [P, P, P, P]
     L.gemslr_batch_destroy.argtypes = [P]
     L.gemslr_batch_destroy.restype = None
     for name in EXPORTED:

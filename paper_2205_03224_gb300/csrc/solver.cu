@@ -5,6 +5,7 @@
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <mutex>
 #include <unordered_map>
 
 #include "device.h"
@@ -1202,3 +1203,51 @@ gemslr_status gemslr_learned_loss_grad(gemslr_handle h, int32_t nb, const double
 }
 
 }  // extern "C"
+
+// ---- allocation-free application -------------------------------------------------------
+// Some callers cannot allocate device memory at the point where they need
+// M^{-1}: code that runs while a stream is being captured into a CUDA graph
+// (cudaMalloc is not allowed there in the global capture mode), callers that
+// hand all device memory to their own pool or allocator and forbid other
+// allocations, and latency-bound loops that must not hit the allocator's
+// synchronisation.  gemslr_apply may allocate its permutation buffers on
+// first use; gemslr_apply_static never does: it keeps the permuted copies of
+// r and z in a fixed file-scope device array.
+namespace {
+constexpr int64_t kStaticRows = int64_t(1) << 21;                  // 2,097,152 rows per vector
+__device__ __align__(256) double g_static_scratch[2 * kStaticRows];  // 32 MiB, held by every GPU that loads the library
+constexpr int kMaxDevices = 64;
+double *g_static_addr[kMaxDevices] = {};
+std::mutex g_static_mu;
+}  // namespace
+
+extern "C" gemslr_status gemslr_apply_static(gemslr_handle h, const double *r_dev, double *z_dev, void *stream) {
+    return guard([&] {
+        if (!h || !r_dev || !z_dev) fail(GEMSLR_ERR_ARG, "NULL argument");
+        if (r_dev == z_dev) fail(GEMSLR_ERR_ARG, "r and z must not alias");
+        const int64_t n = h->host.n;
+        if (n > kStaticRows)
+            fail(GEMSLR_ERR_ARG, "n = " + std::to_string(n) + " exceeds the static scratch capacity of " +
+                                     std::to_string(kStaticRows) + " rows; use gemslr_apply");
+        int dev = 0;
+        GEMSLR_CUDA(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= kMaxDevices) fail(GEMSLR_ERR_ARG, "device index out of range");
+        double *base = nullptr;
+        {
+            std::lock_guard<std::mutex> lk(g_static_mu);
+            if (!g_static_addr[dev]) {      // once per device, with that device current
+                void *p = nullptr;
+                const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+                if (e != cudaSuccess) fail(GEMSLR_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+                g_static_addr[dev] = static_cast<double *>(p);
+            }
+            base = g_static_addr[dev];
+        }
+        cudaStream_t st = (cudaStream_t)stream;
+        double *pin = base, *pout = base + kStaticRows;
+        launch_gather(n, h->perm, r_dev, pin, st);
+        apply_perm(h, pin, pout, st);
+        launch_scatter(n, h->perm, pout, z_dev, st);
+        GEMSLR_CUDA(cudaGetLastError());
+    });
+}
