@@ -382,6 +382,64 @@ def run_batch(args):
     return 0
 
 
+def run_learned(args):
+    """c5: 96^3 shifted (indefinite) operator; FGMRES(60) with and without the learned stage."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_03224_gb300 import Gemslr, partition_geometric
+    c = gi.CONFIGS["c5"]
+    A, xyz, b = gi.config_problem("c5")
+    part = partition_geometric(A, xyz, c["nlev"], c["p"])
+    t0 = time.perf_counter()
+    G = Gemslr(A, part, ilu=c["ilu"], tau=c["tau"], lfil=c["lfil"], rank=c["rank"], precision=args.precision)
+    setup_s = time.perf_counter() - t0
+    b_dev = torch.from_numpy(b).cuda()
+    stream = torch.cuda.current_stream()
+    As = A.to_scipy()
+
+    def timed_solves():
+        out = []
+        for _ in range(args.warmup):
+            G.solve(b_dev, restart=c["restart"], rtol=c["rtol"], maxit=args.maxit, check=False)
+        ms = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, info = G.solve(b_dev, restart=c["restart"], rtol=c["rtol"], maxit=args.maxit, check=False)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res = float(np.linalg.norm(b - As @ x.cpu().numpy()) / np.linalg.norm(b))
+        return dict(ms=statistics.mean(ms), iterations=info[0]["iters"], converged=info[0]["converged"],
+                    rel_residual=res)
+
+    plain = timed_solves()
+    t0 = time.perf_counter()
+    hist = G.learned_train(xyz, channels=32, npairs=args.npairs, epochs=args.epochs, batch=64, lr=1e-3, seed=c["seed"])
+    train_s = time.perf_counter() - t0
+    learned = timed_solves()
+    accepted = learned["converged"] and (not plain["converged"] or learned["iterations"] < plain["iterations"])
+    if not accepted and not learned["converged"] and not plain["converged"]:
+        accepted = learned["rel_residual"] < plain["rel_residual"]
+    line = {
+        "metric": METRIC, "workload": "c5", "unit": "ms per FGMRES solve (maxit cap)",
+        "config": {"workload": "3-D 7-pt Laplacian - 0.1 h^-2 I (indefinite) 96^3 (n=884736), 4 levels x "
+                               f"{c['p']} subdomains, ILUT(1e-3,10), rank 32, FGMRES(60) to 1e-8 (maxit {args.maxit}), "
+                               "4-layer 27-tap CNN (32 ch, BF16 weights, FP32 accumulation), seed 4",
+                   "precision": args.precision},
+        "setup_s": setup_s, "train_s": train_s, "train_pairs": args.npairs, "epochs": args.epochs,
+        "loss_history": [float(v) for v in hist],
+        "plain": plain, "learned": learned, "learned_accepted": bool(accepted),
+        "learned_info": G.learned_info(),
+    }
+    if not accepted:
+        G.learned_enable(False)
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -390,13 +448,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
-                    help="c2 (default line), c3: 128^3 shifted (mixed), c4: batched systems")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2 (default line), c3: 128^3 shifted (mixed), c4: batched systems, c5: learned stage")
+    ap.add_argument("--maxit", type=int, default=1000)
+    ap.add_argument("--npairs", type=int, default=20000)
+    ap.add_argument("--epochs", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "c4":
         return run_batch(args)
+    if args.workload == "c5":
+        return run_learned(args)
     if args.workload == "c3":
         global CONFIG, WORKLOAD
         CONFIG = "c3"

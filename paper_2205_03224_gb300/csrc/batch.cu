@@ -25,6 +25,8 @@ void launch_bspmv(int64_t nrows, const int64_t *rp, const int32_t *ci, const dou
                   const double *b, double *y, double *zcol, const int32_t *jp, int64_t ld, cudaStream_t st);
 void launch_bgs(int pass, const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, double *w,
                 cudaStream_t st);
+void launch_bgs_subnorm(const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, double *w,
+                        cudaStream_t st);
 void launch_bgs_final(const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, const double *w, double *vin,
                       cudaStream_t st);
 void launch_bnorm2(const BatchSegs &S, double *partial, const double *x, double *out, cudaStream_t st);
@@ -309,6 +311,7 @@ void batch_step(gemslr_batch_ctx *B, cudaStream_t st, cudaGraphConditionalHandle
     launch_bspmv(B->N, B->A_rp, B->A_ci, B->A_v, B->zout, nullptr, B->w, B->Z, B->K.j, L, st);
     launch_bgs(1, B->S, B->K, B->V, L, B->w, st);
     launch_bgs(2, B->S, B->K, B->V, L, B->w, st);
+    launch_bgs_subnorm(B->S, B->K, B->V, L, B->w, st);
     launch_bgs_final(B->S, B->K, B->V, L, B->w, B->vin, st);
     launch_bstep_end(B->K, h, use_cond, st);
 }

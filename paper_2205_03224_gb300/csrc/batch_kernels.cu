@@ -233,8 +233,9 @@ namespace {
 // Per-CTA partial dot products of columns 0..ncols-1 of V (and of w itself
 // when with_norm) with w over rows [r0, r1), for the 8 right-hand sides.
 // Threads: r = tid & 7, row group = tid >> 3 (32 groups); 4 columns at a time.
+// w may have been written earlier in the same kernel, so it is read through L2.
 __device__ void bdots_block(const double *__restrict__ V, int64_t ldv, int ncols, bool with_norm,
-                            const double *__restrict__ w, int64_t r0, int64_t r1, double *partial_cta) {
+                            const double *w, int64_t r0, int64_t r1, double *partial_cta) {
     __shared__ double red[8][4][R8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int r = threadIdx.x & 7, grp = threadIdx.x >> 3;
@@ -242,7 +243,7 @@ __device__ void bdots_block(const double *__restrict__ V, int64_t ldv, int ncols
     for (int c0 = 0; c0 < ntot; c0 += 4) {
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
         for (int64_t g = r0 + grp; g < r1; g += 32) {
-            const double wi = w[g * R8 + r];
+            const double wi = __ldcg(w + g * R8 + r);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int c = c0 + u;
@@ -349,21 +350,11 @@ k_bgs(int pass, const BatchSegs S, BatchKrylov K, double *__restrict__ V, int64_
                     K.hbuf[(int64_t)p * kMaxCols + cc] = out[cc * R8 + rr];
                 }
             } else {
-                double hh = 0.0;
                 for (int cc = 0; cc < ncols; ++cc) {
                     const double h2 = out[cc * R8 + rr];
                     hcol[cc] += h2;
                     K.hbuf[(int64_t)p * kMaxCols + cc] = h2;
-                    hh += h2 * h2;
                 }
-                const double rest = out[ncols * R8 + rr] - hh;
-                const double beta = sqrt(rest > 0.0 ? rest : 0.0);
-                double htot = 0.0;
-                for (int cc = 0; cc < ncols; ++cc) htot += hcol[cc] * hcol[cc];
-                K.wn2[p] = htot + beta * beta;          // ||A z_j||^2 by Pythagoras
-                K.beta[p] = beta;
-                hcol[j + 1] = beta;
-                bgivens(K, p, j);
             }
         } else if (pass == 2) {
             for (int cc = 0; cc < ncols; ++cc) K.hbuf[(int64_t)p * kMaxCols + cc] = 0.0;
@@ -373,12 +364,13 @@ k_bgs(int pass, const BatchSegs S, BatchKrylov K, double *__restrict__ V, int64_
     if (threadIdx.x == 0) S.sys_counter[s] = 0u;
 }
 
-// w -= V h2; V[:, j+1] = w / beta for pairs still running (0 otherwise); vin = same.
+// w -= V h2 and an explicit ||w_p||^2 per pair (Pythagoras would lose all
+// accuracy to cancellation after the second pass); the per-system finisher
+// sets beta_p and the pair's Givens update.
 __global__ void __launch_bounds__(256)
-k_bgs_final(const BatchSegs S, BatchKrylov K, double *__restrict__ V, int64_t ldv, const double *__restrict__ w,
-            double *__restrict__ vin) {
+k_bgs_subnorm(const BatchSegs S, BatchKrylov K, const double *__restrict__ V, int64_t ldv, double *__restrict__ w) {
     __shared__ double hs[R8][kMaxCols];
-    __shared__ double inv[R8];
+    __shared__ double out[R8];
     const int c = blockIdx.x, s = S.cta_sys[c];
     const int64_t r0 = S.cta_r0[c], r1 = S.cta_r1[c];
     const int j = *K.j, ncols = j + 1;
@@ -386,6 +378,45 @@ k_bgs_final(const BatchSegs S, BatchKrylov K, double *__restrict__ V, int64_t ld
         const int rr = idx / ncols, cc = idx % ncols;
         hs[rr][cc] = K.hbuf[(int64_t)(s * R8 + rr) * kMaxCols + cc];
     }
+    __syncthreads();
+    for (int64_t idx = r0 * R8 + threadIdx.x; idx < r1 * R8; idx += blockDim.x) {
+        const int rr = (int)(idx % R8);
+        double x = w[idx];
+        for (int cc = 0; cc < ncols; ++cc) x -= V[(int64_t)cc * ldv + idx] * hs[rr][cc];
+        w[idx] = x;
+    }
+    __syncthreads();
+    bdots_block(nullptr, 0, 0, true, w, r0, r1, K.partial + (int64_t)c * (kMaxCols + 1) * R8);
+    const int ca = S.sys_cta0[s], cb = S.sys_cta0[s + 1];
+    if (!last_of(&S.sys_counter[s], (unsigned)(cb - ca))) return;
+    bdots_finish(K.partial, ca, cb, 1, out);
+    if (threadIdx.x < R8) {
+        const int rr = threadIdx.x, p = s * R8 + rr;
+        const int m1 = K.m + 1;
+        double *hcol = K.H + (int64_t)p * m1 * K.m + (int64_t)j * m1;
+        if (K.run[p]) {
+            const double beta = sqrt(out[rr]);
+            double htot = 0.0;
+            for (int cc = 0; cc < ncols; ++cc) htot += hcol[cc] * hcol[cc];
+            K.wn2[p] = htot + beta * beta;          // ||A z_j||^2
+            K.beta[p] = beta;
+            hcol[j + 1] = beta;
+            bgivens(K, p, j);
+        } else {
+            K.beta[p] = 0.0;
+        }
+    }
+    if (threadIdx.x == 0) S.sys_counter[s] = 0u;
+}
+
+// V[:, j+1] = w / beta for pairs still running (0 otherwise); vin = same.
+__global__ void __launch_bounds__(256)
+k_bgs_final(const BatchSegs S, BatchKrylov K, double *__restrict__ V, int64_t ldv, const double *__restrict__ w,
+            double *__restrict__ vin) {
+    __shared__ double inv[R8];
+    const int c = blockIdx.x, s = S.cta_sys[c];
+    const int64_t r0 = S.cta_r0[c], r1 = S.cta_r1[c];
+    const int j = *K.j;
     if (threadIdx.x < R8) {
         const int p = s * R8 + threadIdx.x;
         inv[threadIdx.x] = (K.run[p] && K.beta[p] > 0.0) ? 1.0 / K.beta[p] : 0.0;
@@ -393,10 +424,7 @@ k_bgs_final(const BatchSegs S, BatchKrylov K, double *__restrict__ V, int64_t ld
     __syncthreads();
     double *vn = V + (int64_t)(j + 1) * ldv;
     for (int64_t idx = r0 * R8 + threadIdx.x; idx < r1 * R8; idx += blockDim.x) {
-        const int rr = (int)(idx % R8);
-        double x = w[idx];
-        for (int cc = 0; cc < ncols; ++cc) x -= V[(int64_t)cc * ldv + idx] * hs[rr][cc];
-        const double v = x * inv[rr];
+        const double v = w[idx] * inv[idx % R8];
         vn[idx] = v;
         vin[idx] = v;
     }
@@ -623,6 +651,11 @@ void launch_bspmv(int64_t nrows, const int64_t *rp, const int32_t *ci, const dou
 void launch_bgs(int pass, const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, double *w,
                 cudaStream_t st) {
     k_bgs<<<S.ncta, 256, 0, st>>>(pass, S, K, V, ldv, w);
+    count_launch();
+}
+void launch_bgs_subnorm(const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, double *w,
+                        cudaStream_t st) {
+    k_bgs_subnorm<<<S.ncta, 256, 0, st>>>(S, K, V, ldv, w);
     count_launch();
 }
 void launch_bgs_final(const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, const double *w, double *vin,

@@ -50,12 +50,16 @@ void launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *
                  const double *b, double *y, int lanes, cudaStream_t st, double *zcol = nullptr,
                  const KrylovCtl *ctl = nullptr);
 void launch_gs_dots(int64_t len, const double *V, int64_t ldv, const double *w, double *partial, unsigned *counter,
-                    KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, int grid, cudaStream_t st);
+                    KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *hbuf, int grid,
+                    cudaStream_t st);
 void launch_gs_sub(int64_t len, double *V, int64_t ldv, double *w, double *partial, unsigned *counter,
                    KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *h2buf, int grid,
                    cudaStream_t st, double *vcopy = nullptr);
-void launch_gs_sub2(int64_t len, double *V, int64_t ldv, const double *w, const double *h2, KrylovCtl *ctl,
-                    cudaStream_t st, double *vcopy = nullptr);
+void launch_gs_sub2(int64_t len, double *V, int64_t ldv, double *w, const double *h2, double *partial,
+                    unsigned *counter, KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, int grid,
+                    cudaStream_t st);
+void launch_gs_scale(int64_t len, double *V, int64_t ldv, const double *w, const KrylovCtl *ctl, double *vcopy,
+                     cudaStream_t st);
 void launch_gs_next(KrylovCtl *ctl, cudaStream_t st);
 void launch_norm2(int64_t len, const double *x, double *partial, unsigned *counter, double *out, int grid,
                   cudaStream_t st);

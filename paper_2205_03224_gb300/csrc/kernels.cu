@@ -301,7 +301,9 @@ __device__ __forceinline__ void reduce_partials(const double *partial, int ncols
 // written to partial[blockIdx.x * (ncols + 1) + c].  Columns are taken eight
 // at a time with register accumulators so that every thread keeps many
 // independent loads in flight; one block-wide reduction at the end.
-__device__ void block_dots(const double *__restrict__ V, int64_t ldv, int ncols, const double *__restrict__ w,
+// w may have been written earlier in the same kernel by this CTA, so it is
+// read through L2 (ld.global.cg), never through the non-coherent read-only path.
+__device__ void block_dots(const double *__restrict__ V, int64_t ldv, int ncols, const double *w,
                            int64_t i0, int64_t i1, double *partial) {
     __shared__ double red[kReduceThreads / 32][kMaxCols + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -310,7 +312,7 @@ __device__ void block_dots(const double *__restrict__ V, int64_t ldv, int ncols,
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc[u] = 0.0;
         for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const double wi = w[i];
+            const double wi = __ldcg(w + i);
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int c = c0 + u;
@@ -376,13 +378,19 @@ __device__ void givens_step(KrylovCtl *ctl, double *H, double *cs, double *sn, d
         ctl->stop = 1;
 }
 
-// After h (ncols values) and ||w||^2 are known: record h in column j of H,
-// decide on a second pass and, if none, the norm of the projected vector.
+// After h (ncols values) and ||w||^2 are known: record h in column j of H and
+// in hbuf (the projection coefficients of the next kernel: the Givens update
+// below rotates the column of H in place), decide on a second pass and, if
+// none, the norm of the projected vector.
 __device__ void after_first_pass(KrylovCtl *ctl, const double *red, int ncols, double *H, double *cs,
-                                 double *sn, double *g) {
+                                 double *sn, double *g, double *hbuf) {
     const int j = ctl->j, m1 = ctl->m + 1;
     double hh = 0.0;
-    for (int c = 0; c < ncols; ++c) { H[(int64_t)j * m1 + c] = red[c]; hh += red[c] * red[c]; }
+    for (int c = 0; c < ncols; ++c) {
+        H[(int64_t)j * m1 + c] = red[c];
+        hbuf[c] = red[c];
+        hh += red[c] * red[c];
+    }
     const double ww = red[ncols];
     ctl->wnorm2 = ww;
     const double rest = ww - hh;      // ||w - V h||^2 by Pythagoras
@@ -402,7 +410,8 @@ __device__ void after_first_pass(KrylovCtl *ctl, const double *red, int ncols, d
 // A step is only launched while its cycle is active (ctl->stop == 0).
 __global__ void __launch_bounds__(kReduceThreads)
 k_gs_dots(int64_t len, const double *__restrict__ V, int64_t ldv, const double *__restrict__ w,
-          double *partial, unsigned *counter, KrylovCtl *ctl, double *H, double *cs, double *sn, double *g) {
+          double *partial, unsigned *counter, KrylovCtl *ctl, double *H, double *cs, double *sn, double *g,
+          double *hbuf) {
     if (ctl->stop) {
         if (blockIdx.x == 0 && threadIdx.x == 0) ctl->reorth = 0;
         return;
@@ -415,14 +424,15 @@ k_gs_dots(int64_t len, const double *__restrict__ V, int64_t ldv, const double *
     __shared__ double red[kMaxCols + 1];
     reduce_partials(partial, ncols + 1, red);
     if (threadIdx.x == 0) {
-        after_first_pass(ctl, red, ncols, H, cs, sn, g);
+        after_first_pass(ctl, red, ncols, H, cs, sn, g, hbuf);
         *counter = 0u;
     }
 }
 
-// Pass 2: w -= V h.  Without reorthogonalisation the result is scaled into
-// V[:, j+1] (unless the step ended the cycle); otherwise w is kept, the
-// second-pass coefficients h2 are reduced into h2buf and added to H.
+// Pass 2: w -= V h with h from h2buf (the first-pass coefficients).  Without
+// reorthogonalisation the result is scaled into V[:, j+1] (unless the step
+// ended the cycle); otherwise w is kept, the second-pass coefficients h2 are
+// reduced into h2buf (every CTA has read it by then) and added to H.
 __global__ void __launch_bounds__(kReduceThreads)
 k_gs_sub(int64_t len, double *__restrict__ V, int64_t ldv, double *__restrict__ w, double *partial,
          unsigned *counter, KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *h2buf,
@@ -431,7 +441,7 @@ k_gs_sub(int64_t len, double *__restrict__ V, int64_t ldv, double *__restrict__ 
     if (!again && (ctl->stop || ctl->breakdown)) return;
     __shared__ double hs[kMaxCols];
     const int j = ctl->j, ncols = j + 1, m1 = ctl->m + 1;
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = H[(int64_t)j * m1 + c];
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = __ldcg(h2buf + c);
     __syncthreads();
     const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
     const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
@@ -453,14 +463,36 @@ k_gs_sub(int64_t len, double *__restrict__ V, int64_t ldv, double *__restrict__ 
     __shared__ double red[kMaxCols + 1];
     reduce_partials(partial, ncols + 1, red);
     if (threadIdx.x == 0) {
-        double hh = 0.0;
         for (int c = 0; c < ncols; ++c) {
             H[(int64_t)j * m1 + c] += red[c];
             h2buf[c] = red[c];
-            hh += red[c] * red[c];
         }
-        const double rest = red[ncols] - hh;
-        const double beta = sqrt(rest > 0.0 ? rest : 0.0);
+        *counter = 0u;
+    }
+}
+
+// Pass 3 (only after a second Gram-Schmidt pass): w -= V h2 and an explicit
+// ||w||^2 (Pythagoras would lose all accuracy to cancellation here); the
+// finisher sets beta, the breakdown flag and the Givens update.
+__global__ void __launch_bounds__(kReduceThreads)
+k_gs_sub2(int64_t len, const double *__restrict__ V, int64_t ldv, double *__restrict__ w,
+          const double *__restrict__ h2, double *partial, unsigned *counter, KrylovCtl *ctl, double *H, double *cs,
+          double *sn, double *g) {
+    if (!ctl->reorth) return;
+    __shared__ double hs[kMaxCols];
+    const int j = ctl->j, ncols = j + 1, m1 = ctl->m + 1;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = __ldcg(h2 + c);
+    __syncthreads();
+    const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) w[i] = project_out(V, ldv, ncols, hs, i, w[i]);
+    __syncthreads();
+    block_dots(nullptr, 0, 0, w, i0, i1, partial);
+    if (!finish_block(counter)) return;
+    __shared__ double red[1];
+    reduce_partials(partial, 1, red);
+    if (threadIdx.x == 0) {
+        const double beta = sqrt(red[0]);
         ctl->beta = beta;
         ctl->breakdown = beta <= 1e-14 * sqrt(ctl->wnorm2) ? 1 : 0;
         H[(int64_t)j * m1 + j + 1] = beta;
@@ -469,19 +501,14 @@ k_gs_sub(int64_t len, double *__restrict__ V, int64_t ldv, double *__restrict__ 
     }
 }
 
-// Pass 3 (only after a second Gram-Schmidt pass): V[:, j+1] = (w - V h2) / beta.
-__global__ void __launch_bounds__(kReduceThreads)
-k_gs_sub2(int64_t len, double *__restrict__ V, int64_t ldv, const double *__restrict__ w,
-          const double *__restrict__ h2, KrylovCtl *ctl, double *__restrict__ vcopy) {
+// After a second pass: V[:, j+1] = w / beta (and its copy), unless the cycle ended.
+__global__ void k_gs_scale(int64_t len, double *__restrict__ V, int64_t ldv, const double *__restrict__ w,
+                           const KrylovCtl *ctl, double *__restrict__ vcopy) {
     if (!ctl->reorth || ctl->stop || ctl->breakdown) return;
-    __shared__ double hs[kMaxCols];
-    const int j = ctl->j, ncols = j + 1;
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = __ldcg(h2 + c);
-    __syncthreads();
     const double inv = 1.0 / ctl->beta;
-    double *vn = V + (int64_t)(j + 1) * ldv;
+    double *vn = V + (int64_t)(ctl->j + 1) * ldv;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
-        const double x = project_out(V, ldv, ncols, hs, i, w[i]) * inv;
+        const double x = w[i] * inv;
         vn[i] = x;
         if (vcopy) vcopy[i] = x;
     }
@@ -689,8 +716,10 @@ void launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *
     count_launch();
 }
 void launch_gs_dots(int64_t len, const double *V, int64_t ldv, const double *w, double *partial, unsigned *counter,
-                    KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, int grid, cudaStream_t st) {
-    k_gs_dots<<<grid, kReduceThreads, 0, st>>>(len, V, ldv, w, partial, counter, ctl, H, cs, sn, g); count_launch();
+                    KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *hbuf, int grid,
+                    cudaStream_t st) {
+    k_gs_dots<<<grid, kReduceThreads, 0, st>>>(len, V, ldv, w, partial, counter, ctl, H, cs, sn, g, hbuf);
+    count_launch();
 }
 void launch_gs_sub(int64_t len, double *V, int64_t ldv, double *w, double *partial, unsigned *counter,
                    KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *h2buf, int grid,
@@ -698,9 +727,15 @@ void launch_gs_sub(int64_t len, double *V, int64_t ldv, double *w, double *parti
     k_gs_sub<<<grid, kReduceThreads, 0, st>>>(len, V, ldv, w, partial, counter, ctl, H, cs, sn, g, h2buf, vcopy);
     count_launch();
 }
-void launch_gs_sub2(int64_t len, double *V, int64_t ldv, const double *w, const double *h2, KrylovCtl *ctl,
-                    cudaStream_t st, double *vcopy) {
-    k_gs_sub2<<<grid_for(len, 256, 1216), 256, 0, st>>>(len, V, ldv, w, h2, ctl, vcopy);
+void launch_gs_sub2(int64_t len, double *V, int64_t ldv, double *w, const double *h2, double *partial,
+                    unsigned *counter, KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, int grid,
+                    cudaStream_t st) {
+    k_gs_sub2<<<grid, kReduceThreads, 0, st>>>(len, V, ldv, w, h2, partial, counter, ctl, H, cs, sn, g);
+    count_launch();
+}
+void launch_gs_scale(int64_t len, double *V, int64_t ldv, const double *w, const KrylovCtl *ctl, double *vcopy,
+                     cudaStream_t st) {
+    k_gs_scale<<<grid_for(len, 256, 1216), 256, 0, st>>>(len, V, ldv, w, ctl, vcopy);
     count_launch();
 }
 void launch_gs_next(KrylovCtl *ctl, cudaStream_t st) { k_gs_next<<<1, 32, 0, st>>>(ctl); count_launch(); }

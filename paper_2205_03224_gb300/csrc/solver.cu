@@ -235,10 +235,13 @@ void build_lowrank(gemslr_ctx *h, int l, cudaStream_t st) {
         double beta = 0.0;
         for (int j = p; j < m; ++j) {
             g_hat(h, l, V + (size_t)j * s, w, st);
-            launch_gs_dots(s, V, s, w, h->partial, h->counter, h->ctl, Hd, nullptr, nullptr, nullptr, h->red_grid, st);
+            launch_gs_dots(s, V, s, w, h->partial, h->counter, h->ctl, Hd, nullptr, nullptr, nullptr, h->h2, h->red_grid,
+                           st);
             launch_gs_sub(s, V, s, w, h->partial, h->counter, h->ctl, Hd, nullptr, nullptr, nullptr, h->h2,
                           h->red_grid, st);
-            launch_gs_sub2(s, V, s, w, h->h2, h->ctl, st);
+            launch_gs_sub2(s, V, s, w, h->h2, h->partial, h->counter, h->ctl, Hd, nullptr, nullptr, nullptr,
+                           h->red_grid, st);
+            launch_gs_scale(s, V, s, w, h->ctl, nullptr, st);
             launch_gs_next(h->ctl, st);
             read_ctl(h, st);
             beta = h->ctl_host->beta;
@@ -322,7 +325,8 @@ void fgmres_step(gemslr_ctx *h, cudaStream_t st) {
     }
     {
         ProfScope ps("gs_dots", st);
-        launch_gs_dots(n, h->V, n, h->w, h->partial, h->counter, h->ctl, h->Hs, h->cs, h->sn, h->g, h->red_grid, st);
+        launch_gs_dots(n, h->V, n, h->w, h->partial, h->counter, h->ctl, h->Hs, h->cs, h->sn, h->g, h->h2,
+                       h->red_grid, st);
     }
     {
         ProfScope ps("gs_sub", st);
@@ -331,7 +335,9 @@ void fgmres_step(gemslr_ctx *h, cudaStream_t st) {
     }
     {
         ProfScope ps("gs_sub2", st);
-        launch_gs_sub2(n, h->V, n, h->w, h->h2, h->ctl, st, h->vin);
+        launch_gs_sub2(n, h->V, n, h->w, h->h2, h->partial, h->counter, h->ctl, h->Hs, h->cs, h->sn, h->g,
+                       h->red_grid, st);
+        launch_gs_scale(n, h->V, n, h->w, h->ctl, h->vin, st);
     }
 }
 

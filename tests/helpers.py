@@ -15,6 +15,9 @@ CASES = {
     "tinyparts": ((6, 5, 4), 0.3, 0.0, 3, 16, "ilu0", 0.0, 0, 3),
     "bigblock": ((240, 240), 0.5, 0.0, 2, 2, "ilu0", 0.0, 0, 4),
     "c2": ((64, 64, 64), 0.1, 0.0, 4, 64, "ilut", 1e-3, 10, 32),
+    # indefinite (shift 0.1 h^-2): the DGKS test skips the second Gram-Schmidt
+    # pass at step 7 of the first cycle, every other step takes it
+    "indef24": ((24, 24, 24), 0.0, 0.1, 4, 8, "ilut", 1e-3, 10, 8),
 }
 
 

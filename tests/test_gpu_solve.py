@@ -39,6 +39,37 @@ def test_fgmres_matches_oracle_iterations(torch_cuda, name):
     assert rel_err(x, x_ref) <= 1e-6
 
 
+@pytest.mark.parametrize("name", ["c1", "indef24"])
+def test_fgmres_residual_history_matches_oracle(torch_cuda, name):
+    """Within one cycle the GPU's Givens estimate after k steps equals the
+    oracle's (Sec. 4.1: FGMRES minimises the same residual whatever the
+    orthogonalisation scheme) and the true residual of the iterate the GPU
+    returns.  indef24 takes the single-pass branch of the DGKS test once, so a
+    projection with wrong coefficients there breaks every later step."""
+    torch = torch_cuda
+    from paper_2205_03224_gb300 import Gemslr
+    A, xyz, part = problem(name)
+    M = oracle_hierarchy(name)
+    As = A.to_scipy()
+    b = gi.rhs_uniform(M.n, 2 if name == "indef24" else 1)
+    _, info_ref = fgmres(As, b, M.apply, restart=40, rtol=1e-14, maxit=20)
+    hist = info_ref["hist"]
+    assert len(hist) == 20
+    G = Gemslr.from_factors(A, part, M.factors())
+    bd = torch.from_numpy(b).cuda()
+    single = 0
+    for k in (1, 2, 6, 7, 8, 9, 12, 20):
+        x, info = G.solve(bd, restart=40, rtol=1e-14, maxit=k, check=False)
+        est = info[0]["rel_res_est"]
+        true = np.linalg.norm(b - As @ x.cpu().numpy()) / np.linalg.norm(b)
+        assert info[0]["iters"] == k
+        assert abs(est - hist[k - 1]) <= 1e-6 * hist[k - 1], (k, est, hist[k - 1])
+        assert abs(true - est) <= 1e-6 * est, (k, est, true)
+        single = k - info[0]["reorth"]
+    if name == "indef24":
+        assert single >= 1          # the single-pass branch ran
+
+
 @pytest.mark.parametrize("name", ["c1", "small3d"])
 def test_library_setup_matches_oracle_factors(torch_cuda, name):
     from paper_2205_03224_gb300 import Gemslr
