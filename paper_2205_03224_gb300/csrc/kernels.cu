@@ -116,11 +116,9 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
     }
     consumer_barrier();
     if constexpr (LanesPerRow<VT>::value == 1) {
-        // FP32: consumer warp 0 walks every chunk, one lane per row, and loads
-        // the next chunk's rows, lengths, columns and values into registers
-        // while the current chunk's x gathers are in flight; rows of one
-        // chunk are ordered after the previous chunk by __syncwarp alone.
-        if (warp == 0) consume_chunks_lane_per_row<VT>(ring, full, empty, abort_flag, c1 - c0, xs, lane);
+        // FP32: the consumer warps take the chunks in turn, one lane per row,
+        // each loading its next chunk into registers while the others work.
+        consume_chunks_round_robin<VT>(ring, full, empty, abort_flag, c1 - c0, xs, warp, lane);
     } else {
         bool aborted = false;
         const int r = lane >> 2, sub = lane & 3;
@@ -300,14 +298,20 @@ __device__ __forceinline__ void reduce_partials(const double *partial, int ncols
 // Block partial sums of V[:, c] . w for c < ncols and of w . w (slot ncols),
 // written to partial[blockIdx.x * (ncols + 1) + c].  Columns are taken eight
 // at a time with register accumulators so that every thread keeps many
-// independent loads in flight; one block-wide reduction at the end.
+// independent loads in flight.  The CTA reduction goes through shared memory
+// (warp u sums column u: eight values per lane, then one warp reduction),
+// which issues about a third of the FP64 adds of eight full-warp butterflies;
+// on this part FP64 instructions, not bytes, bound the Gram-Schmidt kernels.
 // w may have been written earlier in the same kernel by this CTA, so it is
 // read through L2 (ld.global.cg), never through the non-coherent read-only path.
+// Requires blockDim.x == kReduceThreads (8 warps).
 __device__ void block_dots(const double *__restrict__ V, int64_t ldv, int ncols, const double *w,
                            int64_t i0, int64_t i1, double *partial) {
-    __shared__ double red[kReduceThreads / 32][kMaxCols + 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    static_assert(kReduceThreads == 256, "one warp per column of an eight-column group");
+    __shared__ double tred[8][kReduceThreads];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int c0 = 0; c0 <= ncols; c0 += 8) {
+        const int nc = min(8, ncols + 1 - c0);
         double acc[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc[u] = 0.0;
@@ -316,38 +320,37 @@ __device__ void block_dots(const double *__restrict__ V, int64_t ldv, int ncols,
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int c = c0 + u;
-                if (c < ncols) acc[u] += V[(int64_t)c * ldv + i] * wi;
-                else if (c == ncols) acc[u] += wi * wi;
+                if (c < ncols) acc[u] = fma(V[(int64_t)c * ldv + i], wi, acc[u]);
+                else if (c == ncols) acc[u] = fma(wi, wi, acc[u]);
             }
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const double x = warp_sum(acc[u]);
-            if (lane == 0 && c0 + u <= ncols) red[warp][c0 + u] = x;
+        for (int u = 0; u < 8; ++u)
+            if (u < nc) tred[u][threadIdx.x] = acc[u];
+        __syncthreads();
+        if (warp < nc) {
+            double sum = tred[warp][lane];
+#pragma unroll
+            for (int q = 1; q < kReduceThreads / 32; ++q) sum += tred[warp][q * 32 + lane];
+            sum = warp_sum(sum);
+            if (lane == 0) partial[(int64_t)blockIdx.x * (ncols + 1) + c0 + warp] = sum;
         }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int c = threadIdx.x; c <= ncols; c += blockDim.x) {
-        double sum = 0.0;
-        for (int q = 0; q < nw; ++q) sum += red[q][c];
-        partial[(int64_t)blockIdx.x * (ncols + 1) + c] = sum;
-    }
-    __syncthreads();
 }
 
-// x_i - sum_c V[i, c] h_c with four independent partial sums.
+// x_i - sum_c V[i, c] h_c with two independent partial sums (one FP64 add
+// to combine them: FP64 instructions are the scarce resource here).
 __device__ __forceinline__ double project_out(const double *__restrict__ V, int64_t ldv, int ncols,
                                               const double *hs, int64_t i, double x) {
-    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    double a1 = 0.0;
     int c = 0;
-    for (; c + 3 < ncols; c += 4) {
-        x -= V[(int64_t)c * ldv + i] * hs[c];
-        a1 -= V[(int64_t)(c + 1) * ldv + i] * hs[c + 1];
-        a2 -= V[(int64_t)(c + 2) * ldv + i] * hs[c + 2];
-        a3 -= V[(int64_t)(c + 3) * ldv + i] * hs[c + 3];
+    for (; c + 1 < ncols; c += 2) {
+        x = fma(-V[(int64_t)c * ldv + i], hs[c], x);
+        a1 = fma(-V[(int64_t)(c + 1) * ldv + i], hs[c + 1], a1);
     }
-    for (; c < ncols; ++c) x -= V[(int64_t)c * ldv + i] * hs[c];
-    return x + (a1 + a2 + a3);
+    if (c < ncols) x = fma(-V[(int64_t)c * ldv + i], hs[c], x);
+    return ncols > 1 ? x + a1 : x;
 }
 
 // Givens update of column j of the (m+1) x m Hessenberg matrix H (FGMRES).

@@ -42,9 +42,11 @@ __device__ void reduce_columns(const T *partial, int nparts, int ncols1, T *out)
     }
 #pragma unroll
     for (int u = 0; u < kColsPerWarp; ++u) {
-        const int c = warp + nw * u;
-        const T v = warp_sum(acc[u]);
-        if (lane == 0 && c < ncols1) out[c] = v;
+        const int c = warp + nw * u;          // uniform over the warp
+        if (c < ncols1) {
+            const T v = warp_sum(acc[u]);
+            if (lane == 0) out[c] = v;
+        }
     }
     __syncthreads();
 }
@@ -166,38 +168,56 @@ __device__ __forceinline__ bool fetch_row(const unsigned char *ring, uint64_t *f
     return true;
 }
 
+// Named barriers 2 .. 1+kConsumerWarps hand the sweep from one consumer warp
+// to the next (64 threads: the signalling warp arrives, the next one waits).
+__device__ __forceinline__ void handoff_wait(int warp) {
+    asm volatile("bar.sync %0, 64;" ::"r"(2 + warp) : "memory");
+}
+__device__ __forceinline__ void handoff_signal(int next_warp) {
+    asm volatile("bar.arrive %0, 64;" ::"r"(2 + next_warp) : "memory");
+}
+
+// Lane-per-row substitutions (FP32).  Chunk k belongs to consumer warp
+// k % kConsumerWarps.  A warp loads its next chunk's rows, columns and values
+// into registers while the other warps work, then waits for the previous
+// chunk's warp, gathers x, computes its rows, stores them and hands on; the
+// barrier orders the stores before the next warp's gathers.  Every warp runs
+// the same sequence of waits and signals whatever happens (an expired wait
+// only skips the arithmetic), so the hand-off chain always completes.
 template <typename VT>
-__device__ void consume_chunks_lane_per_row(const unsigned char *ring, uint64_t *full, uint64_t *empty,
-                                            volatile int *abort_flag, int nchunk, VT *xs, int lane) {
-    if (nchunk <= 0) return;
-    RowRegs<VT> cur, nxt;
-    if (!fetch_row<VT>(ring, full, abort_flag, 0, lane, cur)) { *abort_flag = 1; return; }
-    for (int k = 0; k < nchunk; ++k) {
-        VT xv[kRegEntries];
+__device__ void consume_chunks_round_robin(const unsigned char *ring, uint64_t *full, uint64_t *empty,
+                                           volatile int *abort_flag, int nchunk, VT *xs, int warp, int lane) {
+    constexpr int NW = kConsumerWarps;
+    bool ok = true;
+    for (int k = warp; k < nchunk; k += NW) {
+        RowRegs<VT> R;
+        if (ok) ok = fetch_row<VT>(ring, full, abort_flag, k, lane, R);
+        if (!ok && lane == 0) *abort_flag = 1;
+        if (k > 0) handoff_wait(warp);
+        if (ok && !*abort_flag) {
+            VT xv[kRegEntries];
 #pragma unroll
-        for (int q = 0; q < kRegEntries; ++q) xv[q] = (q < cur.len) ? xs[cur.col[q]] : (VT)0;
-        const VT self = cur.active ? xs[cur.row] : (VT)0;
-        bool more = true;
-        if (k + 1 < nchunk) more = fetch_row<VT>(ring, full, abort_flag, k + 1, lane, nxt);
-        VT a0 = 0, a1 = 0;
+            for (int q = 0; q < kRegEntries; ++q) xv[q] = (q < R.len) ? xs[R.col[q]] : (VT)0;
+            const VT self = R.active ? xs[R.row] : (VT)0;
+            VT a0 = 0, a1 = 0;
 #pragma unroll
-        for (int q = 0; q < kRegEntries; q += 2) {
-            a0 += cur.val[q] * xv[q];
-            a1 += cur.val[q + 1] * xv[q + 1];
+            for (int q = 0; q < kRegEntries; q += 2) {
+                a0 += R.val[q] * xv[q];
+                a1 += R.val[q + 1] * xv[q + 1];
+            }
+            if (R.len > kRegEntries) {          // long rows: the rest straight from the staged chunk
+                const int *hdr = reinterpret_cast<const int *>(ring + (size_t)R.st * kStageBytes);
+                const int pr = (R.nrow + 3) & ~3;
+                const int *cols = hdr + 4 + 2 * pr;
+                const int ne = R.S * R.nrow;
+                const VT *vals = reinterpret_cast<const VT *>(cols + ((ne + 3) & ~3));
+                for (int q = kRegEntries; q < R.len; ++q) a0 += vals[q * R.nrow + lane] * xs[cols[q * R.nrow + lane]];
+            }
+            if (R.active) xs[R.row] = (self - (a0 + a1)) * R.dinv;
         }
-        if (cur.len > kRegEntries) {          // long rows: the rest straight from the staged chunk
-            const int *hdr = reinterpret_cast<const int *>(ring + (size_t)cur.st * kStageBytes);
-            const int pr = (cur.nrow + 3) & ~3;
-            const int *cols = hdr + 4 + 2 * pr;
-            const int ne = cur.S * cur.nrow;
-            const VT *vals = reinterpret_cast<const VT *>(cols + ((ne + 3) & ~3));
-            for (int q = kRegEntries; q < cur.len; ++q) a0 += vals[q * cur.nrow + lane] * xs[cols[q * cur.nrow + lane]];
-        }
-        if (cur.active) xs[cur.row] = (self - (a0 + a1)) * cur.dinv;
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[cur.st]);
-        if (!more) { *abort_flag = 1; return; }
-        cur = nxt;
+        if (k + 1 < nchunk) handoff_signal((warp + 1) % NW);
+        if (ok && lane == 0) mbar_arrive(&empty[R.st]);
     }
 }
 
