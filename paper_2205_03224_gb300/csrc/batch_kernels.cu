@@ -32,9 +32,10 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
         float *__restrict__ scratch) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *ring = smem;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStageBytes * kStages);
-    uint64_t *empty = full + kStages;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + kStages + 1);
+    constexpr int CPG = 1, kSlots = kRingData / kStageBytes;   // the warps share every chunk: one per copy
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kRingData);
+    uint64_t *empty = full + kSlots;
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + kSlots + 1);
     float *xs_smem = reinterpret_cast<float *>(smem + kRingBytes);
     const int b = blockIdx.x;
     const int64_t r0 = lv.blk_r0[b];
@@ -43,32 +44,16 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c0 = lv.C.blk_chunk[b], c1 = lv.C.blk_chunk[b + 1];
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kSlots; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kConsumerWarps);
+            mbar_init(&empty[s], CPG * kConsumerWarps);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (warp == kConsumerWarps) {
-        if (lane == 0) {
-            int issued = 0;
-            for (int c = c0; c < c1; ++c) {
-                const int k = c - c0, st = k % kStages;
-                if (k >= kStages && !wait_bounded(&empty[st], ((k / kStages) - 1) & 1, abort_flag)) {
-                    *abort_flag = 1;
-                    atomicExch(lv.err, 1);
-                    break;
-                }
-                const unsigned bytes = (unsigned)(lv.C.off[c + 1] - lv.C.off[c]);
-                mbar_expect_tx(&full[st], bytes);
-                bulk_load(ring + (size_t)st * kStageBytes, lv.C.data + lv.C.off[c], bytes, &full[st]);
-                issued = k + 1;
-            }
-            for (int k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
-                wait_bounded(&full[k % kStages], (k / kStages) & 1, nullptr);
-        }
+        produce_chunks<CPG>(lv.C.data, lv.C.off, c0, c1, ring, full, empty, abort_flag, lv.err, lane);
         return;
     }
     const int ct = threadIdx.x;
@@ -91,14 +76,16 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
     consumer_barrier();
     bool aborted = false;
     const int rr = lane >> 3, r = lane & 7;
+    const unsigned char *base = nullptr;
     for (int c = c0; c < c1; ++c) {
-        const int k = c - c0, st = k % kStages;
-        if (!aborted && !poll_bounded(&full[st], (k / kStages) & 1, abort_flag)) {
+        const int k = c - c0;
+        base = aborted ? nullptr : next_chunk<float, CPG>(ring, full, abort_flag, k, base);
+        if (!aborted && !base) {
             aborted = true;
             *abort_flag = 1;
         }
         if (!aborted) {
-            const int *hdr = reinterpret_cast<const int *>(ring + (size_t)st * kStageBytes);
+            const int *hdr = reinterpret_cast<const int *>(base);
             const int nrow = hdr[0], S = hdr[1], upper = hdr[2];
             const int pr = (nrow + 3) & ~3;
             const int *rows = hdr + 4;
@@ -123,7 +110,7 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
                 xs[row * R8 + r] = y;
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[st]);
+            if (lane == 0) mbar_arrive(&empty[chunk_slot<CPG>(k)]);
         }
         consumer_barrier();
     }

@@ -211,6 +211,12 @@ void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, Chun
                     ++q;
                 }
             }
+            {   // the kernels find a chunk in its group from the sizes of the chunks before it
+                const size_t pr4 = (size_t)((hdr[0] + 3) & ~3), ne4 = (size_t)hdr[1] * (size_t)hdr[0];
+                const size_t dev = 16 + 8 * pr4 + pad16(ne4 * 4) + pad16(ne4 * sizeof(VT)) +
+                                   (hdr[2] ? pad16((size_t)hdr[0] * sizeof(VT)) : 0);
+                if (dev != bytes) fail(GEMSLR_ERR_ARG, "chunk header does not describe its size");
+            }
             out.off.push_back((int64_t)out.data.size());
             start += n;
         }
@@ -262,9 +268,25 @@ void upload_level(const HostLevel &hl, int64_t n, bool schur, Arena &a, DevLevel
         v.F_rp = a.upload(hl.F.rp);
         v.F_ci = a.upload(fci);
         v.F_v = a.upload(convert<VT>(hl.F.v));
+        std::vector<int32_t> frows, fblk(1, 0);
+        for (size_t b = 0; b + 1 < hl.bp.size(); ++b) {
+            for (int64_t i = hl.bp[b]; i < hl.bp[b + 1]; ++i)
+                if (hl.F.rp[i + 1] > hl.F.rp[i]) frows.push_back((int32_t)i);
+            fblk.push_back((int32_t)frows.size());
+        }
+        if (frows.empty()) frows.push_back(0);
+        v.F_rows = a.upload(frows);
+        v.F_blk = a.upload(fblk);
         v.E_rp = a.upload(hl.E.rp);
         v.E_ci = a.upload(hl.E.ci);
         v.E_v = a.upload(convert<VT>(hl.E.v));
+    }
+    if (!schur) {
+        v.F_rp = nullptr;
+        v.F_ci = nullptr;
+        v.F_v = nullptr;
+        v.F_rows = nullptr;
+        v.F_blk = nullptr;
     }
     v.k = 0;
     v.W = nullptr;

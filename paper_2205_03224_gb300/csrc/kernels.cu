@@ -35,9 +35,9 @@ template <> __device__ __forceinline__ double wval<double, double>(double w) { r
 
 
 // ---- level-scheduled substitutions over one block --------------------------
-// One CTA per diagonal block.  Warp kConsumerWarps is the producer: one lane
-// streams the block's chunks (see kernels.cuh) into a ring of kStages
-// shared-memory stages with bulk copies completing on mbarriers.  The
+// One CTA per diagonal block.  Warp kConsumerWarps is the producer: it
+// streams the block's chunks (see kernels.cuh) into a shared-memory ring,
+// CPG chunks per bulk copy completing on an mbarrier.  The
 // consumer warps keep the block's vector x in shared memory (or global memory
 // for blocks that do not fit) and, chunk by chunk, compute
 //   x_i = (x_i - sum_j T_ij x_j) * (U ? 1/u_ii : 1)
@@ -50,9 +50,12 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
        double *__restrict__ out_final, VT *__restrict__ scratch) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *ring = smem;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStageBytes * kStages);
-    uint64_t *empty = full + kStages;
-    uint64_t *cbar = empty + kStages;
+    // FP32: kGroupChunks chunks per copy, one per consumer warp; FP64: one
+    constexpr int CPG = LanesPerRow<VT>::value == 1 ? kGroupChunks : 1;
+    constexpr int kSlots = kRingData / (CPG * kStageBytes);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kRingData);
+    uint64_t *empty = full + kSlots;
+    uint64_t *cbar = empty + kSlots;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(cbar + 1);
     VT *xs_smem = reinterpret_cast<VT *>(smem + kRingBytes);
 
@@ -63,10 +66,10 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c0 = lv.C.blk_chunk[b], c1 = lv.C.blk_chunk[b + 1];
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kSlots; ++s) {
             mbar_init(&full[s], 1);
             // FP32 chunks are released by one consumer warp, FP64 chunks by all of them
-            mbar_init(&empty[s], LanesPerRow<VT>::value == 1 ? 1 : kConsumerWarps);
+            mbar_init(&empty[s], CPG * (LanesPerRow<VT>::value == 1 ? 1 : kConsumerWarps));
         }
         mbar_init(cbar, kConsumerWarps);
         *abort_flag = 0;
@@ -75,24 +78,7 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
     __syncthreads();
 
     if (warp == kConsumerWarps) {            // producer warp
-        if (lane == 0) {
-            int issued = 0;
-            for (int c = c0; c < c1; ++c) {
-                const int k = c - c0, st = k % kStages;
-                if (k >= kStages && !wait_bounded(&empty[st], ((k / kStages) - 1) & 1, abort_flag)) {
-                    *abort_flag = 1;
-                    atomicExch(lv.err, 1);
-                    break;
-                }
-                const unsigned bytes = (unsigned)(lv.C.off[c + 1] - lv.C.off[c]);
-                mbar_expect_tx(&full[st], bytes);
-                bulk_load(ring + (size_t)st * kStageBytes, lv.C.data + lv.C.off[c], bytes, &full[st]);
-                issued = k + 1;
-            }
-            // no copy may still be in flight when the CTA exits
-            for (int k = issued > kStages ? issued - kStages : 0; k < issued; ++k)
-                wait_bounded(&full[k % kStages], (k / kStages) & 1, nullptr);
-        }
+        produce_chunks<CPG>(lv.C.data, lv.C.off, c0, c1, ring, full, empty, abort_flag, lv.err, lane);
         return;
     }
 
@@ -102,16 +88,31 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
     constexpr int NC = 32 * kConsumerWarps;
     VT *mine = work + lv.s + r0;
     VT *xs = SMEM ? xs_smem : (MODE == 1 ? scratch + r0 : mine);
-    for (int i = ct; i < nr; i += NC) {
-        if (MODE == 1) {
+    if (MODE == 1) {
+        // right-hand side F y2: zero, then the (few) block rows with F entries,
+        // one thread per row so that their index and value loads overlap
+        for (int i = ct; i < nr; i += NC) xs[i] = (VT)0;
+        consumer_barrier();
+        const int f1 = lv.F_blk[b + 1];
+        for (int t = lv.F_blk[b] + ct; t < f1; t += NC) {
+            const int64_t g = lv.F_rows[t];
             VT acc = 0;
-            const int64_t g = r0 + i;
             for (int64_t p = lv.F_rp[g]; p < lv.F_rp[g + 1]; ++p) acc += lv.F_v[p] * work[lv.F_ci[p]];
-            xs[i] = acc;
-        } else if (in) {
-            xs[i] = (VT)in[lv.s + r0 + i];
-        } else if (SMEM) {
-            xs[i] = mine[i];
+            xs[g - r0] = acc;
+        }
+    } else if (in || SMEM) {
+        // eight independent loads in flight per thread
+        const double *src_d = in ? in + lv.s + r0 : nullptr;
+        for (int i0 = ct; i0 < nr; i0 += 8 * NC) {
+            VT v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u * NC;
+                v[u] = i < nr ? (src_d ? (VT)src_d[i] : mine[i]) : (VT)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + u * NC < nr) xs[i0 + u * NC] = v[u];
         }
     }
     consumer_barrier();
@@ -122,14 +123,15 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
     } else {
         bool aborted = false;
         const int r = lane >> 2, sub = lane & 3;
+        const unsigned char *base = nullptr;
         for (int c = c0; c < c1; ++c) {
-            const int k = c - c0, st = k % kStages;
-            if (!aborted && !poll_bounded(&full[st], (k / kStages) & 1, abort_flag)) {
+            const int k = c - c0;
+            base = aborted ? nullptr : next_chunk<VT, CPG>(ring, full, abort_flag, k, base);
+            if (!aborted && !base) {
                 aborted = true;
                 *abort_flag = 1;
             }
             if (!aborted) {
-                const unsigned char *base = ring + (size_t)st * kStageBytes;
                 const int *hdr = reinterpret_cast<const int *>(base);
                 const int nrow = hdr[0], S = hdr[1], upper = hdr[2];
                 const int pr = (nrow + 3) & ~3;
@@ -161,7 +163,7 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
                     }
                 }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[st]);
+                if (lane == 0) mbar_arrive(&empty[chunk_slot<CPG>(k)]);
             }
             consumer_barrier();
         }

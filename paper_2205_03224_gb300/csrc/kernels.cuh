@@ -16,8 +16,7 @@ constexpr int kMaxCols = 160;     // Krylov columns per Gram-Schmidt pass (m + 1
 // Triangular factors of one level as a sequence of "chunks" per block: the L
 // chunks of a block in wavefront (level-set) order, then its U chunks.  A
 // chunk holds <= kChunkRows independent rows of one wavefront and is one
-// contiguous, 16-byte aligned byte range (<= kStageBytes) that a single bulk
-// copy moves into shared memory:
+// contiguous, 16-byte aligned byte range of <= kStageBytes:
 //   int32 {nrows, S, upper, maxlen}   S = entry slots per row
 //   int32 rows[pad4(nrows)]           block-local row of every slot
 //   int32 lens[pad4(nrows)]           entries of every slot
@@ -27,13 +26,21 @@ constexpr int kMaxCols = 160;     // Krylov columns per Gram-Schmidt pass (m + 1
 // Entry q of row slot t sits at
 //   FP32 (one lane per row, S = maxlen):          q*nrows + t
 //   FP64 (four lanes per row, S = 4*ceil(maxlen/4)): ((q/4)*nrows + t)*4 + q%4
-// so a warp always reads consecutive addresses.
+// so a warp always reads consecutive addresses.  The chunks of a block move
+// into a shared-memory ring of kRingData bytes CPG at a time: group g (chunks
+// CPG*g onwards, contiguous in global memory) is one bulk copy into ring slot
+// g % (kRingData / (CPG*kStageBytes)), and a chunk is found in its slot by
+// skipping the chunks before it (their sizes follow from their headers).
+// The FP32 substitutions move kGroupChunks chunks per copy (one per consumer
+// warp); the FP64 and batched ones, whose warps share every chunk, move one.
 constexpr int kStageBytes = 4096;
-constexpr int kStages = 16;
+constexpr int kGroupChunks = 4;
+constexpr int kRingData = 16 * kStageBytes;
+constexpr int kMaxSlots = kRingData / kStageBytes;
 constexpr int kConsumerWarps = 4;
 constexpr int kChunkRows = 32;
 constexpr int kTrsvThreads2 = 32 * (kConsumerWarps + 1);
-constexpr int kRingBytes = kStageBytes * kStages + 2 * kStages * 8 + 64;   // ring + mbarriers + flags
+constexpr int kRingBytes = kRingData + 2 * kMaxSlots * 8 + 64;   // ring + mbarriers + flags
 template <typename VT> struct LanesPerRow { static constexpr int value = 4; };
 template <> struct LanesPerRow<float> { static constexpr int value = 1; };
 
@@ -55,6 +62,8 @@ struct LevelView {
     const int64_t *F_rp;       // d rows
     const int32_t *F_ci;       // global column (>= e)
     const VT *F_v;
+    const int32_t *F_rows;     // level-local rows with F entries, ascending (so grouped by block)
+    const int32_t *F_blk;      // nblk + 1 ranges of every block's rows in F_rows
     const int64_t *E_rp;       // stail rows
     const int32_t *E_ci;       // level-local column
     const VT *E_v;

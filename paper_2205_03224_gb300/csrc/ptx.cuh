@@ -122,25 +122,123 @@ __device__ __forceinline__ bool wait_bounded(uint64_t *bar, unsigned parity, vol
     return true;
 }
 
+// Producer warp of the staged substitutions: streams the chunks [c0, c1)
+// (byte ranges off[c] .. off[c+1] of data) into the ring, CPG chunks per
+// bulk copy: group g goes to slot g % kGroups and completes on
+// full[slot]; a slot is reused once its consumers have arrived on
+// empty[slot].  The group offsets are read 32 groups at a time by the whole
+// warp (the next batch while the current one is issued), so that no copy
+// waits on a global load of its own size; lane 0 issues the copies.  On an
+// expired wait the CTA's abort flag and the device error word are set.
+// Before returning, lane 0 waits for the copies still in flight.
+template <int CPG>
+__device__ __forceinline__ void produce_chunks(const unsigned char *data, const int64_t *off, int c0, int c1,
+                                               unsigned char *ring, uint64_t *full, uint64_t *empty,
+                                               volatile int *abort_flag, int32_t *err, int lane) {
+    constexpr int kGroups = kRingData / (CPG * kStageBytes), kGroupBytes = CPG * kStageBytes;
+    const int ngroup = (c1 - c0 + CPG - 1) / CPG;
+    auto group_range = [&](int g, int64_t &a, int64_t &b) {
+        a = off[c0 + CPG * g];
+        b = off[min(c0 + CPG * (g + 1), c1)];
+    };
+    int issued = 0;
+    int64_t o0 = 0, o1 = 0;
+    if (lane < ngroup) group_range(lane, o0, o1);
+    for (int base = 0; base < ngroup; base += 32) {
+        int64_t n0 = 0, n1 = 0;
+        if (base + 32 + lane < ngroup) group_range(base + 32 + lane, n0, n1);
+        const int cnt = min(32, ngroup - base);
+        bool ok = true;
+        for (int t = 0; t < cnt; ++t) {
+            const int64_t s0 = __shfl_sync(0xffffffffu, o0, t), s1 = __shfl_sync(0xffffffffu, o1, t);
+            const int g = base + t, slot = g % kGroups;
+            if (g >= kGroups) {
+                const bool got = lane == 0 ? wait_bounded(&empty[slot], ((g / kGroups) - 1) & 1, abort_flag) : true;
+                if (!__all_sync(0xffffffffu, got)) {
+                    if (lane == 0) {
+                        *abort_flag = 1;
+                        atomicExch(err, 1);
+                    }
+                    ok = false;
+                    break;
+                }
+            }
+            if (lane == 0) {
+                const unsigned bytes = (unsigned)(s1 - s0);
+                mbar_expect_tx(&full[slot], bytes);
+                bulk_load(ring + (size_t)slot * kGroupBytes, data + s0, bytes, &full[slot]);
+            }
+            issued = g + 1;
+        }
+        if (!ok) break;
+        o0 = n0;
+        o1 = n1;
+    }
+    if (lane == 0)
+        for (int g = issued > kGroups ? issued - kGroups : 0; g < issued; ++g)
+            wait_bounded(&full[g % kGroups], (g / kGroups) & 1, nullptr);
+}
+
+// Bytes of one chunk (see kernels.cuh).
+template <typename VT>
+__device__ __forceinline__ int chunk_size(const int *hdr) {
+    const int nrow = hdr[0], S = hdr[1], pr = (nrow + 3) & ~3, ne = S * nrow;
+    return 16 + 8 * pr + ((ne * 4 + 15) & ~15) + ((ne * (int)sizeof(VT) + 15) & ~15) +
+           (hdr[2] ? ((nrow * (int)sizeof(VT) + 15) & ~15) : 0);
+}
+
+// Wait until chunk k (block-relative) is in shared memory and return it: its
+// group of CPG chunks is in slot (k / CPG) % kGroups, after the chunks
+// before it.
+template <typename VT, int CPG>
+__device__ __forceinline__ const unsigned char *wait_chunk(const unsigned char *ring, uint64_t *full,
+                                                           volatile int *abort_flag, int k) {
+    constexpr int kGroups = kRingData / (CPG * kStageBytes), kGroupBytes = CPG * kStageBytes;
+    const int g = k / CPG, slot = g % kGroups;
+    if (!poll_bounded(&full[slot], (g / kGroups) & 1, abort_flag)) return nullptr;
+    const unsigned char *p = ring + (size_t)slot * kGroupBytes;
+    for (int i = 0; i < k % CPG; ++i) p += chunk_size<VT>(reinterpret_cast<const int *>(p));
+    return p;
+}
+
+// For consumers that take the chunks in order: chunk k follows chunk k-1
+// (at prev) in the same group, else it starts a group that must be waited for.
+template <typename VT, int CPG>
+__device__ __forceinline__ const unsigned char *next_chunk(const unsigned char *ring, uint64_t *full,
+                                                           volatile int *abort_flag, int k,
+                                                           const unsigned char *prev) {
+    constexpr int kGroups = kRingData / (CPG * kStageBytes), kGroupBytes = CPG * kStageBytes;
+    if (k % CPG != 0) return prev + chunk_size<VT>(reinterpret_cast<const int *>(prev));
+    const int g = k / CPG, slot = g % kGroups;
+    if (!poll_bounded(&full[slot], (g / kGroups) & 1, abort_flag)) return nullptr;
+    return ring + (size_t)slot * kGroupBytes;
+}
+
+// Ring slot of chunk k for CPG chunks per copy.
+template <int CPG>
+__device__ __forceinline__ int chunk_slot(int k) { return (k / CPG) % (kRingData / (CPG * kStageBytes)); }
+
 // Registers holding one row slot of a chunk (lane-per-row layout).
 constexpr int kRegEntries = 16;
 template <typename VT>
 struct RowRegs {
-    int row, len, nrow, S, st;
+    const unsigned char *base;
+    int row, len, nrow, S;
     int col[kRegEntries];
     VT val[kRegEntries];
     VT dinv;
     bool upper, active;
 };
 
-// Wait for chunk k and copy this lane's row slot into registers.
+// Copy this lane's row slot of the chunk at p (shared memory) into registers.
+// Branch-free: every lane loads all kRegEntries slots, at indices clamped into
+// the chunk (inactive lanes read the last row slot, slots past S read slot
+// S-1), and keeps zeros (column 0, value 0) past its row's length, so that all
+// the loads of a chunk are in flight together.
 template <typename VT>
-__device__ __forceinline__ bool fetch_row(const unsigned char *ring, uint64_t *full, volatile int *abort_flag,
-                                          int k, int lane, RowRegs<VT> &R) {
-    const int st = k % kStages;
-    R.st = st;
-    if (!poll_bounded(&full[st], (k / kStages) & 1, abort_flag)) return false;
-    const int *hdr = reinterpret_cast<const int *>(ring + (size_t)st * kStageBytes);
+__device__ __forceinline__ void fetch_row(const unsigned char *p, int lane, RowRegs<VT> &R) {
+    const int *hdr = reinterpret_cast<const int *>(p);
+    R.base = p;
     R.nrow = hdr[0];
     R.S = hdr[1];
     R.upper = hdr[2] != 0;
@@ -152,20 +250,22 @@ __device__ __forceinline__ bool fetch_row(const unsigned char *ring, uint64_t *f
     const VT *vals = reinterpret_cast<const VT *>(cols + ((ne + 3) & ~3));
     const int nv = (int)((((size_t)ne * sizeof(VT) + 15) & ~(size_t)15) / sizeof(VT));
     R.active = lane < R.nrow;
-    R.row = R.active ? rows[lane] : 0;
-    R.len = R.active ? lens[lane] : 0;
-    R.dinv = (R.active && R.upper) ? vals[nv + lane] : (VT)1;
+    const int t = R.active ? lane : R.nrow - 1;
+    const int row = rows[t], len = lens[t];
+    R.row = row;
+    R.len = R.active ? len : 0;
+    const VT di = vals[R.upper ? nv + t : 0];       // L chunks have no 1/u_ii (and >= 1 entry)
+    R.dinv = (R.active && R.upper) ? di : (VT)1;
+    const int smax = R.S > 0 ? R.S - 1 : 0;
 #pragma unroll
     for (int q = 0; q < kRegEntries; ++q) {
-        if (q < R.len) {
-            R.col[q] = cols[q * R.nrow + lane];
-            R.val[q] = vals[q * R.nrow + lane];
-        } else {
-            R.col[q] = 0;
-            R.val[q] = 0;
-        }
+        const int e = min(q, smax) * R.nrow + t;
+        const int c = cols[e];
+        const VT v = vals[e];
+        const bool live = q < R.len;
+        R.col[q] = live ? c : 0;
+        R.val[q] = live ? v : (VT)0;
     }
-    return true;
 }
 
 // Named barriers 2 .. 1+kConsumerWarps hand the sweep from one consumer warp
@@ -178,27 +278,31 @@ __device__ __forceinline__ void handoff_signal(int next_warp) {
 }
 
 // Lane-per-row substitutions (FP32).  Chunk k belongs to consumer warp
-// k % kConsumerWarps.  A warp loads its next chunk's rows, columns and values
-// into registers while the other warps work, then waits for the previous
-// chunk's warp, gathers x, computes its rows, stores them and hands on; the
-// barrier orders the stores before the next warp's gathers.  Every warp runs
-// the same sequence of waits and signals whatever happens (an expired wait
-// only skips the arithmetic), so the hand-off chain always completes.
+// k % kConsumerWarps (one chunk of every group).  A warp loads its next
+// chunk's rows, columns and values into registers while the other warps
+// work, then waits for the previous chunk's warp, gathers x, computes its
+// rows, stores them and hands on; the barrier orders the stores before the
+// next warp's gathers.  Every warp runs the same sequence of waits and
+// signals whatever happens (an expired wait only skips the arithmetic), so
+// the hand-off chain always completes.
 template <typename VT>
 __device__ void consume_chunks_round_robin(const unsigned char *ring, uint64_t *full, uint64_t *empty,
                                            volatile int *abort_flag, int nchunk, VT *xs, int warp, int lane) {
+    static_assert(kConsumerWarps == kGroupChunks, "one chunk of every group per consumer warp");
     constexpr int NW = kConsumerWarps;
     bool ok = true;
     for (int k = warp; k < nchunk; k += NW) {
         RowRegs<VT> R;
-        if (ok) ok = fetch_row<VT>(ring, full, abort_flag, k, lane, R);
+        const unsigned char *p = ok ? wait_chunk<VT, kGroupChunks>(ring, full, abort_flag, k) : nullptr;
+        ok = p != nullptr;
         if (!ok && lane == 0) *abort_flag = 1;
+        if (ok) fetch_row<VT>(p, lane, R);
         if (k > 0) handoff_wait(warp);
         if (ok && !*abort_flag) {
             VT xv[kRegEntries];
 #pragma unroll
-            for (int q = 0; q < kRegEntries; ++q) xv[q] = (q < R.len) ? xs[R.col[q]] : (VT)0;
-            const VT self = R.active ? xs[R.row] : (VT)0;
+            for (int q = 0; q < kRegEntries; ++q) xv[q] = xs[R.col[q]];     // padded slots: x_0 * 0
+            const VT self = xs[R.row];
             VT a0 = 0, a1 = 0;
 #pragma unroll
             for (int q = 0; q < kRegEntries; q += 2) {
@@ -206,9 +310,8 @@ __device__ void consume_chunks_round_robin(const unsigned char *ring, uint64_t *
                 a1 += R.val[q + 1] * xv[q + 1];
             }
             if (R.len > kRegEntries) {          // long rows: the rest straight from the staged chunk
-                const int *hdr = reinterpret_cast<const int *>(ring + (size_t)R.st * kStageBytes);
                 const int pr = (R.nrow + 3) & ~3;
-                const int *cols = hdr + 4 + 2 * pr;
+                const int *cols = reinterpret_cast<const int *>(R.base) + 4 + 2 * pr;
                 const int ne = R.S * R.nrow;
                 const VT *vals = reinterpret_cast<const VT *>(cols + ((ne + 3) & ~3));
                 for (int q = kRegEntries; q < R.len; ++q) a0 += vals[q * R.nrow + lane] * xs[cols[q * R.nrow + lane]];
@@ -217,7 +320,7 @@ __device__ void consume_chunks_round_robin(const unsigned char *ring, uint64_t *
         }
         __syncwarp();
         if (k + 1 < nchunk) handoff_signal((warp + 1) % NW);
-        if (ok && lane == 0) mbar_arrive(&empty[R.st]);
+        if (ok && lane == 0) mbar_arrive(&empty[chunk_slot<kGroupChunks>(k)]);
     }
 }
 
