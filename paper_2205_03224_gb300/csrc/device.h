@@ -52,6 +52,12 @@ void launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *
 void launch_gs_dots(int64_t len, const double *V, int64_t ldv, const double *w, double *partial, unsigned *counter,
                     KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *hbuf, int grid,
                     cudaStream_t st);
+// w = A z (z also stored in column j of zcol), then the first Gram-Schmidt pass
+// (rows split over `grid` CTAs; for matrices with short rows).
+void launch_gs_spmv_dots(int64_t len, const int64_t *rp, const int32_t *ci, const double *av, const double *z,
+                         double *zcol, const double *V, int64_t ldv, double *w, double *partial, unsigned *counter,
+                         KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *hbuf, int grid,
+                         cudaStream_t st);
 void launch_gs_sub(int64_t len, double *V, int64_t ldv, double *w, double *partial, unsigned *counter,
                    KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *h2buf, int grid,
                    cudaStream_t st, double *vcopy = nullptr);

@@ -297,62 +297,113 @@ __device__ __forceinline__ void reduce_partials(const double *partial, int ncols
     reduce_columns<double>(partial, (int)gridDim.x, ncols1, out);
 }
 
-// Block partial sums of V[:, c] . w for c < ncols and of w . w (slot ncols),
-// written to partial[blockIdx.x * (ncols + 1) + c].  Columns are taken eight
-// at a time with register accumulators so that every thread keeps many
-// independent loads in flight.  The CTA reduction goes through shared memory
-// (warp u sums column u: eight values per lane, then one warp reduction),
-// which issues about a third of the FP64 adds of eight full-warp butterflies;
-// on this part FP64 instructions, not bytes, bound the Gram-Schmidt kernels.
-// w may have been written earlier in the same kernel by this CTA, so it is
-// read through L2 (ld.global.cg), never through the non-coherent read-only path.
-// Requires blockDim.x == kReduceThreads (8 warps).
-__device__ void block_dots(const double *__restrict__ V, int64_t ldv, int ncols, const double *w,
-                           int64_t i0, int64_t i1, double *partial) {
-    static_assert(kReduceThreads == 256, "one warp per column of an eight-column group");
-    __shared__ double tred[8][kReduceThreads];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int c0 = 0; c0 <= ncols; c0 += 8) {
-        const int nc = min(8, ncols + 1 - c0);
-        double acc[8];
+// Partial dots of the NC columns V[:, c0 .. c0+NC) with w over the CTA's rows
+// (and w . w into acc[NC] when WW).  The row loop issues every load of a row
+// (two rows per iteration) before any arithmetic, so each thread keeps
+// 2 (NC + 1) loads in flight: these passes are bound by memory latency and
+// FP64 issue, not by bandwidth.  w is read through L2 (ld.global.cg): it may
+// have been written earlier in the same kernel.
+template <int NC, bool WW>
+__device__ __forceinline__ void dots_group(const double *__restrict__ V, int64_t ldv, int c0, const double *w,
+                                           int64_t i0, int64_t i1, double *acc) {
+    const double *vc[NC > 0 ? NC : 1];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] = 0.0;
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const double wi = __ldcg(w + i);
+    for (int u = 0; u < NC; ++u) vc[u] = V + (int64_t)(c0 + u) * ldv;
+    const int64_t st = blockDim.x;
+    int64_t i = i0 + threadIdx.x;
+    for (; i + st < i1; i += 2 * st) {
+        const double wa = __ldcg(w + i), wb = __ldcg(w + i + st);
+        double va[NC > 0 ? NC : 1], vb[NC > 0 ? NC : 1];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int c = c0 + u;
-                if (c < ncols) acc[u] = fma(V[(int64_t)c * ldv + i], wi, acc[u]);
-                else if (c == ncols) acc[u] = fma(wi, wi, acc[u]);
-            }
+        for (int u = 0; u < NC; ++u) {
+            va[u] = vc[u][i];
+            vb[u] = vc[u][i + st];
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (u < nc) tred[u][threadIdx.x] = acc[u];
-        __syncthreads();
-        if (warp < nc) {
-            double sum = tred[warp][lane];
+        for (int u = 0; u < NC; ++u) acc[u] = fma(vb[u], wb, fma(va[u], wa, acc[u]));
+        if (WW) acc[NC] = fma(wb, wb, fma(wa, wa, acc[NC]));
+    }
+    if (i < i1) {
+        const double wa = __ldcg(w + i);
 #pragma unroll
-            for (int q = 1; q < kReduceThreads / 32; ++q) sum += tred[warp][q * 32 + lane];
-            sum = warp_sum(sum);
-            if (lane == 0) partial[(int64_t)blockIdx.x * (ncols + 1) + c0 + warp] = sum;
-        }
-        __syncthreads();
+        for (int u = 0; u < NC; ++u) acc[u] = fma(vc[u][i], wa, acc[u]);
+        if (WW) acc[NC] = fma(wa, wa, acc[NC]);
     }
 }
 
-// x_i - sum_c V[i, c] h_c with two independent partial sums (one FP64 add
-// to combine them: FP64 instructions are the scarce resource here).
+// Block partial sums of V[:, c] . w for c < ncols and of w . w (slot ncols),
+// written to partial[blockIdx.x * (ncols + 1) + c].  Columns go in groups of
+// 8, 4, 2 and 1 (the group width is uniform, so the row loops have no
+// branches), w . w with the first group.  The CTA reduction goes through
+// shared memory (warp s sums slot s: eight values per lane, then one warp
+// reduction), far fewer FP64 adds than full-warp butterflies per column.
+// Requires blockDim.x == kReduceThreads (8 warps).
+__device__ void block_dots(const double *__restrict__ V, int64_t ldv, int ncols, const double *w,
+                           int64_t i0, int64_t i1, double *partial) {
+    static_assert(kReduceThreads == 256, "eight warps reduce the slots of a group");
+    __shared__ double tred[9][kReduceThreads];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int c0 = 0;
+    bool first = true;
+    while (first || c0 < ncols) {
+        const int rem = ncols - c0;
+        const int nc = rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : rem;
+        double acc[9];
+#pragma unroll
+        for (int u = 0; u < 9; ++u) acc[u] = 0.0;
+        switch (nc + (first ? 16 : 0)) {
+            case 8: dots_group<8, false>(V, ldv, c0, w, i0, i1, acc); break;
+            case 4: dots_group<4, false>(V, ldv, c0, w, i0, i1, acc); break;
+            case 2: dots_group<2, false>(V, ldv, c0, w, i0, i1, acc); break;
+            case 1: dots_group<1, false>(V, ldv, c0, w, i0, i1, acc); break;
+            case 24: dots_group<8, true>(V, ldv, c0, w, i0, i1, acc); break;
+            case 20: dots_group<4, true>(V, ldv, c0, w, i0, i1, acc); break;
+            case 18: dots_group<2, true>(V, ldv, c0, w, i0, i1, acc); break;
+            case 17: dots_group<1, true>(V, ldv, c0, w, i0, i1, acc); break;
+            default: dots_group<0, true>(V, ldv, c0, w, i0, i1, acc); break;    // ncols == 0
+        }
+        const int ns = nc + (first ? 1 : 0);          // slots: nc columns, then w . w (in acc[nc])
+#pragma unroll
+        for (int u = 0; u < 9; ++u)
+            if (u < ns) tred[u][threadIdx.x] = acc[u];
+        __syncthreads();
+        for (int sl = warp; sl < ns; sl += kReduceThreads / 32) {
+            double sum = tred[sl][lane];
+#pragma unroll
+            for (int q = 1; q < kReduceThreads / 32; ++q) sum += tred[sl][q * 32 + lane];
+            sum = warp_sum(sum);
+            const int col = sl < nc ? c0 + sl : ncols;
+            if (lane == 0) partial[(int64_t)blockIdx.x * (ncols + 1) + col] = sum;
+        }
+        __syncthreads();
+        c0 += nc;
+        first = false;
+    }
+}
+
+// x_i - sum_c V[i, c] h_c, columns eight at a time with all eight loads
+// issued first; hs must hold zeros from ncols up to the next multiple of 8
+// (the padded slots load the last column again and multiply it by zero).
 __device__ __forceinline__ double project_out(const double *__restrict__ V, int64_t ldv, int ncols,
                                               const double *hs, int64_t i, double x) {
     double a1 = 0.0;
-    int c = 0;
-    for (; c + 1 < ncols; c += 2) {
-        x = fma(-V[(int64_t)c * ldv + i], hs[c], x);
-        a1 = fma(-V[(int64_t)(c + 1) * ldv + i], hs[c + 1], a1);
+    for (int c0 = 0; c0 < ncols; c0 += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = V[(int64_t)min(c0 + u, ncols - 1) * ldv + i];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            x = fma(-v[u], hs[c0 + u], x);
+            a1 = fma(-v[u + 1], hs[c0 + u + 1], a1);
+        }
     }
-    if (c < ncols) x = fma(-V[(int64_t)c * ldv + i], hs[c], x);
-    return ncols > 1 ? x + a1 : x;
+    return x + a1;
+}
+
+// hs[c] = h[c] for c < ncols, zeros up to the next multiple of 8.
+__device__ __forceinline__ void load_coefficients(double *hs, const double *h, int ncols) {
+    const int np = (ncols + 7) & ~7;
+    for (int c = threadIdx.x; c < np; c += blockDim.x) hs[c] = c < ncols ? __ldcg(h + c) : 0.0;
 }
 
 // Givens update of column j of the (m+1) x m Hessenberg matrix H (FGMRES).
@@ -386,16 +437,20 @@ __device__ void givens_step(KrylovCtl *ctl, double *H, double *cs, double *sn, d
 // After h (ncols values) and ||w||^2 are known: record h in column j of H and
 // in hbuf (the projection coefficients of the next kernel: the Givens update
 // below rotates the column of H in place), decide on a second pass and, if
-// none, the norm of the projected vector.
+// none, the norm of the projected vector.  Called by one whole warp: the
+// stores and ||h||^2 are spread over its lanes, lane 0 takes the decisions.
 __device__ void after_first_pass(KrylovCtl *ctl, const double *red, int ncols, double *H, double *cs,
                                  double *sn, double *g, double *hbuf) {
+    const int lane = threadIdx.x & 31;
     const int j = ctl->j, m1 = ctl->m + 1;
     double hh = 0.0;
-    for (int c = 0; c < ncols; ++c) {
+    for (int c = lane; c < ncols; c += 32) {
         H[(int64_t)j * m1 + c] = red[c];
         hbuf[c] = red[c];
-        hh += red[c] * red[c];
+        hh = fma(red[c], red[c], hh);
     }
+    hh = warp_sum(hh);
+    if (lane != 0) return;
     const double ww = red[ncols];
     ctl->wnorm2 = ww;
     const double rest = ww - hh;      // ||w - V h||^2 by Pythagoras
@@ -428,10 +483,61 @@ k_gs_dots(int64_t len, const double *__restrict__ V, int64_t ldv, const double *
     if (!finish_block(counter)) return;
     __shared__ double red[kMaxCols + 1];
     reduce_partials(partial, ncols + 1, red);
-    if (threadIdx.x == 0) {
-        after_first_pass(ctl, red, ncols, H, cs, sn, g, hbuf);
-        *counter = 0u;
+    if (threadIdx.x < 32) after_first_pass(ctl, red, ncols, H, cs, sn, g, hbuf);
+    if (threadIdx.x == 0) *counter = 0u;
+}
+
+// Pass 1 fused with the product that forms w: w = A z on the CTA's rows (one
+// thread per row, CSR), z copied into column j of zcol (the FGMRES basis Z),
+// then the same partial dots and finisher as k_gs_dots.  Every row of w is
+// written and read back by the same thread, so no CTA-wide ordering is needed.
+__global__ void __launch_bounds__(kReduceThreads)
+k_gs_spmv_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+               const double *__restrict__ av, const double *__restrict__ z, double *__restrict__ zcol,
+               const double *__restrict__ V, int64_t ldv, double *w, double *partial, unsigned *counter,
+               KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *hbuf) {
+    if (ctl->stop) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->reorth = 0;
+        return;
     }
+    const int j = ctl->j, ncols = j + 1;
+    const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
+    double *zj = zcol + (int64_t)j * len;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        // the first eight entries of the row with all index, value and x
+        // loads in flight together (indices clamped into the row), the rest
+        // (rows longer than eight) one by one
+        const int64_t p0 = rp[i], p1 = rp[i + 1];
+        double a0 = 0.0, a1 = 0.0;
+        if (p1 > p0) {
+            int cc[8];
+            double vv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int64_t pq = p0 + q < p1 ? p0 + q : p0;
+                cc[q] = ci[pq];
+                vv[q] = p0 + q < p1 ? av[pq] : 0.0;
+            }
+            double zz[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) zz[q] = z[cc[q]];
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+                a0 = fma(vv[q], zz[q], a0);
+                a1 = fma(vv[q + 1], zz[q + 1], a1);
+            }
+            for (int64_t p = p0 + 8; p < p1; ++p) a0 = fma(av[p], z[ci[p]], a0);
+        }
+        w[i] = a0 + a1;
+        zj[i] = z[i];
+    }
+    block_dots(V, ldv, ncols, w, i0, i1, partial);
+    if (!finish_block(counter)) return;
+    __shared__ double red[kMaxCols + 1];
+    reduce_partials(partial, ncols + 1, red);
+    if (threadIdx.x < 32) after_first_pass(ctl, red, ncols, H, cs, sn, g, hbuf);
+    if (threadIdx.x == 0) *counter = 0u;
 }
 
 // Pass 2: w -= V h with h from h2buf (the first-pass coefficients).  Without
@@ -446,7 +552,7 @@ k_gs_sub(int64_t len, double *__restrict__ V, int64_t ldv, double *__restrict__ 
     if (!again && (ctl->stop || ctl->breakdown)) return;
     __shared__ double hs[kMaxCols];
     const int j = ctl->j, ncols = j + 1, m1 = ctl->m + 1;
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = __ldcg(h2buf + c);
+    load_coefficients(hs, h2buf, ncols);
     __syncthreads();
     const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
     const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
@@ -467,13 +573,11 @@ k_gs_sub(int64_t len, double *__restrict__ V, int64_t ldv, double *__restrict__ 
     if (!finish_block(counter)) return;
     __shared__ double red[kMaxCols + 1];
     reduce_partials(partial, ncols + 1, red);
-    if (threadIdx.x == 0) {
-        for (int c = 0; c < ncols; ++c) {
-            H[(int64_t)j * m1 + c] += red[c];
-            h2buf[c] = red[c];
-        }
-        *counter = 0u;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) {
+        H[(int64_t)j * m1 + c] += red[c];
+        h2buf[c] = red[c];
     }
+    if (threadIdx.x == 0) *counter = 0u;
 }
 
 // Pass 3 (only after a second Gram-Schmidt pass): w -= V h2 and an explicit
@@ -486,7 +590,7 @@ k_gs_sub2(int64_t len, const double *__restrict__ V, int64_t ldv, double *__rest
     if (!ctl->reorth) return;
     __shared__ double hs[kMaxCols];
     const int j = ctl->j, ncols = j + 1, m1 = ctl->m + 1;
-    for (int c = threadIdx.x; c < ncols; c += blockDim.x) hs[c] = __ldcg(h2 + c);
+    load_coefficients(hs, h2, ncols);
     __syncthreads();
     const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
     const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
@@ -724,6 +828,14 @@ void launch_gs_dots(int64_t len, const double *V, int64_t ldv, const double *w, 
                     KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *hbuf, int grid,
                     cudaStream_t st) {
     k_gs_dots<<<grid, kReduceThreads, 0, st>>>(len, V, ldv, w, partial, counter, ctl, H, cs, sn, g, hbuf);
+    count_launch();
+}
+void launch_gs_spmv_dots(int64_t len, const int64_t *rp, const int32_t *ci, const double *av, const double *z,
+                         double *zcol, const double *V, int64_t ldv, double *w, double *partial, unsigned *counter,
+                         KrylovCtl *ctl, double *H, double *cs, double *sn, double *g, double *hbuf, int grid,
+                         cudaStream_t st) {
+    k_gs_spmv_dots<<<grid, kReduceThreads, 0, st>>>(len, rp, ci, av, z, zcol, V, ldv, w, partial, counter, ctl, H, cs,
+                                                     sn, g, hbuf);
     count_launch();
 }
 void launch_gs_sub(int64_t len, double *V, int64_t ldv, double *w, double *partial, unsigned *counter,

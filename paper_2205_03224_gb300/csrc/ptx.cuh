@@ -21,31 +21,43 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 
 // Column sums of per-CTA partials [nparts][ncols1] into out[0..ncols1) (shared
-// memory), by all warps of the finishing CTA: warp w owns columns w, w+nw, ...,
-// its lanes stride over the partials (callers use 256-thread CTAs: 8 warps),
-// so every lane keeps up to kColsPerWarp
-// independent loads in flight; the summation order is fixed (deterministic).
-constexpr int kColsPerWarp = (kMaxCols + 1 + 7) / 8;
+// memory), by all warps of the finishing CTA.  Warp w takes columns w, w+nw,
+// w+2nw, w+3nw together; its lanes load up to eight partial rows each for all
+// four columns before any addition (one memory round trip per pass of 256
+// rows), add them in a fixed pairwise tree and finish with a warp
+// reduction.  The summation order is fixed (deterministic).  Short dependent
+// chains matter here: one FP64 add takes on the order of a hundred cycles on
+// this part when nothing else is in flight.
 template <typename T>
 __device__ void reduce_columns(const T *partial, int nparts, int ncols1, T *out) {
+    constexpr int RP = 8, CW = 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    T acc[kColsPerWarp];
+    for (int cb = warp; cb < ncols1; cb += CW * nw) {
+        T acc[CW];
 #pragma unroll
-    for (int u = 0; u < kColsPerWarp; ++u) acc[u] = 0;
-    for (int p = lane; p < nparts; p += 32) {
-        const T *row = partial + (int64_t)p * ncols1;
+        for (int u = 0; u < CW; ++u) acc[u] = 0;
+        for (int p0 = 0; p0 < nparts; p0 += 32 * RP) {
+            T v[CW][RP];
 #pragma unroll
-        for (int u = 0; u < kColsPerWarp; ++u) {
-            const int c = warp + nw * u;
-            if (c < ncols1) acc[u] += __ldcg(row + c);
+            for (int u = 0; u < CW; ++u) {
+                const int c = cb + u * nw;
+#pragma unroll
+                for (int q = 0; q < RP; ++q) {
+                    const int p = p0 + q * 32 + lane;
+                    v[u][q] = (c < ncols1 && p < nparts) ? __ldcg(partial + (int64_t)p * ncols1 + c) : (T)0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CW; ++u)
+                acc[u] += ((v[u][0] + v[u][1]) + (v[u][2] + v[u][3])) + ((v[u][4] + v[u][5]) + (v[u][6] + v[u][7]));
         }
-    }
 #pragma unroll
-    for (int u = 0; u < kColsPerWarp; ++u) {
-        const int c = warp + nw * u;          // uniform over the warp
-        if (c < ncols1) {
-            const T v = warp_sum(acc[u]);
-            if (lane == 0) out[c] = v;
+        for (int u = 0; u < CW; ++u) {
+            const int c = cb + u * nw;          // uniform over the warp
+            if (c < ncols1) {
+                const T t = warp_sum(acc[u]);
+                if (lane == 0) out[c] = t;
+            }
         }
     }
     __syncthreads();

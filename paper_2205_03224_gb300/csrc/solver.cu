@@ -319,11 +319,15 @@ void finish_setup(gemslr_ctx *h, bool compute_lowrank) {
 void fgmres_step(gemslr_ctx *h, cudaStream_t st) {
     const int64_t n = h->host.n;
     apply_perm(h, h->vin, h->zout, st);
-    {
-        ProfScope ps("spmv_A", st);
-        launch_spmv(n, h->A_rp, h->A_ci, h->A_v, h->zout, nullptr, h->w, h->spmv_lanes, st, h->Z, h->ctl);
-    }
-    {
+    if (h->spmv_lanes <= 8) {       // short rows: the product is fused into the first pass
+        ProfScope ps("spmv_gs_dots", st);
+        launch_gs_spmv_dots(n, h->A_rp, h->A_ci, h->A_v, h->zout, h->Z, h->V, n, h->w, h->partial, h->counter,
+                            h->ctl, h->Hs, h->cs, h->sn, h->g, h->h2, h->red_grid, st);
+    } else {
+        {
+            ProfScope ps("spmv_A", st);
+            launch_spmv(n, h->A_rp, h->A_ci, h->A_v, h->zout, nullptr, h->w, h->spmv_lanes, st, h->Z, h->ctl);
+        }
         ProfScope ps("gs_dots", st);
         launch_gs_dots(n, h->V, n, h->w, h->partial, h->counter, h->ctl, h->Hs, h->cs, h->sn, h->g, h->h2,
                        h->red_grid, st);
