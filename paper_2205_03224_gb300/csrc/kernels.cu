@@ -400,6 +400,47 @@ __device__ __forceinline__ double project_out(const double *__restrict__ V, int6
     return x + a1;
 }
 
+// project_out for the two rows ia and ib together: all sixteen loads of a
+// column group are issued before its arithmetic.
+__device__ __forceinline__ void project_pair(const double *__restrict__ V, int64_t ldv, int ncols, const double *hs,
+                                             int64_t ia, int64_t ib, double &xa, double &xb) {
+    double a1 = 0.0, b1 = 0.0;
+    for (int c0 = 0; c0 < ncols; c0 += 8) {
+        double va[8], vb[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t off = (int64_t)min(c0 + u, ncols - 1) * ldv;
+            va[u] = V[off + ia];
+            vb[u] = V[off + ib];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            xa = fma(-va[u], hs[c0 + u], xa);
+            a1 = fma(-va[u + 1], hs[c0 + u + 1], a1);
+            xb = fma(-vb[u], hs[c0 + u], xb);
+            b1 = fma(-vb[u + 1], hs[c0 + u + 1], b1);
+        }
+    }
+    xa += a1;
+    xb += b1;
+}
+
+// Sum of v over the CTA (kReduceThreads threads), valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double ws[kReduceThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) ws[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < kReduceThreads / 32; ++q) t += ws[q];
+    }
+    __syncthreads();
+    return t;
+}
+
 // hs[c] = h[c] for c < ncols, zeros up to the next multiple of 8.
 __device__ __forceinline__ void load_coefficients(double *hs, const double *h, int ncols) {
     const int np = (ncols + 7) & ~7;
@@ -558,7 +599,24 @@ k_gs_sub(int64_t len, double *__restrict__ V, int64_t ldv, double *__restrict__ 
     const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
     const double inv = again ? 0.0 : 1.0 / ctl->beta;
     double *vn = V + (int64_t)(j + 1) * ldv;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const int64_t st = blockDim.x;
+    int64_t i = i0 + threadIdx.x;
+    for (; i + st < i1; i += 2 * st) {
+        double xa = w[i], xb = w[i + st];
+        project_pair(V, ldv, ncols, hs, i, i + st, xa, xb);
+        if (again) {
+            w[i] = xa;
+            w[i + st] = xb;
+        } else {
+            vn[i] = xa * inv;
+            vn[i + st] = xb * inv;
+            if (vcopy) {
+                vcopy[i] = xa * inv;
+                vcopy[i + st] = xb * inv;
+            }
+        }
+    }
+    if (i < i1) {
         const double x = project_out(V, ldv, ncols, hs, i, w[i]);
         if (again) {
             w[i] = x;
@@ -581,8 +639,9 @@ k_gs_sub(int64_t len, double *__restrict__ V, int64_t ldv, double *__restrict__ 
 }
 
 // Pass 3 (only after a second Gram-Schmidt pass): w -= V h2 and an explicit
-// ||w||^2 (Pythagoras would lose all accuracy to cancellation here); the
-// finisher sets beta, the breakdown flag and the Givens update.
+// ||w||^2 in the same sweep (Pythagoras would lose all accuracy to
+// cancellation here); the finisher sets beta, the breakdown flag and the
+// Givens update.
 __global__ void __launch_bounds__(kReduceThreads)
 k_gs_sub2(int64_t len, const double *__restrict__ V, int64_t ldv, double *__restrict__ w,
           const double *__restrict__ h2, double *partial, unsigned *counter, KrylovCtl *ctl, double *H, double *cs,
@@ -594,9 +653,24 @@ k_gs_sub2(int64_t len, const double *__restrict__ V, int64_t ldv, double *__rest
     __syncthreads();
     const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
     const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) w[i] = project_out(V, ldv, ncols, hs, i, w[i]);
-    __syncthreads();
-    block_dots(nullptr, 0, 0, w, i0, i1, partial);
+    // w -= V h2 and ||w||^2 in the same sweep
+    double ww = 0.0;
+    const int64_t st = blockDim.x;
+    int64_t i = i0 + threadIdx.x;
+    for (; i + st < i1; i += 2 * st) {
+        double xa = w[i], xb = w[i + st];
+        project_pair(V, ldv, ncols, hs, i, i + st, xa, xb);
+        w[i] = xa;
+        w[i + st] = xb;
+        ww = fma(xb, xb, fma(xa, xa, ww));
+    }
+    if (i < i1) {
+        const double x = project_out(V, ldv, ncols, hs, i, w[i]);
+        w[i] = x;
+        ww = fma(x, x, ww);
+    }
+    ww = block_sum(ww);
+    if (threadIdx.x == 0) partial[blockIdx.x] = ww;
     if (!finish_block(counter)) return;
     __shared__ double red[1];
     reduce_partials(partial, 1, red);
