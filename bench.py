@@ -37,6 +37,14 @@ WORKLOAD = ("3-D 7-pt convection-diffusion 64^3 (n=262144, beta=0.1), 4 levels x
 UNIT = "solves/s (FGMRES to 1e-8)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 1.203      # FP64 FMA probe on this machine's GB300 (0.601 TFMA/s)
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# roofline kernel from one ncu --set full capture of the same workload
+# (profiles/trsv_c2_apply_<precision>.md); an entry must be removed when that
+# kernel changes.
+NCU_TRAFFIC = {
+    ("c2", "mixed", "trsv_up_L0"): 45_667_072 + 7_936,
+    ("c2", "fp64", "trsv_up_L0"): 76_670_208 + 919_040,
+}
 
 
 def cfg():
@@ -263,8 +271,9 @@ def run_ours(args):
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
     achieved = ab[top] / (top_ms * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC.get((CONFIG, args.precision, top))
     roofline = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "bytes_per_launch": ab[top],
+                "frac": achieved / hbm, "traffic": traffic, "bytes_per_launch": ab[top],
                 "ms_per_launch": top_ms,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     total_prof = sum(v[0] for v in prof.values())

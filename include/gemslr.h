@@ -328,6 +328,17 @@ gemslr_status gemslr_learned_loss_grad(gemslr_handle h, int32_t nb, const double
  * gemslr_profile_reset: drops the accumulated totals.
  */
 uint64_t gemslr_kernel_launches(void);
+/*
+ * gemslr_selftest_wait (no counterpart in the paper): exercises the bounded
+ * device waits every staged kernel relies on.  One CTA waits on an mbarrier
+ * that nothing completes, once with the suspending wait and once with the
+ * polling wait, each bounded by `cycles` SM clock cycles (> 0).  Returns
+ * GEMSLR_ERR_TIMEOUT when both waits gave up and the context is still usable
+ * afterwards (the expected outcome), GEMSLR_ERR_CUDA on a CUDA error,
+ * GEMSLR_ERR_ARG if a wait returned or cycles <= 0.  Uses the default stream
+ * and synchronises the device.
+ */
+gemslr_status gemslr_selftest_wait(int64_t cycles);
 void gemslr_profile_enable(int32_t on);
 void gemslr_profile_reset(void);
 int32_t gemslr_profile_read(char *names, size_t len, double *ms, int64_t *counts, int32_t maxn);

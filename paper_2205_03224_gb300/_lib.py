@@ -69,7 +69,7 @@ EXPORTED = [
     "gemslr_setup_batch", "gemslr_batch_apply", "gemslr_batch_fgmres_solve", "gemslr_batch_stats",
     "gemslr_batch_last_error", "gemslr_batch_destroy",
     "gemslr_learned_train", "gemslr_learned_enable", "gemslr_learned_info", "gemslr_learned_params",
-    "gemslr_learned_loss_grad", "gemslr_apply_static",
+    "gemslr_learned_loss_grad", "gemslr_apply_static", "gemslr_selftest_wait",
 ]
 
 _lib = None
@@ -125,6 +125,7 @@ def load():
     L.gemslr_learned_params.argtypes = [P, i32, P, i64]
     L.gemslr_learned_loss_grad.argtypes = [P, i32, P, P, P, P]
     L.gemslr_apply_static.argtypes = [P, P, P, P]
+    L.gemslr_selftest_wait.argtypes = [i64]
     L.gemslr_batch_destroy.argtypes = [P]
     L.gemslr_batch_destroy.restype = None
     for name in EXPORTED:
@@ -184,6 +185,11 @@ def mat_struct(M, keep):
 
 def kernel_launches():
     return int(load().gemslr_kernel_launches())
+
+
+def selftest_wait(cycles):
+    """Status name of gemslr_selftest_wait (\"ERR_TIMEOUT\" is the expected outcome)."""
+    return STATUS.get(load().gemslr_selftest_wait(int(cycles)), "?")
 
 
 def profile_enable(on=True):

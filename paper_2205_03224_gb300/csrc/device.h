@@ -67,6 +67,8 @@ void launch_gs_sub2(int64_t len, double *V, int64_t ldv, double *w, const double
 void launch_gs_scale(int64_t len, double *V, int64_t ldv, const double *w, const KrylovCtl *ctl, double *vcopy,
                      cudaStream_t st);
 void launch_gs_next(KrylovCtl *ctl, cudaStream_t st);
+// Two bounded waits on an mbarrier nothing completes (see gemslr_selftest_wait).
+void launch_wait_selftest(long long limit, int32_t *gave_up, cudaStream_t st);
 void launch_norm2(int64_t len, const double *x, double *partial, unsigned *counter, double *out, int grid,
                   cudaStream_t st);
 void launch_scale_by_norm(int64_t len, const double *x, const double *n2, double *v, cudaStream_t st,

@@ -240,6 +240,25 @@ k_lowrank(const LevelView<VT, WT> lv, VT *__restrict__ work, const VT *__restric
     }
 }
 
+// ---- bounded-wait self-test ---------------------------------------------------
+// An mbarrier that nothing ever completes: warp 0 waits on it with the
+// suspending wait, warp 1 with the polling wait, both bounded by `limit`
+// clock cycles.  gave_up[w] = 1 when warp w's wait expired (it must).
+__global__ void k_wait_selftest(long long limit, int32_t *gave_up) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    const bool got = warp == 0 ? wait_bounded(&bar, 0, &abort_flag, limit)
+                               : poll_bounded(&bar, 0, &abort_flag, limit);
+    if ((threadIdx.x & 31) == 0) gave_up[warp] = got ? 0 : 1;
+}
+
 // ---- vectors ----------------------------------------------------------------
 __global__ void k_gather(int64_t n, const int32_t *__restrict__ perm, const double *__restrict__ src,
                          double *__restrict__ dst) {
@@ -927,6 +946,10 @@ void launch_gs_sub2(int64_t len, double *V, int64_t ldv, double *w, const double
 void launch_gs_scale(int64_t len, double *V, int64_t ldv, const double *w, const KrylovCtl *ctl, double *vcopy,
                      cudaStream_t st) {
     k_gs_scale<<<grid_for(len, 256, 1216), 256, 0, st>>>(len, V, ldv, w, ctl, vcopy);
+    count_launch();
+}
+void launch_wait_selftest(long long limit, int32_t *gave_up, cudaStream_t st) {
+    k_wait_selftest<<<1, 64, 0, st>>>(limit, gave_up);
     count_launch();
 }
 void launch_gs_next(KrylovCtl *ctl, cudaStream_t st) { k_gs_next<<<1, 32, 0, st>>>(ctl); count_launch(); }

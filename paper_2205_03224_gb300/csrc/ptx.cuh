@@ -97,15 +97,20 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
+// Every wait is bounded: about 2 s of clock cycles (or `limit`), or until
+// another warp of the CTA has raised `abort`.
+constexpr long long kSpinCycles = 4000000000ll;
+
 // Polling wait (no suspension) for the consumers' critical path, bounded like wait_bounded.
-__device__ __forceinline__ bool poll_bounded(uint64_t *bar, unsigned parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool poll_bounded(uint64_t *bar, unsigned parity, volatile int *abort_flag,
+                                             long long limit = kSpinCycles) {
     if (mbar_test_wait(bar, parity)) return true;
     const long long t0 = clock64();
     unsigned spins = 0;
     while (!mbar_test_wait(bar, parity)) {
         if ((++spins & 63u) == 0u) {
             if (*abort_flag) return false;
-            if (clock64() - t0 > 4000000000ll) return false;
+            if (clock64() - t0 > limit) return false;
         }
     }
     return true;
@@ -121,15 +126,12 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
                  : "memory");
 }
 
-// Every wait is bounded: about 2 s of clock cycles, or until another warp of
-// the CTA has raised `abort`.
-constexpr long long kSpinCycles = 4000000000ll;
-
-__device__ __forceinline__ bool wait_bounded(uint64_t *bar, unsigned parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool wait_bounded(uint64_t *bar, unsigned parity, volatile int *abort_flag,
+                                             long long limit = kSpinCycles) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (abort_flag && *abort_flag) return false;
-        if (clock64() - t0 > kSpinCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }

@@ -805,6 +805,28 @@ void gemslr_destroy(gemslr_handle h) { delete h; }
 
 uint64_t gemslr_kernel_launches(void) { return launches_total(); }
 
+gemslr_status gemslr_selftest_wait(int64_t cycles) {
+    return guard([&] {
+        if (cycles <= 0) fail(GEMSLR_ERR_ARG, "cycles must be positive");
+        int32_t *dev = nullptr;
+        GEMSLR_CUDA(cudaMalloc(&dev, 2 * sizeof(int32_t)));
+        int32_t host[2] = {0, 0};
+        cudaError_t e = cudaMemset(dev, 0, 2 * sizeof(int32_t));
+        if (e == cudaSuccess) {
+            launch_wait_selftest((long long)cycles, dev, 0);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(host, dev, sizeof(host), cudaMemcpyDeviceToHost);
+        // the context must still be usable after the expired waits
+        if (e == cudaSuccess) e = cudaMemset(dev, 0, 2 * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        cudaFree(dev);
+        if (e != cudaSuccess) fail(GEMSLR_ERR_CUDA, cudaGetErrorString(e));
+        if (host[0] != 1 || host[1] != 1) fail(GEMSLR_ERR_ARG, "a wait on an mbarrier that nothing completes returned");
+        fail(GEMSLR_ERR_TIMEOUT, "bounded waits expired as expected (self-test)");
+    });
+}
+
 void gemslr_profile_enable(int32_t on) { profile_enable(on != 0); }
 
 void gemslr_profile_reset(void) { profile_reset(); }
