@@ -190,7 +190,7 @@ void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, Chun
             hdr[0] = (int32_t)n;
             hdr[1] = (int32_t)S;
             hdr[2] = upper ? 1 : 0;
-            hdr[3] = (int32_t)maxlen;
+            hdr[3] = 0;                                          // slices that follow in the chunk
             const int64_t pr = (n + 3) & ~int64_t(3);
             int32_t *rr = hdr + 4, *ll = rr + pr, *cc = ll + pr;
             VT *vv = reinterpret_cast<VT *>(reinterpret_cast<unsigned char *>(cc) + pad16((size_t)(S * n) * 4));
@@ -224,20 +224,42 @@ void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, Chun
 }
 
 template <typename VT>
-void build_chunks(const Csr &L, const Csr &U, const std::vector<int64_t> &bp, ChunkHost<VT> &out, int max_rows) {
+void build_chunks(const Csr &L, const Csr &U, const std::vector<int64_t> &bp, ChunkHost<VT> &out, int max_rows,
+                  int max_slices) {
     validate_tri(L, bp, false);
     validate_tri(U, bp, true);
     for (size_t b = 0; b + 1 < bp.size(); ++b) {
+        const size_t first = out.off.size() - 1;
         append_factor_chunks<VT>(L, bp[b], bp[b + 1], false, out, out.maxwf_L, max_rows);
         append_factor_chunks<VT>(U, bp[b], bp[b + 1], true, out, out.maxwf_U, max_rows);
+        if (max_slices >= 2) {
+            // pair consecutive slices into one chunk (<= kStageBytes) by dropping the
+            // boundary between them; the first slice's header says one follows
+            std::vector<int64_t> keep(out.off.begin(), out.off.begin() + (int64_t)first + 1);
+            size_t c = first;
+            const size_t last = out.off.size() - 1;
+            while (c < last) {
+                const int64_t a0 = out.off[c], a1 = out.off[c + 1];
+                if (c + 1 < last && out.off[c + 2] - a0 <= (int64_t)kStageBytes) {
+                    reinterpret_cast<int32_t *>(out.data.data() + a0)[3] = 1;
+                    keep.push_back(out.off[c + 2]);
+                    c += 2;
+                } else {
+                    keep.push_back(a1);
+                    c += 1;
+                }
+            }
+            out.off.swap(keep);
+        }
         out.blk_chunk.push_back((int32_t)(out.off.size() - 1));
     }
     if (out.data.empty()) out.data.resize(16, 0);
 }
 
 
-template void build_chunks<float>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<float> &, int);
-template void build_chunks<double>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<double> &, int);
+template void build_chunks<float>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<float> &, int, int);
+template void build_chunks<double>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<double> &, int,
+                                   int);
 
 namespace {
 
@@ -254,7 +276,7 @@ void upload_level(const HostLevel &hl, int64_t n, bool schur, Arena &a, DevLevel
     for (size_t b = 0; b + 1 < hl.bp.size(); ++b) maxrows = std::max(maxrows, hl.bp[b + 1] - hl.bp[b]);
     d.smem_rows = (kRingBytes + maxrows * (int64_t)sizeof(VT) <= smem_limit) ? (int)maxrows : 0;
     ChunkHost<VT> ch;
-    build_chunks<VT>(hl.L, hl.U, hl.bp, ch, kChunkRows);
+    build_chunks<VT>(hl.L, hl.U, hl.bp, ch, kChunkRows, LanesPerRow<VT>::value == 1 ? 2 : 1);
     v.C.data = a.upload(ch.data);
     v.C.off = a.upload(ch.off);
     v.C.blk_chunk = a.upload(ch.blk_chunk);

@@ -103,9 +103,11 @@ struct ChunkHost {
 };
 
 // Chunks (layout in kernels.cuh) of the block-diagonal factors L, U of one
-// level with at most max_rows row slots per chunk.
+// level: slices of at most max_rows row slots, up to max_slices (1 or 2)
+// consecutive slices per chunk.
 template <typename VT>
-void build_chunks(const Csr &L, const Csr &U, const std::vector<int64_t> &bp, ChunkHost<VT> &out, int max_rows);
+void build_chunks(const Csr &L, const Csr &U, const std::vector<int64_t> &bp, ChunkHost<VT> &out, int max_rows,
+                  int max_slices);
 
 // ---- device memory arena ------------------------------------------------------------
 class Arena {

@@ -17,7 +17,10 @@ constexpr int kMaxCols = 160;     // Krylov columns per Gram-Schmidt pass (m + 1
 // chunks of a block in wavefront (level-set) order, then its U chunks.  A
 // chunk holds <= kChunkRows independent rows of one wavefront and is one
 // contiguous, 16-byte aligned byte range of <= kStageBytes:
-//   int32 {nrows, S, upper, maxlen}   S = entry slots per row
+//   int32 {nrows, S, upper, more}     S = entry slots per row; more = 1 when
+//                                     a second slice of the same layout follows
+//                                     in the same chunk (FP32: two consecutive
+//                                     wavefront slices per chunk when they fit)
 //   int32 rows[pad4(nrows)]           block-local row of every slot
 //   int32 lens[pad4(nrows)]           entries of every slot
 //   int32 cols[pad4(S*nrows)]         block-local columns

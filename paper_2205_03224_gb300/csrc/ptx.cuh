@@ -193,12 +193,18 @@ __device__ __forceinline__ void produce_chunks(const unsigned char *data, const 
             wait_bounded(&full[g % kGroups], (g / kGroups) & 1, nullptr);
 }
 
-// Bytes of one chunk (see kernels.cuh).
+// Bytes of one slice, and of one chunk (a slice and, when its header says
+// so, the slice after it); see kernels.cuh.
 template <typename VT>
-__device__ __forceinline__ int chunk_size(const int *hdr) {
+__device__ __forceinline__ int slice_size(const int *hdr) {
     const int nrow = hdr[0], S = hdr[1], pr = (nrow + 3) & ~3, ne = S * nrow;
     return 16 + 8 * pr + ((ne * 4 + 15) & ~15) + ((ne * (int)sizeof(VT) + 15) & ~15) +
            (hdr[2] ? ((nrow * (int)sizeof(VT) + 15) & ~15) : 0);
+}
+template <typename VT>
+__device__ __forceinline__ int chunk_size(const int *hdr) {
+    const int a = slice_size<VT>(hdr);
+    return hdr[3] ? a + slice_size<VT>(hdr + a / 4) : a;
 }
 
 // Wait until chunk k (block-relative) is in shared memory and return it: its
@@ -282,6 +288,29 @@ __device__ __forceinline__ void fetch_row(const unsigned char *p, int lane, RowR
     }
 }
 
+// x_row = (x_row - sum_q val_q x_col_q) * dinv for this lane's row slot.
+template <typename VT>
+__device__ __forceinline__ void solve_row(const RowRegs<VT> &R, VT *xs, int lane) {
+    VT xv[kRegEntries];
+#pragma unroll
+    for (int q = 0; q < kRegEntries; ++q) xv[q] = xs[R.col[q]];     // padded slots: x_0 * 0
+    const VT self = xs[R.row];
+    VT a0 = 0, a1 = 0;
+#pragma unroll
+    for (int q = 0; q < kRegEntries; q += 2) {
+        a0 += R.val[q] * xv[q];
+        a1 += R.val[q + 1] * xv[q + 1];
+    }
+    if (R.len > kRegEntries) {          // long rows: the rest straight from the staged slice
+        const int pr = (R.nrow + 3) & ~3;
+        const int *cols = reinterpret_cast<const int *>(R.base) + 4 + 2 * pr;
+        const int ne = R.S * R.nrow;
+        const VT *vals = reinterpret_cast<const VT *>(cols + ((ne + 3) & ~3));
+        for (int q = kRegEntries; q < R.len; ++q) a0 += vals[q * R.nrow + lane] * xs[cols[q * R.nrow + lane]];
+    }
+    if (R.active) xs[R.row] = (self - (a0 + a1)) * R.dinv;
+}
+
 // Named barriers 2 .. 1+kConsumerWarps hand the sweep from one consumer warp
 // to the next (64 threads: the signalling warp arrives, the next one waits).
 __device__ __forceinline__ void handoff_wait(int warp) {
@@ -293,10 +322,10 @@ __device__ __forceinline__ void handoff_signal(int next_warp) {
 
 // Lane-per-row substitutions (FP32).  Chunk k belongs to consumer warp
 // k % kConsumerWarps (one chunk of every group).  A warp loads its next
-// chunk's rows, columns and values into registers while the other warps
-// work, then waits for the previous chunk's warp, gathers x, computes its
-// rows, stores them and hands on; the barrier orders the stores before the
-// next warp's gathers.  Every warp runs the same sequence of waits and
+// chunk (one or two slices: consecutive wavefronts) into registers while the
+// other warps work, then waits for the previous chunk's warp, gathers x,
+// computes its rows (the second slice after a __syncwarp), stores them and
+// hands on; the barrier orders the stores before the next warp's gathers.  Every warp runs the same sequence of waits and
 // signals whatever happens (an expired wait only skips the arithmetic), so
 // the hand-off chain always completes.
 template <typename VT>
@@ -306,31 +335,23 @@ __device__ void consume_chunks_round_robin(const unsigned char *ring, uint64_t *
     constexpr int NW = kConsumerWarps;
     bool ok = true;
     for (int k = warp; k < nchunk; k += NW) {
-        RowRegs<VT> R;
+        RowRegs<VT> R, R2;
         const unsigned char *p = ok ? wait_chunk<VT, kGroupChunks>(ring, full, abort_flag, k) : nullptr;
         ok = p != nullptr;
         if (!ok && lane == 0) *abort_flag = 1;
-        if (ok) fetch_row<VT>(p, lane, R);
+        bool two = false;
+        if (ok) {
+            fetch_row<VT>(p, lane, R);
+            two = reinterpret_cast<const int *>(p)[3] != 0;
+            if (two) fetch_row<VT>(p + slice_size<VT>(reinterpret_cast<const int *>(p)), lane, R2);
+        }
         if (k > 0) handoff_wait(warp);
         if (ok && !*abort_flag) {
-            VT xv[kRegEntries];
-#pragma unroll
-            for (int q = 0; q < kRegEntries; ++q) xv[q] = xs[R.col[q]];     // padded slots: x_0 * 0
-            const VT self = xs[R.row];
-            VT a0 = 0, a1 = 0;
-#pragma unroll
-            for (int q = 0; q < kRegEntries; q += 2) {
-                a0 += R.val[q] * xv[q];
-                a1 += R.val[q + 1] * xv[q + 1];
+            solve_row<VT>(R, xs, lane);
+            if (two) {
+                __syncwarp();                   // the first slice's rows before the second's gathers
+                solve_row<VT>(R2, xs, lane);
             }
-            if (R.len > kRegEntries) {          // long rows: the rest straight from the staged chunk
-                const int pr = (R.nrow + 3) & ~3;
-                const int *cols = reinterpret_cast<const int *>(R.base) + 4 + 2 * pr;
-                const int ne = R.S * R.nrow;
-                const VT *vals = reinterpret_cast<const VT *>(cols + ((ne + 3) & ~3));
-                for (int q = kRegEntries; q < R.len; ++q) a0 += vals[q * R.nrow + lane] * xs[cols[q * R.nrow + lane]];
-            }
-            if (R.active) xs[R.row] = (self - (a0 + a1)) * R.dinv;
         }
         __syncwarp();
         if (k + 1 < nchunk) handoff_signal((warp + 1) % NW);
