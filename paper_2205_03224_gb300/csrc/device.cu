@@ -183,6 +183,7 @@ void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, Chun
             if (n == 0) fail(GEMSLR_ERR_UNSUPPORTED, "a factor row has too many entries for the staged substitution");
             const size_t bytes = chunk_bytes<VT>(n, maxlen, upper);
             const int64_t S = chunk_slots<VT>(maxlen);
+            out.max_slots = std::max(out.max_slots, (int)S);
             const size_t base = out.data.size();
             out.data.resize(base + bytes, 0);
             unsigned char *p = out.data.data() + base;
@@ -280,6 +281,7 @@ void upload_level(const HostLevel &hl, int64_t n, bool schur, Arena &a, DevLevel
     v.C.data = a.upload(ch.data);
     v.C.off = a.upload(ch.off);
     v.C.blk_chunk = a.upload(ch.blk_chunk);
+    v.max_slots = ch.max_slots;
     d.nwf_L = ch.maxwf_L;
     d.nwf_U = ch.maxwf_U;
     d.nchunks = (int64_t)ch.off.size() - 1;

@@ -100,6 +100,7 @@ struct ChunkHost {
     std::vector<int64_t> off{0};
     std::vector<int32_t> blk_chunk{0};
     int maxwf_L = 0, maxwf_U = 0;
+    int max_slots = 0;                 // largest S of any slice
 };
 
 // Chunks (layout in kernels.cuh) of the block-diagonal factors L, U of one

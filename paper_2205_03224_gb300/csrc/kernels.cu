@@ -44,7 +44,7 @@ template <> __device__ __forceinline__ double wval<double, double>(double w) { r
 // with the rows of a chunk spread over the consumer warps, lane per row.
 // MODE 0: right-hand side from `in` (FP64 user vector) or `work`; result in work.
 // MODE 1: right-hand side F y2 (gathered from work's tail); work[rows] -= result.
-template <typename VT, typename WT, int MODE, bool SMEM>
+template <typename VT, typename WT, int MODE, bool SMEM, int NE>
 __global__ void __launch_bounds__(kTrsvThreads2)
 k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict__ work,
        double *__restrict__ out_final, VT *__restrict__ scratch) {
@@ -119,7 +119,7 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
     if constexpr (LanesPerRow<VT>::value == 1) {
         // FP32: the consumer warps take the chunks in turn, one lane per row,
         // each loading its next chunk into registers while the others work.
-        consume_chunks_round_robin<VT>(ring, full, empty, abort_flag, c1 - c0, xs, warp, lane);
+        consume_chunks_round_robin<VT, NE>(ring, full, empty, abort_flag, c1 - c0, xs, warp, lane);
     } else {
         bool aborted = false;
         const int r = lane >> 2, sub = lane & 3;
@@ -847,21 +847,60 @@ void launch_trsv(const LevelView<VT, WT> &lv, int mode, int smem_rows, const dou
     if (lv.nblk == 0) return;
     const bool smem = smem_rows > 0;
     const size_t bytes = kRingBytes + (smem ? (size_t)smem_rows * sizeof(VT) : 0);
-    if (mode == 0) {
-        if (smem) { k_trsv<VT, WT, 0, true><<<lv.nblk, kTrsvThreads2, bytes, st>>>(lv, in, work, out_final, scratch); count_launch(); }
-        else { k_trsv<VT, WT, 0, false><<<lv.nblk, kTrsvThreads2, bytes, st>>>(lv, in, work, out_final, scratch); count_launch(); }
-    } else {
-        if (smem) { k_trsv<VT, WT, 1, true><<<lv.nblk, kTrsvThreads2, bytes, st>>>(lv, in, work, out_final, scratch); count_launch(); }
-        else { k_trsv<VT, WT, 1, false><<<lv.nblk, kTrsvThreads2, bytes, st>>>(lv, in, work, out_final, scratch); count_launch(); }
+    // FP32: register slots sized to the level's longest row (4, 8, 12 or 16)
+    const int ne = LanesPerRow<VT>::value != 1 ? 16 : lv.max_slots <= 4 ? 4 : lv.max_slots <= 8 ? 8
+                                                 : lv.max_slots <= 12 ? 12 : 16;
+#define GEMSLR_TRSV(M, S, N) k_trsv<VT, WT, M, S, N><<<lv.nblk, kTrsvThreads2, bytes, st>>>(lv, in, work, out_final, scratch)
+#define GEMSLR_TRSV_NE(M, S)                  \
+    switch (ne) {                             \
+        case 4: GEMSLR_TRSV(M, S, 4); break;  \
+        case 8: GEMSLR_TRSV(M, S, 8); break;  \
+        case 12: GEMSLR_TRSV(M, S, 12); break; \
+        default: GEMSLR_TRSV(M, S, 16); break; \
     }
+    if constexpr (LanesPerRow<VT>::value == 1) {
+        if (mode == 0) {
+            if (smem) { GEMSLR_TRSV_NE(0, true) }
+            else { GEMSLR_TRSV_NE(0, false) }
+        } else {
+            if (smem) { GEMSLR_TRSV_NE(1, true) }
+            else { GEMSLR_TRSV_NE(1, false) }
+        }
+    } else {
+        if (mode == 0) {
+            if (smem) GEMSLR_TRSV(0, true, 16);
+            else GEMSLR_TRSV(0, false, 16);
+        } else {
+            if (smem) GEMSLR_TRSV(1, true, 16);
+            else GEMSLR_TRSV(1, false, 16);
+        }
+    }
+#undef GEMSLR_TRSV_NE
+#undef GEMSLR_TRSV
+    count_launch();
 }
 
 template <typename VT, typename WT>
 void set_trsv_smem_limit(int bytes) {
-    cudaFuncSetAttribute(k_trsv<VT, WT, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_trsv<VT, WT, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_trsv<VT, WT, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
-    cudaFuncSetAttribute(k_trsv<VT, WT, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
+    auto set = [&](auto fn, int b) { cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, b); };
+    set(k_trsv<VT, WT, 0, true, 16>, bytes);
+    set(k_trsv<VT, WT, 1, true, 16>, bytes);
+    set(k_trsv<VT, WT, 0, false, 16>, kRingBytes);
+    set(k_trsv<VT, WT, 1, false, 16>, kRingBytes);
+    if constexpr (LanesPerRow<VT>::value == 1) {
+        set(k_trsv<VT, WT, 0, true, 4>, bytes);
+        set(k_trsv<VT, WT, 0, true, 8>, bytes);
+        set(k_trsv<VT, WT, 0, true, 12>, bytes);
+        set(k_trsv<VT, WT, 1, true, 4>, bytes);
+        set(k_trsv<VT, WT, 1, true, 8>, bytes);
+        set(k_trsv<VT, WT, 1, true, 12>, bytes);
+        set(k_trsv<VT, WT, 0, false, 4>, kRingBytes);
+        set(k_trsv<VT, WT, 0, false, 8>, kRingBytes);
+        set(k_trsv<VT, WT, 0, false, 12>, kRingBytes);
+        set(k_trsv<VT, WT, 1, false, 4>, kRingBytes);
+        set(k_trsv<VT, WT, 1, false, 8>, kRingBytes);
+        set(k_trsv<VT, WT, 1, false, 12>, kRingBytes);
+    }
 }
 
 template <typename VT, typename WT>

@@ -59,6 +59,7 @@ struct LevelView {
     int64_t s, e;              // rows [s, e) of the multilevel order
     int64_t stail;             // n - e
     int32_t nblk;
+    int32_t max_slots;         // longest chunk row (entry slots) of the level's factors
     const int64_t *blk_row;    // nblk + 1, level-local
     ChunkView C;               // L and U of every block (see above)
     int32_t *err;              // device error word (1: a bounded wait expired)

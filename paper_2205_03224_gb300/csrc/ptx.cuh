@@ -238,14 +238,16 @@ __device__ __forceinline__ const unsigned char *next_chunk(const unsigned char *
 template <int CPG>
 __device__ __forceinline__ int chunk_slot(int k) { return (k / CPG) % (kRingData / (CPG * kStageBytes)); }
 
-// Registers holding one row slot of a chunk (lane-per-row layout).
+// Registers holding one row slot of a chunk (lane-per-row layout): NE entry
+// slots (the launch picks NE >= the level's longest row where it can; longer
+// rows finish from shared memory).
 constexpr int kRegEntries = 16;
-template <typename VT>
+template <typename VT, int NE = kRegEntries>
 struct RowRegs {
     const unsigned char *base;
     int row, len, nrow, S;
-    int col[kRegEntries];
-    VT val[kRegEntries];
+    int col[NE];
+    VT val[NE];
     VT dinv;
     bool upper, active;
 };
@@ -255,8 +257,8 @@ struct RowRegs {
 // the chunk (inactive lanes read the last row slot, slots past S read slot
 // S-1), and keeps zeros (column 0, value 0) past its row's length, so that all
 // the loads of a chunk are in flight together.
-template <typename VT>
-__device__ __forceinline__ void fetch_row(const unsigned char *p, int lane, RowRegs<VT> &R) {
+template <typename VT, int NE>
+__device__ __forceinline__ void fetch_row(const unsigned char *p, int lane, RowRegs<VT, NE> &R) {
     const int *hdr = reinterpret_cast<const int *>(p);
     R.base = p;
     R.nrow = hdr[0];
@@ -278,7 +280,7 @@ __device__ __forceinline__ void fetch_row(const unsigned char *p, int lane, RowR
     R.dinv = (R.active && R.upper) ? di : (VT)1;
     const int smax = R.S > 0 ? R.S - 1 : 0;
 #pragma unroll
-    for (int q = 0; q < kRegEntries; ++q) {
+    for (int q = 0; q < NE; ++q) {
         const int e = min(q, smax) * R.nrow + t;
         const int c = cols[e];
         const VT v = vals[e];
@@ -289,24 +291,25 @@ __device__ __forceinline__ void fetch_row(const unsigned char *p, int lane, RowR
 }
 
 // x_row = (x_row - sum_q val_q x_col_q) * dinv for this lane's row slot.
-template <typename VT>
-__device__ __forceinline__ void solve_row(const RowRegs<VT> &R, VT *xs, int lane) {
-    VT xv[kRegEntries];
+template <typename VT, int NE>
+__device__ __forceinline__ void solve_row(const RowRegs<VT, NE> &R, VT *xs, int lane) {
+    static_assert(NE % 2 == 0, "two partial sums");
+    VT xv[NE];
 #pragma unroll
-    for (int q = 0; q < kRegEntries; ++q) xv[q] = xs[R.col[q]];     // padded slots: x_0 * 0
+    for (int q = 0; q < NE; ++q) xv[q] = xs[R.col[q]];     // padded slots: x_0 * 0
     const VT self = xs[R.row];
     VT a0 = 0, a1 = 0;
 #pragma unroll
-    for (int q = 0; q < kRegEntries; q += 2) {
+    for (int q = 0; q < NE; q += 2) {
         a0 += R.val[q] * xv[q];
         a1 += R.val[q + 1] * xv[q + 1];
     }
-    if (R.len > kRegEntries) {          // long rows: the rest straight from the staged slice
+    if (R.len > NE) {                   // long rows: the rest straight from the staged slice
         const int pr = (R.nrow + 3) & ~3;
         const int *cols = reinterpret_cast<const int *>(R.base) + 4 + 2 * pr;
         const int ne = R.S * R.nrow;
         const VT *vals = reinterpret_cast<const VT *>(cols + ((ne + 3) & ~3));
-        for (int q = kRegEntries; q < R.len; ++q) a0 += vals[q * R.nrow + lane] * xs[cols[q * R.nrow + lane]];
+        for (int q = NE; q < R.len; ++q) a0 += vals[q * R.nrow + lane] * xs[cols[q * R.nrow + lane]];
     }
     if (R.active) xs[R.row] = (self - (a0 + a1)) * R.dinv;
 }
@@ -328,29 +331,29 @@ __device__ __forceinline__ void handoff_signal(int next_warp) {
 // hands on; the barrier orders the stores before the next warp's gathers.  Every warp runs the same sequence of waits and
 // signals whatever happens (an expired wait only skips the arithmetic), so
 // the hand-off chain always completes.
-template <typename VT>
+template <typename VT, int NE>
 __device__ void consume_chunks_round_robin(const unsigned char *ring, uint64_t *full, uint64_t *empty,
                                            volatile int *abort_flag, int nchunk, VT *xs, int warp, int lane) {
     static_assert(kConsumerWarps == kGroupChunks, "one chunk of every group per consumer warp");
     constexpr int NW = kConsumerWarps;
     bool ok = true;
     for (int k = warp; k < nchunk; k += NW) {
-        RowRegs<VT> R, R2;
+        RowRegs<VT, NE> R, R2;
         const unsigned char *p = ok ? wait_chunk<VT, kGroupChunks>(ring, full, abort_flag, k) : nullptr;
         ok = p != nullptr;
         if (!ok && lane == 0) *abort_flag = 1;
         bool two = false;
         if (ok) {
-            fetch_row<VT>(p, lane, R);
+            fetch_row<VT, NE>(p, lane, R);
             two = reinterpret_cast<const int *>(p)[3] != 0;
-            if (two) fetch_row<VT>(p + slice_size<VT>(reinterpret_cast<const int *>(p)), lane, R2);
+            if (two) fetch_row<VT, NE>(p + slice_size<VT>(reinterpret_cast<const int *>(p)), lane, R2);
         }
         if (k > 0) handoff_wait(warp);
         if (ok && !*abort_flag) {
-            solve_row<VT>(R, xs, lane);
+            solve_row<VT, NE>(R, xs, lane);
             if (two) {
                 __syncwarp();                   // the first slice's rows before the second's gathers
-                solve_row<VT>(R2, xs, lane);
+                solve_row<VT, NE>(R2, xs, lane);
             }
         }
         __syncwarp();
