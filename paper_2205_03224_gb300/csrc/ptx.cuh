@@ -246,7 +246,7 @@ template <typename VT, int NE = kRegEntries>
 struct RowRegs {
     const unsigned char *base;
     int row, len, nrow, S;
-    int col[NE];
+    int col[NE];               // byte offsets into x (column * sizeof(VT)), computed before the wait
     VT val[NE];
     VT dinv;
     bool upper, active;
@@ -285,7 +285,7 @@ __device__ __forceinline__ void fetch_row(const unsigned char *p, int lane, RowR
         const int c = cols[e];
         const VT v = vals[e];
         const bool live = q < R.len;
-        R.col[q] = live ? c : 0;
+        R.col[q] = live ? c * (int)sizeof(VT) : 0;
         R.val[q] = live ? v : (VT)0;
     }
 }
@@ -296,7 +296,8 @@ __device__ __forceinline__ void solve_row(const RowRegs<VT, NE> &R, VT *xs, int 
     static_assert(NE % 2 == 0, "two partial sums");
     VT xv[NE];
 #pragma unroll
-    for (int q = 0; q < NE; ++q) xv[q] = xs[R.col[q]];     // padded slots: x_0 * 0
+    for (int q = 0; q < NE; ++q)            // padded slots: x_0 * 0
+        xv[q] = *reinterpret_cast<const VT *>(reinterpret_cast<const unsigned char *>(xs) + R.col[q]);
     const VT self = xs[R.row];
     VT a0 = 0, a1 = 0;
 #pragma unroll
@@ -348,16 +349,18 @@ __device__ void consume_chunks_round_robin(const unsigned char *ring, uint64_t *
             two = reinterpret_cast<const int *>(p)[3] != 0;
             if (two) fetch_row<VT, NE>(p + slice_size<VT>(reinterpret_cast<const int *>(p)), lane, R2);
         }
+        const bool go = ok && !*abort_flag;     // read before the wait, off the critical path
         if (k > 0) handoff_wait(warp);
-        if (ok && !*abort_flag) {
+        if (go) {
             solve_row<VT, NE>(R, xs, lane);
             if (two) {
                 __syncwarp();                   // the first slice's rows before the second's gathers
                 solve_row<VT, NE>(R2, xs, lane);
             }
         }
-        __syncwarp();
+        // bar.arrive orders each lane's own stores before the next warp's gathers
         if (k + 1 < nchunk) handoff_signal((warp + 1) % NW);
+        __syncwarp();                           // every lane is done with the staged chunk
         if (ok && lane == 0) mbar_arrive(&empty[chunk_slot<kGroupChunks>(k)]);
     }
 }
