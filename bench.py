@@ -144,8 +144,13 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------------------------
 def algorithmic_bytes(fac, n, nnzA, sv=8, si=4, sw=8):
-    """Bytes each kernel class must move per launch (values, indices, vectors), by the layout."""
+    """Bytes each kernel class must move per launch (values, indices, vectors), by the layout.
+
+    The previous level's W u is added by the kernels that first read each of its
+    tail rows, so its W reads (rows x k) are charged to the next level's down
+    sweep and coupling kernel, or to the last level."""
     out = {}
+    prev_k = 0
     for l, lv in enumerate(fac["levels"]):
         d = lv["L"].shape[0]
         s = lv["E"].shape[0]
@@ -153,13 +158,15 @@ def algorithmic_bytes(fac, n, nnzA, sv=8, si=4, sw=8):
         nl = lv["L"].nnz
         nu_off = lv["U"].nnz - d
         tri = (nl + nu_off) * (sv + si) + d * sv + 2 * d * 4 * 2      # entries, 1/u_ii, slot rows/lengths
-        out[f"trsv_down_L{l}"] = tri + 2 * d * sv
+        out[f"trsv_down_L{l}"] = tri + 2 * d * sv + d * prev_k * sw
         out[f"trsv_up_L{l}"] = tri + lv["F"].nnz * (2 * sv + si) + (d + 1) * 8 + 2 * d * sv
-        out[f"couple_EWt_L{l}"] = lv["E"].nnz * (2 * sv + si) + (s + 1) * 8 + 2 * s * sv + s * k * sw
-        out[f"lowrank_Wu_L{l}"] = s * k * sw + 2 * s * sv if k else 0
+        out[f"couple_EWt_L{l}"] = (lv["E"].nnz * (2 * sv + si) + (s + 1) * 8 + 2 * s * sv + s * k * sw
+                                   + s * prev_k * sw)
+        prev_k = k
     last = fac["last"]
     dl = last["L"].shape[0]
-    out["trsv_last"] = (last["L"].nnz + last["U"].nnz - dl) * (sv + si) + dl * sv + 2 * dl * 8 + 2 * dl * sv
+    out["trsv_last"] = ((last["L"].nnz + last["U"].nnz - dl) * (sv + si) + dl * sv + 2 * dl * 8 + 2 * dl * sv
+                        + dl * prev_k * sw)
     out["spmv_A"] = nnzA * 12 + (n + 1) * 8 + 2 * n * 8
     return out
 

@@ -361,30 +361,35 @@ void apply_levels(DevHierarchy<VT, WT> &d, int from, const double *in, VT *work,
     static const char *kDown[] = {"trsv_down_L0", "trsv_down_L1", "trsv_down_L2", "trsv_down_L3", "trsv_down_L4+"};
     static const char *kUp[] = {"trsv_up_L0", "trsv_up_L1", "trsv_up_L2", "trsv_up_L3", "trsv_up_L4+"};
     static const char *kCouple[] = {"couple_EWt_L0", "couple_EWt_L1", "couple_EWt_L2", "couple_EWt_L3", "couple_EWt_L4+"};
-    static const char *kLow[] = {"lowrank_Wu_L0", "lowrank_Wu_L1", "lowrank_Wu_L2", "lowrank_Wu_L3", "lowrank_Wu_L4+"};
     // learned correction at the deepest Schur level (active only when that level is part of this application)
     const bool learn = d.learned && d.learned->enabled && nl >= 1 && from <= nl - 1;
+    // W_l u_l of the level before is added where its tail rows are first read
+    PendingLowRank<VT, WT> pend;
     for (int l = from; l < nl; ++l) {
         DevLevel<VT, WT> &L = d.lev[l];
         const double *src = (l == from) ? in : nullptr;
         {
             ProfScope ps(kDown[std::min(l, 4)], st);
-            launch_trsv<VT, WT>(L.view, 0, L.smem_rows, src, work, nullptr, d.scratch, st);
+            launch_trsv<VT, WT>(L.view, 0, L.smem_rows, src, work, nullptr, d.scratch, st, pend);
         }
         {
             ProfScope ps(kCouple[std::min(l, 4)], st);
-            launch_couple<VT, WT>(L.view, src, work, d.partial, d.counter, d.u, st);
+            launch_couple<VT, WT>(L.view, src, work, d.partial, d.counter, d.u, st, pend);
         }
         if (learn && l == nl - 1) learned_save<VT>(*d.learned, L.view.e, work, st);   // z2 of level l*
-        {
-            ProfScope ps(kLow[std::min(l, 4)], st);
-            launch_lowrank<VT, WT>(L.view, work, d.u, st);
+        pend = PendingLowRank<VT, WT>();
+        if (L.view.k > 0 && L.view.stail > 0) {
+            pend.W = L.view.W;
+            pend.u = d.u;
+            pend.ld = L.view.stail;
+            pend.row0 = L.view.e;
+            pend.k = L.view.k;
         }
     }
     {
         ProfScope ps("trsv_last", st);
         launch_trsv<VT, WT>(d.last.view, 0, d.last.smem_rows, from == nl ? in : nullptr, work,
-                            learn ? nullptr : out_final, d.scratch, st);
+                            learn ? nullptr : out_final, d.scratch, st, pend);
     }
     if (learn) {
         // S_hat y2 = C y2 - E (LU)^{-1} F y2 on a scratch vector, then y2 += N(rho)

@@ -33,15 +33,15 @@ int profile_read(char *names, size_t len, double *ms, int64_t *counts, int maxn)
 uint64_t launches_total();
 
 // ---- launchers (kernels.cu) --------------------------------------------------
+// pl: the previous level's pending W u (MODE 0 only; default: none).
 template <typename VT, typename WT>
 void launch_trsv(const LevelView<VT, WT> &lv, int mode, int smem_rows, const double *in, VT *work,
-                 double *out_final, VT *scratch, cudaStream_t st);
+                 double *out_final, VT *scratch, cudaStream_t st,
+                 const PendingLowRank<VT, WT> &pl = PendingLowRank<VT, WT>());
 template <typename VT, typename WT> void set_trsv_smem_limit(int bytes);
 template <typename VT, typename WT>
 void launch_couple(const LevelView<VT, WT> &lv, const double *in, VT *work, VT *partial, unsigned *counter,
-                   VT *u, cudaStream_t st);
-template <typename VT, typename WT>
-void launch_lowrank(const LevelView<VT, WT> &lv, VT *work, const VT *u, cudaStream_t st);
+                   VT *u, cudaStream_t st, const PendingLowRank<VT, WT> &pl = PendingLowRank<VT, WT>());
 void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t st);
 void launch_scatter(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t st);
 void launch_zero(int64_t n, double *x, cudaStream_t st);

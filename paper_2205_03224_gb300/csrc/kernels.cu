@@ -8,7 +8,9 @@
 //   k_couple         z2 = b2 - E_l z1 and the partial sums of W_l^T z2; the last
 //                    CTA to finish reduces them in a fixed order and forms
 //                    u = H_l (W_l^T z2), H_l = (I - R_l)^-1 - I (eq. gemslr5);
-//   k_lowrank        z2 += W_l u  (the right-hand side u2 + z2 of level l+1);
+//   W_l u            (the right-hand side u2 + z2 of level l+1) is added by the
+//                    kernels that first read each tail row: the next level's
+//                    down sweep and coupling kernel, or the last level;
 //   last level       k_trsv on the block-Jacobi blocks (Sec. 4.3);
 //   k_trsv   (up)    y1 = z1 - U^-1 L^-1 (F_l y2), F_l y2 formed row by row as
 //                    the right-hand side of the forward sweep.
@@ -33,6 +35,28 @@ template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v
 template <typename VT, typename WT> __device__ __forceinline__ VT wval(WT w) { return (VT)to_f(w); }
 template <> __device__ __forceinline__ double wval<double, double>(double w) { return w; }
 
+// Row g's share of the previous level's W u (see PendingLowRank): eight
+// columns at a time with their loads issued first.  u is read through L2:
+// the coupling kernel that reads it also rewrites it in its finisher.
+template <typename VT, typename WT>
+__device__ __forceinline__ VT pending_row(const PendingLowRank<VT, WT> &pl, int64_t g) {
+    const WT *w = pl.W + (g - pl.row0);
+    VT a0 = 0, a1 = 0;
+    int c = 0;
+    for (; c + 7 < pl.k; c += 8) {
+        WT wv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) wv[q] = w[(int64_t)(c + q) * pl.ld];
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+            a0 += wval<VT, WT>(wv[q]) * __ldcg(pl.u + c + q);
+            a1 += wval<VT, WT>(wv[q + 1]) * __ldcg(pl.u + c + q + 1);
+        }
+    }
+    for (; c < pl.k; ++c) a0 += wval<VT, WT>(w[(int64_t)c * pl.ld]) * __ldcg(pl.u + c);
+    return a0 + a1;
+}
+
 
 // ---- level-scheduled substitutions over one block --------------------------
 // One CTA per diagonal block.  Warp kConsumerWarps is the producer: it
@@ -47,7 +71,7 @@ template <> __device__ __forceinline__ double wval<double, double>(double w) { r
 template <typename VT, typename WT, int MODE, bool SMEM, int NE>
 __global__ void __launch_bounds__(kTrsvThreads2)
 k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict__ work,
-       double *__restrict__ out_final, VT *__restrict__ scratch) {
+       double *__restrict__ out_final, VT *__restrict__ scratch, const PendingLowRank<VT, WT> pl) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *ring = smem;
     // FP32: kGroupChunks chunks per copy, one per consumer warp; FP64: one
@@ -100,6 +124,9 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
             for (int64_t p = lv.F_rp[g]; p < lv.F_rp[g + 1]; ++p) acc += lv.F_v[p] * work[lv.F_ci[p]];
             xs[g - r0] = acc;
         }
+    } else if (pl.W) {
+        // right-hand side z2 + W u of the previous level (MODE 0, never the first level)
+        for (int i = ct; i < nr; i += NC) xs[i] = mine[i] + pending_row<VT, WT>(pl, lv.s + r0 + i);
     } else if (in || SMEM) {
         // eight independent loads in flight per thread
         const double *src_d = in ? in + lv.s + r0 : nullptr;
@@ -185,7 +212,8 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
 template <typename VT, typename WT>
 __global__ void __launch_bounds__(kCoupleRows)
 k_couple(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict__ work,
-         VT *__restrict__ partial, unsigned *__restrict__ counter, VT *__restrict__ u_out) {
+         VT *__restrict__ partial, unsigned *__restrict__ counter, VT *u_out,
+         const PendingLowRank<VT, WT> pl) {
     __shared__ VT zs[kCoupleRows];
     __shared__ VT ts[kMaxRank];
     __shared__ int last;
@@ -194,6 +222,7 @@ k_couple(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restri
     const int64_t i = i0 + threadIdx.x;
     if (i < i1) {
         VT z = in ? (VT)in[lv.e + i] : work[lv.e + i];
+        if (pl.W) z += pending_row<VT, WT>(pl, lv.e + i);
         for (int64_t p = lv.E_rp[i]; p < lv.E_rp[i + 1]; ++p) z -= lv.E_v[p] * work[lv.s + lv.E_ci[p]];
         work[lv.e + i] = z;
         zs[threadIdx.x] = z;
@@ -222,22 +251,6 @@ k_couple(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restri
         u_out[c] = acc;
     }
     if (threadIdx.x == 0) *counter = 0u;
-}
-
-// work[e + i] += sum_c W[i, c] u[c]
-template <typename VT, typename WT>
-__global__ void __launch_bounds__(256)
-k_lowrank(const LevelView<VT, WT> lv, VT *__restrict__ work, const VT *__restrict__ u) {
-    __shared__ VT us[kMaxRank];
-    const int k = lv.k;
-    for (int c = threadIdx.x; c < k; c += blockDim.x) us[c] = u[c];
-    __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < lv.stail;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        VT acc = 0;
-        for (int c = 0; c < k; ++c) acc += wval<VT, WT>(lv.W[(int64_t)c * lv.stail + i]) * us[c];
-        work[lv.e + i] += acc;
-    }
 }
 
 // ---- bounded-wait self-test ---------------------------------------------------
@@ -843,14 +856,15 @@ static int grid_for(int64_t n, int threads, int cap) {
 
 template <typename VT, typename WT>
 void launch_trsv(const LevelView<VT, WT> &lv, int mode, int smem_rows, const double *in, VT *work,
-                 double *out_final, VT *scratch, cudaStream_t st) {
+                 double *out_final, VT *scratch, cudaStream_t st, const PendingLowRank<VT, WT> &pl) {
     if (lv.nblk == 0) return;
     const bool smem = smem_rows > 0;
     const size_t bytes = kRingBytes + (smem ? (size_t)smem_rows * sizeof(VT) : 0);
     // FP32: register slots sized to the level's longest row (4, 8, 12 or 16)
     const int ne = LanesPerRow<VT>::value != 1 ? 16 : lv.max_slots <= 4 ? 4 : lv.max_slots <= 8 ? 8
                                                  : lv.max_slots <= 12 ? 12 : 16;
-#define GEMSLR_TRSV(M, S, N) k_trsv<VT, WT, M, S, N><<<lv.nblk, kTrsvThreads2, bytes, st>>>(lv, in, work, out_final, scratch)
+#define GEMSLR_TRSV(M, S, N) \
+    k_trsv<VT, WT, M, S, N><<<lv.nblk, kTrsvThreads2, bytes, st>>>(lv, in, work, out_final, scratch, pl)
 #define GEMSLR_TRSV_NE(M, S)                  \
     switch (ne) {                             \
         case 4: GEMSLR_TRSV(M, S, 4); break;  \
@@ -905,31 +919,26 @@ void set_trsv_smem_limit(int bytes) {
 
 template <typename VT, typename WT>
 void launch_couple(const LevelView<VT, WT> &lv, const double *in, VT *work, VT *partial, unsigned *counter,
-                   VT *u, cudaStream_t st) {
+                   VT *u, cudaStream_t st, const PendingLowRank<VT, WT> &pl) {
     if (lv.stail == 0) return;
     const int grid = (int)((lv.stail + kCoupleRows - 1) / kCoupleRows);
-    k_couple<VT, WT><<<grid, kCoupleRows, 0, st>>>(lv, in, work, partial, counter, u); count_launch();
+    k_couple<VT, WT><<<grid, kCoupleRows, 0, st>>>(lv, in, work, partial, counter, u, pl); count_launch();
 }
 
-template <typename VT, typename WT>
-void launch_lowrank(const LevelView<VT, WT> &lv, VT *work, const VT *u, cudaStream_t st) {
-    if (lv.k == 0 || lv.stail == 0) return;
-    k_lowrank<VT, WT><<<grid_for(lv.stail, 256, 1216), 256, 0, st>>>(lv, work, u); count_launch();
-}
 
 template void launch_trsv<double, double>(const LevelView<double, double> &, int, int, const double *, double *,
-                                          double *, double *, cudaStream_t);
+                                          double *, double *, cudaStream_t, const PendingLowRank<double, double> &);
 template void launch_trsv<float, __nv_bfloat16>(const LevelView<float, __nv_bfloat16> &, int, int, const double *,
-                                                float *, double *, float *, cudaStream_t);
+                                                float *, double *, float *, cudaStream_t,
+                                                const PendingLowRank<float, __nv_bfloat16> &);
 template void set_trsv_smem_limit<double, double>(int);
 template void set_trsv_smem_limit<float, __nv_bfloat16>(int);
 template void launch_couple<double, double>(const LevelView<double, double> &, const double *, double *, double *,
-                                            unsigned *, double *, cudaStream_t);
+                                            unsigned *, double *, cudaStream_t,
+                                            const PendingLowRank<double, double> &);
 template void launch_couple<float, __nv_bfloat16>(const LevelView<float, __nv_bfloat16> &, const double *, float *,
-                                                  float *, unsigned *, float *, cudaStream_t);
-template void launch_lowrank<double, double>(const LevelView<double, double> &, double *, const double *, cudaStream_t);
-template void launch_lowrank<float, __nv_bfloat16>(const LevelView<float, __nv_bfloat16> &, float *, const float *,
-                                                   cudaStream_t);
+                                                  float *, unsigned *, float *, cudaStream_t,
+                                                  const PendingLowRank<float, __nv_bfloat16> &);
 
 void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t st) {
     if (n > 0) { k_gather<<<grid_for(n, 256, 4864), 256, 0, st>>>(n, perm, src, dst); count_launch(); }

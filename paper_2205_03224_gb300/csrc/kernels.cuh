@@ -76,6 +76,18 @@ struct LevelView {
     const VT *H;               // k x k, column-major
 };
 
+// The low-rank term W u of the previous level (Alg. 2 step 7: the right-hand
+// side of level l+1 is z2 + W u), applied by the kernels that first read each
+// row of that level's tail instead of by a separate pass: row g of the
+// multilevel order takes sum_c W[g - row0 + c*ld] u[c].  W == nullptr: none.
+template <typename VT, typename WT>
+struct PendingLowRank {
+    const WT *W = nullptr;
+    const VT *u = nullptr;
+    int64_t ld = 0, row0 = 0;
+    int32_t k = 0;
+};
+
 // Control block of one FGMRES / Arnoldi step sequence (device memory).
 struct KrylovCtl {
     int32_t j;            // current column
