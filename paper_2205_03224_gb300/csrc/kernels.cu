@@ -117,12 +117,41 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
         // one thread per row so that their index and value loads overlap
         for (int i = ct; i < nr; i += NC) xs[i] = (VT)0;
         consumer_barrier();
+        // four rows per thread at a time, each step's loads for all of them in
+        // flight together (row ids, row extents, the first two entries, x)
         const int f1 = lv.F_blk[b + 1];
-        for (int t = lv.F_blk[b] + ct; t < f1; t += NC) {
-            const int64_t g = lv.F_rows[t];
-            VT acc = 0;
-            for (int64_t p = lv.F_rp[g]; p < lv.F_rp[g + 1]; ++p) acc += lv.F_v[p] * work[lv.F_ci[p]];
-            xs[g - r0] = acc;
+        for (int t0 = lv.F_blk[b] + ct; t0 < f1; t0 += 4 * NC) {
+            int64_t g[4], pa[4], pb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) g[u] = t0 + u * NC < f1 ? lv.F_rows[t0 + u * NC] : -1;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                pa[u] = g[u] >= 0 ? lv.F_rp[g[u]] : 0;
+                pb[u] = g[u] >= 0 ? lv.F_rp[g[u] + 1] : 0;
+            }
+            int32_t cc[4][2];
+            VT vv[4][2];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const bool live = pa[u] + q < pb[u];
+                    const int64_t pq = live ? pa[u] + q : pa[u];
+                    cc[u][q] = g[u] >= 0 ? lv.F_ci[pq] : 0;
+                    vv[u][q] = live ? lv.F_v[pq] : (VT)0;
+                }
+            VT xv[4][2];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) xv[u][q] = g[u] >= 0 ? work[cc[u][q]] : (VT)0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (g[u] < 0) continue;
+                VT acc = vv[u][0] * xv[u][0] + vv[u][1] * xv[u][1];
+                for (int64_t p = pa[u] + 2; p < pb[u]; ++p) acc += lv.F_v[p] * work[lv.F_ci[p]];
+                xs[g[u] - r0] = acc;
+            }
         }
     } else if (pl.W) {
         // right-hand side z2 + W u of the previous level (MODE 0, never the first level)
