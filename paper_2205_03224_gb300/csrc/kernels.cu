@@ -35,25 +35,29 @@ template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v
 template <typename VT, typename WT> __device__ __forceinline__ VT wval(WT w) { return (VT)to_f(w); }
 template <> __device__ __forceinline__ double wval<double, double>(double w) { return w; }
 
-// Row g's share of the previous level's W u (see PendingLowRank): eight
-// columns at a time with their loads issued first.  u is read through L2:
+// Row g's share of the previous level's W u (see PendingLowRank): sixteen
+// columns at a time with all their loads issued first (columns past k load
+// the last column again and are multiplied by zero).  u is read through L2:
 // the coupling kernel that reads it also rewrites it in its finisher.
 template <typename VT, typename WT>
 __device__ __forceinline__ VT pending_row(const PendingLowRank<VT, WT> &pl, int64_t g) {
     const WT *w = pl.W + (g - pl.row0);
     VT a0 = 0, a1 = 0;
-    int c = 0;
-    for (; c + 7 < pl.k; c += 8) {
-        WT wv[8];
+    for (int c0 = 0; c0 < pl.k; c0 += 16) {
+        WT wv[16];
+        VT uv[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) wv[q] = w[(int64_t)(c + q) * pl.ld];
+        for (int q = 0; q < 16; ++q) {
+            const int c = min(c0 + q, pl.k - 1);
+            wv[q] = w[(int64_t)c * pl.ld];
+            uv[q] = c0 + q < pl.k ? __ldcg(pl.u + c) : (VT)0;
+        }
 #pragma unroll
-        for (int q = 0; q < 8; q += 2) {
-            a0 += wval<VT, WT>(wv[q]) * __ldcg(pl.u + c + q);
-            a1 += wval<VT, WT>(wv[q + 1]) * __ldcg(pl.u + c + q + 1);
+        for (int q = 0; q < 16; q += 2) {
+            a0 += wval<VT, WT>(wv[q]) * uv[q];
+            a1 += wval<VT, WT>(wv[q + 1]) * uv[q + 1];
         }
     }
-    for (; c < pl.k; ++c) a0 += wval<VT, WT>(w[(int64_t)c * pl.ld]) * __ldcg(pl.u + c);
     return a0 + a1;
 }
 
@@ -249,23 +253,60 @@ k_couple(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restri
     const int64_t i0 = (int64_t)blockIdx.x * kCoupleRows;
     const int64_t i1 = min(i0 + (int64_t)kCoupleRows, lv.stail);
     const int64_t i = i0 + threadIdx.x;
+    VT z = 0;
     if (i < i1) {
-        VT z = in ? (VT)in[lv.e + i] : work[lv.e + i];
+        z = in ? (VT)in[lv.e + i] : work[lv.e + i];
         if (pl.W) z += pending_row<VT, WT>(pl, lv.e + i);
-        for (int64_t p = lv.E_rp[i]; p < lv.E_rp[i + 1]; ++p) z -= lv.E_v[p] * work[lv.s + lv.E_ci[p]];
+        // the row's first two E entries with all their loads together, then the rest
+        const int64_t pa = lv.E_rp[i], pb = lv.E_rp[i + 1];
+        int32_t cc[2];
+        VT vv[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const bool live = pa + q < pb;
+            const int64_t pq = live ? pa + q : pa;
+            cc[q] = pb > pa ? lv.E_ci[pq] : 0;
+            vv[q] = live ? lv.E_v[pq] : (VT)0;
+        }
+        const VT x0 = work[lv.s + cc[0]], x1 = work[lv.s + cc[1]];
+        z -= vv[0] * x0;
+        z -= vv[1] * x1;
+        for (int64_t p = pa + 2; p < pb; ++p) z -= lv.E_v[p] * work[lv.s + lv.E_ci[p]];
         work[lv.e + i] = z;
-        zs[threadIdx.x] = z;
     }
+    zs[threadIdx.x] = z;
     const int k = lv.k;
     if (k == 0) return;
     __syncthreads();
+    // partial W^T z2: warp w takes columns w, w+nw, w+2nw, w+3nw together, each
+    // lane its eight rows of every one of them, all 32 loads before any FMA
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int c = warp; c < k; c += nwarp) {
-        VT acc = 0;
-        const WT *wc = lv.W + (int64_t)c * lv.stail;
-        for (int64_t r = i0 + lane; r < i1; r += 32) acc += wval<VT, WT>(wc[r]) * zs[r - i0];
-        acc = warp_sum(acc);
-        if (lane == 0) partial[(int64_t)blockIdx.x * k + c] = acc;
+    const int64_t nr = i1 - i0;
+    static_assert(kCoupleRows == 256, "eight rows per lane");
+    for (int cb = warp; cb < k; cb += 4 * nwarp) {
+        WT wv[4][8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = min(cb + u * nwarp, k - 1);
+            const WT *wc = lv.W + (int64_t)c * lv.stail + i0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) wv[u][q] = wc[min((int64_t)(lane + 32 * q), nr - 1)];
+        }
+        VT acc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            acc[u] = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[u] += wval<VT, WT>(wv[u][q]) * zs[lane + 32 * q];   // zs = 0 past i1
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = cb + u * nwarp;        // uniform over the warp
+            if (c < k) {
+                const VT t = warp_sum(acc[u]);
+                if (lane == 0) partial[(int64_t)blockIdx.x * k + c] = t;
+            }
+        }
     }
     __threadfence();
     __syncthreads();
@@ -273,11 +314,23 @@ k_couple(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restri
     __syncthreads();
     if (!last) return;
     __threadfence();
+    // u = H t: every thread's row of H is loaded while the partials are reduced
+    constexpr int kHPre = sizeof(VT) == 4 ? 32 : 16;
+    VT hrow[kHPre];
+    const int c = threadIdx.x;
+#pragma unroll
+    for (int d = 0; d < kHPre; ++d) hrow[d] = (c < k && d < k) ? lv.H[c + (int64_t)d * k] : (VT)0;
     reduce_columns<VT>(partial, (int)gridDim.x, k, ts);
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int cc2 = c; cc2 < k; cc2 += blockDim.x) {
         VT acc = 0;
-        for (int d = 0; d < k; ++d) acc += lv.H[c + (int64_t)d * k] * ts[d];
-        u_out[c] = acc;
+        if (cc2 == c) {
+#pragma unroll
+            for (int d = 0; d < kHPre; ++d) acc += hrow[d] * (d < k ? ts[d] : (VT)0);
+            for (int d = kHPre; d < k; ++d) acc += lv.H[cc2 + (int64_t)d * k] * ts[d];
+        } else {
+            for (int d = 0; d < k; ++d) acc += lv.H[cc2 + (int64_t)d * k] * ts[d];
+        }
+        u_out[cc2] = acc;
     }
     if (threadIdx.x == 0) *counter = 0u;
 }
