@@ -304,7 +304,7 @@ k_couple(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restri
             const int c = cb + u * nwarp;        // uniform over the warp
             if (c < k) {
                 const VT t = warp_sum(acc[u]);
-                if (lane == 0) partial[(int64_t)blockIdx.x * k + c] = t;
+                if (lane == 0) partial[(int64_t)c * gridDim.x + blockIdx.x] = t;
             }
         }
     }
@@ -446,7 +446,7 @@ __device__ __forceinline__ void dots_group(const double *__restrict__ V, int64_t
 }
 
 // Block partial sums of V[:, c] . w for c < ncols and of w . w (slot ncols),
-// written to partial[blockIdx.x * (ncols + 1) + c].  Columns go in groups of
+// written to partial[c * gridDim.x + blockIdx.x].  Columns go in groups of
 // 8, 4, 2 and 1 (the group width is uniform, so the row loops have no
 // branches), w . w with the first group.  The CTA reduction goes through
 // shared memory (warp s sums slot s: eight values per lane, then one warp
@@ -487,7 +487,7 @@ __device__ void block_dots(const double *__restrict__ V, int64_t ldv, int ncols,
             for (int q = 1; q < kReduceThreads / 32; ++q) sum += tred[sl][q * 32 + lane];
             sum = warp_sum(sum);
             const int col = sl < nc ? c0 + sl : ncols;
-            if (lane == 0) partial[(int64_t)blockIdx.x * (ncols + 1) + col] = sum;
+            if (lane == 0) partial[(int64_t)col * gridDim.x + blockIdx.x] = sum;
         }
         __syncthreads();
         c0 += nc;

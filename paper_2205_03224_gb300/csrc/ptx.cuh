@@ -20,12 +20,13 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 
-// Column sums of per-CTA partials [nparts][ncols1] into out[0..ncols1) (shared
-// memory), by all warps of the finishing CTA.  Warp w takes columns w, w+nw,
-// w+2nw, w+3nw together; its lanes load up to eight partial rows each for all
-// four columns before any addition (one memory round trip per pass of 256
-// rows), add them in a fixed pairwise tree and finish with a warp
-// reduction.  The summation order is fixed (deterministic).  Short dependent
+// Column sums of per-CTA partials (column-major: partial c of CTA p at
+// c * nparts + p, so a warp's loads of one column are contiguous) into
+// out[0..ncols1) (shared memory), by all warps of the finishing CTA.  Warp w
+// takes columns w, w+nw, w+2nw, w+3nw together; its lanes load up to eight
+// partials each for all four columns before any addition (one memory round
+// trip per pass of 256 CTAs), add them in a fixed pairwise tree and finish
+// with a warp reduction.  The summation order is fixed (deterministic).  Short dependent
 // chains matter here: one FP64 add takes on the order of a hundred cycles on
 // this part when nothing else is in flight.
 template <typename T>
@@ -44,7 +45,7 @@ __device__ void reduce_columns(const T *partial, int nparts, int ncols1, T *out)
 #pragma unroll
                 for (int q = 0; q < RP; ++q) {
                     const int p = p0 + q * 32 + lane;
-                    v[u][q] = (c < ncols1 && p < nparts) ? __ldcg(partial + (int64_t)p * ncols1 + c) : (T)0;
+                    v[u][q] = (c < ncols1 && p < nparts) ? __ldcg(partial + (int64_t)c * nparts + p) : (T)0;
                 }
             }
 #pragma unroll
