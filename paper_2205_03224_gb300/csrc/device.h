@@ -67,6 +67,16 @@ void launch_gs_sub2(int64_t len, double *V, int64_t ldv, double *w, const double
 void launch_gs_scale(int64_t len, double *V, int64_t ldv, const double *w, const KrylovCtl *ctl, double *vcopy,
                      cudaStream_t st);
 void launch_gs_next(KrylovCtl *ctl, cudaStream_t st);
+// FGMRES with delayed reorthogonalisation (see kernels.cu): step reduction,
+// step update, cycle close, and the two back substitutions (R may be null).
+void launch_dgs_dots(int64_t len, const int64_t *rp, const int32_t *ci, const double *av, const double *z, double *zcol,
+                     const double *V, int64_t ldv, const double *vt, double *w, double *partial, unsigned *counter,
+                     KrylovCtl *ctl, const DgsBufs &B, int grid, cudaStream_t st);
+void launch_dgs_update(int64_t len, double *V, int64_t ldv, double *vt, const double *w, const KrylovCtl *ctl,
+                       const DgsBufs &B, cudaStream_t st);
+void launch_dgs_close(int64_t len, const double *V, int64_t ldv, const double *vt, double *partial, unsigned *counter,
+                      KrylovCtl *ctl, const DgsBufs &B, int grid, cudaStream_t st);
+void launch_lsq2(const KrylovCtl *ctl, const double *H, const double *g, const double *R, double *y, cudaStream_t st);
 // Two bounded waits on an mbarrier nothing completes (see gemslr_selftest_wait).
 void launch_wait_selftest(long long limit, int32_t *gave_up, cudaStream_t st);
 void launch_norm2(int64_t len, const double *x, double *partial, unsigned *counter, double *out, int grid,

@@ -451,10 +451,10 @@ __device__ __forceinline__ void dots_group(const double *__restrict__ V, int64_t
 // branches), w . w with the first group.  The CTA reduction goes through
 // shared memory (warp s sums slot s: eight values per lane, then one warp
 // reduction), far fewer FP64 adds than full-warp butterflies per column.
-// Requires blockDim.x == kReduceThreads (8 warps).
+// Requires blockDim.x == kReduceThreads.
 __device__ void block_dots(const double *__restrict__ V, int64_t ldv, int ncols, const double *w,
                            int64_t i0, int64_t i1, double *partial) {
-    static_assert(kReduceThreads == 256, "eight warps reduce the slots of a group");
+    static_assert(kReduceThreads % 32 == 0 && kReduceThreads / 32 >= 1, "whole warps");
     __shared__ double tred[9][kReduceThreads];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int c0 = 0;
@@ -811,6 +811,361 @@ __global__ void k_gs_scale(int64_t len, double *__restrict__ V, int64_t ldv, con
     }
 }
 
+// ---- FGMRES with delayed reorthogonalisation ------------------------------------------
+// One reduction per step.  The Krylov direction of step j, vt, is the first
+// Gram-Schmidt pass of the previous product normalised by a Pythagorean
+// estimate; the step's single reduction over V_{j-1} yields both its second
+// pass (a = V^T vt, nu = ||vt - V a||) and, by linearity of M^{-1}, every
+// coefficient of the new product w = A M^{-1} vt against the final basis.  The
+// stored preconditioned vectors Zt = M^{-1} vt relate to those of the final
+// basis by an upper triangular R (Zt = Z R), so x = Zt R^{-1} y.  Column j-1
+// of the Hessenberg matrix is final at step j; the step's stopping test uses
+// column j rotated provisionally.
+
+// Dots of the NC columns V[:, c0..) with vt (acc[0..NC)) and w (acc[NC..2NC)),
+// and when FIRST vt.vt, vt.w, w.w in acc[2NC..2NC+3); two rows per iteration,
+// every load before any arithmetic.
+template <int NC, bool FIRST>
+__device__ __forceinline__ void dots2_group(const double *__restrict__ V, int64_t ldv, int c0, const double *vt,
+                                            const double *w, int64_t i0, int64_t i1, double *acc) {
+    const double *vc[NC > 0 ? NC : 1];
+#pragma unroll
+    for (int u = 0; u < NC; ++u) vc[u] = V + (int64_t)(c0 + u) * ldv;
+    const int64_t st = blockDim.x;
+    int64_t i = i0 + threadIdx.x;
+    for (; i + st < i1; i += 2 * st) {
+        const double ta = __ldcg(vt + i), tb = __ldcg(vt + i + st);
+        const double wa = __ldcg(w + i), wb = __ldcg(w + i + st);
+        double va[NC > 0 ? NC : 1], vb[NC > 0 ? NC : 1];
+#pragma unroll
+        for (int u = 0; u < NC; ++u) {
+            va[u] = vc[u][i];
+            vb[u] = vc[u][i + st];
+        }
+#pragma unroll
+        for (int u = 0; u < NC; ++u) {
+            acc[u] = fma(vb[u], tb, fma(va[u], ta, acc[u]));
+            acc[NC + u] = fma(vb[u], wb, fma(va[u], wa, acc[NC + u]));
+        }
+        if (FIRST) {
+            acc[2 * NC] = fma(tb, tb, fma(ta, ta, acc[2 * NC]));
+            acc[2 * NC + 1] = fma(tb, wb, fma(ta, wa, acc[2 * NC + 1]));
+            acc[2 * NC + 2] = fma(wb, wb, fma(wa, wa, acc[2 * NC + 2]));
+        }
+    }
+    if (i < i1) {
+        const double ta = __ldcg(vt + i), wa = __ldcg(w + i);
+#pragma unroll
+        for (int u = 0; u < NC; ++u) {
+            const double v = vc[u][i];
+            acc[u] = fma(v, ta, acc[u]);
+            acc[NC + u] = fma(v, wa, acc[NC + u]);
+        }
+        if (FIRST) {
+            acc[2 * NC] = fma(ta, ta, acc[2 * NC]);
+            acc[2 * NC + 1] = fma(ta, wa, acc[2 * NC + 1]);
+            acc[2 * NC + 2] = fma(wa, wa, acc[2 * NC + 2]);
+        }
+    }
+}
+
+// Block partials of V[:, c].vt (slot c), V[:, c].w (slot nc + c) for c < nc,
+// vt.vt, vt.w, w.w (slots 2nc .. 2nc+2), written column-major like block_dots.
+__device__ void block_dots2(const double *__restrict__ V, int64_t ldv, int nc, const double *vt, const double *w,
+                            int64_t i0, int64_t i1, double *partial) {
+    __shared__ double tred[19][kReduceThreads];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int c0 = 0;
+    bool first = true;
+    while (first || c0 < nc) {
+        const int rem = nc - c0;
+        const int g = rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : rem;
+        double acc[19];
+#pragma unroll
+        for (int u = 0; u < 19; ++u) acc[u] = 0.0;
+        switch (g + (first ? 16 : 0)) {
+            case 8: dots2_group<8, false>(V, ldv, c0, vt, w, i0, i1, acc); break;
+            case 4: dots2_group<4, false>(V, ldv, c0, vt, w, i0, i1, acc); break;
+            case 2: dots2_group<2, false>(V, ldv, c0, vt, w, i0, i1, acc); break;
+            case 1: dots2_group<1, false>(V, ldv, c0, vt, w, i0, i1, acc); break;
+            case 24: dots2_group<8, true>(V, ldv, c0, vt, w, i0, i1, acc); break;
+            case 20: dots2_group<4, true>(V, ldv, c0, vt, w, i0, i1, acc); break;
+            case 18: dots2_group<2, true>(V, ldv, c0, vt, w, i0, i1, acc); break;
+            case 17: dots2_group<1, true>(V, ldv, c0, vt, w, i0, i1, acc); break;
+            default: dots2_group<0, true>(V, ldv, c0, vt, w, i0, i1, acc); break;
+        }
+        const int ns = 2 * g + (first ? 3 : 0);
+#pragma unroll
+        for (int u = 0; u < 19; ++u)
+            if (u < ns) tred[u][threadIdx.x] = acc[u];
+        __syncthreads();
+        for (int sl = warp; sl < ns; sl += kReduceThreads / 32) {
+            double sum = tred[sl][lane];
+#pragma unroll
+            for (int q = 1; q < kReduceThreads / 32; ++q) sum += tred[sl][q * 32 + lane];
+            sum = warp_sum(sum);
+            const int col = sl < g ? c0 + sl : sl < 2 * g ? nc + c0 + (sl - g) : 2 * nc + (sl - 2 * g);
+            if (lane == 0) partial[(int64_t)col * gridDim.x + blockIdx.x] = sum;
+        }
+        __syncthreads();
+        c0 += g;
+        first = false;
+    }
+}
+
+// Column jc of H (rows 0..jc+1 in col) through the rotations 0..jc-1; with a
+// second column col2 (or nullptr) carried through the same rotations in the
+// same loop (two independent chains).
+__device__ __forceinline__ void rotate_columns(const double *cs, const double *sn, int jc, double *col,
+                                               double *col2) {
+    for (int i = 0; i < jc; ++i) {
+        const double c = cs[i], s = sn[i];
+        const double t = c * col[i] + s * col[i + 1];
+        col[i + 1] = -s * col[i] + c * col[i + 1];
+        col[i] = t;
+        if (col2) {
+            const double t2 = c * col2[i] + s * col2[i + 1];
+            col2[i + 1] = -s * col2[i] + c * col2[i + 1];
+            col2[i] = t2;
+        }
+    }
+}
+
+// Final Givens step on column jc of Hrot (already rotated by 0..jc-1):
+// rotation jc, g, residual estimate.
+__device__ __forceinline__ double givens_close(double *col, int jc, double *cs, double *sn, double *g) {
+    const double den = hypot(col[jc], col[jc + 1]);
+    const double c = den == 0.0 ? 1.0 : col[jc] / den;
+    const double s = den == 0.0 ? 0.0 : col[jc + 1] / den;
+    cs[jc] = c;
+    sn[jc] = s;
+    col[jc] = den;
+    col[jc + 1] = 0.0;
+    g[jc + 1] = -s * g[jc];
+    g[jc] = c * g[jc];
+    return fabs(g[jc + 1]);
+}
+
+// Step j: w = A z (z also stored in column j of Zt), then the reduction over
+// V_{j-1} with vt and w; the finisher (warp 0) finalises column j-1, stores
+// column j of R, forms the first-pass column h1 of step j, its lagged norm and
+// the coefficients of the next direction, and decides whether the cycle ends.
+__global__ void __launch_bounds__(kReduceThreads)
+k_dgs_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
+           const double *__restrict__ av, const double *__restrict__ z, double *__restrict__ zcol,
+           const double *__restrict__ V, int64_t ldv, const double *vt, double *w, double *partial, unsigned *counter,
+           KrylovCtl *ctl, DgsBufs B) {
+    if (ctl->stop) return;
+    const int j = ctl->j;
+    const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
+    double *zj = zcol + (int64_t)j * len;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int64_t p0 = rp[i], p1 = rp[i + 1];
+        double a0 = 0.0, a1 = 0.0;
+        if (p1 > p0) {
+            int cc[8];
+            double vv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int64_t pq = p0 + q < p1 ? p0 + q : p0;
+                cc[q] = ci[pq];
+                vv[q] = p0 + q < p1 ? av[pq] : 0.0;
+            }
+            double zz[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) zz[q] = z[cc[q]];
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+                a0 = fma(vv[q], zz[q], a0);
+                a1 = fma(vv[q + 1], zz[q + 1], a1);
+            }
+            for (int64_t p = p0 + 8; p < p1; ++p) a0 = fma(av[p], z[ci[p]], a0);
+        }
+        w[i] = a0 + a1;
+        zj[i] = z[i];
+    }
+    block_dots2(V, ldv, j, vt, w, i0, i1, partial);
+    if (!finish_block(counter)) return;
+    __shared__ double red[2 * kMaxCols + 3];
+    reduce_partials(partial, 2 * j + 3, red);
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    const int m1 = ctl->m + 1;
+    const double *a = red, *b = red + j;
+    const double gam = red[2 * j], dlt = red[2 * j + 1], om = red[2 * j + 2];
+    double aa = 0.0, ab = 0.0;
+    for (int c = lane; c < j; c += 32) {
+        aa = fma(a[c], a[c], aa);
+        ab = fma(a[c], b[c], ab);
+    }
+    aa = warp_sum(aa);
+    ab = warp_sum(ab);
+    const double nu = sqrt(fmax(gam - aa, 0.0));
+    const double bprev = ctl->btil;
+    // column j-1 final (raw), a and column j of R
+    for (int c = lane; c < j; c += 32) {
+        B.a[c] = a[c];
+        B.R[c + (int64_t)j * m1] = a[c];
+        B.Hraw[(int64_t)(j - 1) * m1 + c] = B.hprev[c] + bprev * a[c];
+    }
+    if (lane == 0) {
+        B.R[j + (int64_t)j * m1] = nu;
+        if (j > 0) B.Hraw[(int64_t)(j - 1) * m1 + j] = bprev * nu;
+    }
+    __syncwarp();
+    // g = Hraw[0..j, 0..j-1] a, V_j^T vt-product, h1 = (V_j^T w - g) / nu
+    const double vjw = j > 0 ? (dlt - ab) / nu : dlt / nu;
+    double gg = 0.0, gv = 0.0, hh = 0.0;
+    for (int r = lane; r <= j; r += 32) {
+        double gr = 0.0;
+        for (int c = (r > 0 ? r - 1 : 0); c < j; ++c) gr = fma(B.Hraw[(int64_t)c * m1 + r], a[c], gr);
+        const double vr = r < j ? b[r] : vjw;
+        const double h1 = (vr - gr) / nu;
+        B.hprev[r] = h1;
+        B.coef[r] = fma(nu, h1, gr);
+        gg = fma(gr, gr, gg);
+        gv = fma(gr, vr, gv);
+        hh = fma(h1, h1, hh);
+    }
+    gg = warp_sum(gg);
+    gv = warp_sum(gv);
+    hh = warp_sum(hh);
+    __syncwarp();
+    if (lane != 0) return;
+    const double w2 = (om - 2.0 * gv + gg) / (nu * nu);
+    const double rest = w2 - hh;
+    const double bt = rest > 0.0 ? sqrt(rest) : 0.0;
+    ctl->nu = nu;
+    ctl->btil = bt;
+    ctl->wnorm2 = w2;
+    // final rotation of column j-1 and provisional rotation of column j
+    __shared__ double colp[kMaxCols + 1], coln[kMaxCols + 2];
+    if (j > 0)
+        for (int i = 0; i <= j; ++i) colp[i] = B.Hraw[(int64_t)(j - 1) * m1 + i];
+    for (int i = 0; i <= j; ++i) coln[i] = B.hprev[i];
+    coln[j + 1] = bt;
+    rotate_columns(B.cs, B.sn, j > 0 ? j - 1 : 0, colp, j > 0 ? coln : nullptr);
+    if (j > 0) {
+        givens_close(colp, j - 1, B.cs, B.sn, B.g);
+        for (int i = 0; i <= j; ++i) B.Hrot[(int64_t)(j - 1) * m1 + i] = colp[i];
+        const double c = B.cs[j - 1], s = B.sn[j - 1];      // rotation j-1 on column j
+        const double t = c * coln[j - 1] + s * coln[j];
+        coln[j] = -s * coln[j - 1] + c * coln[j];
+        coln[j - 1] = t;
+    }
+    const double den = hypot(coln[j], coln[j + 1]);
+    const double prelim = den == 0.0 ? 0.0 : fabs(coln[j + 1] / den * B.g[j]);
+    ctl->resid = prelim;
+    ctl->iters += 1;
+    const bool bad = !isfinite(prelim) || !isfinite(nu) || !isfinite(bt);
+    if (bad) ctl->nonfinite = 1;
+    ctl->breakdown = bt <= 1e-14 * sqrt(fabs(w2)) ? 1 : 0;
+    if (prelim <= ctl->tol_abs || ctl->breakdown || bad || ctl->iters >= ctl->maxit || j + 1 >= ctl->m) ctl->stop = 1;
+    *counter = 0u;
+}
+
+// Step j, second sweep: V[:, j] = (vt - V_{j-1} a) / nu and the next direction
+// vt = (w - V_{j-1} coef[0..j) - v_j coef[j]) / (nu btil), in place (skipped
+// after a breakdown).  Two rows per thread, each column group's loads first.
+__global__ void __launch_bounds__(256)
+k_dgs_update(int64_t len, double *__restrict__ V, int64_t ldv, double *vt, const double *__restrict__ w,
+             const KrylovCtl *ctl, DgsBufs B) {
+    __shared__ double as[kMaxCols], cf[kMaxCols + 8];
+    const int j = ctl->j;
+    const double nu = ctl->nu, bt = ctl->btil;
+    const bool next = !ctl->breakdown && bt > 0.0;
+    const int np = (j + 7) & ~7;
+    for (int c = threadIdx.x; c < np; c += blockDim.x) {
+        as[c] = c < j ? __ldcg(B.a + c) : 0.0;
+        cf[c] = c < j ? __ldcg(B.coef + c) : 0.0;
+    }
+    __syncthreads();
+    const double cj = __ldcg(B.coef + j);
+    const double inv_nu = 1.0 / nu, inv_nb = next ? 1.0 / (nu * bt) : 0.0;
+    double *vj = V + (int64_t)j * ldv;
+    const int64_t st = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += st) {
+        double xa = 0.0, xc = 0.0, ya = 0.0, yc = 0.0;
+        for (int c0 = 0; c0 < j; c0 += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = V[(int64_t)min(c0 + u, j - 1) * ldv + i];
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                xa = fma(v[u], as[c0 + u], xa);
+                ya = fma(v[u + 1], as[c0 + u + 1], ya);
+                xc = fma(v[u], cf[c0 + u], xc);
+                yc = fma(v[u + 1], cf[c0 + u + 1], yc);
+            }
+        }
+        const double t = __ldcg(vt + i);
+        const double v = (t - (xa + ya)) * inv_nu;
+        vj[i] = v;
+        if (next) vt[i] = (w[i] - (xc + yc) - v * cj) * inv_nb;
+    }
+}
+
+// End of a cycle: the reduction of the last direction against V_j finalises
+// column j (after a breakdown the direction is not formed: a = 0, h_{j+1,j} =
+// 0); final rotation of column j, jdone = j + 1.
+__global__ void __launch_bounds__(kReduceThreads)
+k_dgs_close(int64_t len, const double *__restrict__ V, int64_t ldv, const double *vt, double *partial,
+            unsigned *counter, KrylovCtl *ctl, DgsBufs B) {
+    const int j = ctl->j;
+    const bool brk = ctl->breakdown || !(ctl->btil > 0.0);
+    const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
+    if (!brk) block_dots(V, ldv, j + 1, vt, i0, i1, partial);
+    if (!finish_block(counter)) return;
+    __shared__ double red[kMaxCols + 1];
+    if (!brk) reduce_partials(partial, j + 2, red);
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x, m1 = ctl->m + 1;
+    double aa = 0.0;
+    if (!brk)
+        for (int c = lane; c <= j; c += 32) aa = fma(red[c], red[c], aa);
+    aa = warp_sum(aa);
+    const double nu = brk ? 0.0 : sqrt(fmax(red[j + 1] - aa, 0.0));
+    const double bt = brk ? 0.0 : ctl->btil;
+    for (int c = lane; c <= j; c += 32) B.Hraw[(int64_t)j * m1 + c] = B.hprev[c] + (brk ? 0.0 : bt * red[c]);
+    if (lane == 0) B.Hraw[(int64_t)j * m1 + j + 1] = bt * nu;
+    __syncwarp();
+    if (lane != 0) return;
+    __shared__ double col[kMaxCols + 2];
+    for (int i = 0; i <= j + 1; ++i) col[i] = B.Hraw[(int64_t)j * m1 + i];
+    rotate_columns(B.cs, B.sn, j, col, nullptr);
+    const double r = givens_close(col, j, B.cs, B.sn, B.g);
+    for (int i = 0; i <= j + 1; ++i) B.Hrot[(int64_t)j * m1 + i] = col[i];
+    ctl->resid = r;
+    ctl->jdone = j + 1;
+    if (!isfinite(r)) ctl->nonfinite = 1;
+    *counter = 0u;
+}
+
+// y = Hrot^{-1} g over the first jdone columns, then (R != nullptr) y = R^{-1} y;
+// column-oriented back substitutions, one CTA (the updates of a column in
+// parallel, one dependent step per column).
+__global__ void __launch_bounds__(256)
+k_lsq2(const KrylovCtl *ctl, const double *__restrict__ H, const double *__restrict__ g, const double *R,
+       double *__restrict__ y) {
+    __shared__ double s[kMaxCols];
+    const int jd = ctl->jdone, m1 = ctl->m + 1;
+    for (int i = threadIdx.x; i < jd; i += blockDim.x) s[i] = g[i];
+    __syncthreads();
+    for (int pass = 0; pass < (R ? 2 : 1); ++pass) {
+        const double *T = pass == 0 ? H : R;
+        for (int i = jd - 1; i >= 0; --i) {
+            const double yi = s[i] / T[(int64_t)i * m1 + i];
+            for (int r = threadIdx.x; r < i; r += blockDim.x) s[r] = fma(-T[(int64_t)i * m1 + r], yi, s[r]);
+            __syncthreads();
+            if (threadIdx.x == 0) s[i] = yi;
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < jd; i += blockDim.x) y[i] = s[i];
+}
+
 // Advance to the next column (one thread).
 __global__ void k_gs_next(KrylovCtl *ctl) {
     if (threadIdx.x == 0 && blockIdx.x == 0 && !ctl->stop) ctl->j += 1;
@@ -1080,6 +1435,26 @@ void launch_gs_scale(int64_t len, double *V, int64_t ldv, const double *w, const
 }
 void launch_wait_selftest(long long limit, int32_t *gave_up, cudaStream_t st) {
     k_wait_selftest<<<1, 64, 0, st>>>(limit, gave_up);
+    count_launch();
+}
+void launch_dgs_dots(int64_t len, const int64_t *rp, const int32_t *ci, const double *av, const double *z, double *zcol,
+                     const double *V, int64_t ldv, const double *vt, double *w, double *partial, unsigned *counter,
+                     KrylovCtl *ctl, const DgsBufs &B, int grid, cudaStream_t st) {
+    k_dgs_dots<<<grid, kReduceThreads, 0, st>>>(len, rp, ci, av, z, zcol, V, ldv, vt, w, partial, counter, ctl, B);
+    count_launch();
+}
+void launch_dgs_update(int64_t len, double *V, int64_t ldv, double *vt, const double *w, const KrylovCtl *ctl,
+                       const DgsBufs &B, cudaStream_t st) {
+    k_dgs_update<<<grid_for(len, 256, 1216), 256, 0, st>>>(len, V, ldv, vt, w, ctl, B);
+    count_launch();
+}
+void launch_dgs_close(int64_t len, const double *V, int64_t ldv, const double *vt, double *partial, unsigned *counter,
+                      KrylovCtl *ctl, const DgsBufs &B, int grid, cudaStream_t st) {
+    k_dgs_close<<<grid, kReduceThreads, 0, st>>>(len, V, ldv, vt, partial, counter, ctl, B);
+    count_launch();
+}
+void launch_lsq2(const KrylovCtl *ctl, const double *H, const double *g, const double *R, double *y, cudaStream_t st) {
+    k_lsq2<<<1, 256, 0, st>>>(ctl, H, g, R, y);
     count_launch();
 }
 void launch_gs_next(KrylovCtl *ctl, cudaStream_t st) { k_gs_next<<<1, 32, 0, st>>>(ctl); count_launch(); }

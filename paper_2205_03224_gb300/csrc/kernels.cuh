@@ -110,6 +110,23 @@ struct KrylovCtl {
     int32_t restarts;     // completed cycles that did not converge
     int32_t converged;    // true residual met tol_abs
     double rnorm;         // ||b - A x|| after the last cycle
+    double nu;            // delayed CGS2: norm of the reorthogonalised direction of this step
+    double btil;          // delayed CGS2: lagged norm of the next direction
+};
+
+// Device buffers of FGMRES with delayed reorthogonalisation (one reduction
+// per step): the unrotated Hessenberg matrix, the rotated one with its
+// rotations and right-hand side, the triangular R relating the stored
+// directions' preconditioned vectors to those of the final basis, and the
+// per-step coefficient vectors.
+struct DgsBufs {
+    double *Hraw;          // (m+1) x m, column-major
+    double *Hrot;          // (m+1) x m, column-major (least-squares factor)
+    double *cs, *sn, *g;   // rotations and rotated right-hand side
+    double *R;             // (m+1) x (m+1), column-major, upper triangular
+    double *a;             // kMaxCols: V^T (direction) of this step
+    double *coef;          // kMaxCols: projection coefficients of the next direction
+    double *hprev;         // kMaxCols: first-pass column of the previous step
 };
 
 }  // namespace gemslr

@@ -39,6 +39,8 @@ struct gemslr_ctx {
     int m_alloc = 0;
     double *V = nullptr, *Z = nullptr, *w = nullptr, *xh = nullptr, *bh = nullptr, *r = nullptr;
     double *Hs = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *h2 = nullptr;
+    // delayed reorthogonalisation (linear M^{-1}): unrotated H, R, per-step vectors
+    double *Hraw = nullptr, *Rz = nullptr, *da = nullptr, *dcoef = nullptr, *dhprev = nullptr;
     double *partial = nullptr, *n2 = nullptr;
     unsigned *counter = nullptr;
     KrylovCtl *ctl = nullptr;
@@ -53,6 +55,7 @@ struct gemslr_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int graph_m = 0;
+    bool graph_dcgs = false;       // which step the captured graph runs
     bool graph_failed = false;
     uint64_t graph_k_top = 0, graph_k_cycle = 0, graph_k_step = 0;
     LearnedHost *learned = nullptr;
@@ -95,12 +98,15 @@ void ensure_krylov(gemslr_ctx *h, int m) {
         h->r = (double *)h->arena.alloc(8 * n);
         h->w = (double *)h->arena.alloc(8 * n);
         h->red_grid = sm_count();                 // one CTA per SM: few partials for the finisher
-        h->partial = (double *)h->arena.alloc(8 * (size_t)h->red_grid * (kMaxCols + 1));
+        h->partial = (double *)h->arena.alloc(8 * (size_t)h->red_grid * (2 * kMaxCols + 4));
         h->counter = (unsigned *)h->arena.alloc(16);
         GEMSLR_CUDA(cudaMemset(h->counter, 0, 16));
         h->n2 = (double *)h->arena.alloc(8 * 4);
         h->ctl = (KrylovCtl *)h->arena.alloc(sizeof(KrylovCtl));
         h->h2 = (double *)h->arena.alloc(8 * kMaxCols);
+        h->da = (double *)h->arena.alloc(8 * kMaxCols);
+        h->dcoef = (double *)h->arena.alloc(8 * kMaxCols);
+        h->dhprev = (double *)h->arena.alloc(8 * kMaxCols);
         h->vin = (double *)h->arena.alloc(8 * n);
         h->zout = (double *)h->arena.alloc(8 * n);
         GEMSLR_CUDA(cudaMallocHost(&h->ctl_host, sizeof(KrylovCtl)));
@@ -116,6 +122,8 @@ void ensure_krylov(gemslr_ctx *h, int m) {
         h->sn = (double *)h->arena.alloc(8 * (size_t)(m + 1));
         h->g = (double *)h->arena.alloc(8 * (size_t)(m + 2));
         h->y = (double *)h->arena.alloc(8 * (size_t)(m + 1));
+        h->Hraw = (double *)h->arena.alloc(8 * (size_t)(m + 1) * m);
+        h->Rz = (double *)h->arena.alloc(8 * (size_t)(m + 1) * (m + 1));
         h->m_alloc = m;
     }
 }
@@ -345,6 +353,56 @@ void fgmres_step(gemslr_ctx *h, cudaStream_t st) {
     }
 }
 
+// FGMRES with delayed reorthogonalisation applies only where M^{-1} is linear
+// (not with the learned stage) and the fused product suits A (short rows).
+bool use_dcgs(const gemslr_ctx *h) {
+    const bool learned = (h->d64.learned && h->d64.learned->enabled) || (h->d32.learned && h->d32.learned->enabled);
+    return !learned && h->spmv_lanes <= 8;
+}
+
+DgsBufs dgs_bufs(gemslr_ctx *h) {
+    DgsBufs B;
+    B.Hraw = h->Hraw;
+    B.Hrot = h->Hs;
+    B.cs = h->cs;
+    B.sn = h->sn;
+    B.g = h->g;
+    B.R = h->Rz;
+    B.a = h->da;
+    B.coef = h->dcoef;
+    B.hprev = h->dhprev;
+    return B;
+}
+
+// One step with delayed reorthogonalisation: z = M^{-1} vt, the fused product
+// and reduction, then the basis column and the next direction.
+void fgmres_step_d(gemslr_ctx *h, cudaStream_t st) {
+    const int64_t n = h->host.n;
+    const DgsBufs B = dgs_bufs(h);
+    apply_perm(h, h->vin, h->zout, st);
+    {
+        ProfScope ps("dgs_spmv_dots", st);
+        launch_dgs_dots(n, h->A_rp, h->A_ci, h->A_v, h->zout, h->Z, h->V, n, h->vin, h->w, h->partial, h->counter,
+                        h->ctl, B, h->red_grid, st);
+    }
+    {
+        ProfScope ps("dgs_update", st);
+        launch_dgs_update(n, h->V, n, h->vin, h->w, h->ctl, B, st);
+    }
+}
+
+// End of a delayed cycle: close the last column, y = Hrot^{-1} g, y = R^{-1} y,
+// x += Zt y, r = b - A x, ||r||^2 into n2[1].
+void fgmres_cycle_end_d(gemslr_ctx *h, cudaStream_t st) {
+    const int64_t n = h->host.n;
+    const DgsBufs B = dgs_bufs(h);
+    launch_dgs_close(n, h->V, n, h->vin, h->partial, h->counter, h->ctl, B, h->red_grid, st);
+    launch_lsq2(h->ctl, h->Hs, h->g, h->Rz, h->y, st);
+    launch_update_x(n, h->Z, n, h->ctl, h->y, h->xh, st);
+    launch_spmv(n, h->A_rp, h->A_ci, h->A_v, h->xh, h->bh, h->r, h->spmv_lanes, st);
+    launch_norm2(n, h->r, h->partial, h->counter, h->n2 + 1, h->red_grid, st);
+}
+
 // End of a cycle: x += Z y, r = b - A x, ||r||^2 into n2[1].
 void fgmres_cycle_end(gemslr_ctx *h, cudaStream_t st) {
     const int64_t n = h->host.n;
@@ -356,7 +414,7 @@ void fgmres_cycle_end(gemslr_ctx *h, cudaStream_t st) {
 
 // Host-driven loop (used while profiling): the host reads the control block
 // after every step and every cycle.
-void fgmres_host_loop(gemslr_ctx *h, int m, cudaStream_t st) {
+void fgmres_host_loop(gemslr_ctx *h, int m, bool dcgs, cudaStream_t st) {
     const int64_t n = h->host.n;
     launch_zero(n, h->xh, st);
     GEMSLR_CUDA(cudaMemcpyAsync(h->r, h->bh, 8 * n, cudaMemcpyDeviceToDevice, st));
@@ -365,12 +423,14 @@ void fgmres_host_loop(gemslr_ctx *h, int m, cudaStream_t st) {
         launch_cycle_start(h->ctl, h->g, h->n2 + 1, st);
         launch_scale_by_norm(n, h->r, h->n2 + 1, h->V, st, h->vin);
         for (int j = 0; j < m; ++j) {
-            fgmres_step(h, st);
+            if (dcgs) fgmres_step_d(h, st);
+            else fgmres_step(h, st);
             launch_gs_next(h->ctl, st);
             read_ctl(h, st);
             if (h->ctl_host->stop) break;
         }
-        fgmres_cycle_end(h, st);
+        if (dcgs) fgmres_cycle_end_d(h, st);
+        else fgmres_cycle_end(h, st);
         const double rn = std::sqrt(read_scalar(h, h->n2 + 1, st));
         read_ctl(h, st);
         KrylovCtl &k = *h->ctl_host;
@@ -415,9 +475,9 @@ namespace {
 //   WHILE (cycle) { cycle start; WHILE (step) { FGMRES step }; cycle end }
 // with both conditions set by device kernels from the control block, so a
 // solve needs no host round trip.  Built once per restart length.
-bool ensure_solve_graph(gemslr_ctx *h, int m) {
+bool ensure_solve_graph(gemslr_ctx *h, int m, bool dcgs) {
     if (h->graph_failed) return false;
-    if (h->graph_exec && h->graph_m == m) return true;
+    if (h->graph_exec && h->graph_m == m && h->graph_dcgs == dcgs) return true;
     try {
         if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
         if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
@@ -443,12 +503,14 @@ bool ensure_solve_graph(gemslr_ctx *h, int m) {
         launch_cycle_start_g(h->ctl, h->g, h->n2 + 1, hs, cs);
         launch_scale_by_norm(n, h->r, h->n2 + 1, h->V, cs, h->vin);
         cudaGraph_t body_step = capture_while_node(cs, hs);
-        fgmres_cycle_end(h, cs);
+        if (dcgs) fgmres_cycle_end_d(h, cs);
+        else fgmres_cycle_end(h, cs);
         launch_cycle_end_g(h->ctl, h->n2 + 1, hc, cs);
         GEMSLR_CUDA(cudaStreamEndCapture(cs, &body_cycle));
         const uint64_t k2 = launches_total();
         GEMSLR_CUDA(cudaStreamBeginCaptureToGraph(cs, body_step, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-        fgmres_step(h, cs);
+        if (dcgs) fgmres_step_d(h, cs);
+        else fgmres_step(h, cs);
         launch_step_end_g(h->ctl, hs, cs);
         GEMSLR_CUDA(cudaStreamEndCapture(cs, &body_step));
         const uint64_t k3 = launches_total();
@@ -458,6 +520,7 @@ bool ensure_solve_graph(gemslr_ctx *h, int m) {
         h->graph_k_step = k3 - k2;
         count_launch(-(int)(k3 - k0));      // capture launches nothing
         h->graph_m = m;
+        h->graph_dcgs = dcgs;
         return true;
     } catch (const Error &e) {
         cudaGetLastError();
@@ -718,7 +781,8 @@ gemslr_status gemslr_fgmres_solve(gemslr_handle h, const double *b_dev, double *
             // see kernels inside conditional graph nodes)
             const char *env = std::getenv("GEMSLR_SOLVE_GRAPH");
             const bool allow_graph = !(env && env[0] == '0');
-            const bool use_graph = allow_graph && !profile_enabled() && ensure_solve_graph(h, m);
+            const bool dcgs = use_dcgs(h);
+            const bool use_graph = allow_graph && !profile_enabled() && ensure_solve_graph(h, m, dcgs);
             if (use_graph) {
                 GEMSLR_CUDA(cudaGraphLaunch(h->graph_exec, st));
                 read_ctl(h, st);
@@ -726,7 +790,7 @@ gemslr_status gemslr_fgmres_solve(gemslr_handle h, const double *b_dev, double *
                 count_launch((int)(h->graph_k_top + (uint64_t)(k.restarts + 1) * h->graph_k_cycle +
                                    (uint64_t)k.iters * h->graph_k_step));
             } else {
-                fgmres_host_loop(h, m, st);
+                fgmres_host_loop(h, m, dcgs, st);
             }
             const KrylovCtl &k = *h->ctl_host;
             GEMSLR_CUDA(cudaMemcpyAsync(h->err_host, h->mixed ? h->d32.err : h->d64.err, 4, cudaMemcpyDeviceToHost, st));
