@@ -913,37 +913,78 @@ __device__ void block_dots2(const double *__restrict__ V, int64_t ldv, int nc, c
     }
 }
 
-// Column jc of H (rows 0..jc+1 in col) through the rotations 0..jc-1; with a
-// second column col2 (or nullptr) carried through the same rotations in the
-// same loop (two independent chains).
-__device__ __forceinline__ void rotate_columns(const double *cs, const double *sn, int jc, double *col,
-                                               double *col2) {
-    for (int i = 0; i < jc; ++i) {
-        const double c = cs[i], s = sn[i];
-        const double t = c * col[i] + s * col[i + 1];
-        col[i + 1] = -s * col[i] + c * col[i + 1];
-        col[i] = t;
-        if (col2) {
-            const double t2 = c * col2[i] + s * col2[i + 1];
-            col2[i + 1] = -s * col2[i] + c * col2[i + 1];
-            col2[i] = t2;
-        }
-    }
-}
-
 // Final Givens step on column jc of Hrot (already rotated by 0..jc-1):
-// rotation jc, g, residual estimate.
+// rotation jc, g, residual estimate.  One reciprocal square root instead of
+// hypot and two divisions: on this part a dependent FP64 operation costs on
+// the order of a hundred cycles, so the finisher's critical path counts
+// operations, not flops (the entries are O(||b||), far from overflow).
 __device__ __forceinline__ double givens_close(double *col, int jc, double *cs, double *sn, double *g) {
-    const double den = hypot(col[jc], col[jc + 1]);
-    const double c = den == 0.0 ? 1.0 : col[jc] / den;
-    const double s = den == 0.0 ? 0.0 : col[jc + 1] / den;
+    const double x = col[jc], y = col[jc + 1];
+    const double q = fma(x, x, y * y);
+    const double inv = q > 0.0 ? rsqrt(q) : 0.0;
+    const double c = q > 0.0 ? x * inv : 1.0;
+    const double s = q > 0.0 ? y * inv : 0.0;
     cs[jc] = c;
     sn[jc] = s;
-    col[jc] = den;
+    col[jc] = q * inv;
     col[jc + 1] = 0.0;
     g[jc + 1] = -s * g[jc];
     g[jc] = c * g[jc];
     return fabs(g[jc + 1]);
+}
+
+// Rotations 0..jc-1 (cs, sn) applied to col[0..jc] (shared memory) by one
+// warp.  The carried entry obeys r_{i+1} = -s_i r_i + c_i col[i+1], an affine
+// recurrence: every lane composes the maps of its contiguous segment, a
+// shuffle scan combines the lanes (earlier segments first), and each lane then
+// walks its segment from its prefix.  Dependent FP64 steps: about
+// (jc / 32) + 2 log2(32) instead of 2 jc.
+__device__ __forceinline__ void rotate_column_warp(const double *cs, const double *sn, int jc, double *col) {
+    const int lane = threadIdx.x & 31;
+    if (jc <= 0) return;
+    const int per = (jc + 31) / 32;                 // <= 5 for kMaxCols
+    const int lo = min(lane * per, jc), hi = min(lo + per, jc);
+    double h[6], cc[5], ss[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const int i = lo + q;
+        cc[q] = i < hi ? cs[i] : 1.0;
+        ss[q] = i < hi ? sn[i] : 0.0;
+        h[q + 1] = i < hi ? col[i + 1] : 0.0;
+    }
+    const double h0 = col[0];
+    __syncwarp();
+    double A = 1.0, Bv = 0.0;                       // this segment's composed map
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+        if (lo + q < hi) {
+            Bv = fma(-ss[q], Bv, cc[q] * h[q + 1]);
+            A = -ss[q] * A;
+        }
+    double Ai = A, Bi = Bv;                         // inclusive scan over lanes
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double Ao = __shfl_up_sync(0xffffffffu, Ai, off), Bo = __shfl_up_sync(0xffffffffu, Bi, off);
+        if (lane >= off) {
+            Bi = fma(Ai, Bo, Bi);
+            Ai = Ai * Ao;
+        }
+    }
+    double Ae = __shfl_up_sync(0xffffffffu, Ai, 1), Be = __shfl_up_sync(0xffffffffu, Bi, 1);
+    if (lane == 0) {
+        Ae = 1.0;
+        Be = 0.0;
+    }
+    double r = fma(Ae, h0, Be);                     // carried entry at the start of the segment
+#pragma unroll
+    for (int q = 0; q < 5; ++q)
+        if (lo + q < hi) {
+            const double tq = fma(cc[q], r, ss[q] * h[q + 1]);
+            r = fma(-ss[q], r, cc[q] * h[q + 1]);
+            col[lo + q] = tq;
+            if (lo + q == jc - 1) col[jc] = r;
+        }
+    __syncwarp();
 }
 
 // Step j: w = A z (z also stored in column j of Zt), then the reduction over
@@ -989,73 +1030,102 @@ k_dgs_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restric
     if (!finish_block(counter)) return;
     __shared__ double red[2 * kMaxCols + 3];
     reduce_partials(partial, 2 * j + 3, red);
-    if (threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
+    // finisher, all threads: rotations, the previous first-pass column and the
+    // columns being finalised live in shared memory for the serial parts
+    __shared__ double s_cs[kMaxCols], s_sn[kMaxCols], s_g[kMaxCols + 1];
+    __shared__ double hcol[kMaxCols + 1], h1s[kMaxCols + 2], sc[4];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int m1 = ctl->m + 1;
     const double *a = red, *b = red + j;
     const double gam = red[2 * j], dlt = red[2 * j + 1], om = red[2 * j + 2];
-    double aa = 0.0, ab = 0.0;
-    for (int c = lane; c < j; c += 32) {
-        aa = fma(a[c], a[c], aa);
-        ab = fma(a[c], b[c], ab);
-    }
-    aa = warp_sum(aa);
-    ab = warp_sum(ab);
-    const double nu = sqrt(fmax(gam - aa, 0.0));
     const double bprev = ctl->btil;
-    // column j-1 final (raw), a and column j of R
-    for (int c = lane; c < j; c += 32) {
+    for (int c = t; c <= j; c += blockDim.x) {
+        s_cs[c] = B.cs[c];
+        s_sn[c] = B.sn[c];
+        s_g[c] = B.g[c];
+    }
+    if (warp == 0) {
+        double aa = 0.0, ab = 0.0;
+        for (int c = lane; c < j; c += 32) {
+            aa = fma(a[c], a[c], aa);
+            ab = fma(a[c], b[c], ab);
+        }
+        aa = warp_sum(aa);
+        ab = warp_sum(ab);
+        if (lane == 0) {
+            sc[0] = sqrt(fmax(gam - aa, 0.0));
+            sc[1] = ab;
+        }
+    }
+    __syncthreads();
+    const double nu = sc[0], inv_nu = 1.0 / nu;
+    const double vjw = (dlt - sc[1]) * inv_nu;   // v_j . w
+    // column j-1, now final: rows 0..j-1 from the previous first pass, row j
+    for (int c = t; c < j; c += blockDim.x) {
+        const double hv = B.hprev[c] + bprev * a[c];
+        hcol[c] = hv;
+        B.Hraw[(int64_t)(j - 1) * m1 + c] = hv;
         B.a[c] = a[c];
         B.R[c + (int64_t)j * m1] = a[c];
-        B.Hraw[(int64_t)(j - 1) * m1 + c] = B.hprev[c] + bprev * a[c];
     }
-    if (lane == 0) {
-        B.R[j + (int64_t)j * m1] = nu;
+    if (t == 0) {
+        hcol[j] = bprev * nu;
         if (j > 0) B.Hraw[(int64_t)(j - 1) * m1 + j] = bprev * nu;
+        B.R[j + (int64_t)j * m1] = nu;
     }
-    __syncwarp();
-    // g = Hraw[0..j, 0..j-1] a, V_j^T vt-product, h1 = (V_j^T w - g) / nu
-    const double vjw = j > 0 ? (dlt - ab) / nu : dlt / nu;
-    double gg = 0.0, gv = 0.0, hh = 0.0;
-    for (int r = lane; r <= j; r += 32) {
-        double gr = 0.0;
-        for (int c = (r > 0 ? r - 1 : 0); c < j; ++c) gr = fma(B.Hraw[(int64_t)c * m1 + r], a[c], gr);
+    __syncthreads();
+    // g = Hraw[0..j, 0..j-1] a (row r per thread; columns before j-1 are
+    // final since earlier steps, column j-1 is in hcol), then the first-pass
+    // column h1 = (V_j^T w - g) / nu and the next direction's coefficients
+    // V_j^T w
+    for (int r = t; r <= j; r += blockDim.x) {
+        double g0 = 0.0, g1 = 0.0;
+        int c = r > 0 ? r - 1 : 0;
+        for (; c + 1 < j - 1; c += 2) {
+            g0 = fma(B.Hraw[(int64_t)c * m1 + r], a[c], g0);
+            g1 = fma(B.Hraw[(int64_t)(c + 1) * m1 + r], a[c + 1], g1);
+        }
+        if (c < j - 1) g0 = fma(B.Hraw[(int64_t)c * m1 + r], a[c], g0);
+        if (j > 0 && r <= j) g0 = fma(hcol[r], a[j - 1], g0);
         const double vr = r < j ? b[r] : vjw;
-        const double h1 = (vr - gr) / nu;
+        const double h1 = (vr - (g0 + g1)) * inv_nu;
+        h1s[r] = h1;
         B.hprev[r] = h1;
-        B.coef[r] = fma(nu, h1, gr);
-        gg = fma(gr, gr, gg);
-        gv = fma(gr, vr, gv);
-        hh = fma(h1, h1, hh);
+        B.coef[r] = vr;
     }
-    gg = warp_sum(gg);
-    gv = warp_sum(gv);
-    hh = warp_sum(hh);
-    __syncwarp();
-    if (lane != 0) return;
-    const double w2 = (om - 2.0 * gv + gg) / (nu * nu);
-    const double rest = w2 - hh;
-    const double bt = rest > 0.0 ? sqrt(rest) : 0.0;
+    if (warp == 0) {
+        double vv = 0.0;
+        for (int r = lane; r < j; r += 32) vv = fma(b[r], b[r], vv);
+        vv = warp_sum(vv);
+        if (lane == 0) sc[2] = vv + vjw * vjw;
+    }
+    __syncthreads();
+    const double rest = om - sc[2];                 // ||w - V_j V_j^T w||^2 (Pythagoras)
+    const double bt = rest > 0.0 ? sqrt(rest) * inv_nu : 0.0;
+    // rotations 0..j-2 on column j-1 (warp 0) and on column j (warp 1)
+    if (warp == 0) rotate_column_warp(s_cs, s_sn, j - 1, hcol);
+    else if (warp == 1) rotate_column_warp(s_cs, s_sn, j - 1, h1s);
+    __syncthreads();
+    if (t != 0) return;
+    const double w2 = om * inv_nu * inv_nu;
     ctl->nu = nu;
     ctl->btil = bt;
     ctl->wnorm2 = w2;
-    // final rotation of column j-1 and provisional rotation of column j
-    __shared__ double colp[kMaxCols + 1], coln[kMaxCols + 2];
-    if (j > 0)
-        for (int i = 0; i <= j; ++i) colp[i] = B.Hraw[(int64_t)(j - 1) * m1 + i];
-    for (int i = 0; i <= j; ++i) coln[i] = B.hprev[i];
-    coln[j + 1] = bt;
-    rotate_columns(B.cs, B.sn, j > 0 ? j - 1 : 0, colp, j > 0 ? coln : nullptr);
+    h1s[j + 1] = bt;
     if (j > 0) {
-        givens_close(colp, j - 1, B.cs, B.sn, B.g);
-        for (int i = 0; i <= j; ++i) B.Hrot[(int64_t)(j - 1) * m1 + i] = colp[i];
-        const double c = B.cs[j - 1], s = B.sn[j - 1];      // rotation j-1 on column j
-        const double t = c * coln[j - 1] + s * coln[j];
-        coln[j] = -s * coln[j - 1] + c * coln[j];
-        coln[j - 1] = t;
+        givens_close(hcol, j - 1, s_cs, s_sn, s_g);
+        B.cs[j - 1] = s_cs[j - 1];
+        B.sn[j - 1] = s_sn[j - 1];
+        B.g[j - 1] = s_g[j - 1];
+        B.g[j] = s_g[j];
+        for (int i = 0; i <= j; ++i) B.Hrot[(int64_t)(j - 1) * m1 + i] = hcol[i];
+        const double c = s_cs[j - 1], s = s_sn[j - 1];      // rotation j-1 on column j
+        const double tt = c * h1s[j - 1] + s * h1s[j];
+        h1s[j] = -s * h1s[j - 1] + c * h1s[j];
+        h1s[j - 1] = tt;
     }
-    const double den = hypot(coln[j], coln[j + 1]);
-    const double prelim = den == 0.0 ? 0.0 : fabs(coln[j + 1] / den * B.g[j]);
+    const double qd = fma(h1s[j], h1s[j], h1s[j + 1] * h1s[j + 1]);
+    const double prelim = qd > 0.0 ? fabs(h1s[j + 1] * rsqrt(qd) * s_g[j]) : 0.0;
     ctl->resid = prelim;
     ctl->iters += 1;
     const bool bad = !isfinite(prelim) || !isfinite(nu) || !isfinite(bt);
@@ -1067,7 +1137,7 @@ k_dgs_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restric
 
 // Step j, second sweep: V[:, j] = (vt - V_{j-1} a) / nu and the next direction
 // vt = (w - V_{j-1} coef[0..j) - v_j coef[j]) / (nu btil), in place (skipped
-// after a breakdown).  Two rows per thread, each column group's loads first.
+// after a breakdown).  Each column group's loads are issued first.
 __global__ void __launch_bounds__(256)
 k_dgs_update(int64_t len, double *__restrict__ V, int64_t ldv, double *vt, const double *__restrict__ w,
              const KrylovCtl *ctl, DgsBufs B) {
@@ -1120,22 +1190,41 @@ k_dgs_close(int64_t len, const double *__restrict__ V, int64_t ldv, const double
     if (!finish_block(counter)) return;
     __shared__ double red[kMaxCols + 1];
     if (!brk) reduce_partials(partial, j + 2, red);
-    if (threadIdx.x >= 32) return;
-    const int lane = threadIdx.x, m1 = ctl->m + 1;
-    double aa = 0.0;
-    if (!brk)
-        for (int c = lane; c <= j; c += 32) aa = fma(red[c], red[c], aa);
-    aa = warp_sum(aa);
-    const double nu = brk ? 0.0 : sqrt(fmax(red[j + 1] - aa, 0.0));
+    __shared__ double s_cs[kMaxCols], s_sn[kMaxCols], s_g[kMaxCols + 1], col[kMaxCols + 2], sc[1];
+    const int t = threadIdx.x, lane = t & 31, m1 = ctl->m + 1;
+    for (int c = t; c <= j; c += blockDim.x) {
+        s_cs[c] = B.cs[c];
+        s_sn[c] = B.sn[c];
+        s_g[c] = B.g[c];
+    }
+    if (t < 32) {
+        double aa = 0.0;
+        if (!brk)
+            for (int c = lane; c <= j; c += 32) aa = fma(red[c], red[c], aa);
+        aa = warp_sum(aa);
+        if (lane == 0) sc[0] = brk ? 0.0 : sqrt(fmax(red[j + 1] - aa, 0.0));
+    }
+    __syncthreads();
+    const double nu = sc[0];
     const double bt = brk ? 0.0 : ctl->btil;
-    for (int c = lane; c <= j; c += 32) B.Hraw[(int64_t)j * m1 + c] = B.hprev[c] + (brk ? 0.0 : bt * red[c]);
-    if (lane == 0) B.Hraw[(int64_t)j * m1 + j + 1] = bt * nu;
-    __syncwarp();
-    if (lane != 0) return;
-    __shared__ double col[kMaxCols + 2];
-    for (int i = 0; i <= j + 1; ++i) col[i] = B.Hraw[(int64_t)j * m1 + i];
-    rotate_columns(B.cs, B.sn, j, col, nullptr);
-    const double r = givens_close(col, j, B.cs, B.sn, B.g);
+    for (int c = t; c <= j; c += blockDim.x) {
+        const double hv = B.hprev[c] + (brk ? 0.0 : bt * red[c]);
+        col[c] = hv;
+        B.Hraw[(int64_t)j * m1 + c] = hv;
+    }
+    if (t == 0) {
+        col[j + 1] = bt * nu;
+        B.Hraw[(int64_t)j * m1 + j + 1] = bt * nu;
+    }
+    __syncthreads();
+    if (t < 32) rotate_column_warp(s_cs, s_sn, j, col);
+    __syncthreads();
+    if (t != 0) return;
+    const double r = givens_close(col, j, s_cs, s_sn, s_g);
+    B.cs[j] = s_cs[j];
+    B.sn[j] = s_sn[j];
+    B.g[j] = s_g[j];
+    B.g[j + 1] = s_g[j + 1];
     for (int i = 0; i <= j + 1; ++i) B.Hrot[(int64_t)j * m1 + i] = col[i];
     ctl->resid = r;
     ctl->jdone = j + 1;
