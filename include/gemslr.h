@@ -187,6 +187,11 @@ typedef struct {
     int32_t restart;     /* FGMRES cycle length m                               */
     int32_t maxit;       /* total inner iterations (1,000 in the paper)         */
     double rtol;         /* stop when ||b - A x|| <= rtol ||b|| (true residual) */
+    int32_t ortho;       /* single system only: 0 = automatic (delayed
+                            reorthogonalisation, one reduction per step, where
+                            M^{-1} is linear, i.e. without the learned stage);
+                            1 = classical Gram-Schmidt with a second pass when
+                            the first cancels (three reductions per step)     */
 } gemslr_solve_opts;
 
 typedef struct {

@@ -50,7 +50,7 @@ class LearnedOpts(ctypes.Structure):
 
 
 class SolveOpts(ctypes.Structure):
-    _fields_ = [("restart", i32), ("maxit", i32), ("rtol", f64)]
+    _fields_ = [("restart", i32), ("maxit", i32), ("rtol", f64), ("ortho", i32)]
 
 
 class SolveInfo(ctypes.Structure):

@@ -106,13 +106,16 @@ class Gemslr:
                                        nrhs, _stream(torch)))
         return z
 
-    def solve(self, b, restart=50, rtol=1e-8, maxit=1000, check=True):
-        """FGMRES(restart) on A x = b; returns (x, [info dict per right-hand side])."""
+    def solve(self, b, restart=50, rtol=1e-8, maxit=1000, check=True, ortho="auto"):
+        """FGMRES(restart) on A x = b; returns (x, [info dict per right-hand side]).
+
+        ortho: "auto" (delayed reorthogonalisation where M^{-1} is linear) or
+        "cgs2" (classical Gram-Schmidt with a selective second pass)."""
         import torch
         b = b.contiguous() if b.dim() == 1 else b.t().contiguous().t()
         x = torch.empty_like(b)
         nrhs = 1 if b.dim() == 1 else b.shape[1]
-        so = L.SolveOpts(restart, maxit, rtol)
+        so = L.SolveOpts(restart, maxit, rtol, {"auto": 0, "cgs2": 1}[ortho])
         info = (L.SolveInfo * nrhs)()
         st = self._lib.gemslr_fgmres_solve(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
                                            nrhs, ctypes.byref(so), info, _stream(torch))
@@ -255,7 +258,7 @@ class GemslrBatch:
         import torch
         b = b.contiguous()
         x = torch.empty_like(b)
-        so = L.SolveOpts(restart, maxit, rtol)
+        so = L.SolveOpts(restart, maxit, rtol, 0)
         info = (L.SolveInfo * (self.nsys * nrhs))()
         st = self._lib.gemslr_batch_fgmres_solve(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
                                                  nrhs, ctypes.byref(so), info, _stream(torch))

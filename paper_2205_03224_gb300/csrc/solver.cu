@@ -745,7 +745,8 @@ gemslr_status gemslr_fgmres_solve(gemslr_handle h, const double *b_dev, double *
     gemslr_status st_ = guard([&] {
         if (!h || !opts || !info || nrhs < 0 || (nrhs > 0 && (!b_dev || !x_dev)))
             fail(GEMSLR_ERR_ARG, "invalid argument");
-        if (opts->restart < 1 || opts->maxit < 1 || !(opts->rtol > 0)) fail(GEMSLR_ERR_ARG, "invalid solve options");
+        if (opts->restart < 1 || opts->maxit < 1 || !(opts->rtol > 0) || opts->ortho < 0 || opts->ortho > 1)
+            fail(GEMSLR_ERR_ARG, "invalid solve options");
         cudaStream_t st = (cudaStream_t)stream;
         const int64_t n = h->host.n;
         const int m = opts->restart;
@@ -781,7 +782,7 @@ gemslr_status gemslr_fgmres_solve(gemslr_handle h, const double *b_dev, double *
             // see kernels inside conditional graph nodes)
             const char *env = std::getenv("GEMSLR_SOLVE_GRAPH");
             const bool allow_graph = !(env && env[0] == '0');
-            const bool dcgs = use_dcgs(h);
+            const bool dcgs = opts->ortho == 0 && use_dcgs(h);
             const bool use_graph = allow_graph && !profile_enabled() && ensure_solve_graph(h, m, dcgs);
             if (use_graph) {
                 GEMSLR_CUDA(cudaGraphLaunch(h->graph_exec, st));

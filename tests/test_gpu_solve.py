@@ -20,8 +20,9 @@ def torch_cuda():
 RESTART = {"c1": 30, "small3d": 20, "shifted": 30, "c2": 50}
 
 
+@pytest.mark.parametrize("ortho", ["auto", "cgs2"])
 @pytest.mark.parametrize("name", ["c1", "small3d", "shifted", "c2"])
-def test_fgmres_matches_oracle_iterations(torch_cuda, name):
+def test_fgmres_matches_oracle_iterations(torch_cuda, name, ortho):
     torch = torch_cuda
     from paper_2205_03224_gb300 import Gemslr
     A, xyz, part = problem(name)
@@ -30,7 +31,7 @@ def test_fgmres_matches_oracle_iterations(torch_cuda, name):
     As = A.to_scipy()
     x_ref, info_ref = fgmres(As, b, M.apply, restart=RESTART[name], rtol=1e-8)
     G = Gemslr.from_factors(A, part, M.factors())
-    x, info = G.solve(torch.from_numpy(b).cuda(), restart=RESTART[name], rtol=1e-8)
+    x, info = G.solve(torch.from_numpy(b).cuda(), restart=RESTART[name], rtol=1e-8, ortho=ortho)
     x = x.cpu().numpy()
     assert info[0]["converged"]
     assert abs(info[0]["iters"] - info_ref["iters"]) <= 1
@@ -39,12 +40,15 @@ def test_fgmres_matches_oracle_iterations(torch_cuda, name):
     assert rel_err(x, x_ref) <= 1e-6
 
 
+@pytest.mark.parametrize("ortho", ["auto", "cgs2"])
 @pytest.mark.parametrize("name", ["c1", "indef24"])
-def test_fgmres_residual_history_matches_oracle(torch_cuda, name):
+def test_fgmres_residual_history_matches_oracle(torch_cuda, name, ortho):
     """Within one cycle the GPU's Givens estimate after k steps equals the
     oracle's (Sec. 4.1: FGMRES minimises the same residual whatever the
     orthogonalisation scheme) and the true residual of the iterate the GPU
-    returns.  indef24 takes the single-pass branch of the DGKS test once, so a
+    returns, for both orthogonalisations: the delayed one (one reduction per
+    step) and classical Gram-Schmidt with a selective second pass, where
+    indef24 takes the single-pass branch of the DGKS test once, so a
     projection with wrong coefficients there breaks every later step."""
     torch = torch_cuda
     from paper_2205_03224_gb300 import Gemslr
@@ -59,14 +63,14 @@ def test_fgmres_residual_history_matches_oracle(torch_cuda, name):
     bd = torch.from_numpy(b).cuda()
     single = 0
     for k in (1, 2, 6, 7, 8, 9, 12, 20):
-        x, info = G.solve(bd, restart=40, rtol=1e-14, maxit=k, check=False)
+        x, info = G.solve(bd, restart=40, rtol=1e-14, maxit=k, check=False, ortho=ortho)
         est = info[0]["rel_res_est"]
         true = np.linalg.norm(b - As @ x.cpu().numpy()) / np.linalg.norm(b)
         assert info[0]["iters"] == k
         assert abs(est - hist[k - 1]) <= 1e-6 * hist[k - 1], (k, est, hist[k - 1])
         assert abs(true - est) <= 1e-6 * est, (k, est, true)
         single = k - info[0]["reorth"]
-    if name == "indef24":
+    if name == "indef24" and ortho == "cgs2":
         assert single >= 1          # the single-pass branch ran
 
 
