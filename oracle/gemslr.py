@@ -58,10 +58,14 @@ class OracleGemslr:
     ilu : "ilu0" | "ilut" | "exact" (ILUT with tau = 0 and no fill limit)
     rank : int or list (per Schur level); 0 disables the correction
     last_ilu : factor kind of the last-level blocks (defaults to ``ilu``)
+    inner_steps : Alg. 2 step 9; 0 applies the standard recursion at level 0,
+        k > 0 solves S_hat_0 y2 = z2 there by k steps of right-preconditioned
+        GMRES (``inner_gmres``)
     """
 
     def __init__(self, A, part, ilu="ilu0", tau=1e-3, lfil=10, rank=8, last_ilu=None,
-                 arnoldi_tol=1e-2, max_cycles=20, lowrank=True):
+                 arnoldi_tol=1e-2, max_cycles=20, lowrank=True, inner_steps=0):
+        self.inner_steps = int(inner_steps)
         A = sp.csr_matrix(A)
         self.n = A.shape[0]
         self.part = part
@@ -111,11 +115,56 @@ class OracleGemslr:
         b1, b2 = r[:d], r[d:]
         z1 = _ilu.lu_solve(lv["L"], lv["U"], b1)                 # z1 = U^-1 L^-1 b1
         z2 = b2 - lv["E"] @ z1                                   # z2 = b2 - E z1
-        W, H = lv["W"], lv["H"]
-        u2 = W @ (H @ (W.T @ z2)) if W.shape[1] else np.zeros_like(z2)
-        y2 = self.solve_level(u2 + z2, l + 1)                    # y2 = Solve(u2 + z2, l+1)
+        if l == 0 and self.inner_steps > 0:
+            y2 = self.inner_gmres(z2, self.inner_steps)          # S_hat_0 y2 = z2 by GMRES
+        else:
+            y2 = self.precond_schur(z2, l)                       # y2 = Solve(z2 + u2, l+1)
         y1 = z1 - _ilu.lu_solve(lv["L"], lv["U"], lv["F"] @ y2)  # y1 = z1 - U^-1 L^-1 F y2
         return np.concatenate([y1, y2])
+
+    def precond_schur(self, z2, l):
+        """Eq. 6 at level l: C_l^-1 (z2 + W_l H_l W_l^T z2), C_l^-1 the levels below."""
+        lv = self.levels[l]
+        W, H = lv["W"], lv["H"]
+        u2 = W @ (H @ (W.T @ z2)) if W.shape[1] else np.zeros_like(z2)
+        return self.solve_level(u2 + z2, l + 1)
+
+    def s_hat(self, v, l):
+        """Inexact Schur complement S_hat_l v = C_l v - E_l U_l^-1 L_l^-1 F_l v (Sec. 4.1)."""
+        lv = self.levels[l]
+        C = self.Ahat[lv["e"]:, lv["e"]:]
+        return C @ v - lv["E"] @ _ilu.lu_solve(lv["L"], lv["U"], lv["F"] @ v)
+
+    def inner_gmres(self, z2, k, l=0):
+        """Alg. 2 step 9: k steps of GMRES on S_hat_l y = z2 from y = 0, right
+        preconditioned by ``precond_schur`` (Eq. 6).  Arnoldi with modified
+        Gram-Schmidt on the vectors v_j; y = sum_j c_j M_S^-1 v_j with c the
+        minimiser of ||beta e_1 - H c|| over the (j+1) x j Hessenberg matrix.
+        A happy breakdown (h_{j+1,j} <= 1e-14 ||S_hat M_S^-1 v_j||) ends the
+        steps early with the exact solution of the projected problem."""
+        beta = np.linalg.norm(z2)
+        if beta == 0.0:
+            return np.zeros_like(z2)
+        V = [z2 / beta]
+        Z = []
+        H = np.zeros((k + 1, k))
+        steps = 0
+        for j in range(k):
+            Z.append(self.precond_schur(V[j], l))
+            w = self.s_hat(Z[j], l)
+            w0 = np.linalg.norm(w)
+            for i in range(j + 1):
+                H[i, j] = V[i] @ w
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            steps = j + 1
+            if H[j + 1, j] <= 1e-14 * w0:
+                break
+            V.append(w / H[j + 1, j])
+        rhs = np.zeros(steps + 1)
+        rhs[0] = beta
+        c = np.linalg.lstsq(H[:steps + 1, :steps], rhs, rcond=None)[0]
+        return np.column_stack(Z) @ c
 
     def apply_perm(self, r_hat):
         """M^{-1} in the multilevel ordering."""
