@@ -183,6 +183,25 @@ gemslr_status gemslr_export_factors(gemslr_handle h, gemslr_factors *f);
 gemslr_status gemslr_apply(gemslr_handle h, const double *r_dev, double *z_dev, int32_t nrhs,
                            void *stream);
 
+/*
+ * Inner GMRES at the root level (Alg. 2 step 9).  With steps > 0, every
+ * application of M^{-1} (gemslr_apply, gemslr_apply_static and the FGMRES
+ * solves) replaces the root level's y2 = M_S^{-1} z2 by `steps` steps of
+ * right-preconditioned GMRES from y2 = 0 on S_hat_0 y2 = z2, where
+ * S_hat_0 = C_0 - E_0 U_0^{-1} L_0^{-1} F_0 is the inexact Schur complement of
+ * the root level (Sec. 4.1) and M_S^{-1} its preconditioner: the level-0
+ * low-rank correction (Eq. 6) followed by the levels below.  The Arnoldi
+ * vectors use the application's precision with FP64 sums; a happy breakdown
+ * (h_{j+1,j} <= 1e-14 ||S_hat_0 z_j||) ends the steps early.  M^{-1} becomes
+ * nonlinear; FGMRES (flexible) then uses classical Gram-Schmidt with a second
+ * pass.  steps = 0 restores the standard application.  The first call with
+ * steps > 0 allocates the Arnoldi storage (about (2 steps + 3) x (n - level_ptr[1])
+ * vector entries plus a copy of the rows [level_ptr[1], n) of P^T A P).
+ * Errors: ARG (steps outside [0, 8], no Schur level, or the learned stage
+ * enabled: the two are exclusive), CUDA, NOMEM.
+ */
+gemslr_status gemslr_set_inner_steps(gemslr_handle h, int32_t steps);
+
 typedef struct {
     int32_t restart;     /* FGMRES cycle length m                               */
     int32_t maxit;       /* total inner iterations (1,000 in the paper)         */

@@ -69,7 +69,7 @@ EXPORTED = [
     "gemslr_setup_batch", "gemslr_batch_apply", "gemslr_batch_fgmres_solve", "gemslr_batch_stats",
     "gemslr_batch_last_error", "gemslr_batch_destroy",
     "gemslr_learned_train", "gemslr_learned_enable", "gemslr_learned_info", "gemslr_learned_params",
-    "gemslr_learned_loss_grad", "gemslr_apply_static", "gemslr_selftest_wait",
+    "gemslr_learned_loss_grad", "gemslr_apply_static", "gemslr_selftest_wait", "gemslr_set_inner_steps",
 ]
 
 _lib = None
@@ -121,6 +121,7 @@ def load():
     L.gemslr_batch_last_error.argtypes = []
     L.gemslr_learned_train.argtypes = [P, P, ctypes.POINTER(LearnedOpts), P]
     L.gemslr_learned_enable.argtypes = [P, i32]
+    L.gemslr_set_inner_steps.argtypes = [P, i32]
     L.gemslr_learned_info.argtypes = [P, P]
     L.gemslr_learned_params.argtypes = [P, i32, P, i64]
     L.gemslr_learned_loss_grad.argtypes = [P, i32, P, P, P, P]

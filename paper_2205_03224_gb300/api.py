@@ -136,6 +136,11 @@ class Gemslr:
                     nnz_factors=int(out[4]), bytes_per_apply=float(out[5]), setup_ms=float(out[6]),
                     device_bytes=int(out[7]), levels=lev)
 
+    def set_inner_steps(self, steps):
+        """Alg. 2 step 9: `steps` GMRES steps on the root level's inexact Schur
+        complement inside every M^{-1} (0 restores the standard application)."""
+        L.check(self._lib.gemslr_set_inner_steps(self._h, int(steps)))
+
     # ---- learned interface correction (an addition to the method) ----
     def learned_train(self, coords, channels=32, npairs=20000, epochs=10, batch=64, lr=1e-3, seed=4):
         """Train the level-l* correction network on the method's own pairs; returns the loss per epoch."""

@@ -355,16 +355,120 @@ void upload_hierarchy(const Hierarchy &h, Arena &a, DevHierarchy<VT, WT> &d, int
 }
 
 template <typename VT, typename WT>
+void setup_inner(const Hierarchy &h, Arena &a, DevHierarchy<VT, WT> &d, int k, int sms) {
+    DevInner<VT> &I = d.inner;
+    if (k > 0 && !I.work2) {
+        const int64_t e0 = h.lev[0].e, n = h.n, m = n - e0;
+        // rows [e0, n) of A_hat with global columns, values in the application's precision
+        const Csr &A = h.Ahat;
+        std::vector<int64_t> rp(m + 1);
+        for (int64_t i = 0; i <= m; ++i) rp[i] = A.rp[e0 + i] - A.rp[e0];
+        std::vector<int32_t> ci(A.ci.begin() + A.rp[e0], A.ci.begin() + A.rp[n]);
+        std::vector<double> v(A.v.begin() + A.rp[e0], A.v.begin() + A.rp[n]);
+        InnerView<VT> &iv = I.iv;
+        iv.m = m;
+        iv.e0 = e0;
+        iv.rp = a.upload(rp);
+        iv.ci = a.upload(ci);
+        iv.v = a.upload(convert<VT>(v));
+        const size_t mm = (size_t)std::max<int64_t>(m, 1);
+        iv.V = (VT *)a.alloc(sizeof(VT) * mm * (kMaxInner + 1));
+        iv.Z = (VT *)a.alloc(sizeof(VT) * mm * kMaxInner);
+        iv.w = (VT *)a.alloc(sizeof(VT) * mm);
+        iv.H = (double *)a.alloc(sizeof(double) * (kMaxInner + 1) * kMaxInner);
+        GEMSLR_CUDA(cudaMemset(iv.H, 0, sizeof(double) * (kMaxInner + 1) * kMaxInner));
+        iv.grid = (int)std::max<int64_t>(1, std::min<int64_t>((m + kReduceThreads - 1) / kReduceThreads, 2 * sms));
+        iv.partial = (double *)a.alloc(sizeof(double) * iv.grid * (kMaxInner + 2));
+        iv.counter = (unsigned *)a.alloc(16);
+        GEMSLR_CUDA(cudaMemset(iv.counter, 0, 16));
+        iv.ctl = (InnerCtl *)a.alloc(sizeof(InnerCtl));
+        GEMSLR_CUDA(cudaMemset(iv.ctl, 0, sizeof(InnerCtl)));
+        I.work2 = (VT *)a.alloc(sizeof(VT) * std::max<int64_t>(n, 1));
+        GEMSLR_CUDA(cudaMemset(I.work2, 0, sizeof(VT) * std::max<int64_t>(n, 1)));
+        I.zero_rp = (int64_t *)a.alloc(sizeof(int64_t) * (mm + 1));
+        GEMSLR_CUDA(cudaMemset(I.zero_rp, 0, sizeof(int64_t) * (mm + 1)));
+    }
+    I.k = k;
+    I.iv.k = k;
+}
+
+// Alg. 2 at the root level with step 9: z1 = U^-1 L^-1 b1, z2 = b2 - E z1,
+// k GMRES steps on S_hat_0 y2 = z2 (inner.cu) whose preconditioner is the
+// level-0 correction plus the levels below, y1 = z1 - U^-1 L^-1 F y2.
+template <typename VT, typename WT>
+void apply_root_inner(DevHierarchy<VT, WT> &d, const double *in, VT *work, double *out_final, cudaStream_t st) {
+    DevLevel<VT, WT> &L0 = d.lev[0];
+    DevInner<VT> &I = d.inner;
+    const InnerView<VT> &iv = I.iv;
+    VT *work2 = I.work2;
+    {
+        ProfScope ps("trsv_down_L0", st);
+        launch_trsv<VT, WT>(L0.view, 0, L0.smem_rows, in, work, nullptr, d.scratch, st);
+    }
+    LevelView<VT, WT> v0 = L0.view;
+    v0.k = 0;                                       // z2 only: the correction acts inside the preconditioner
+    {
+        ProfScope ps("couple_EWt_L0", st);
+        launch_couple<VT, WT>(v0, in, work, d.partial, d.counter, d.u, st);
+    }
+    {
+        ProfScope ps("inner_start", st);
+        launch_inner_norm<VT>(iv, work + iv.e0, st);
+        launch_inner_start<VT>(iv, work + iv.e0, work2, st);
+    }
+    LevelView<VT, WT> vz = L0.view;
+    vz.E_rp = I.zero_rp;                            // E_0 empty: z2 = v_j unchanged, u = H_0 W_0^T v_j
+    PendingLowRank<VT, WT> pend;
+    if (L0.view.k > 0 && L0.view.stail > 0) {
+        pend.W = L0.view.W;
+        pend.u = d.u;
+        pend.ld = L0.view.stail;
+        pend.row0 = L0.view.e;
+        pend.k = L0.view.k;
+    }
+    for (int j = 0; j < I.k; ++j) {
+        if (pend.W) {
+            ProfScope ps("couple_EWt_L0", st);
+            launch_couple<VT, WT>(vz, nullptr, work2, d.partial, d.counter, d.u, st);
+        }
+        apply_levels<VT, WT>(d, 1, nullptr, work2, nullptr, st, pend);   // z_j = M_S^-1 v_j in the tail
+        {
+            ProfScope ps("inner_trsv_L0", st);                              // level part: -U^-1 L^-1 F z_j
+            launch_trsv<VT, WT>(L0.view, 1, L0.smem_rows, nullptr, work2, nullptr, d.scratch, st);
+        }
+        {
+            ProfScope ps("inner_spmv_gs", st);
+            launch_inner_spmv_dots<VT>(iv, j, work2, st);
+            launch_inner_sub_dots<VT>(iv, j, st);
+            launch_inner_scale<VT>(iv, j, work2, st);
+        }
+    }
+    {
+        ProfScope ps("inner_finish", st);
+        launch_inner_lsq<VT>(iv, st);
+        launch_inner_combine<VT>(iv, work, out_final, st);
+    }
+    {
+        ProfScope ps("trsv_up_L0", st);
+        launch_trsv<VT, WT>(L0.view, 1, L0.smem_rows, nullptr, work, out_final, d.scratch, st);
+    }
+}
+
+template <typename VT, typename WT>
 void apply_levels(DevHierarchy<VT, WT> &d, int from, const double *in, VT *work, double *out_final,
-                  cudaStream_t st) {
+                  cudaStream_t st, const PendingLowRank<VT, WT> &pend0) {
     const int nl = (int)d.lev.size();
+    if (from == 0 && nl >= 1 && d.inner.k > 0) {
+        apply_root_inner<VT, WT>(d, in, work, out_final, st);
+        return;
+    }
     static const char *kDown[] = {"trsv_down_L0", "trsv_down_L1", "trsv_down_L2", "trsv_down_L3", "trsv_down_L4+"};
     static const char *kUp[] = {"trsv_up_L0", "trsv_up_L1", "trsv_up_L2", "trsv_up_L3", "trsv_up_L4+"};
     static const char *kCouple[] = {"couple_EWt_L0", "couple_EWt_L1", "couple_EWt_L2", "couple_EWt_L3", "couple_EWt_L4+"};
     // learned correction at the deepest Schur level (active only when that level is part of this application)
     const bool learn = d.learned && d.learned->enabled && nl >= 1 && from <= nl - 1;
     // W_l u_l of the level before is added where its tail rows are first read
-    PendingLowRank<VT, WT> pend;
+    PendingLowRank<VT, WT> pend = pend0;
     for (int l = from; l < nl; ++l) {
         DevLevel<VT, WT> &L = d.lev[l];
         const double *src = (l == from) ? in : nullptr;
@@ -429,6 +533,9 @@ template void upload_hierarchy<float, __nv_bfloat16>(const Hierarchy &, Arena &,
                                                      DevHierarchy<float, __nv_bfloat16> &, int);
 template void set_lowrank<double, double>(DevLevel<double, double> &, const HostLevel &, Arena &);
 template void apply_levels<double, double>(DevHierarchy<double, double> &, int, const double *, double *, double *,
-                                           cudaStream_t);
+                                           cudaStream_t, const PendingLowRank<double, double> &);
+template void setup_inner<double, double>(const Hierarchy &, Arena &, DevHierarchy<double, double> &, int, int);
+template void setup_inner<float, __nv_bfloat16>(const Hierarchy &, Arena &, DevHierarchy<float, __nv_bfloat16> &,
+                                                int, int);
 
 }  // namespace gemslr

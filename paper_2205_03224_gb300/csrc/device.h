@@ -147,6 +147,30 @@ struct DevLevel {
     int64_t nchunks = 0;
 };
 
+// Inner GMRES of the root level (inner.cu); k = 0: the standard application.
+template <typename VT>
+struct DevInner {
+    int k = 0;
+    InnerView<VT> iv{};
+    VT *work2 = nullptr;          // n: Arnoldi operands in the multilevel order
+    int64_t *zero_rp = nullptr;   // m + 1 zeros: an empty E_0 (u = H_0 W_0^T v only)
+};
+
+template <typename VT>
+void launch_inner_norm(const InnerView<VT> &iv, const VT *z2, cudaStream_t st);
+template <typename VT>
+void launch_inner_start(const InnerView<VT> &iv, const VT *z2, VT *work2, cudaStream_t st);
+template <typename VT>
+void launch_inner_spmv_dots(const InnerView<VT> &iv, int j, const VT *work2, cudaStream_t st);
+template <typename VT>
+void launch_inner_sub_dots(const InnerView<VT> &iv, int j, cudaStream_t st);
+template <typename VT>
+void launch_inner_scale(const InnerView<VT> &iv, int j, VT *work2, cudaStream_t st);
+template <typename VT>
+void launch_inner_lsq(const InnerView<VT> &iv, cudaStream_t st);
+template <typename VT>
+void launch_inner_combine(const InnerView<VT> &iv, VT *work, double *out_final, cudaStream_t st);
+
 template <typename VT, typename WT>
 struct DevHierarchy {
     std::vector<DevLevel<VT, WT>> lev;   // Schur levels
@@ -158,6 +182,7 @@ struct DevHierarchy {
     VT *u = nullptr;                     // kMaxRank
     int32_t *err = nullptr;              // device error word of the substitution kernels
     LearnedStage<VT> *learned = nullptr; // optional learned correction at the deepest Schur level
+    DevInner<VT> inner;                  // optional inner GMRES at the root level (Alg. 2 step 9)
 };
 
 // Learned-stage glue (learned.cu).
@@ -186,10 +211,16 @@ void set_lowrank(DevLevel<VT, WT> &d, const HostLevel &hl, Arena &a);
 // Apply levels >= from (Alg. 2 recursion entered at level `from`).  With
 // `in` non-null the right-hand side is read from it (FP64, multilevel
 // order); otherwise from the tail of `work` starting at level `from`.
-// out_final (optional) receives the FP64 result of every level.
+// out_final (optional) receives the FP64 result of every level.  pend0: a
+// W u term to add to the right-hand side of level `from` (from > 0).  With
+// from == 0 and inner steps set, the root level runs Alg. 2 step 9.
 template <typename VT, typename WT>
 void apply_levels(DevHierarchy<VT, WT> &d, int from, const double *in, VT *work, double *out_final,
-                  cudaStream_t st);
+                  cudaStream_t st, const PendingLowRank<VT, WT> &pend0 = PendingLowRank<VT, WT>());
+
+// Allocate (once) and switch on the inner GMRES with k steps (k = 0: off).
+template <typename VT, typename WT>
+void setup_inner(const Hierarchy &h, Arena &a, DevHierarchy<VT, WT> &d, int k, int sms);
 
 // z = M^{-1} r in the multilevel order.  `in` FP64 (length n), `out` FP64.
 // start_level > 0 applies the sub-hierarchy of levels >= start_level to the

@@ -129,4 +129,38 @@ struct DgsBufs {
     double *hprev;         // kMaxCols: first-pass column of the previous step
 };
 
+// Inner GMRES at the root level (Alg. 2 step 9): up to kMaxInner steps of
+// right-preconditioned GMRES on S_hat_0 y2 = z2, S_hat_0 = C_0 - E_0 U^-1 L^-1 F_0
+// (Sec. 4.1), preconditioned by the level-0 correction and the levels below.
+constexpr int kMaxInner = 8;
+
+struct InnerCtl {
+    int32_t steps;         // Arnoldi steps taken (columns of H in use)
+    int32_t done;          // 1: z2 = 0 or a happy breakdown ended the steps
+    double beta;           // ||z2||
+    double wn0;            // ||S_hat z_j|| before orthogonalisation (breakdown test)
+    double h2[kMaxInner + 1];  // second-pass coefficients of the current step
+    double c[kMaxInner];   // least-squares coefficients of y2 = sum_j c_j z_j
+};
+
+// Device state of the inner GMRES.  Vectors have the tail length m = n - e0
+// (rows [e0, n) of the multilevel order).
+template <typename VT>
+struct InnerView {
+    int64_t m;                 // n - e0
+    int64_t e0;                // first tail row
+    int32_t k;                 // steps per application (<= kMaxInner)
+    const int64_t *rp;         // rows [e0, n) of A_hat: m + 1 offsets
+    const int32_t *ci;         // global columns
+    const VT *v;
+    VT *V;                     // m x (k + 1), column-major: Arnoldi basis
+    VT *Z;                     // m x k: preconditioned basis (M_S^-1 v_j)
+    VT *w;                     // m
+    double *H;                 // (kMaxInner + 1) x kMaxInner, column-major
+    double *partial;           // grid x (kMaxInner + 2), column-major
+    unsigned *counter;
+    InnerCtl *ctl;
+    int grid;                  // CTAs of the reduction kernels
+};
+
 }  // namespace gemslr

@@ -357,7 +357,8 @@ void fgmres_step(gemslr_ctx *h, cudaStream_t st) {
 // (not with the learned stage) and the fused product suits A (short rows).
 bool use_dcgs(const gemslr_ctx *h) {
     const bool learned = (h->d64.learned && h->d64.learned->enabled) || (h->d32.learned && h->d32.learned->enabled);
-    return !learned && h->spmv_lanes <= 8;
+    const bool inner = h->d64.inner.k > 0 || h->d32.inner.k > 0;     // Alg. 2 step 9 makes M^{-1} nonlinear
+    return !learned && !inner && h->spmv_lanes <= 8;
 }
 
 DgsBufs dgs_bufs(gemslr_ctx *h) {
@@ -1154,6 +1155,8 @@ gemslr_status gemslr_learned_train(gemslr_handle h, const int32_t *coords, const
                                    double *loss_history) {
     return guard([&] {
         if (!h || !coords || !o) fail(GEMSLR_ERR_ARG, "NULL argument");
+        if (h->d64.inner.k > 0 || h->d32.inner.k > 0)
+            fail(GEMSLR_ERR_ARG, "inner steps and the learned stage are exclusive");
         if (o->npairs < 1 || o->epochs < 0 || o->batch < 1 || !(o->lr > 0)) fail(GEMSLR_ERR_ARG, "invalid learned options");
         if (!h->learned) h->learned = new LearnedHost();
         LearnedHost &Lh = *h->learned;
@@ -1216,9 +1219,29 @@ gemslr_status gemslr_learned_train(gemslr_handle h, const int32_t *coords, const
     });
 }
 
+gemslr_status gemslr_set_inner_steps(gemslr_handle h, int32_t steps) {
+    return guard([&] {
+        if (!h || steps < 0 || steps > kMaxInner) fail(GEMSLR_ERR_ARG, "inner steps must be in [0, 8]");
+        if (steps > 0 && h->host.lev.empty()) fail(GEMSLR_ERR_ARG, "inner steps need a Schur level");
+        const bool learned = (h->d64.learned && h->d64.learned->enabled) || (h->d32.learned && h->d32.learned->enabled);
+        if (steps > 0 && learned) fail(GEMSLR_ERR_ARG, "inner steps and the learned stage are exclusive");
+        if (h->mixed) setup_inner<float, __nv_bfloat16>(h->host, h->arena, h->d32, steps, sm_count());
+        else setup_inner<double, double>(h->host, h->arena, h->d64, steps, sm_count());
+        if (h->graph_exec) {                 // the captured solve depends on M^{-1}: rebuild on next use
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+            cudaGraphDestroy(h->graph);
+            h->graph = nullptr;
+        }
+        GEMSLR_CUDA(cudaDeviceSynchronize());
+    });
+}
+
 gemslr_status gemslr_learned_enable(gemslr_handle h, int32_t on) {
     return guard([&] {
         if (!h || !h->learned) fail(GEMSLR_ERR_ARG, "no learned stage on this handle");
+        if (on && (h->d64.inner.k > 0 || h->d32.inner.k > 0))
+            fail(GEMSLR_ERR_ARG, "inner steps and the learned stage are exclusive");
         h->learned->st64.enabled = h->learned->st32.enabled = on != 0;
         if (h->graph_exec) {                 // the captured solve depends on the stage: rebuild on next use
             cudaGraphExecDestroy(h->graph_exec);

@@ -18,6 +18,8 @@ CASES = {
     # indefinite (shift 0.1 h^-2): the DGKS test skips the second Gram-Schmidt
     # pass at step 7 of the first cycle, every other step takes it
     "indef24": ((24, 24, 24), 0.0, 0.1, 4, 8, "ilut", 1e-3, 10, 8),
+    # a 5-unknown root Schur system: 8 inner GMRES steps end in a happy breakdown
+    "tiny2d": ((9, 5), 0.3, 0.0, 2, 2, "ilu0", 0.0, 0, 2),
 }
 
 
