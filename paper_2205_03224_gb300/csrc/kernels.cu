@@ -1157,10 +1157,11 @@ k_dgs_update(int64_t len, double *__restrict__ V, int64_t ldv, double *vt, const
     const int64_t st = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += st) {
         double xa = 0.0, xc = 0.0, ya = 0.0, yc = 0.0;
-        for (int c0 = 0; c0 < j; c0 += 8) {
+        int c0 = 0;
+        for (; c0 + 8 <= j; c0 += 8) {
             double v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = V[(int64_t)min(c0 + u, j - 1) * ldv + i];
+            for (int u = 0; u < 8; ++u) v[u] = V[(int64_t)(c0 + u) * ldv + i];
 #pragma unroll
             for (int u = 0; u < 8; u += 2) {
                 xa = fma(v[u], as[c0 + u], xa);
@@ -1168,6 +1169,33 @@ k_dgs_update(int64_t len, double *__restrict__ V, int64_t ldv, double *vt, const
                 xc = fma(v[u], cf[c0 + u], xc);
                 yc = fma(v[u + 1], cf[c0 + u + 1], yc);
             }
+        }
+        // the remaining j % 8 columns in groups of 4, 2 and 1 (uniform over the grid)
+        if (c0 + 4 <= j) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = V[(int64_t)(c0 + u) * ldv + i];
+#pragma unroll
+            for (int u = 0; u < 4; u += 2) {
+                xa = fma(v[u], as[c0 + u], xa);
+                ya = fma(v[u + 1], as[c0 + u + 1], ya);
+                xc = fma(v[u], cf[c0 + u], xc);
+                yc = fma(v[u + 1], cf[c0 + u + 1], yc);
+            }
+            c0 += 4;
+        }
+        if (c0 + 2 <= j) {
+            const double v0 = V[(int64_t)c0 * ldv + i], v1 = V[(int64_t)(c0 + 1) * ldv + i];
+            xa = fma(v0, as[c0], xa);
+            ya = fma(v1, as[c0 + 1], ya);
+            xc = fma(v0, cf[c0], xc);
+            yc = fma(v1, cf[c0 + 1], yc);
+            c0 += 2;
+        }
+        if (c0 < j) {
+            const double v0 = V[(int64_t)c0 * ldv + i];
+            xa = fma(v0, as[c0], xa);
+            xc = fma(v0, cf[c0], xc);
         }
         const double t = __ldcg(vt + i);
         const double v = (t - (xa + ya)) * inv_nu;
