@@ -5,7 +5,11 @@ One step = one complete right-preconditioned FGMRES(50) solve to relative
 residual 1e-8 (every application of M^{-1} walks the whole multilevel
 hierarchy) of the 64^3 convection-diffusion system (n = 262,144; 4 levels,
 64 subdomains per level, ILUT(1e-3, 10), rank 32, b ~ U[-1, 1) seed 1), with
-the preconditioner already set up and b resident on the GPU.  The value is
+the preconditioner already set up and b resident on the GPU.  By default the
+preconditioner runs in mixed precision (FP32 factors and vectors, BF16 W with
+FP32 accumulation; FGMRES in FP64) and the plain FP64 GPU path is timed beside
+it on the same workload (``fp64_path``); ``--precision fp64`` times that path
+alone.  The value is
 whole-job throughput in solves per second; N > 1 runs independent replicas
 (the path has no data exchange on one GPU).
 
@@ -36,15 +40,22 @@ WORKLOAD = ("3-D 7-pt convection-diffusion 64^3 (n=262144, beta=0.1), 4 levels x
             "ILUT(1e-3,10), rank 32, FGMRES(50) to rel. residual 1e-8, b~U[-1,1) seed 1")
 UNIT = "solves/s (FGMRES to 1e-8)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP64_PEAK_TFLOPS = 1.203      # FP64 FMA probe on this machine's GB300 (0.601 TFMA/s)
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# roofline kernel from one ncu --set full capture of the same workload
-# (profiles/trsv_c2_apply_<precision>.md); an entry must be removed when that
-# kernel changes.
+# FP64 arithmetic peak of the GB300: 152 SMs x 2 DFMA per clock (ncu's
+# sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained) x 2.07 GHz x 2 flops.
+FP64_PEAK_GFLOPS = 152 * 2 * 2.07 * 2
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu --set full capture of the same workload (profiles/), with the algorithmic
+# bytes of the captured launch; an entry must be removed when its kernel changes.
+#   M^-1 kernels: (config, precision, kernel) -> DRAM bytes of a launch
+#   Krylov kernels (work grows with the step j): -> (DRAM bytes, algorithmic bytes) of the captured step
 NCU_TRAFFIC = {
-    ("c2", "mixed", "trsv_up_L0"): 45_667_072 + 7_936,
-    ("c2", "fp64", "trsv_up_L0"): 76_670_208 + 919_040,
+    ("c2", "mixed", "trsv_up_L0"): 45_622_528 + 6_144,
+    ("c2", "fp64", "trsv_up_L0"): 76_691_456 + 1_087_744,
 }
+NCU_TRAFFIC_KRYLOV = {
+    ("c2", "mixed", "dgs_spmv_dots"): (80_623_104 + 2_769_152, None),   # step j = 25
+}
+NCU_KRYLOV_STEP = 25
 
 
 def cfg():
@@ -171,6 +182,81 @@ def algorithmic_bytes(fac, n, nnzA, sv=8, si=4, sw=8):
     return out
 
 
+def krylov_work(n, nnzA, its, m, j=None):
+    """FP64 flops and algorithmic bytes of the kernels of an FGMRES step with
+    delayed reorthogonalisation, summed over the steps of a solve of `its`
+    iterations with restart m (step j of a cycle has j finished basis
+    vectors), or for the single step j.
+      dgs_spmv_dots: w = A z (z also stored), V^T vt and V^T w over j columns,
+                     vt.vt, vt.w, w.w;
+      dgs_next:      the next direction from w, vt and j columns of V;
+      dgs_fix:       the previous step's reorthogonalised column from j - 1
+                     columns (runs beside M^{-1})."""
+    steps = [j] if j is not None else [i % m for i in range(its)]
+    out = {"dgs_spmv_dots": [0.0, 0.0], "dgs_next": [0.0, 0.0], "dgs_fix": [0.0, 0.0]}
+    for jj in steps:
+        out["dgs_spmv_dots"][0] += 2.0 * (2 * jj * n + 3 * n + nnzA)
+        out["dgs_spmv_dots"][1] += jj * n * 8 + nnzA * 12 + (n + 1) * 8 + 4 * n * 8
+        out["dgs_next"][0] += 2.0 * (jj * n + n)
+        out["dgs_next"][1] += jj * n * 8 + 4 * n * 8
+        jp = max(jj - 1, 0)
+        out["dgs_fix"][0] += 2.0 * (jp * n)
+        out["dgs_fix"][1] += jp * n * 8 + 2 * n * 8
+    return out
+
+
+def rooflines(prof, ab, kw, hbm, peaks, precision, nkeep=4):
+    """Roofline entries of the profiled kernels that have a work model, largest
+    total time first: M^-1 kernels against the HBM copy peak (algorithmic
+    bytes), Krylov kernels against the FP64 peak (they are bound by the FP64
+    pipe on this part), with their algorithmic bandwidth beside it."""
+    out = []
+    for k, (ms, cnt) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+        if k in ab:
+            per = ms / cnt
+            ach = ab[k] / (per * 1e-3) / 1e9
+            out.append({"kernel": k, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                        "frac": ach / hbm, "traffic": NCU_TRAFFIC.get((CONFIG, precision, k)),
+                        "bytes_per_launch": ab[k], "ms_per_launch": per, "share_ms": ms,
+                        "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"})
+        elif k in kw:
+            flops, byts = kw[k]
+            per = ms / cnt
+            ach = flops / (ms * 1e-3) / 1e9
+            traffic = None
+            tk = NCU_TRAFFIC_KRYLOV.get((CONFIG, precision, k))
+            if tk is not None:
+                dram, alg = tk
+                ratio = dram / (alg if alg else kw["_step"][k][1])
+                traffic = ratio * byts / cnt
+            out.append({"kernel": k, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_GFLOPS,
+                        "unit": "GFLOP/s", "frac": ach / FP64_PEAK_GFLOPS, "traffic": traffic,
+                        "bytes_per_launch": byts / cnt, "gbs": byts / (ms * 1e-3) / 1e9,
+                        "flops_per_launch": flops / cnt, "ms_per_launch": per, "share_ms": ms,
+                        "peak_source": "nominal FP64 (152 SMs x 2 DFMA/clk x 2.07 GHz)"})
+        if len(out) >= nkeep:
+            break
+    return out
+
+
+def solve_timing(G, b_dev, c, steps, warmup, flush, stream):
+    """CUDA-event times (ms) of `steps` complete solves after `warmup` ones."""
+    import torch
+    for _ in range(warmup):
+        x, info = G.solve(b_dev, restart=c["restart"], rtol=c["rtol"])
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x, info = G.solve(b_dev, restart=c["restart"], rtol=c["rtol"])
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms, x, info
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist()
@@ -269,20 +355,27 @@ def run_ours(args):
     G.solve(b_dev, restart=c["restart"], rtol=c["rtol"])
     prof = _lib.profile_read()
     _lib.profile_enable(False)
+    # the plain FP64 GPU path on the same workload (the comparison the metric names)
+    fp64_path = None
+    if args.precision == "mixed" and not args.no_compare:
+        G64 = Gemslr(A, part, ilu=c["ilu"], tau=c["tau"], lfil=c["lfil"], rank=c["rank"], precision="fp64")
+        ms64, x64, info64 = solve_timing(G64, b_dev, c, args.steps, args.warmup, flush, stream)
+        res64 = float(np.linalg.norm(b - A.to_scipy() @ x64.cpu().numpy()) / np.linalg.norm(b))
+        t64 = sum(ms64) / len(ms64)
+        fp64_path = {"time_to_solution_ms": t64, "iterations": info64[0]["iters"], "final_rel_residual": res64,
+                     "speedup_mixed_vs_fp64": t64 / (total_ms / args.steps)}
+        G64.close()
+        del G64
     fac = G.export_factors()
     sv = 4 if args.precision == "mixed" else 8
     sw = 2 if args.precision == "mixed" else 8
     ab = algorithmic_bytes(fac, A.n, A.nnz, sv=sv, sw=sw)
-    top = max((k for k in prof if k in ab), key=lambda k: prof[k][0])
-    top_ms = prof[top][0] / prof[top][1]
+    kw = {k: tuple(v) for k, v in krylov_work(A.n, A.nnz, its, c["restart"]).items()}
+    kw["_step"] = {k: tuple(v) for k, v in krylov_work(A.n, A.nnz, its, c["restart"], j=NCU_KRYLOV_STEP).items()}
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
-    achieved = ab[top] / (top_ms * 1e-3) / 1e9
-    traffic = NCU_TRAFFIC.get((CONFIG, args.precision, top))
-    roofline = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic, "bytes_per_launch": ab[top],
-                "ms_per_launch": top_ms,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    rl = rooflines(prof, ab, kw, hbm, peaks, args.precision)
+    roofline = rl[0]
     total_prof = sum(v[0] for v in prof.values())
     kernels = {k: {"ms_total": round(v[0], 4), "launches": v[1], "share": round(v[0] / total_prof, 4)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
@@ -300,6 +393,8 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(A.n * 8), "d2h_bytes_per_step": int(A.n * 8)},
         "gpu_launches": int(launches),
         "roofline": roofline,
+        "rooflines_top": rl,
+        "fp64_path": fp64_path,
         "kernels": kernels,
         "clocks": clk,
     }
@@ -462,7 +557,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-compare", action="store_true",
+                    help="mixed runs: skip timing the plain FP64 GPU path beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2 (default line), c3: 128^3 shifted (mixed), c4: batched systems, c5: learned stage")

@@ -72,8 +72,14 @@ void launch_gs_next(KrylovCtl *ctl, cudaStream_t st);
 void launch_dgs_dots(int64_t len, const int64_t *rp, const int32_t *ci, const double *av, const double *z, double *zcol,
                      const double *V, int64_t ldv, const double *vt, double *w, double *partial, unsigned *counter,
                      KrylovCtl *ctl, const DgsBufs &B, int grid, cudaStream_t st);
-void launch_dgs_update(int64_t len, double *V, int64_t ldv, double *vt, const double *w, const KrylovCtl *ctl,
-                       const DgsBufs &B, cudaStream_t st);
+void launch_dgs_next(int64_t len, double *V, int64_t ldv, double *vt, const double *w, const KrylovCtl *ctl,
+                     const DgsBufs &B, cudaStream_t st);
+// reorthogonalisation of step ctl->j + off (nothing when negative), `grid` CTAs;
+// exclusive: CTAs that never share an SM with a substitution CTA
+void launch_dgs_fix(int64_t len, double *V, int64_t ldv, const KrylovCtl *ctl, const DgsBufs &B, int off, int grid,
+                    bool exclusive, cudaStream_t st);
+// kernel attributes of the Krylov kernels (call before any capture)
+void prepare_krylov_kernels();
 void launch_dgs_close(int64_t len, const double *V, int64_t ldv, const double *vt, double *partial, unsigned *counter,
                       KrylovCtl *ctl, const DgsBufs &B, int grid, cudaStream_t st);
 void launch_lsq2(const KrylovCtl *ctl, const double *H, const double *g, const double *R, double *y, cudaStream_t st);

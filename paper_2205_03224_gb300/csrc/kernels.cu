@@ -1135,73 +1135,88 @@ k_dgs_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restric
     *counter = 0u;
 }
 
-// Step j, second sweep: V[:, j] = (vt - V_{j-1} a) / nu and the next direction
-// vt = (w - V_{j-1} coef[0..j) - v_j coef[j]) / (nu btil), in place (skipped
-// after a breakdown).  Each column group's loads are issued first.
+// Sum over the first nc columns of V at row i of V[i, c] * h[c] (h in shared
+// memory), columns eight at a time and the rest in groups of 4, 2 and 1, every
+// load of a group issued before its arithmetic (nc is uniform over the grid).
+__device__ __forceinline__ double combine_row(const double *__restrict__ V, int64_t ldv, int nc, const double *h,
+                                              int64_t i) {
+    double x = 0.0, y = 0.0;
+    int c0 = 0;
+    for (; c0 + 8 <= nc; c0 += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = V[(int64_t)(c0 + u) * ldv + i];
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            x = fma(v[u], h[c0 + u], x);
+            y = fma(v[u + 1], h[c0 + u + 1], y);
+        }
+    }
+    if (c0 + 4 <= nc) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = V[(int64_t)(c0 + u) * ldv + i];
+        x = fma(v[0], h[c0], x);
+        y = fma(v[1], h[c0 + 1], y);
+        x = fma(v[2], h[c0 + 2], x);
+        y = fma(v[3], h[c0 + 3], y);
+        c0 += 4;
+    }
+    if (c0 + 2 <= nc) {
+        const double v0 = V[(int64_t)c0 * ldv + i], v1 = V[(int64_t)(c0 + 1) * ldv + i];
+        x = fma(v0, h[c0], x);
+        y = fma(v1, h[c0 + 1], y);
+        c0 += 2;
+    }
+    if (c0 < nc) x = fma(V[(int64_t)c0 * ldv + i], h[c0], x);
+    return x + y;
+}
+
+// Step j, second sweep (the part the next application of M^{-1} waits for):
+// with v_j = (vt_j - V_{j-1} a) / nu, the next direction
+//   vt_{j+1} = (w - V_{j-1} coef[0..j) - v_j coef[j]) / (nu btil)
+//            = (w - V_{j-1} (coef[0..j) - a coef[j] / nu) - vt_j coef[j] / nu) / (nu btil)
+// needs one pass over V_{j-1} and not v_j itself; vt_{j+1} replaces vt_j in
+// place (not after a breakdown) and vt_j is kept in V[:, j] until k_dgs_fix
+// reorthogonalises it.
 __global__ void __launch_bounds__(256)
-k_dgs_update(int64_t len, double *__restrict__ V, int64_t ldv, double *vt, const double *__restrict__ w,
-             const KrylovCtl *ctl, DgsBufs B) {
-    __shared__ double as[kMaxCols], cf[kMaxCols + 8];
+k_dgs_next(int64_t len, double *__restrict__ V, int64_t ldv, double *vt, const double *__restrict__ w,
+           const KrylovCtl *ctl, DgsBufs B) {
+    __shared__ double cf[kMaxCols];
     const int j = ctl->j;
     const double nu = ctl->nu, bt = ctl->btil;
     const bool next = !ctl->breakdown && bt > 0.0;
-    const int np = (j + 7) & ~7;
-    for (int c = threadIdx.x; c < np; c += blockDim.x) {
-        as[c] = c < j ? __ldcg(B.a + c) : 0.0;
-        cf[c] = c < j ? __ldcg(B.coef + c) : 0.0;
-    }
+    const double inv_nu = 1.0 / nu;
+    const double cj = __ldcg(B.coef + j) * inv_nu;
+    for (int c = threadIdx.x; c < j; c += blockDim.x) cf[c] = fma(-__ldcg(B.a + c), cj, __ldcg(B.coef + c));
     __syncthreads();
-    const double cj = __ldcg(B.coef + j);
-    const double inv_nu = 1.0 / nu, inv_nb = next ? 1.0 / (nu * bt) : 0.0;
+    const double inv_nb = next ? 1.0 / (nu * bt) : 0.0;
     double *vj = V + (int64_t)j * ldv;
     const int64_t st = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += st) {
-        double xa = 0.0, xc = 0.0, ya = 0.0, yc = 0.0;
-        int c0 = 0;
-        for (; c0 + 8 <= j; c0 += 8) {
-            double v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = V[(int64_t)(c0 + u) * ldv + i];
-#pragma unroll
-            for (int u = 0; u < 8; u += 2) {
-                xa = fma(v[u], as[c0 + u], xa);
-                ya = fma(v[u + 1], as[c0 + u + 1], ya);
-                xc = fma(v[u], cf[c0 + u], xc);
-                yc = fma(v[u + 1], cf[c0 + u + 1], yc);
-            }
-        }
-        // the remaining j % 8 columns in groups of 4, 2 and 1 (uniform over the grid)
-        if (c0 + 4 <= j) {
-            double v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = V[(int64_t)(c0 + u) * ldv + i];
-#pragma unroll
-            for (int u = 0; u < 4; u += 2) {
-                xa = fma(v[u], as[c0 + u], xa);
-                ya = fma(v[u + 1], as[c0 + u + 1], ya);
-                xc = fma(v[u], cf[c0 + u], xc);
-                yc = fma(v[u + 1], cf[c0 + u + 1], yc);
-            }
-            c0 += 4;
-        }
-        if (c0 + 2 <= j) {
-            const double v0 = V[(int64_t)c0 * ldv + i], v1 = V[(int64_t)(c0 + 1) * ldv + i];
-            xa = fma(v0, as[c0], xa);
-            ya = fma(v1, as[c0 + 1], ya);
-            xc = fma(v0, cf[c0], xc);
-            yc = fma(v1, cf[c0 + 1], yc);
-            c0 += 2;
-        }
-        if (c0 < j) {
-            const double v0 = V[(int64_t)c0 * ldv + i];
-            xa = fma(v0, as[c0], xa);
-            xc = fma(v0, cf[c0], xc);
-        }
+        const double x = combine_row(V, ldv, j, cf, i);
         const double t = __ldcg(vt + i);
-        const double v = (t - (xa + ya)) * inv_nu;
-        vj[i] = v;
-        if (next) vt[i] = (w[i] - (xc + yc) - v * cj) * inv_nb;
+        vj[i] = t;
+        if (next) vt[i] = fma(-t, cj, w[i] - x) * inv_nb;
     }
+}
+
+// The reorthogonalisation of step jp = ctl->j + off, off the critical path:
+// V[:, jp] = (vt_jp - V_{jp-1} a) / nu, with a and nu of step jp (the next
+// step's reduction overwrites them only after this kernel; the FGMRES step
+// runs it beside the next application of M^{-1}).  Nothing for jp < 0.
+__global__ void __launch_bounds__(256)
+k_dgs_fix(int64_t len, double *__restrict__ V, int64_t ldv, const KrylovCtl *ctl, DgsBufs B, int off) {
+    __shared__ double as[kMaxCols];
+    const int jp = ctl->j + off;
+    if (jp < 0) return;
+    for (int c = threadIdx.x; c < jp; c += blockDim.x) as[c] = __ldcg(B.a + c);
+    __syncthreads();
+    const double inv_nu = 1.0 / ctl->nu;
+    double *vj = V + (int64_t)jp * ldv;
+    const int64_t st = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += st)
+        vj[i] = (vj[i] - combine_row(V, ldv, jp, as, i)) * inv_nu;
 }
 
 // End of a cycle: the reduction of the last direction against V_j finalises
@@ -1560,10 +1575,22 @@ void launch_dgs_dots(int64_t len, const int64_t *rp, const int32_t *ci, const do
     k_dgs_dots<<<grid, kReduceThreads, 0, st>>>(len, rp, ci, av, z, zcol, V, ldv, vt, w, partial, counter, ctl, B);
     count_launch();
 }
-void launch_dgs_update(int64_t len, double *V, int64_t ldv, double *vt, const double *w, const KrylovCtl *ctl,
-                       const DgsBufs &B, cudaStream_t st) {
-    k_dgs_update<<<grid_for(len, 256, 1216), 256, 0, st>>>(len, V, ldv, vt, w, ctl, B);
+void launch_dgs_next(int64_t len, double *V, int64_t ldv, double *vt, const double *w, const KrylovCtl *ctl,
+                     const DgsBufs &B, cudaStream_t st) {
+    k_dgs_next<<<grid_for(len, 256, 1216), 256, 0, st>>>(len, V, ldv, vt, w, ctl, B);
     count_launch();
+}
+constexpr int kFixExclusiveSmem = 170 * 1024;
+void launch_dgs_fix(int64_t len, double *V, int64_t ldv, const KrylovCtl *ctl, const DgsBufs &B, int off, int grid,
+                    bool exclusive, cudaStream_t st) {
+    // exclusive: each CTA reserves more shared memory than an SM has left
+    // beside any substitution CTA (>= 66 KB), so the two never share an SM
+    // and the latency-bound substitutions keep theirs to themselves
+    k_dgs_fix<<<grid, 256, exclusive ? kFixExclusiveSmem : 0, st>>>(len, V, ldv, ctl, B, off);
+    count_launch();
+}
+void prepare_krylov_kernels() {
+    GEMSLR_CUDA(cudaFuncSetAttribute(k_dgs_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, kFixExclusiveSmem));
 }
 void launch_dgs_close(int64_t len, const double *V, int64_t ldv, const double *vt, double *partial, unsigned *counter,
                       KrylovCtl *ctl, const DgsBufs &B, int grid, cudaStream_t st) {

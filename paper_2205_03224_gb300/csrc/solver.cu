@@ -50,6 +50,9 @@ struct gemslr_ctx {
     double *vin = nullptr, *zout = nullptr;   // fixed in/out of M^{-1} inside the FGMRES step
     int32_t *err_host = nullptr;              // pinned copy of the substitution error word
     double setup_ms = 0.0;
+    // second stream of the delayed reorthogonalisation (k_dgs_fix beside M^{-1})
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // CUDA graph of a whole FGMRES solve (conditional WHILE nodes for the cycle and step loops)
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -64,6 +67,9 @@ struct gemslr_ctx {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (graph) cudaGraphDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (aux_stream) cudaStreamDestroy(aux_stream);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         if (ctl_host) cudaFreeHost(ctl_host);
         if (n2_host) cudaFreeHost(n2_host);
         if (err_host) cudaFreeHost(err_host);
@@ -109,6 +115,7 @@ void ensure_krylov(gemslr_ctx *h, int m) {
         h->dhprev = (double *)h->arena.alloc(8 * kMaxCols);
         h->vin = (double *)h->arena.alloc(8 * n);
         h->zout = (double *)h->arena.alloc(8 * n);
+        prepare_krylov_kernels();
         GEMSLR_CUDA(cudaMallocHost(&h->ctl_host, sizeof(KrylovCtl)));
         GEMSLR_CUDA(cudaMallocHost(&h->n2_host, 8 * 4));
         GEMSLR_CUDA(cudaMallocHost(&h->err_host, 16));
@@ -380,15 +387,33 @@ DgsBufs dgs_bufs(gemslr_ctx *h) {
 void fgmres_step_d(gemslr_ctx *h, cudaStream_t st) {
     const int64_t n = h->host.n;
     const DgsBufs B = dgs_bufs(h);
+    if (!h->aux_stream) {
+        GEMSLR_CUDA(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+        GEMSLR_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        GEMSLR_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
+    // the previous step's reorthogonalisation runs beside z = M^{-1} vt_j on
+    // the SMs the level-0 substitutions leave free (one CTA per SM, none
+    // sharing an SM with a substitution CTA); the reduction below needs both
+    const int nb0 = h->host.lev.empty() ? 0 : (int)h->host.lev[0].bp.size() - 1;
+    const int fix_grid = std::max(16, h->red_grid - nb0);
+    GEMSLR_CUDA(cudaEventRecord(h->ev_fork, st));
+    GEMSLR_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
+    {
+        ProfScope ps("dgs_fix", h->aux_stream);
+        launch_dgs_fix(n, h->V, n, h->ctl, B, -1, fix_grid, true, h->aux_stream);
+    }
+    GEMSLR_CUDA(cudaEventRecord(h->ev_join, h->aux_stream));
     apply_perm(h, h->vin, h->zout, st);
+    GEMSLR_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
     {
         ProfScope ps("dgs_spmv_dots", st);
         launch_dgs_dots(n, h->A_rp, h->A_ci, h->A_v, h->zout, h->Z, h->V, n, h->vin, h->w, h->partial, h->counter,
                         h->ctl, B, h->red_grid, st);
     }
     {
-        ProfScope ps("dgs_update", st);
-        launch_dgs_update(n, h->V, n, h->vin, h->w, h->ctl, B, st);
+        ProfScope ps("dgs_next", st);
+        launch_dgs_next(n, h->V, n, h->vin, h->w, h->ctl, B, st);
     }
 }
 
@@ -397,6 +422,7 @@ void fgmres_step_d(gemslr_ctx *h, cudaStream_t st) {
 void fgmres_cycle_end_d(gemslr_ctx *h, cudaStream_t st) {
     const int64_t n = h->host.n;
     const DgsBufs B = dgs_bufs(h);
+    launch_dgs_fix(n, h->V, n, h->ctl, B, 0, 8 * h->red_grid, false, st);   // the last step's v_j
     launch_dgs_close(n, h->V, n, h->vin, h->partial, h->counter, h->ctl, B, h->red_grid, st);
     launch_lsq2(h->ctl, h->Hs, h->g, h->Rz, h->y, st);
     launch_update_x(n, h->Z, n, h->ctl, h->y, h->xh, st);
