@@ -48,12 +48,20 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2.07 * 2
 # bytes of the captured launch; an entry must be removed when its kernel changes.
 #   M^-1 kernels: (config, precision, kernel) -> DRAM bytes of a launch
 #   Krylov kernels (work grows with the step j): -> (DRAM bytes, algorithmic bytes) of the captured step
-NCU_TRAFFIC = {
-    ("c2", "mixed", "trsv_up_L0"): 45_622_528 + 6_144,
-    ("c2", "fp64", "trsv_up_L0"): 76_691_456 + 1_087_744,
+NCU_TRAFFIC = {    # profiles/trsv_c2_apply_<precision>.md
+    ("c2", "mixed", "trsv_down_L0"): 43_782_144, ("c2", "mixed", "trsv_down_L1"): 5_065_216,
+    ("c2", "mixed", "trsv_down_L2"): 487_680, ("c2", "mixed", "trsv_last"): 170_496,
+    ("c2", "mixed", "trsv_up_L2"): 329_472, ("c2", "mixed", "trsv_up_L1"): 3_443_968,
+    ("c2", "mixed", "trsv_up_L0"): 45_622_528 + 4_352,
+    ("c2", "fp64", "trsv_down_L0"): 73_523_456 + 741_120, ("c2", "fp64", "trsv_down_L1"): 12_471_040,
+    ("c2", "fp64", "trsv_down_L2"): 1_317_632, ("c2", "fp64", "trsv_last"): 367_872,
+    ("c2", "fp64", "trsv_up_L2"): 560_128, ("c2", "fp64", "trsv_up_L1"): 4_947_968,
+    ("c2", "fp64", "trsv_up_L0"): 76_690_944 + 829_952,
 }
-NCU_TRAFFIC_KRYLOV = {
-    ("c2", "mixed", "dgs_spmv_dots"): (80_623_104 + 2_769_152, None),   # step j = 25
+NCU_TRAFFIC_KRYLOV = {    # profiles/krylov_c2_mixed.md, step j = 25
+    ("c2", "mixed", "dgs_spmv_dots"): (80_603_648 + 2_561_536, None),
+    ("c2", "mixed", "dgs_next"): (56_632_576 + 128_512, None),
+    ("c2", "mixed", "dgs_fix"): (52_450_560 + 25_088, None),
 }
 NCU_KRYLOV_STEP = 25
 
@@ -275,6 +283,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     G = Gemslr(A, part, ilu=c["ilu"], tau=c["tau"], lfil=c["lfil"], rank=c["rank"], precision=args.precision)
     setup_s = time.perf_counter() - t0
+    if args.inner:
+        G.set_inner_steps(args.inner)
     st = G.stats()
     b_dev = torch.from_numpy(b).cuda()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
@@ -359,6 +369,8 @@ def run_ours(args):
     fp64_path = None
     if args.precision == "mixed" and not args.no_compare:
         G64 = Gemslr(A, part, ilu=c["ilu"], tau=c["tau"], lfil=c["lfil"], rank=c["rank"], precision="fp64")
+        if args.inner:
+            G64.set_inner_steps(args.inner)
         ms64, x64, info64 = solve_timing(G64, b_dev, c, args.steps, args.warmup, flush, stream)
         res64 = float(np.linalg.norm(b - A.to_scipy() @ x64.cpu().numpy()) / np.linalg.norm(b))
         t64 = sum(ms64) / len(ms64)
@@ -385,7 +397,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/bf16+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "inner_steps": args.inner,
+                   "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "Krylov basis 2 x 107 MB > L2; 256 MB buffer written between solves"},
         "time_to_solution_ms": total_ms / args.steps, "iterations": its, "final_rel_residual": res,
         "applies_per_s": 1e3 / apply_ms, "apply_ms": apply_ms, "setup_s": setup_s,
@@ -527,6 +540,12 @@ def run_learned(args):
                     rel_residual=res)
 
     plain = timed_solves()
+    inner = None
+    if args.inner:
+        G.set_inner_steps(args.inner)
+        inner = timed_solves()
+        inner["inner_steps"] = args.inner
+        G.set_inner_steps(0)
     t0 = time.perf_counter()
     hist = G.learned_train(xyz, channels=32, npairs=args.npairs, epochs=args.epochs, batch=64, lr=1e-3, seed=c["seed"])
     train_s = time.perf_counter() - t0
@@ -542,7 +561,7 @@ def run_learned(args):
                    "precision": args.precision},
         "setup_s": setup_s, "train_s": train_s, "train_pairs": args.npairs, "epochs": args.epochs,
         "loss_history": [float(v) for v in hist],
-        "plain": plain, "learned": learned, "learned_accepted": bool(accepted),
+        "plain": plain, "inner": inner, "learned": learned, "learned_accepted": bool(accepted),
         "learned_info": G.learned_info(),
     }
     if not accepted:
@@ -566,6 +585,8 @@ def main():
     ap.add_argument("--maxit", type=int, default=1000)
     ap.add_argument("--npairs", type=int, default=20000)
     ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--inner", type=int, default=0,
+                    help="GMRES steps on the root level's Schur system inside M^-1 (Alg. 2 step 9; 0 = standard)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

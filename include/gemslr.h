@@ -265,7 +265,11 @@ void gemslr_destroy(gemslr_handle h);
  * gemslr_batch_fgmres_solve: info has nsys * nrhs entries (system-major).
  * gemslr_batch_stats: out[0..7] = nsys, total rows, factor nonzeros, bytes of one
  * application (approximate), setup ms, autotuning ms, tuned rows per CTA of the
- * coupling kernels and of the Krylov kernels.
+ * coupling kernels and of the Krylov kernels; with nout > 8, out[8] = the fewest
+ * right-hand sides a substitution CTA handles (8, 4, 2 or 1: a level whose
+ * largest block's vector for 8 right-hand sides does not fit in shared memory
+ * splits them over several CTAs; 0: a block too large even for 1 keeps its
+ * vector in global memory).
  */
 #define GEMSLR_BATCH_RHS 8
 typedef struct gemslr_batch_ctx *gemslr_batch;

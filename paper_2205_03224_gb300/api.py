@@ -274,7 +274,8 @@ class GemslrBatch:
         return x, infos
 
     def stats(self):
-        out = np.zeros(8)
-        L.check(self._lib.gemslr_batch_stats(self._h, L.ptr(out), 8), batch=True)
+        out = np.zeros(9)
+        L.check(self._lib.gemslr_batch_stats(self._h, L.ptr(out), 9), batch=True)
         return dict(nsys=int(out[0]), rows=int(out[1]), nnz_factors=int(out[2]), bytes_per_apply=float(out[3]),
-                    setup_ms=float(out[4]), tune_ms=float(out[5]), rows_couple=int(out[6]), rows_krylov=int(out[7]))
+                    setup_ms=float(out[4]), tune_ms=float(out[5]), rows_couple=int(out[6]), rows_krylov=int(out[7]),
+                    rhs_per_cta=int(out[8]))

@@ -16,7 +16,7 @@
 #include "device.h"
 
 namespace gemslr {
-void launch_btrsv(const BatchLevel &lv, int mode, bool smem, size_t smem_bytes, const double *in, float *work,
+void launch_btrsv(const BatchLevel &lv, int mode, int rpc, size_t smem_bytes, const double *in, float *work,
                   double *out_final, float *scratch, cudaStream_t st);
 void set_btrsv_smem_limit(int bytes);
 void launch_bcouple(const BatchLevel &lv, const double *in, float *work, cudaStream_t st);
@@ -49,7 +49,7 @@ using namespace gemslr;
 
 struct BLevelHost {          // device level plus what the launcher needs
     BatchLevel v{};
-    bool smem = false;
+    int rpc = 0;              // right-hand sides per substitution CTA (0: vector in global memory)
     size_t smem_bytes = 0;
 };
 
@@ -193,8 +193,31 @@ void build_batch_level(gemslr_batch_ctx *B, int l, bool last, int rows_cta, BLev
     v.C.blk_chunk = a.upload(ch.blk_chunk);
     v.err = B->err;
     const int optin = dev_smem_optin();
-    out.smem_bytes = (size_t)kRingBytes + (size_t)maxrows * kBatchRhs * sizeof(float);
-    out.smem = out.smem_bytes <= (size_t)optin;
+    // the most right-hand sides per CTA whose block vectors fit in shared
+    // memory; a split (fewer than kBatchRhs) multiplies the CTAs, and is taken
+    // only while they all fit on the GPU at once: otherwise the CTAs would run
+    // in many waves, slower than one wave with the vectors in global memory
+    out.rpc = 0;
+    out.smem_bytes = 0;
+    for (int rpc = kBatchRhs; rpc >= 1; rpc /= 2) {
+        const size_t bytes = (size_t)kRingBytes + (size_t)maxrows * rpc * sizeof(float);
+        if (bytes <= (size_t)optin) {
+            out.rpc = rpc;
+            out.smem_bytes = bytes;
+            break;
+        }
+    }
+    if (out.rpc > 0 && out.rpc < kBatchRhs) {
+        int dev = 0, sms = 1, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        const int64_t resident = (int64_t)sms * std::max<int64_t>(1, per_sm / (int64_t)out.smem_bytes);
+        if ((int64_t)v.nblk * (kBatchRhs / out.rpc) > resident) {
+            out.rpc = 0;
+            out.smem_bytes = 0;
+        }
+    }
     if (!last) {
         v.F_rp = a.upload(F_rp);
         v.F_ci = a.upload(F_ci);
@@ -228,14 +251,14 @@ void batch_apply_layout(gemslr_batch_ctx *B, const double *in, double *out, cuda
     const int ns = B->nlev - 1;
     for (int l = 0; l < ns; ++l) {
         const double *src = l == 0 ? in : nullptr;
-        launch_btrsv(B->lev[l].v, 0, B->lev[l].smem, B->lev[l].smem_bytes, src, B->work, nullptr, B->scratch, st);
+        launch_btrsv(B->lev[l].v, 0, B->lev[l].rpc, B->lev[l].smem_bytes, src, B->work, nullptr, B->scratch, st);
         launch_bcouple(B->lev[l].v, src, B->work, st);
         launch_blowrank(B->lev[l].v, B->work, st);
     }
     const BLevelHost &la = B->lev[ns];
-    launch_btrsv(la.v, 0, la.smem, la.smem_bytes, ns == 0 ? in : nullptr, B->work, out, B->scratch, st);
+    launch_btrsv(la.v, 0, la.rpc, la.smem_bytes, ns == 0 ? in : nullptr, B->work, out, B->scratch, st);
     for (int l = ns - 1; l >= 0; --l)
-        launch_btrsv(B->lev[l].v, 1, B->lev[l].smem, B->lev[l].smem_bytes, nullptr, B->work, out, B->scratch, st);
+        launch_btrsv(B->lev[l].v, 1, B->lev[l].rpc, B->lev[l].smem_bytes, nullptr, B->work, out, B->scratch, st);
 }
 
 void build_segments(gemslr_batch_ctx *B, int rows) {
@@ -596,6 +619,11 @@ gemslr_status gemslr_batch_stats(gemslr_batch B, double *out, int32_t nout) {
         out[5] = B->tune_ms;
         out[6] = B->rows_couple;
         out[7] = B->rows_krylov;
+        if (nout > 8) {                    // fewest right-hand sides per substitution CTA (0: global memory)
+            int rpc = kBatchRhs;
+            for (auto &l : B->lev) rpc = std::min(rpc, l.rpc);
+            out[8] = rpc;
+        }
     });
 }
 

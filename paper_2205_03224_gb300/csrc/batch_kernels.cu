@@ -23,13 +23,20 @@ __device__ __forceinline__ bool last_of(unsigned *counter, unsigned n) {
 }  // namespace
 
 // ---- M^{-1} stages -------------------------------------------------------------------
-// Level-scheduled substitutions, one CTA per block of any system; the lanes of
-// a warp are 4 rows x 8 right-hand sides.  MODE 0: right-hand side from `in`
-// (FP64) or `work`.  MODE 1: right-hand side F y2, then work[rows] -= result.
-template <int MODE, bool SMEM>
+// Level-scheduled substitutions over the blocks of every system.  A block's
+// right-hand sides are split over kBatchRhs / RPC CTAs of RPC each, so that
+// the block's vector (rows x RPC) fits in shared memory: CTA c works on block
+// c / (kBatchRhs / RPC), right-hand sides RPC * (c % (kBatchRhs / RPC)) on.
+// The lanes of a warp are up to 4 rows x RPC right-hand sides.  MODE 0:
+// right-hand side from `in` (FP64) or `work`.  MODE 1: right-hand side F y2,
+// then work[rows] -= result.  Without SMEM (blocks too large even for RPC = 1)
+// RPC is kBatchRhs and the vector stays in global memory.
+template <int MODE, bool SMEM, int RPC>
 __global__ void __launch_bounds__(kTrsvThreads2)
 k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ work, double *__restrict__ out_final,
         float *__restrict__ scratch) {
+    static_assert(SMEM || RPC == R8, "the global-memory path keeps all right-hand sides");
+    constexpr int kSplit = R8 / RPC;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *ring = smem;
     constexpr int CPG = 1, kSlots = kRingData / kStageBytes;   // the warps share every chunk: one per copy
@@ -37,7 +44,8 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
     uint64_t *empty = full + kSlots;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + kSlots + 1);
     float *xs_smem = reinterpret_cast<float *>(smem + kRingBytes);
-    const int b = blockIdx.x;
+    const int b = blockIdx.x / kSplit;
+    const int rhs0 = RPC * (blockIdx.x % kSplit);
     const int64_t r0 = lv.blk_r0[b];
     const int nr = lv.blk_nr[b];
     if (nr == 0) return;
@@ -61,8 +69,8 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
     float *mine = work + r0 * R8;
     float *xs = SMEM ? xs_smem : (MODE == 1 ? scratch + lv.blk_f0[b] * R8 : mine);
     const int64_t f0 = lv.blk_f0[b];
-    for (int idx = ct; idx < nr * R8; idx += NC) {
-        const int i = idx / R8, r = idx % R8;
+    for (int idx = ct; idx < nr * RPC; idx += NC) {
+        const int i = idx / RPC, r = rhs0 + idx % RPC;
         if (MODE == 1) {
             float acc = 0.f;
             for (int64_t p = lv.F_rp[f0 + i]; p < lv.F_rp[f0 + i + 1]; ++p) acc += lv.F_v[p] * work[(int64_t)lv.F_ci[p] * R8 + r];
@@ -70,12 +78,12 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
         } else if (in) {
             xs[idx] = (float)in[(r0 + i) * R8 + r];
         } else if (SMEM) {
-            xs[idx] = mine[idx];
+            xs[idx] = mine[i * R8 + r];
         }
     }
     consumer_barrier();
     bool aborted = false;
-    const int rr = lane >> 3, r = lane & 7;
+    const int rr = lane / RPC, r = lane % RPC;
     const unsigned char *base = nullptr;
     for (int c = c0; c < c1; ++c) {
         const int k = c - c0;
@@ -101,13 +109,13 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
                 float a0 = 0.f, a1 = 0.f;
                 int q = 0;
                 for (; q + 1 < len; q += 2) {
-                    a0 += vals[q * nrow + t] * xs[cols[q * nrow + t] * R8 + r];
-                    a1 += vals[(q + 1) * nrow + t] * xs[cols[(q + 1) * nrow + t] * R8 + r];
+                    a0 += vals[q * nrow + t] * xs[cols[q * nrow + t] * RPC + r];
+                    a1 += vals[(q + 1) * nrow + t] * xs[cols[(q + 1) * nrow + t] * RPC + r];
                 }
-                if (q < len) a0 += vals[q * nrow + t] * xs[cols[q * nrow + t] * R8 + r];
-                float y = xs[row * R8 + r] - (a0 + a1);
+                if (q < len) a0 += vals[q * nrow + t] * xs[cols[q * nrow + t] * RPC + r];
+                float y = xs[row * RPC + r] - (a0 + a1);
                 if (upper) y *= dinv[t];
-                xs[row * R8 + r] = y;
+                xs[row * RPC + r] = y;
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[chunk_slot<CPG>(k)]);
@@ -119,11 +127,12 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
         if (ct == 0) atomicExch(lv.err, 1);
         return;
     }
-    for (int idx = ct; idx < nr * R8; idx += NC) {
+    for (int idx = ct; idx < nr * RPC; idx += NC) {
+        const int64_t g = (int64_t)(idx / RPC) * R8 + rhs0 + idx % RPC;
         float y = xs[idx];
-        if (MODE == 1) y = mine[idx] - y;
-        if (SMEM || MODE == 1) mine[idx] = y;
-        if (out_final) out_final[r0 * R8 + idx] = (double)y;
+        if (MODE == 1) y = mine[g] - y;
+        if (SMEM || MODE == 1) mine[g] = y;
+        if (out_final) out_final[r0 * R8 + g] = (double)y;
     }
 }
 
@@ -600,23 +609,44 @@ __global__ void k_bscatter(int64_t nrows, const int32_t *__restrict__ sys_of, co
 }
 
 // ---- launchers ----------------------------------------------------------------------------
-void launch_btrsv(const BatchLevel &lv, int mode, bool smem, size_t smem_bytes, const double *in, float *work,
+template <int MODE, int RPC>
+static void launch_btrsv_smem(const BatchLevel &lv, size_t smem_bytes, const double *in, float *work,
+                              double *out_final, float *scratch, cudaStream_t st) {
+    k_btrsv<MODE, true, RPC><<<lv.nblk * (R8 / RPC), kTrsvThreads2, smem_bytes, st>>>(lv, in, work, out_final, scratch);
+}
+template <int MODE>
+static void launch_btrsv_mode(const BatchLevel &lv, int rpc, size_t smem_bytes, const double *in, float *work,
+                              double *out_final, float *scratch, cudaStream_t st) {
+    switch (rpc) {
+        case 8: launch_btrsv_smem<MODE, 8>(lv, smem_bytes, in, work, out_final, scratch, st); break;
+        case 4: launch_btrsv_smem<MODE, 4>(lv, smem_bytes, in, work, out_final, scratch, st); break;
+        case 2: launch_btrsv_smem<MODE, 2>(lv, smem_bytes, in, work, out_final, scratch, st); break;
+        case 1: launch_btrsv_smem<MODE, 1>(lv, smem_bytes, in, work, out_final, scratch, st); break;
+        default:
+            k_btrsv<MODE, false, R8><<<lv.nblk, kTrsvThreads2, kRingBytes, st>>>(lv, in, work, out_final, scratch);
+    }
+}
+// rpc: right-hand sides per CTA (8, 4, 2, 1: vector in shared memory of
+// kRingBytes + rows * rpc * 4 bytes), 0: vector in global memory
+void launch_btrsv(const BatchLevel &lv, int mode, int rpc, size_t smem_bytes, const double *in, float *work,
                   double *out_final, float *scratch, cudaStream_t st) {
     if (lv.nblk == 0) return;
-    if (mode == 0) {
-        if (smem) k_btrsv<0, true><<<lv.nblk, kTrsvThreads2, smem_bytes, st>>>(lv, in, work, out_final, scratch);
-        else k_btrsv<0, false><<<lv.nblk, kTrsvThreads2, kRingBytes, st>>>(lv, in, work, out_final, scratch);
-    } else {
-        if (smem) k_btrsv<1, true><<<lv.nblk, kTrsvThreads2, smem_bytes, st>>>(lv, in, work, out_final, scratch);
-        else k_btrsv<1, false><<<lv.nblk, kTrsvThreads2, kRingBytes, st>>>(lv, in, work, out_final, scratch);
-    }
+    if (mode == 0) launch_btrsv_mode<0>(lv, rpc, smem_bytes, in, work, out_final, scratch, st);
+    else launch_btrsv_mode<1>(lv, rpc, smem_bytes, in, work, out_final, scratch, st);
     count_launch();
 }
+template <int RPC>
+static void set_btrsv_attr(int bytes) {
+    cudaFuncSetAttribute(k_btrsv<0, true, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_btrsv<1, true, RPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
 void set_btrsv_smem_limit(int bytes) {
-    cudaFuncSetAttribute(k_btrsv<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_btrsv<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    cudaFuncSetAttribute(k_btrsv<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
-    cudaFuncSetAttribute(k_btrsv<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
+    set_btrsv_attr<8>(bytes);
+    set_btrsv_attr<4>(bytes);
+    set_btrsv_attr<2>(bytes);
+    set_btrsv_attr<1>(bytes);
+    cudaFuncSetAttribute(k_btrsv<0, false, R8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
+    cudaFuncSetAttribute(k_btrsv<1, false, R8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
 }
 void launch_bcouple(const BatchLevel &lv, const double *in, float *work, cudaStream_t st) {
     if (lv.ncta == 0) return;

@@ -110,3 +110,31 @@ def test_batch_zero_rhs_and_single_system_iterations(torch_cuda, batch):
     Gm = Gemslr(A, part, precision="mixed", **OPTS)
     x, inf1 = Gm.solve(torch.from_numpy(b).cuda(), restart=20, rtol=1e-8)
     assert abs(inf1[0]["iters"] - info[1 * nrhs + 0]["iters"]) <= 2
+
+
+def test_batch_splits_right_hand_sides_of_large_blocks(torch_cuda):
+    """Blocks whose vector for 8 right-hand sides does not fit in shared
+    memory are handled by several CTAs with fewer right-hand sides each; the
+    result must still equal the single-system mixed application, for every
+    right-hand side (each CTA of a block covers its own share)."""
+    torch = torch_cuda
+    from paper_2205_03224_gb300 import Gemslr, GemslrBatch, partition_geometric
+    sy = []
+    for dims, beta in [((30, 30, 28), 0.2), ((9, 8, 7), 0.1), ((24, 24, 24), 0.3)]:
+        A, xyz = gi.grid_operator(dims, beta=beta)
+        sy.append((A, partition_geometric(A, xyz, 3, 2)))
+    B = GemslrBatch([a for a, _ in sy], [p for _, p in sy], **OPTS)
+    assert B.stats()["rhs_per_cta"] in (1, 2, 4)
+    nrhs = 8
+    R = _stack(sy, nrhs, 17)
+    Z = B.apply(torch.from_numpy(R).cuda(), nrhs).cpu().numpy()
+    off = 0
+    for A, part in sy:
+        n = A.n
+        Gm = Gemslr(A, part, precision="mixed", **OPTS)
+        for r in range(nrhs):
+            rv = R[off + r * n: off + (r + 1) * n]
+            z = Z[off + r * n: off + (r + 1) * n]
+            zm = Gm.apply(torch.from_numpy(rv).cuda()).cpu().numpy()
+            assert np.linalg.norm(z - zm) <= 1e-4 * np.linalg.norm(zm), (n, r)
+        off += n * nrhs
