@@ -189,8 +189,8 @@ gemslr_status gemslr_apply(gemslr_handle h, const double *r_dev, double *z_dev, 
  * solves) replaces the root level's y2 = M_S^{-1} z2 by `steps` steps of
  * right-preconditioned GMRES from y2 = 0 on S_hat_0 y2 = z2, where
  * S_hat_0 = C_0 - E_0 U_0^{-1} L_0^{-1} F_0 is the inexact Schur complement of
- * the root level (Sec. 4.1) and M_S^{-1} its preconditioner: the level-0
- * low-rank correction (Eq. 6) followed by the levels below.  The Arnoldi
+ * the root level (Sec. 2.4) and M_S^{-1} its preconditioner: the level-0
+ * low-rank correction (eq. gemslr6) followed by the levels below.  The Arnoldi
  * vectors use the application's precision with FP64 sums; a happy breakdown
  * (h_{j+1,j} <= 1e-14 ||S_hat_0 z_j||) ends the steps early.  M^{-1} becomes
  * nonlinear; FGMRES (flexible) then uses classical Gram-Schmidt with a second

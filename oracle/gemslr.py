@@ -123,21 +123,21 @@ class OracleGemslr:
         return np.concatenate([y1, y2])
 
     def precond_schur(self, z2, l):
-        """Eq. 6 at level l: C_l^-1 (z2 + W_l H_l W_l^T z2), C_l^-1 the levels below."""
+        """eq. gemslr6 at level l: C_l^-1 (z2 + W_l H_l W_l^T z2), C_l^-1 the levels below."""
         lv = self.levels[l]
         W, H = lv["W"], lv["H"]
         u2 = W @ (H @ (W.T @ z2)) if W.shape[1] else np.zeros_like(z2)
         return self.solve_level(u2 + z2, l + 1)
 
     def s_hat(self, v, l):
-        """Inexact Schur complement S_hat_l v = C_l v - E_l U_l^-1 L_l^-1 F_l v (Sec. 4.1)."""
+        """Inexact Schur complement S_hat_l v = C_l v - E_l U_l^-1 L_l^-1 F_l v (Sec. 2.4)."""
         lv = self.levels[l]
         C = self.Ahat[lv["e"]:, lv["e"]:]
         return C @ v - lv["E"] @ _ilu.lu_solve(lv["L"], lv["U"], lv["F"] @ v)
 
     def inner_gmres(self, z2, k, l=0):
         """Alg. 2 step 9: k steps of GMRES on S_hat_l y = z2 from y = 0, right
-        preconditioned by ``precond_schur`` (Eq. 6).  Arnoldi with modified
+        preconditioned by ``precond_schur`` (eq. gemslr6).  Arnoldi with modified
         Gram-Schmidt on the vectors v_j; y = sum_j c_j M_S^-1 v_j with c the
         minimiser of ||beta e_1 - H c|| over the (j+1) x j Hessenberg matrix.
         A happy breakdown (h_{j+1,j} <= 1e-14 ||S_hat M_S^-1 v_j||) ends the

@@ -1,9 +1,9 @@
 // Inner GMRES at the root level (Alg. 2 step 9).
 //
-// Instead of the single application y2 = M_S^-1 z2 (Eq. 6 and the levels
+// Instead of the single application y2 = M_S^-1 z2 (eq. gemslr6 and the levels
 // below), the root level solves S_hat_0 y2 = z2 by k steps of GMRES from
 // y2 = 0, right preconditioned by M_S^-1, with the inexact Schur complement
-// S_hat_0 = C_0 - E_0 U^-1 L^-1 F_0 of Sec. 4.1.  One product S_hat_0 z is one
+// S_hat_0 = C_0 - E_0 U^-1 L^-1 F_0 of Sec. 2.4.  One product S_hat_0 z is one
 // level-0 substitution and one pass over the tail rows of A_hat:
 //   t = [ -U^-1 L^-1 F_0 z ; z ]   (the level-0 up sweep on a zero level part)
 //   S_hat_0 z = (A_hat t)[e0:n]    (the rows of E_0 meet -U^-1 L^-1 F_0 z, the rows of C_0 meet z)

@@ -131,7 +131,7 @@ struct DgsBufs {
 
 // Inner GMRES at the root level (Alg. 2 step 9): up to kMaxInner steps of
 // right-preconditioned GMRES on S_hat_0 y2 = z2, S_hat_0 = C_0 - E_0 U^-1 L^-1 F_0
-// (Sec. 4.1), preconditioned by the level-0 correction and the levels below.
+// (Sec. 2.4), preconditioned by the level-0 correction and the levels below.
 constexpr int kMaxInner = 8;
 
 struct InnerCtl {

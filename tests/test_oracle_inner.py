@@ -1,9 +1,9 @@
 """Pins for the oracle's inner GMRES at level 0 (Alg. 2 step 9).
 
-At the root level the standard application y2 = M_S^-1 z2 (Eq. 6 followed by
+At the root level the standard application y2 = M_S^-1 z2 (eq. gemslr6 followed by
 the levels below) is replaced by k steps of GMRES on S_hat_0 y2 = z2, right
 preconditioned by M_S^-1, where S_hat_0 = C_0 - E_0 U^-1 L^-1 F_0 is the
-inexact Schur complement of Sec. 4.1.  The pins: the minimiser over the
+inexact Schur complement of Sec. 2.4.  The pins: the minimiser over the
 Krylov space formed densely from a monomial basis (brute force), the exact
 inverse of A when the factors are exact and k reaches the size of the Schur
 system (GMRES terminates), and the monotone residual of GMRES in k.
