@@ -987,6 +987,57 @@ __device__ __forceinline__ void rotate_column_warp(const double *cs, const doubl
     __syncwarp();
 }
 
+// w[i] = (A z)_i and zj[i] = z[i] for the rows [i0, i1) of the CTA, two rows
+// per thread and iteration: the row extents, then the first eight entries'
+// columns and values, then the z values of both rows are each loaded together,
+// so a thread waits for three memory round trips per pair of rows.  Entries
+// past the eighth of a row (none for 7-point stencils) follow one by one.
+__device__ __forceinline__ void spmv_rows_pair(int64_t i0, int64_t i1, const int64_t *__restrict__ rp,
+                                               const int32_t *__restrict__ ci, const double *__restrict__ av,
+                                               const double *__restrict__ z, double *__restrict__ w,
+                                               double *__restrict__ zj) {
+    const int64_t st = blockDim.x;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += 2 * st) {
+        const int64_t ib = i + st;
+        const bool hb = ib < i1;
+        const int64_t pa0 = rp[i], pa1 = rp[i + 1];
+        const int64_t pb0 = hb ? rp[ib] : pa0, pb1 = hb ? rp[ib + 1] : pa0;
+        int ca[8], cb[8];
+        double va[8], vb[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            // absent entries read entry 0 of the matrix (always valid) with weight 0
+            const int64_t qa = pa0 + q < pa1 ? pa0 + q : 0, qb = pb0 + q < pb1 ? pb0 + q : 0;
+            ca[q] = ci[qa];
+            cb[q] = ci[qb];
+            va[q] = pa0 + q < pa1 ? av[qa] : 0.0;
+            vb[q] = pb0 + q < pb1 ? av[qb] : 0.0;
+        }
+        double za[8], zb[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            za[q] = z[ca[q]];
+            zb[q] = z[cb[q]];
+        }
+        double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+            a0 = fma(va[q], za[q], a0);
+            a1 = fma(va[q + 1], za[q + 1], a1);
+            b0 = fma(vb[q], zb[q], b0);
+            b1 = fma(vb[q + 1], zb[q + 1], b1);
+        }
+        for (int64_t p = pa0 + 8; p < pa1; ++p) a0 = fma(av[p], z[ci[p]], a0);
+        w[i] = a0 + a1;
+        zj[i] = z[i];
+        if (hb) {
+            for (int64_t p = pb0 + 8; p < pb1; ++p) b0 = fma(av[p], z[ci[p]], b0);
+            w[ib] = b0 + b1;
+            zj[ib] = z[ib];
+        }
+    }
+}
+
 // Step j: w = A z (z also stored in column j of Zt), then the reduction over
 // V_{j-1} with vt and w; the finisher (warp 0) finalises column j-1, stores
 // column j of R, forms the first-pass column h1 of step j, its lagged norm and
@@ -1001,31 +1052,7 @@ k_dgs_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restric
     const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
     const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
     double *zj = zcol + (int64_t)j * len;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        const int64_t p0 = rp[i], p1 = rp[i + 1];
-        double a0 = 0.0, a1 = 0.0;
-        if (p1 > p0) {
-            int cc[8];
-            double vv[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int64_t pq = p0 + q < p1 ? p0 + q : p0;
-                cc[q] = ci[pq];
-                vv[q] = p0 + q < p1 ? av[pq] : 0.0;
-            }
-            double zz[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) zz[q] = z[cc[q]];
-#pragma unroll
-            for (int q = 0; q < 8; q += 2) {
-                a0 = fma(vv[q], zz[q], a0);
-                a1 = fma(vv[q + 1], zz[q + 1], a1);
-            }
-            for (int64_t p = p0 + 8; p < p1; ++p) a0 = fma(av[p], z[ci[p]], a0);
-        }
-        w[i] = a0 + a1;
-        zj[i] = z[i];
-    }
+    spmv_rows_pair(i0, i1, rp, ci, av, z, w, zj);
     block_dots2(V, ldv, j, vt, w, i0, i1, partial);
     if (!finish_block(counter)) return;
     __shared__ double red[2 * kMaxCols + 3];
@@ -1074,21 +1101,39 @@ k_dgs_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restric
         B.R[j + (int64_t)j * m1] = nu;
     }
     __syncthreads();
-    // g = Hraw[0..j, 0..j-1] a (row r per thread; columns before j-1 are
-    // final since earlier steps, column j-1 is in hcol), then the first-pass
-    // column h1 = (V_j^T w - g) / nu and the next direction's coefficients
-    // V_j^T w
-    for (int r = t; r <= j; r += blockDim.x) {
-        double g0 = 0.0, g1 = 0.0;
-        int c = r > 0 ? r - 1 : 0;
-        for (; c + 1 < j - 1; c += 2) {
-            g0 = fma(B.Hraw[(int64_t)c * m1 + r], a[c], g0);
-            g1 = fma(B.Hraw[(int64_t)(c + 1) * m1 + r], a[c + 1], g1);
+    // g = Hraw[0..j, 0..j-1] a: columns before j-1 are final since earlier
+    // steps (row r has entries in columns >= r-1), column j-1 is in hcol.  Warp
+    // w takes rows w, w + nw, ... four at a time, its lanes the columns, so the
+    // Hraw loads are issued together instead of one dependent chain per row;
+    // the row sums go to h1s, which the loop below overwrites row by row
+    {
+        const int nw = blockDim.x >> 5;
+        for (int rb = warp; rb <= j; rb += 4 * nw) {
+            double acc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = rb + u * nw;
+                acc[u] = 0.0;
+                if (r <= j)
+                    for (int c = (r > 0 ? r - 1 : 0) + lane; c < j - 1; c += 32)
+                        acc[u] = fma(B.Hraw[(int64_t)c * m1 + r], a[c], acc[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = warp_sum(acc[u]);
+            if (lane == 0)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (rb + u * nw <= j) h1s[rb + u * nw] = acc[u];
         }
-        if (c < j - 1) g0 = fma(B.Hraw[(int64_t)c * m1 + r], a[c], g0);
-        if (j > 0 && r <= j) g0 = fma(hcol[r], a[j - 1], g0);
+    }
+    __syncthreads();
+    // the first-pass column h1 = (V_j^T w - g) / nu and the next direction's
+    // coefficients V_j^T w
+    for (int r = t; r <= j; r += blockDim.x) {
+        double g0 = h1s[r];
+        if (j > 0) g0 = fma(hcol[r], a[j - 1], g0);
         const double vr = r < j ? b[r] : vjw;
-        const double h1 = (vr - (g0 + g1)) * inv_nu;
+        const double h1 = (vr - g0) * inv_nu;
         h1s[r] = h1;
         B.hprev[r] = h1;
         B.coef[r] = vr;

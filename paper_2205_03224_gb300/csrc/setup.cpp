@@ -21,6 +21,7 @@ Csr csr_from_abi(const gemslr_csr *A) {
     M.rp.assign(A->rowptr, A->rowptr + A->n + 1);
     int64_t nnz = M.rp[A->n];
     if (M.rp[0] != 0 || nnz < 0) fail(GEMSLR_ERR_ARG, "CSR row pointer must start at 0");
+    if (A->n > 0 && nnz == 0) fail(GEMSLR_ERR_ARG, "CSR matrix without entries");
     for (int64_t i = 0; i < A->n; ++i)
         if (M.rp[i + 1] < M.rp[i]) fail(GEMSLR_ERR_ARG, "CSR row pointer not monotone");
     M.ci.assign(A->colind, A->colind + nnz);
