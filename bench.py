@@ -59,9 +59,7 @@ NCU_TRAFFIC = {    # profiles/trsv_c2_apply_<precision>.md
     ("c2", "fp64", "trsv_up_L0"): 76_690_944 + 829_952,
 }
 NCU_TRAFFIC_KRYLOV = {    # profiles/krylov_c2_mixed.md, step j = 25
-    ("c2", "mixed", "dgs_spmv_dots"): (80_603_648 + 2_561_536, None),
     ("c2", "mixed", "dgs_next"): (56_632_576 + 128_512, None),
-    ("c2", "mixed", "dgs_fix"): (52_450_560 + 25_088, None),
 }
 NCU_KRYLOV_STEP = 25
 
@@ -195,21 +193,20 @@ def krylov_work(n, nnzA, its, m, j=None):
     delayed reorthogonalisation, summed over the steps of a solve of `its`
     iterations with restart m (step j of a cycle has j finished basis
     vectors), or for the single step j.
-      dgs_spmv_dots: w = A z (z also stored), V^T vt and V^T w over j columns,
-                     vt.vt, vt.w, w.w;
-      dgs_next:      the next direction from w, vt and j columns of V;
-      dgs_fix:       the previous step's reorthogonalised column from j - 1
-                     columns (runs beside M^{-1})."""
+      dgs_fix_adots: the previous step's reorthogonalised column (j - 1
+                     columns) and V^T vt, vt.vt over j columns (beside M^-1);
+      dgs_spmv_dots: w = A z (z also stored), V^T w over j columns, w.w, vt.w;
+      dgs_next:      the next direction from w, vt and j columns of V."""
     steps = [j] if j is not None else [i % m for i in range(its)]
-    out = {"dgs_spmv_dots": [0.0, 0.0], "dgs_next": [0.0, 0.0], "dgs_fix": [0.0, 0.0]}
+    out = {"dgs_fix_adots": [0.0, 0.0], "dgs_spmv_dots": [0.0, 0.0], "dgs_next": [0.0, 0.0]}
     for jj in steps:
-        out["dgs_spmv_dots"][0] += 2.0 * (2 * jj * n + 3 * n + nnzA)
-        out["dgs_spmv_dots"][1] += jj * n * 8 + nnzA * 12 + (n + 1) * 8 + 4 * n * 8
+        jp = max(jj - 1, 0)
+        out["dgs_fix_adots"][0] += 2.0 * (jp * n + jj * n + n)
+        out["dgs_fix_adots"][1] += (jp + jj) * n * 8 + 3 * n * 8
+        out["dgs_spmv_dots"][0] += 2.0 * (jj * n + 2 * n + nnzA)
+        out["dgs_spmv_dots"][1] += jj * n * 8 + nnzA * 12 + (n + 1) * 8 + 5 * n * 8
         out["dgs_next"][0] += 2.0 * (jj * n + n)
         out["dgs_next"][1] += jj * n * 8 + 4 * n * 8
-        jp = max(jj - 1, 0)
-        out["dgs_fix"][0] += 2.0 * (jp * n)
-        out["dgs_fix"][1] += jp * n * 8 + 2 * n * 8
     return out
 
 

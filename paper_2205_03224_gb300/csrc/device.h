@@ -78,6 +78,10 @@ void launch_dgs_next(int64_t len, double *V, int64_t ldv, double *vt, const doub
 // exclusive: CTAs that never share an SM with a substitution CTA
 void launch_dgs_fix(int64_t len, double *V, int64_t ldv, const KrylovCtl *ctl, const DgsBufs &B, int off, int grid,
                     bool exclusive, cudaStream_t st);
+// the previous step's reorthogonalisation and V^T vt, vt . vt of the current
+// direction (partials: `grid` x (kMaxCols + 2)), beside M^{-1}
+void launch_dgs_fix_adots(int64_t len, double *V, int64_t ldv, const double *vt, double *partial, unsigned *counter,
+                          KrylovCtl *ctl, const DgsBufs &B, int grid, cudaStream_t st);
 // kernel attributes of the Krylov kernels (call before any capture)
 void prepare_krylov_kernels();
 void launch_dgs_close(int64_t len, const double *V, int64_t ldv, const double *vt, double *partial, unsigned *counter,

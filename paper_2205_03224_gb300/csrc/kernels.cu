@@ -812,106 +812,16 @@ __global__ void k_gs_scale(int64_t len, double *__restrict__ V, int64_t ldv, con
 }
 
 // ---- FGMRES with delayed reorthogonalisation ------------------------------------------
-// One reduction per step.  The Krylov direction of step j, vt, is the first
-// Gram-Schmidt pass of the previous product normalised by a Pythagorean
-// estimate; the step's single reduction over V_{j-1} yields both its second
-// pass (a = V^T vt, nu = ||vt - V a||) and, by linearity of M^{-1}, every
-// coefficient of the new product w = A M^{-1} vt against the final basis.  The
-// stored preconditioned vectors Zt = M^{-1} vt relate to those of the final
-// basis by an upper triangular R (Zt = Z R), so x = Zt R^{-1} y.  Column j-1
-// of the Hessenberg matrix is final at step j; the step's stopping test uses
-// column j rotated provisionally.
-
-// Dots of the NC columns V[:, c0..) with vt (acc[0..NC)) and w (acc[NC..2NC)),
-// and when FIRST vt.vt, vt.w, w.w in acc[2NC..2NC+3); two rows per iteration,
-// every load before any arithmetic.
-template <int NC, bool FIRST>
-__device__ __forceinline__ void dots2_group(const double *__restrict__ V, int64_t ldv, int c0, const double *vt,
-                                            const double *w, int64_t i0, int64_t i1, double *acc) {
-    const double *vc[NC > 0 ? NC : 1];
-#pragma unroll
-    for (int u = 0; u < NC; ++u) vc[u] = V + (int64_t)(c0 + u) * ldv;
-    const int64_t st = blockDim.x;
-    int64_t i = i0 + threadIdx.x;
-    for (; i + st < i1; i += 2 * st) {
-        const double ta = __ldcg(vt + i), tb = __ldcg(vt + i + st);
-        const double wa = __ldcg(w + i), wb = __ldcg(w + i + st);
-        double va[NC > 0 ? NC : 1], vb[NC > 0 ? NC : 1];
-#pragma unroll
-        for (int u = 0; u < NC; ++u) {
-            va[u] = vc[u][i];
-            vb[u] = vc[u][i + st];
-        }
-#pragma unroll
-        for (int u = 0; u < NC; ++u) {
-            acc[u] = fma(vb[u], tb, fma(va[u], ta, acc[u]));
-            acc[NC + u] = fma(vb[u], wb, fma(va[u], wa, acc[NC + u]));
-        }
-        if (FIRST) {
-            acc[2 * NC] = fma(tb, tb, fma(ta, ta, acc[2 * NC]));
-            acc[2 * NC + 1] = fma(tb, wb, fma(ta, wa, acc[2 * NC + 1]));
-            acc[2 * NC + 2] = fma(wb, wb, fma(wa, wa, acc[2 * NC + 2]));
-        }
-    }
-    if (i < i1) {
-        const double ta = __ldcg(vt + i), wa = __ldcg(w + i);
-#pragma unroll
-        for (int u = 0; u < NC; ++u) {
-            const double v = vc[u][i];
-            acc[u] = fma(v, ta, acc[u]);
-            acc[NC + u] = fma(v, wa, acc[NC + u]);
-        }
-        if (FIRST) {
-            acc[2 * NC] = fma(ta, ta, acc[2 * NC]);
-            acc[2 * NC + 1] = fma(ta, wa, acc[2 * NC + 1]);
-            acc[2 * NC + 2] = fma(wa, wa, acc[2 * NC + 2]);
-        }
-    }
-}
-
-// Block partials of V[:, c].vt (slot c), V[:, c].w (slot nc + c) for c < nc,
-// vt.vt, vt.w, w.w (slots 2nc .. 2nc+2), written column-major like block_dots.
-__device__ void block_dots2(const double *__restrict__ V, int64_t ldv, int nc, const double *vt, const double *w,
-                            int64_t i0, int64_t i1, double *partial) {
-    __shared__ double tred[19][kReduceThreads];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int c0 = 0;
-    bool first = true;
-    while (first || c0 < nc) {
-        const int rem = nc - c0;
-        const int g = rem >= 8 ? 8 : rem >= 4 ? 4 : rem >= 2 ? 2 : rem;
-        double acc[19];
-#pragma unroll
-        for (int u = 0; u < 19; ++u) acc[u] = 0.0;
-        switch (g + (first ? 16 : 0)) {
-            case 8: dots2_group<8, false>(V, ldv, c0, vt, w, i0, i1, acc); break;
-            case 4: dots2_group<4, false>(V, ldv, c0, vt, w, i0, i1, acc); break;
-            case 2: dots2_group<2, false>(V, ldv, c0, vt, w, i0, i1, acc); break;
-            case 1: dots2_group<1, false>(V, ldv, c0, vt, w, i0, i1, acc); break;
-            case 24: dots2_group<8, true>(V, ldv, c0, vt, w, i0, i1, acc); break;
-            case 20: dots2_group<4, true>(V, ldv, c0, vt, w, i0, i1, acc); break;
-            case 18: dots2_group<2, true>(V, ldv, c0, vt, w, i0, i1, acc); break;
-            case 17: dots2_group<1, true>(V, ldv, c0, vt, w, i0, i1, acc); break;
-            default: dots2_group<0, true>(V, ldv, c0, vt, w, i0, i1, acc); break;
-        }
-        const int ns = 2 * g + (first ? 3 : 0);
-#pragma unroll
-        for (int u = 0; u < 19; ++u)
-            if (u < ns) tred[u][threadIdx.x] = acc[u];
-        __syncthreads();
-        for (int sl = warp; sl < ns; sl += kReduceThreads / 32) {
-            double sum = tred[sl][lane];
-#pragma unroll
-            for (int q = 1; q < kReduceThreads / 32; ++q) sum += tred[sl][q * 32 + lane];
-            sum = warp_sum(sum);
-            const int col = sl < g ? c0 + sl : sl < 2 * g ? nc + c0 + (sl - g) : 2 * nc + (sl - 2 * g);
-            if (lane == 0) partial[(int64_t)col * gridDim.x + blockIdx.x] = sum;
-        }
-        __syncthreads();
-        c0 += g;
-        first = false;
-    }
-}
+// One reduction after each product.  The Krylov direction of step j, vt, is
+// the first Gram-Schmidt pass of the previous product normalised by a
+// Pythagorean estimate; its second pass (a = V^T vt, nu = ||vt - V a||) needs
+// no product and is reduced beside M^{-1} (k_dgs_fix_adots, which also
+// finalises the previous basis vector), and the reduction after the product
+// gives, by linearity of M^{-1}, every coefficient of w = A M^{-1} vt against
+// the final basis.  The stored preconditioned vectors Zt = M^{-1} vt relate to
+// those of the final basis by an upper triangular R (Zt = Z R), so
+// x = Zt R^{-1} y.  Column j-1 of the Hessenberg matrix is final at step j;
+// the step's stopping test uses column j rotated provisionally.
 
 // Final Givens step on column jc of Hrot (already rotated by 0..jc-1):
 // rotation jc, g, residual estimate.  One reciprocal square root instead of
@@ -992,11 +902,13 @@ __device__ __forceinline__ void rotate_column_warp(const double *cs, const doubl
 // columns and values, then the z values of both rows are each loaded together,
 // so a thread waits for three memory round trips per pair of rows.  Entries
 // past the eighth of a row (none for 7-point stencils) follow one by one.
-__device__ __forceinline__ void spmv_rows_pair(int64_t i0, int64_t i1, const int64_t *__restrict__ rp,
-                                               const int32_t *__restrict__ ci, const double *__restrict__ av,
-                                               const double *__restrict__ z, double *__restrict__ w,
-                                               double *__restrict__ zj) {
+// Returns the thread's share of w . vt.
+__device__ __forceinline__ double spmv_rows_pair(int64_t i0, int64_t i1, const int64_t *__restrict__ rp,
+                                                 const int32_t *__restrict__ ci, const double *__restrict__ av,
+                                                 const double *__restrict__ z, double *__restrict__ w,
+                                                 double *__restrict__ zj, const double *__restrict__ vt) {
     const int64_t st = blockDim.x;
+    double dv = 0.0;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += 2 * st) {
         const int64_t ib = i + st;
         const bool hb = ib < i1;
@@ -1028,20 +940,27 @@ __device__ __forceinline__ void spmv_rows_pair(int64_t i0, int64_t i1, const int
             b1 = fma(vb[q + 1], zb[q + 1], b1);
         }
         for (int64_t p = pa0 + 8; p < pa1; ++p) a0 = fma(av[p], z[ci[p]], a0);
-        w[i] = a0 + a1;
+        const double wa = a0 + a1;
+        w[i] = wa;
         zj[i] = z[i];
+        dv = fma(wa, vt[i], dv);
         if (hb) {
             for (int64_t p = pb0 + 8; p < pb1; ++p) b0 = fma(av[p], z[ci[p]], b0);
-            w[ib] = b0 + b1;
+            const double wb = b0 + b1;
+            w[ib] = wb;
             zj[ib] = z[ib];
+            dv = fma(wb, vt[ib], dv);
         }
     }
+    return dv;
 }
 
-// Step j: w = A z (z also stored in column j of Zt), then the reduction over
-// V_{j-1} with vt and w; the finisher (warp 0) finalises column j-1, stores
-// column j of R, forms the first-pass column h1 of step j, its lagged norm and
-// the coefficients of the next direction, and decides whether the cycle ends.
+// Step j: w = A z (z also stored in column j of Zt), then the reduction of
+// V_{j-1}^T w, w . w and vt . w (V_{j-1}^T vt and vt . vt come from
+// k_dgs_fix_adots, which ran beside M^{-1}); the finisher finalises column
+// j-1, stores column j of R, forms the first-pass column h1 of step j, its
+// lagged norm and the coefficients of the next direction, and decides whether
+// the cycle ends.
 __global__ void __launch_bounds__(kReduceThreads)
 k_dgs_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci,
            const double *__restrict__ av, const double *__restrict__ z, double *__restrict__ zcol,
@@ -1052,19 +971,25 @@ k_dgs_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restric
     const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
     const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
     double *zj = zcol + (int64_t)j * len;
-    spmv_rows_pair(i0, i1, rp, ci, av, z, w, zj);
-    block_dots2(V, ldv, j, vt, w, i0, i1, partial);
+    // w = A z with vt . w; V_{j-1}^T w and w . w (V_{j-1}^T vt and vt . vt were
+    // formed beside M^{-1} by k_dgs_fix_adots): partial slots 0..j-1 V^T w,
+    // j w . w, j+1 vt . w
+    const double dv = block_sum(spmv_rows_pair(i0, i1, rp, ci, av, z, w, zj, vt));
+    if (threadIdx.x == 0) partial[(int64_t)(j + 1) * gridDim.x + blockIdx.x] = dv;
+    block_dots(V, ldv, j, w, i0, i1, partial);
     if (!finish_block(counter)) return;
     __shared__ double red[2 * kMaxCols + 3];
-    reduce_partials(partial, 2 * j + 3, red);
+    double *ash = red + kMaxCols + 2;
+    for (int c = threadIdx.x; c < j; c += blockDim.x) ash[c] = __ldcg(B.apre + c);
+    reduce_partials(partial, j + 2, red);
     // finisher, all threads: rotations, the previous first-pass column and the
     // columns being finalised live in shared memory for the serial parts
     __shared__ double s_cs[kMaxCols], s_sn[kMaxCols], s_g[kMaxCols + 1];
     __shared__ double hcol[kMaxCols + 1], h1s[kMaxCols + 2], sc[4];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int m1 = ctl->m + 1;
-    const double *a = red, *b = red + j;
-    const double gam = red[2 * j], dlt = red[2 * j + 1], om = red[2 * j + 2];
+    const double *a = ash, *b = red;
+    const double gam = ctl->gam_pre, om = red[j], dlt = red[j + 1];
     const double bprev = ctl->btil;
     for (int c = t; c <= j; c += blockDim.x) {
         s_cs[c] = B.cs[c];
@@ -1243,6 +1168,46 @@ k_dgs_next(int64_t len, double *__restrict__ V, int64_t ldv, double *vt, const d
         const double t = __ldcg(vt + i);
         vj[i] = t;
         if (next) vt[i] = fma(-t, cj, w[i] - x) * inv_nb;
+    }
+}
+
+// Beside z = M^{-1} vt_j (second stream, SMs the substitutions leave free):
+// the previous step's reorthogonalisation v_{j-1} = (vt_{j-1} - V_{j-2} a) / nu
+// (as k_dgs_fix), then a = V_{j-1}^T vt_j and vt_j . vt_j, which do not need
+// M^{-1}: into B.apre and ctl->gam_pre.  The fixed column's dot is formed from
+// the value just computed (register), the other columns by block_dots.
+// Partial slots: 0..j-2 V_{j-2}^T vt, j-1 vt . vt (j = 0: slot 0), j v_{j-1} . vt.
+__global__ void __launch_bounds__(kReduceThreads)
+k_dgs_fix_adots(int64_t len, double *V, int64_t ldv, const double *vt, double *partial, unsigned *counter,
+                KrylovCtl *ctl, DgsBufs B) {
+    __shared__ double as[kMaxCols];
+    const int j = ctl->j, jp = j - 1;
+    const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = min((int64_t)blockIdx.x * chunk, len), i1 = min(i0 + chunk, len);
+    double dv = 0.0;
+    if (jp >= 0) {
+        for (int c = threadIdx.x; c < jp; c += blockDim.x) as[c] = __ldcg(B.a + c);
+        __syncthreads();
+        const double inv_nu = 1.0 / ctl->nu;
+        double *vj = V + (int64_t)jp * ldv;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const double v = (vj[i] - combine_row(V, ldv, jp, as, i)) * inv_nu;
+            vj[i] = v;
+            dv = fma(v, vt[i], dv);
+        }
+    }
+    dv = block_sum(dv);
+    if (jp >= 0 && threadIdx.x == 0) partial[(int64_t)j * gridDim.x + blockIdx.x] = dv;
+    const int nc = jp > 0 ? jp : 0;
+    block_dots(V, ldv, nc, vt, i0, i1, partial);
+    if (!finish_block(counter)) return;
+    __shared__ double red[kMaxCols + 2];
+    reduce_partials(partial, jp >= 0 ? j + 1 : 1, red);
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) B.apre[c] = red[c];
+    if (threadIdx.x == 0) {
+        if (jp >= 0) B.apre[jp] = red[j];
+        ctl->gam_pre = red[nc];
+        *counter = 0u;
     }
 }
 
@@ -1634,8 +1599,16 @@ void launch_dgs_fix(int64_t len, double *V, int64_t ldv, const KrylovCtl *ctl, c
     k_dgs_fix<<<grid, 256, exclusive ? kFixExclusiveSmem : 0, st>>>(len, V, ldv, ctl, B, off);
     count_launch();
 }
+void launch_dgs_fix_adots(int64_t len, double *V, int64_t ldv, const double *vt, double *partial, unsigned *counter,
+                          KrylovCtl *ctl, const DgsBufs &B, int grid, cudaStream_t st) {
+    // exclusive: see launch_dgs_fix
+    k_dgs_fix_adots<<<grid, kReduceThreads, kFixExclusiveSmem, st>>>(len, V, ldv, vt, partial, counter, ctl, B);
+    count_launch();
+}
 void prepare_krylov_kernels() {
     GEMSLR_CUDA(cudaFuncSetAttribute(k_dgs_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, kFixExclusiveSmem));
+    GEMSLR_CUDA(cudaFuncSetAttribute(k_dgs_fix_adots, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kFixExclusiveSmem));
 }
 void launch_dgs_close(int64_t len, const double *V, int64_t ldv, const double *vt, double *partial, unsigned *counter,
                       KrylovCtl *ctl, const DgsBufs &B, int grid, cudaStream_t st) {

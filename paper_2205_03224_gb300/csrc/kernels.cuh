@@ -112,6 +112,7 @@ struct KrylovCtl {
     double rnorm;         // ||b - A x|| after the last cycle
     double nu;            // delayed CGS2: norm of the reorthogonalised direction of this step
     double btil;          // delayed CGS2: lagged norm of the next direction
+    double gam_pre;       // delayed CGS2: vt.vt of the current direction (formed beside M^{-1})
 };
 
 // Device buffers of FGMRES with delayed reorthogonalisation (one reduction
@@ -125,6 +126,7 @@ struct DgsBufs {
     double *cs, *sn, *g;   // rotations and rotated right-hand side
     double *R;             // (m+1) x (m+1), column-major, upper triangular
     double *a;             // kMaxCols: V^T (direction) of this step
+    double *apre;          // kMaxCols: the same, formed beside M^{-1} (k_dgs_fix_adots)
     double *coef;          // kMaxCols: projection coefficients of the next direction
     double *hprev;         // kMaxCols: first-pass column of the previous step
 };

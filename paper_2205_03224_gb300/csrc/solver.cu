@@ -40,7 +40,9 @@ struct gemslr_ctx {
     double *V = nullptr, *Z = nullptr, *w = nullptr, *xh = nullptr, *bh = nullptr, *r = nullptr;
     double *Hs = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *y = nullptr, *h2 = nullptr;
     // delayed reorthogonalisation (linear M^{-1}): unrotated H, R, per-step vectors
-    double *Hraw = nullptr, *Rz = nullptr, *da = nullptr, *dcoef = nullptr, *dhprev = nullptr;
+    double *Hraw = nullptr, *Rz = nullptr, *da = nullptr, *dcoef = nullptr, *dhprev = nullptr, *dapre = nullptr;
+    double *partial2 = nullptr;          // partials of the kernel beside M^{-1}
+    unsigned *counter2 = nullptr;
     double *partial = nullptr, *n2 = nullptr;
     unsigned *counter = nullptr;
     KrylovCtl *ctl = nullptr;
@@ -113,6 +115,10 @@ void ensure_krylov(gemslr_ctx *h, int m) {
         h->da = (double *)h->arena.alloc(8 * kMaxCols);
         h->dcoef = (double *)h->arena.alloc(8 * kMaxCols);
         h->dhprev = (double *)h->arena.alloc(8 * kMaxCols);
+        h->dapre = (double *)h->arena.alloc(8 * kMaxCols);
+        h->partial2 = (double *)h->arena.alloc(8 * (size_t)h->red_grid * (kMaxCols + 2));
+        h->counter2 = (unsigned *)h->arena.alloc(16);
+        GEMSLR_CUDA(cudaMemset(h->counter2, 0, 16));
         h->vin = (double *)h->arena.alloc(8 * n);
         h->zout = (double *)h->arena.alloc(8 * n);
         prepare_krylov_kernels();
@@ -378,6 +384,7 @@ DgsBufs dgs_bufs(gemslr_ctx *h) {
     B.R = h->Rz;
     B.a = h->da;
     B.coef = h->dcoef;
+    B.apre = h->dapre;
     B.hprev = h->dhprev;
     return B;
 }
@@ -400,8 +407,8 @@ void fgmres_step_d(gemslr_ctx *h, cudaStream_t st) {
     GEMSLR_CUDA(cudaEventRecord(h->ev_fork, st));
     GEMSLR_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_fork, 0));
     {
-        ProfScope ps("dgs_fix", h->aux_stream);
-        launch_dgs_fix(n, h->V, n, h->ctl, B, -1, fix_grid, true, h->aux_stream);
+        ProfScope ps("dgs_fix_adots", h->aux_stream);
+        launch_dgs_fix_adots(n, h->V, n, h->vin, h->partial2, h->counter2, h->ctl, B, fix_grid, h->aux_stream);
     }
     GEMSLR_CUDA(cudaEventRecord(h->ev_join, h->aux_stream));
     apply_perm(h, h->vin, h->zout, st);
