@@ -82,6 +82,8 @@ void launch_dgs_fix(int64_t len, double *V, int64_t ldv, const KrylovCtl *ctl, c
 // direction (partials: `grid` x (kMaxCols + 2)), beside M^{-1}
 void launch_dgs_fix_adots(int64_t len, double *V, int64_t ldv, const double *vt, double *partial, unsigned *counter,
                           KrylovCtl *ctl, const DgsBufs &B, int grid, cudaStream_t st);
+// the Hessenberg column, rotations and stopping test of the step (one CTA)
+void launch_dgs_tail(KrylovCtl *ctl, const DgsBufs &B, cudaStream_t st);
 // kernel attributes of the Krylov kernels (call before any capture)
 void prepare_krylov_kernels();
 void launch_dgs_close(int64_t len, const double *V, int64_t ldv, const double *vt, double *partial, unsigned *counter,

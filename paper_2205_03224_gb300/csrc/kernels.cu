@@ -982,20 +982,13 @@ k_dgs_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restric
     double *ash = red + kMaxCols + 2;
     for (int c = threadIdx.x; c < j; c += blockDim.x) ash[c] = __ldcg(B.apre + c);
     reduce_partials(partial, j + 2, red);
-    // finisher, all threads: rotations, the previous first-pass column and the
-    // columns being finalised live in shared memory for the serial parts
-    __shared__ double s_cs[kMaxCols], s_sn[kMaxCols], s_g[kMaxCols + 1];
-    __shared__ double hcol[kMaxCols + 1], h1s[kMaxCols + 2], sc[4];
+    // finisher: only what the next-direction sweep needs (a, V_j^T w, nu,
+    // the lagged norm btil, the breakdown test); the Hessenberg column,
+    // rotations and stopping test run beside that sweep (k_dgs_tail)
+    __shared__ double sc[4];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int m1 = ctl->m + 1;
     const double *a = ash, *b = red;
     const double gam = ctl->gam_pre, om = red[j], dlt = red[j + 1];
-    const double bprev = ctl->btil;
-    for (int c = t; c <= j; c += blockDim.x) {
-        s_cs[c] = B.cs[c];
-        s_sn[c] = B.sn[c];
-        s_g[c] = B.g[c];
-    }
     if (warp == 0) {
         double aa = 0.0, ab = 0.0;
         for (int c = lane; c < j; c += 32) {
@@ -1008,17 +1001,61 @@ k_dgs_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restric
             sc[0] = sqrt(fmax(gam - aa, 0.0));
             sc[1] = ab;
         }
+    } else if (warp == 1) {
+        double vv = 0.0;
+        for (int c = lane; c < j; c += 32) vv = fma(b[c], b[c], vv);
+        vv = warp_sum(vv);
+        if (lane == 0) sc[2] = vv;
     }
     __syncthreads();
     const double nu = sc[0], inv_nu = 1.0 / nu;
     const double vjw = (dlt - sc[1]) * inv_nu;   // v_j . w
-    // column j-1, now final: rows 0..j-1 from the previous first pass, row j
     for (int c = t; c < j; c += blockDim.x) {
-        const double hv = B.hprev[c] + bprev * a[c];
-        hcol[c] = hv;
-        B.Hraw[(int64_t)(j - 1) * m1 + c] = hv;
         B.a[c] = a[c];
-        B.R[c + (int64_t)j * m1] = a[c];
+        B.coef[c] = b[c];
+    }
+    if (t != 0) return;
+    B.coef[j] = vjw;
+    const double rest = om - fma(vjw, vjw, sc[2]);  // ||w - V_j V_j^T w||^2 (Pythagoras)
+    const double bt = rest > 0.0 ? sqrt(rest) * inv_nu : 0.0;
+    const double w2 = om * inv_nu * inv_nu;
+    ctl->btil_prev = ctl->btil;
+    ctl->nu = nu;
+    ctl->btil = bt;
+    ctl->wnorm2 = w2;
+    ctl->breakdown = bt <= 1e-14 * sqrt(fabs(w2)) ? 1 : 0;
+    *counter = 0u;
+}
+
+// The rest of step j's finisher, one CTA of two warps on the second stream
+// beside k_dgs_next: column j-1 of the Hessenberg matrix is now final (rows
+// 0..j-1 from the previous first pass plus the lagged correction, row j =
+// btil_prev nu), and so is column j of R; the first-pass column of step j is
+// h1 = (V_j^T w - Hraw[0..j, 0..j-1] a) / nu; rotations 0..j-2 act on both
+// columns (one warp each), rotation j-1 closes column j-1, and the provisional
+// rotation of column j gives the residual estimate that decides whether the
+// cycle ends.  Nothing here is read by k_dgs_next.
+__global__ void __launch_bounds__(64) k_dgs_tail(KrylovCtl *ctl, DgsBufs B) {
+    __shared__ double s_cs[kMaxCols], s_sn[kMaxCols], s_g[kMaxCols + 1];
+    __shared__ double hcol[kMaxCols + 1], h1s[kMaxCols + 2], s_a[kMaxCols], s_cf[kMaxCols + 1];
+    if (ctl->stop) return;                          // no step ran (see k_dgs_dots)
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nw = blockDim.x >> 5;
+    const int j = ctl->j;
+    const int m1 = ctl->m + 1;
+    const double nu = ctl->nu, inv_nu = 1.0 / nu, bprev = ctl->btil_prev, bt = ctl->btil;
+    for (int c = t; c <= j; c += blockDim.x) {
+        s_cs[c] = B.cs[c];
+        s_sn[c] = B.sn[c];
+        s_g[c] = B.g[c];
+        s_cf[c] = __ldcg(B.coef + c);
+        if (c < j) {
+            const double ac = __ldcg(B.a + c);
+            s_a[c] = ac;
+            const double hv = B.hprev[c] + bprev * ac;
+            hcol[c] = hv;
+            B.Hraw[(int64_t)(j - 1) * m1 + c] = hv;
+            B.R[c + (int64_t)j * m1] = ac;
+        }
     }
     if (t == 0) {
         hcol[j] = bprev * nu;
@@ -1029,58 +1066,40 @@ k_dgs_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restric
     // g = Hraw[0..j, 0..j-1] a: columns before j-1 are final since earlier
     // steps (row r has entries in columns >= r-1), column j-1 is in hcol.  Warp
     // w takes rows w, w + nw, ... four at a time, its lanes the columns, so the
-    // Hraw loads are issued together instead of one dependent chain per row;
-    // the row sums go to h1s, which the loop below overwrites row by row
-    {
-        const int nw = blockDim.x >> 5;
-        for (int rb = warp; rb <= j; rb += 4 * nw) {
-            double acc[4];
+    // Hraw loads are issued together; the row sums go to h1s, which the loop
+    // below overwrites row by row
+    for (int rb = warp; rb <= j; rb += 4 * nw) {
+        double acc[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int r = rb + u * nw;
-                acc[u] = 0.0;
-                if (r <= j)
-                    for (int c = (r > 0 ? r - 1 : 0) + lane; c < j - 1; c += 32)
-                        acc[u] = fma(B.Hraw[(int64_t)c * m1 + r], a[c], acc[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u] = warp_sum(acc[u]);
-            if (lane == 0)
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (rb + u * nw <= j) h1s[rb + u * nw] = acc[u];
+        for (int u = 0; u < 4; ++u) {
+            const int r = rb + u * nw;
+            acc[u] = 0.0;
+            if (r <= j)
+                for (int c = (r > 0 ? r - 1 : 0) + lane; c < j - 1; c += 32)
+                    acc[u] = fma(B.Hraw[(int64_t)c * m1 + r], s_a[c], acc[u]);
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = warp_sum(acc[u]);
+        if (lane == 0)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (rb + u * nw <= j) h1s[rb + u * nw] = acc[u];
     }
     __syncthreads();
-    // the first-pass column h1 = (V_j^T w - g) / nu and the next direction's
-    // coefficients V_j^T w
+    // the first-pass column h1 = (V_j^T w - g) / nu
     for (int r = t; r <= j; r += blockDim.x) {
         double g0 = h1s[r];
-        if (j > 0) g0 = fma(hcol[r], a[j - 1], g0);
-        const double vr = r < j ? b[r] : vjw;
-        const double h1 = (vr - g0) * inv_nu;
+        if (j > 0) g0 = fma(hcol[r], s_a[j - 1], g0);
+        const double h1 = (s_cf[r] - g0) * inv_nu;
         h1s[r] = h1;
         B.hprev[r] = h1;
-        B.coef[r] = vr;
-    }
-    if (warp == 0) {
-        double vv = 0.0;
-        for (int r = lane; r < j; r += 32) vv = fma(b[r], b[r], vv);
-        vv = warp_sum(vv);
-        if (lane == 0) sc[2] = vv + vjw * vjw;
     }
     __syncthreads();
-    const double rest = om - sc[2];                 // ||w - V_j V_j^T w||^2 (Pythagoras)
-    const double bt = rest > 0.0 ? sqrt(rest) * inv_nu : 0.0;
     // rotations 0..j-2 on column j-1 (warp 0) and on column j (warp 1)
     if (warp == 0) rotate_column_warp(s_cs, s_sn, j - 1, hcol);
     else if (warp == 1) rotate_column_warp(s_cs, s_sn, j - 1, h1s);
     __syncthreads();
     if (t != 0) return;
-    const double w2 = om * inv_nu * inv_nu;
-    ctl->nu = nu;
-    ctl->btil = bt;
-    ctl->wnorm2 = w2;
     h1s[j + 1] = bt;
     if (j > 0) {
         givens_close(hcol, j - 1, s_cs, s_sn, s_g);
@@ -1100,9 +1119,7 @@ k_dgs_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restric
     ctl->iters += 1;
     const bool bad = !isfinite(prelim) || !isfinite(nu) || !isfinite(bt);
     if (bad) ctl->nonfinite = 1;
-    ctl->breakdown = bt <= 1e-14 * sqrt(fabs(w2)) ? 1 : 0;
     if (prelim <= ctl->tol_abs || ctl->breakdown || bad || ctl->iters >= ctl->maxit || j + 1 >= ctl->m) ctl->stop = 1;
-    *counter = 0u;
 }
 
 // Sum over the first nc columns of V at row i of V[i, c] * h[c] (h in shared
@@ -1603,6 +1620,10 @@ void launch_dgs_fix_adots(int64_t len, double *V, int64_t ldv, const double *vt,
                           KrylovCtl *ctl, const DgsBufs &B, int grid, cudaStream_t st) {
     // exclusive: see launch_dgs_fix
     k_dgs_fix_adots<<<grid, kReduceThreads, kFixExclusiveSmem, st>>>(len, V, ldv, vt, partial, counter, ctl, B);
+    count_launch();
+}
+void launch_dgs_tail(KrylovCtl *ctl, const DgsBufs &B, cudaStream_t st) {
+    k_dgs_tail<<<1, 64, 0, st>>>(ctl, B);
     count_launch();
 }
 void prepare_krylov_kernels() {

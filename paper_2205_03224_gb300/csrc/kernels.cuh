@@ -112,6 +112,7 @@ struct KrylovCtl {
     double rnorm;         // ||b - A x|| after the last cycle
     double nu;            // delayed CGS2: norm of the reorthogonalised direction of this step
     double btil;          // delayed CGS2: lagged norm of the next direction
+    double btil_prev;     // delayed CGS2: btil of the step before (row j of column j-1)
     double gam_pre;       // delayed CGS2: vt.vt of the current direction (formed beside M^{-1})
 };
 

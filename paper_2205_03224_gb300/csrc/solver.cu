@@ -54,7 +54,7 @@ struct gemslr_ctx {
     double setup_ms = 0.0;
     // second stream of the delayed reorthogonalisation (k_dgs_fix beside M^{-1})
     cudaStream_t aux_stream = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
     // CUDA graph of a whole FGMRES solve (conditional WHILE nodes for the cycle and step loops)
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
@@ -72,6 +72,8 @@ struct gemslr_ctx {
         if (aux_stream) cudaStreamDestroy(aux_stream);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
+        if (ev_fork2) cudaEventDestroy(ev_fork2);
+        if (ev_join2) cudaEventDestroy(ev_join2);
         if (ctl_host) cudaFreeHost(ctl_host);
         if (n2_host) cudaFreeHost(n2_host);
         if (err_host) cudaFreeHost(err_host);
@@ -398,6 +400,8 @@ void fgmres_step_d(gemslr_ctx *h, cudaStream_t st) {
         GEMSLR_CUDA(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
         GEMSLR_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
         GEMSLR_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+        GEMSLR_CUDA(cudaEventCreateWithFlags(&h->ev_fork2, cudaEventDisableTiming));
+        GEMSLR_CUDA(cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming));
     }
     // the previous step's reorthogonalisation runs beside z = M^{-1} vt_j on
     // the SMs the level-0 substitutions leave free (one CTA per SM, none
@@ -418,10 +422,19 @@ void fgmres_step_d(gemslr_ctx *h, cudaStream_t st) {
         launch_dgs_dots(n, h->A_rp, h->A_ci, h->A_v, h->zout, h->Z, h->V, n, h->vin, h->w, h->partial, h->counter,
                         h->ctl, B, h->red_grid, st);
     }
+    // the Hessenberg bookkeeping and the stopping test beside the next direction
+    GEMSLR_CUDA(cudaEventRecord(h->ev_fork2, st));
+    GEMSLR_CUDA(cudaStreamWaitEvent(h->aux_stream, h->ev_fork2, 0));
+    {
+        ProfScope ps("dgs_tail", h->aux_stream);
+        launch_dgs_tail(h->ctl, B, h->aux_stream);
+    }
+    GEMSLR_CUDA(cudaEventRecord(h->ev_join2, h->aux_stream));
     {
         ProfScope ps("dgs_next", st);
         launch_dgs_next(n, h->V, n, h->vin, h->w, h->ctl, B, st);
     }
+    GEMSLR_CUDA(cudaStreamWaitEvent(st, h->ev_join2, 0));
 }
 
 // End of a delayed cycle: close the last column, y = Hrot^{-1} g, y = R^{-1} y,
