@@ -1027,15 +1027,16 @@ k_dgs_dots(int64_t len, const int64_t *__restrict__ rp, const int32_t *__restric
     *counter = 0u;
 }
 
-// The rest of step j's finisher, one CTA of two warps on the second stream
-// beside k_dgs_next: column j-1 of the Hessenberg matrix is now final (rows
+// The rest of step j's finisher, one CTA of four warps on the second stream
+// beside k_dgs_next (four warps of 64 registers fit beside seven CTAs of the
+// sweep on one SM): column j-1 of the Hessenberg matrix is now final (rows
 // 0..j-1 from the previous first pass plus the lagged correction, row j =
 // btil_prev nu), and so is column j of R; the first-pass column of step j is
 // h1 = (V_j^T w - Hraw[0..j, 0..j-1] a) / nu; rotations 0..j-2 act on both
 // columns (one warp each), rotation j-1 closes column j-1, and the provisional
 // rotation of column j gives the residual estimate that decides whether the
 // cycle ends.  Nothing here is read by k_dgs_next.
-__global__ void __launch_bounds__(64) k_dgs_tail(KrylovCtl *ctl, DgsBufs B) {
+__global__ void __launch_bounds__(128) k_dgs_tail(KrylovCtl *ctl, DgsBufs B) {
     __shared__ double s_cs[kMaxCols], s_sn[kMaxCols], s_g[kMaxCols + 1];
     __shared__ double hcol[kMaxCols + 1], h1s[kMaxCols + 2], s_a[kMaxCols], s_cf[kMaxCols + 1];
     if (ctl->stop) return;                          // no step ran (see k_dgs_dots)
@@ -1623,7 +1624,7 @@ void launch_dgs_fix_adots(int64_t len, double *V, int64_t ldv, const double *vt,
     count_launch();
 }
 void launch_dgs_tail(KrylovCtl *ctl, const DgsBufs &B, cudaStream_t st) {
-    k_dgs_tail<<<1, 64, 0, st>>>(ctl, B);
+    k_dgs_tail<<<1, 128, 0, st>>>(ctl, B);
     count_launch();
 }
 void prepare_krylov_kernels() {
