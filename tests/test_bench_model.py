@@ -1,0 +1,46 @@
+"""Host logic of bench.py's roofline: the work models of the Krylov kernels
+(closed forms over the steps of a solve) and the choice of the roofline kernel."""
+import importlib.util
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_krylov_work_closed_forms():
+    b = _bench()
+    n, nnz, m = 1000, 7000, 50
+    for its in (1, 17, 50, 73, 120):
+        kw = b.krylov_work(n, nnz, its, m)
+        steps = [i % m for i in range(its)]
+        sj = sum(steps)
+        sjp = sum(max(j - 1, 0) for j in steps)
+        assert kw["dgs_next"][0] == 2.0 * (n * sj + its * n)
+        assert kw["dgs_spmv_dots"][0] == 2.0 * (n * sj + 2 * n * its + nnz * its)
+        assert kw["dgs_fix_adots"][0] == 2.0 * (n * sjp + n * sj + n * its)
+        assert kw["dgs_next"][1] == 8 * n * sj + 32 * n * its
+    one = b.krylov_work(n, nnz, 0, m, j=25)
+    assert one["dgs_next"][0] == 2.0 * (25 * n + n)
+
+
+def test_roofline_picks_the_largest_modelled_kernel():
+    b = _bench()
+    n, nnz = 262144, 1810432
+    kw = {k: tuple(v) for k, v in b.krylov_work(n, nnz, 42, 50).items()}
+    kw["_step"] = {k: tuple(v) for k, v in b.krylov_work(n, nnz, 42, 50, j=25).items()}
+    prof = {"dgs_spmv_dots": (3.0, 42), "trsv_up_L0": (3.2, 42), "unmodelled": (9.0, 1), "dgs_next": (1.0, 42)}
+    ab = {"trsv_up_L0": 44_000_000}
+    rl = b.rooflines(prof, ab, kw, 6800.0, {"hbm_gbs": 6800.0}, "mixed")
+    assert [r["kernel"] for r in rl] == ["trsv_up_L0", "dgs_spmv_dots", "dgs_next"]
+    assert rl[0]["bound"] == "hbm" and rl[1]["bound"] == "alu"
+    t = rl[0]
+    assert abs(t["achieved"] - 44e6 / (3.2 / 42 * 1e-3) / 1e9) < 1e-9 and abs(t["frac"] - t["achieved"] / 6800.0) < 1e-12
+    k = rl[1]
+    assert abs(k["achieved"] - kw["dgs_spmv_dots"][0] / 3.0e-3 / 1e9) < 1e-6
+    assert k["peak"] == b.FP64_PEAK_GFLOPS
