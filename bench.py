@@ -91,7 +91,7 @@ class Clocks:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -296,7 +296,6 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         x, info = G.solve(b_dev, restart=c["restart"], rtol=c["rtol"])
-    its = info[0]["iters"]
     clocks = Clocks(local)
     clocks.start()
     barrier()
@@ -314,6 +313,7 @@ def run_ours(args):
         ms.append(e0.elapsed_time(e1))
     torch.cuda.nvtx.range_pop()
     barrier()
+    its = info[0]["iters"]
     launches = _lib.kernel_launches() - l0
     clk = clocks.stop()
     total_ms = sum(ms)
@@ -572,7 +572,7 @@ def run_learned(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
