@@ -59,9 +59,9 @@ NCU_TRAFFIC = {    # profiles/trsv_c2_apply_<precision>.md
     ("c2", "fp64", "trsv_up_L0"): 76_690_944 + 829_952,
 }
 NCU_TRAFFIC_KRYLOV = {    # profiles/krylov_c2_mixed.md, step j = 25
-    ("c2", "mixed", "dgs_fix_adots"): (54_605_568 + 86_784, None),
-    ("c2", "mixed", "dgs_spmv_dots"): (80_551_936 + 2_378_496, None),
-    ("c2", "mixed", "dgs_next"): (56_632_832 + 157_952, None),
+    ("c2", "mixed", "dgs_fix_adots"): (54_605_056 + 78_592, None),
+    ("c2", "mixed", "dgs_spmv_dots"): (80_561_152 + 2_375_936, None),
+    ("c2", "mixed", "dgs_next"): (56_632_832 + 146_944, None),
 }
 NCU_KRYLOV_STEP = 25
 
