@@ -11,6 +11,11 @@ namespace gemslr {
 namespace {
 constexpr int R8 = kBatchRhs;
 
+// Named barrier 1 over the consumer warps of the batched substitutions.
+__device__ __forceinline__ void batch_consumer_barrier() {
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * kBatchWarps) : "memory");
+}
+
 __device__ __forceinline__ bool last_of(unsigned *counter, unsigned n) {
     __shared__ int last;
     __threadfence();
@@ -32,7 +37,7 @@ __device__ __forceinline__ bool last_of(unsigned *counter, unsigned n) {
 // then work[rows] -= result.  Without SMEM (blocks too large even for RPC = 1)
 // RPC is kBatchRhs and the vector stays in global memory.
 template <int MODE, bool SMEM, int RPC>
-__global__ void __launch_bounds__(kTrsvThreads2)
+__global__ void __launch_bounds__(kBatchTrsvThreads)
 k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ work, double *__restrict__ out_final,
         float *__restrict__ scratch) {
     static_assert(SMEM || RPC == R8, "the global-memory path keeps all right-hand sides");
@@ -54,18 +59,18 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kSlots; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CPG * kConsumerWarps);
+            mbar_init(&empty[s], CPG * kBatchWarps);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (warp == kConsumerWarps) {
+    if (warp == kBatchWarps) {
         produce_chunks<CPG>(lv.C.data, lv.C.off, c0, c1, ring, full, empty, abort_flag, lv.err, lane);
         return;
     }
     const int ct = threadIdx.x;
-    constexpr int NC = 32 * kConsumerWarps;
+    constexpr int NC = 32 * kBatchWarps;
     float *mine = work + r0 * R8;
     float *xs = SMEM ? xs_smem : (MODE == 1 ? scratch + lv.blk_f0[b] * R8 : mine);
     const int64_t f0 = lv.blk_f0[b];
@@ -81,7 +86,7 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
             xs[idx] = mine[i * R8 + r];
         }
     }
-    consumer_barrier();
+    batch_consumer_barrier();
     bool aborted = false;
     const int rr = lane / RPC, r = lane % RPC;
     const unsigned char *base = nullptr;
@@ -102,7 +107,7 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
             const int ne = S * nrow;
             const float *vals = reinterpret_cast<const float *>(cols + ((ne + 3) & ~3));
             const float *dinv = vals + ((ne + 3) & ~3);
-            const int per = (nrow + kConsumerWarps - 1) / kConsumerWarps;   // <= 4 rows per warp
+            const int per = (nrow + kBatchWarps - 1) / kBatchWarps;   // <= 4 rows per warp
             const int t = warp * per + rr;
             if (rr < per && t < nrow) {
                 const int row = rows[t], len = lens[t];
@@ -120,9 +125,9 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[chunk_slot<CPG>(k)]);
         }
-        consumer_barrier();
+        batch_consumer_barrier();
     }
-    consumer_barrier();
+    batch_consumer_barrier();
     if (*abort_flag) {
         if (ct == 0) atomicExch(lv.err, 1);
         return;
@@ -612,7 +617,8 @@ __global__ void k_bscatter(int64_t nrows, const int32_t *__restrict__ sys_of, co
 template <int MODE, int RPC>
 static void launch_btrsv_smem(const BatchLevel &lv, size_t smem_bytes, const double *in, float *work,
                               double *out_final, float *scratch, cudaStream_t st) {
-    k_btrsv<MODE, true, RPC><<<lv.nblk * (R8 / RPC), kTrsvThreads2, smem_bytes, st>>>(lv, in, work, out_final, scratch);
+    k_btrsv<MODE, true, RPC><<<lv.nblk * (R8 / RPC), kBatchTrsvThreads, smem_bytes, st>>>(lv, in, work, out_final,
+                                                                                         scratch);
 }
 template <int MODE>
 static void launch_btrsv_mode(const BatchLevel &lv, int rpc, size_t smem_bytes, const double *in, float *work,
@@ -623,7 +629,7 @@ static void launch_btrsv_mode(const BatchLevel &lv, int rpc, size_t smem_bytes, 
         case 2: launch_btrsv_smem<MODE, 2>(lv, smem_bytes, in, work, out_final, scratch, st); break;
         case 1: launch_btrsv_smem<MODE, 1>(lv, smem_bytes, in, work, out_final, scratch, st); break;
         default:
-            k_btrsv<MODE, false, R8><<<lv.nblk, kTrsvThreads2, kRingBytes, st>>>(lv, in, work, out_final, scratch);
+            k_btrsv<MODE, false, R8><<<lv.nblk, kBatchTrsvThreads, kRingBytes, st>>>(lv, in, work, out_final, scratch);
     }
 }
 // rpc: right-hand sides per CTA (8, 4, 2, 1: vector in shared memory of
