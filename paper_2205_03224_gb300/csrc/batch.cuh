@@ -12,7 +12,7 @@
 namespace gemslr {
 
 constexpr int kBatchRhs = 8;
-constexpr int kBatchWarps = 8;                 // consumer warps of the batched substitutions
+constexpr int kBatchWarps = 16;                // consumer warps of the batched substitutions
 constexpr int kBatchChunkRows = 4 * kBatchWarps; // 4 rows per warp, 8 lanes (one per rhs) each
 constexpr int kBatchTrsvThreads = 32 * (kBatchWarps + 1);
 constexpr int kBatchMaxRank = 64;              // k_eff per system in the batched correction
