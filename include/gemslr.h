@@ -227,6 +227,11 @@ typedef struct {
  * Solve A x = b by restarted right-preconditioned FGMRES(m) with x_0 = 0 and
  * M^{-1} from the handle.  b_dev, x_dev: n x nrhs column-major device arrays in
  * the original ordering; info: nrhs entries (host).  Synchronises `stream`.
+ * With delayed reorthogonalisation the handle also runs work on a second,
+ * internal stream of its own (created on first use), forked from and joined
+ * back into `stream` within every step, so that the next direction's
+ * reorthogonalisation overlaps the application of M^{-1}; the call returns
+ * with both idle.  Calls on one handle must not overlap.
  * Returns NOT_CONVERGED (with info filled) when maxit is reached, NAN when b
  * or the iteration is not finite.
  */
