@@ -195,6 +195,21 @@ def algorithmic_bytes(fac, n, nnzA, sv=8, si=4, sw=8):
     return out
 
 
+def replica_throughput(total_ms, steps, ws, device):
+    """Whole-job throughput of ws independent replicas (one per GPU, the path
+    has no data exchange): every rank timed `steps` solves in total_ms; the
+    job's time is the maximum over ranks, and value = ws * steps / that time.
+    Returns (value, max total_ms).  Needs an initialised process group when
+    ws > 1 (NCCL on GPUs; the host logic is tested with gloo)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as tdist
+        t = torch.tensor([total_ms], device=device, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return ws * steps / (total_ms / 1e3), total_ms
+
+
 def krylov_work(n, nnzA, its, m, j=None):
     """FP64 flops and algorithmic bytes of the kernels of an FGMRES step with
     delayed reorthogonalisation, summed over the steps of a solve of `its`
@@ -321,12 +336,7 @@ def run_ours(args):
     its = info[0]["iters"]
     launches = _lib.kernel_launches() - l0
     clk = clocks.stop()
-    total_ms = sum(ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * args.steps / (total_ms / 1e3)
+    value, total_ms = replica_throughput(sum(ms), args.steps, ws, "cuda")
     x_np = x.cpu().numpy()
     res = float(np.linalg.norm(b - A.to_scipy() @ x_np) / np.linalg.norm(b))
 
