@@ -90,6 +90,17 @@ typedef struct {
     double arnoldi_tol;           /* Ritz accuracy for the low-rank term (1e-2)     */
     int32_t arnoldi_max_cycles;   /* thick-restart cycles (20)                      */
     int32_t strict_pivots;        /* nonzero: a clamped pivot fails the setup      */
+    /* Device allocator for everything a handle keeps on the GPU (factors,
+     * Krylov workspace, graphs' buffers): dev_alloc(bytes, alloc_ctx) returns a
+     * device pointer aligned to at least 256 bytes, or NULL on failure (the call
+     * then fails with NOMEM); dev_free(ptr, alloc_ctx) releases it when the
+     * handle is destroyed, after the device has finished all the handle's
+     * work.  Both NULL (the default): cudaMalloc / cudaFree.
+     * Setting only one of them is an ARG error.  The callbacks run on the
+     * calling thread, inside the library's calls. */
+    void *(*dev_alloc)(size_t bytes, void *alloc_ctx);
+    void (*dev_free)(void *ptr, void *alloc_ctx);
+    void *alloc_ctx;
 } gemslr_options;
 
 /* Fill *opt with the defaults: ILUT(1e-3, 10), rank 0, FP64, 1e-2, 20 cycles. */
@@ -174,6 +185,20 @@ gemslr_status gemslr_factor_sizes(gemslr_handle h, int64_t *counts, int64_t ncou
  * library writes into them.
  */
 gemslr_status gemslr_export_factors(gemslr_handle h, gemslr_factors *f);
+
+/*
+ * Factor files (checkpoint / resume of the set-up, Alg. 1): gemslr_save_factors
+ * writes every factor of the handle (per Schur level L, U, E, F, k, W, H; the
+ * last level's L and U) to `path` in a little-endian binary layout;
+ * gemslr_load_factors reads such a file and builds a handle like
+ * gemslr_setup_from_factors for the same A and partition (nothing is
+ * factored).  Errors: ARG (NULL argument, the file cannot be opened, written
+ * or read, is not a factor file, is corrupt, or belongs to another matrix size
+ * or partition), plus those of gemslr_setup_from_factors.
+ */
+gemslr_status gemslr_save_factors(gemslr_handle h, const char *path);
+gemslr_status gemslr_load_factors(const gemslr_csr *A, const gemslr_partition *part, const char *path,
+                                  const gemslr_options *opt, gemslr_handle *out);
 
 /*
  * z = M^{-1} r (Alg. 2) for nrhs right-hand sides in the ORIGINAL ordering:

@@ -26,10 +26,14 @@ class Partition(ctypes.Structure):
     _fields_ = [("nlev", i32), ("perm", P), ("level_ptr", P), ("nblk", P), ("block_ptr", P)]
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class Options(ctypes.Structure):
     _fields_ = [("ilu_kind", i32), ("ilut_tau", f64), ("ilut_lfil", i32), ("rank", i32 * MAX_LEVELS),
                 ("precision", i32), ("arnoldi_tol", f64), ("arnoldi_max_cycles", i32),
-                ("strict_pivots", i32)]
+                ("strict_pivots", i32), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", P)]
 
 
 class Mat(ctypes.Structure):
@@ -70,6 +74,7 @@ EXPORTED = [
     "gemslr_batch_last_error", "gemslr_batch_destroy",
     "gemslr_learned_train", "gemslr_learned_enable", "gemslr_learned_info", "gemslr_learned_params",
     "gemslr_learned_loss_grad", "gemslr_apply_static", "gemslr_selftest_wait", "gemslr_set_inner_steps",
+    "gemslr_save_factors", "gemslr_load_factors",
 ]
 
 _lib = None
@@ -122,6 +127,8 @@ def load():
     L.gemslr_learned_train.argtypes = [P, P, ctypes.POINTER(LearnedOpts), P]
     L.gemslr_learned_enable.argtypes = [P, i32]
     L.gemslr_set_inner_steps.argtypes = [P, i32]
+    L.gemslr_save_factors.argtypes = [P, ctypes.c_char_p]
+    L.gemslr_load_factors.argtypes = [P, P, ctypes.c_char_p, P, P]
     L.gemslr_learned_info.argtypes = [P, P]
     L.gemslr_learned_params.argtypes = [P, i32, P, i64]
     L.gemslr_learned_loss_grad.argtypes = [P, i32, P, P, P, P]

@@ -1,5 +1,6 @@
 """Python front end of the C ABI (argument marshalling only)."""
 import ctypes
+import os
 
 import numpy as np
 
@@ -27,8 +28,31 @@ def partition_geometric(A, coords, nlev, p, p_last=None):
     return dict(perm=perm, level_ptr=level_ptr, nblk=nblk, block_ptr=block_ptr)
 
 
+def torch_allocator():
+    """(dev_alloc, dev_free) callbacks that take device memory from PyTorch's
+    caching allocator on the current device and stream.  Keep the returned
+    objects alive as long as the handle that uses them."""
+    import torch
+
+    def _alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      torch.cuda.current_stream())
+        except Exception:
+            return None
+
+    def _free(ptr, ctx):
+        try:
+            torch.cuda.caching_allocator_delete(ptr)
+        except Exception:
+            pass
+
+    return L.ALLOC_FN(_alloc), L.FREE_FN(_free)
+
+
 def options(ilu="ilut", tau=1e-3, lfil=10, rank=0, precision="fp64", arnoldi_tol=1e-2, max_cycles=20,
-            strict_pivots=False):
+            strict_pivots=False, allocator=None):
+    """gemslr_options; allocator: None (cudaMalloc) or a (dev_alloc, dev_free) pair of callbacks."""
     o = L.Options()
     L.load().gemslr_default_options(ctypes.byref(o))
     o.ilu_kind = {"ilu0": 0, "ilut": 1}[ilu]
@@ -41,23 +65,40 @@ def options(ilu="ilut", tau=1e-3, lfil=10, rank=0, precision="fp64", arnoldi_tol
     o.arnoldi_tol = arnoldi_tol
     o.arnoldi_max_cycles = max_cycles
     o.strict_pivots = 1 if strict_pivots else 0
+    if allocator is not None:
+        o.dev_alloc, o.dev_free = allocator
     return o
 
 
-class Gemslr:
-    """Handle of a GeMSLR preconditioner living on the current CUDA device."""
+def _resolve_allocator(opts):
+    """The allocator option: "torch" (default: PyTorch's caching allocator) or None (cudaMalloc)."""
+    a = opts.pop("allocator", "torch")
+    if a is None:
+        return None
+    if a == "torch":
+        return torch_allocator()
+    raise ValueError(f"unknown allocator {a!r}")
 
-    def __init__(self, A, part, _handle=None, **opts):
+
+class Gemslr:
+    """Handle of a GeMSLR preconditioner living on the current CUDA device.
+
+    Device memory comes from PyTorch's caching allocator unless allocator=None
+    (then the library calls cudaMalloc itself)."""
+
+    def __init__(self, A, part, _handle=None, _alloc=None, **opts):
         self._lib = L.load()
         self.n = int(len(part["perm"]))
         self.nlev = int(len(part["nblk"]))
         if _handle is not None:
             self._h = _handle
+            self._alloc = _alloc
             return
         keep = []
         csr = L.csr_struct(A, keep)
         prt = L.partition_struct(part, keep)
-        o = options(**opts)
+        self._alloc = _resolve_allocator(opts)
+        o = options(allocator=self._alloc, **opts)
         h = ctypes.c_void_p()
         L.check(self._lib.gemslr_setup(ctypes.byref(csr), ctypes.byref(prt), ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -79,11 +120,30 @@ class Gemslr:
                                     L.mat_struct(f["E"], keep), L.mat_struct(f["F"], keep),
                                     W.shape[1], L.ptr(W) if W.size else None, L.ptr(H) if H.size else None)
         fs = L.Factors(len(lv) + 1, arr, L.mat_struct(fac["last"]["L"], keep), L.mat_struct(fac["last"]["U"], keep))
-        o = options(**opts)
+        alloc = _resolve_allocator(opts)
+        o = options(allocator=alloc, **opts)
         h = ctypes.c_void_p()
         L.check(lib.gemslr_setup_from_factors(ctypes.byref(csr), ctypes.byref(prt), ctypes.byref(fs),
                                               ctypes.byref(o), ctypes.byref(h)))
-        return cls(A, part, _handle=h)
+        return cls(A, part, _handle=h, _alloc=alloc)
+
+    def save_factors(self, path):
+        """Write every factor of the handle to `path` (checkpoint of the set-up)."""
+        L.check(self._lib.gemslr_save_factors(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load_factors(cls, A, part, path, **opts):
+        """Handle from a factor file written by save_factors (nothing is factored)."""
+        lib = L.load()
+        keep = []
+        csr = L.csr_struct(A, keep)
+        prt = L.partition_struct(part, keep)
+        alloc = _resolve_allocator(opts)
+        o = options(allocator=alloc, **opts)
+        h = ctypes.c_void_p()
+        L.check(lib.gemslr_load_factors(ctypes.byref(csr), ctypes.byref(prt), os.fsencode(path), ctypes.byref(o),
+                                        ctypes.byref(h)))
+        return cls(A, part, _handle=h, _alloc=alloc)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -232,7 +292,8 @@ class GemslrBatch:
         n = len(As)
         csrs = (L.CSR * n)(*[L.csr_struct(A, keep) for A in As])
         prts = (L.Partition * n)(*[L.partition_struct(p, keep) for p in parts])
-        o = options(**opts)
+        self._alloc = _resolve_allocator(opts)
+        o = options(allocator=self._alloc, **opts)
         h = ctypes.c_void_p()
         L.check(self._lib.gemslr_setup_batch(n, csrs, prts, ctypes.byref(o), ctypes.byref(h)), batch=True)
         self._h = h

@@ -434,6 +434,9 @@ gemslr_status gemslr_setup_batch(int32_t nsys, const gemslr_csr *A, const gemslr
         if (!out || nsys < 1 || !A || !part) fail(GEMSLR_ERR_ARG, "invalid batch arguments");
         auto t0 = std::chrono::steady_clock::now();
         std::unique_ptr<gemslr_batch_ctx> B(new gemslr_batch_ctx());
+        if (opt && (opt->dev_alloc == nullptr) != (opt->dev_free == nullptr))
+            fail(GEMSLR_ERR_ARG, "dev_alloc and dev_free must be given together");
+        if (opt) B->arena.set_allocator(opt->dev_alloc, opt->dev_free, opt->alloc_ctx);
         B->nsys = nsys;
         B->sys.resize(nsys);
         B->base.assign(1, 0);

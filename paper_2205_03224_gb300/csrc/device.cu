@@ -100,13 +100,26 @@ int profile_read(char *names, size_t len, double *ms, int64_t *counts, int maxn)
 uint64_t launches_total() { return g_launches.load(); }
 
 Arena::~Arena() {
-    for (void *p : ptrs_) cudaFree(p);
+    // cudaFree waits for the device; a caller's allocator may hand the memory
+    // out again at once, so the handle's work must be finished first
+    if (free_fn_ && !ptrs_.empty()) cudaDeviceSynchronize();
+    for (void *p : ptrs_) {
+        if (free_fn_) free_fn_(p, ctx_);
+        else cudaFree(p);
+    }
 }
 
 void *Arena::alloc(size_t bytes) {
     void *p = nullptr;
     const size_t b = bytes ? (bytes + 255) & ~size_t(255) : 256;
-    if (cudaMalloc(&p, b) != cudaSuccess) {
+    if (alloc_fn_) {
+        p = alloc_fn_(b, ctx_);
+        if (!p) fail(GEMSLR_ERR_NOMEM, "device allocation of " + std::to_string(b) + " bytes failed (caller's allocator)");
+        if (reinterpret_cast<uintptr_t>(p) % 256 != 0) {
+            free_fn_(p, ctx_);
+            fail(GEMSLR_ERR_ARG, "caller's allocator returned a pointer not aligned to 256 bytes");
+        }
+    } else if (cudaMalloc(&p, b) != cudaSuccess) {
         cudaGetLastError();
         fail(GEMSLR_ERR_NOMEM, "device allocation of " + std::to_string(b) + " bytes failed");
     }

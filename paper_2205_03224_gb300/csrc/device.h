@@ -136,6 +136,12 @@ void build_chunks(const Csr &L, const Csr &U, const std::vector<int64_t> &bp, Ch
 class Arena {
   public:
     ~Arena();
+    // caller's device allocator (both null: cudaMalloc / cudaFree); before any alloc
+    void set_allocator(void *(*a)(size_t, void *), void (*f)(void *, void *), void *ctx) {
+        alloc_fn_ = a;
+        free_fn_ = f;
+        ctx_ = ctx;
+    }
     void *alloc(size_t bytes);
     template <typename T> T *upload(const std::vector<T> &v) {
         T *p = (T *)alloc(v.size() * sizeof(T));
@@ -147,6 +153,9 @@ class Arena {
   private:
     std::vector<void *> ptrs_;
     size_t total_ = 0;
+    void *(*alloc_fn_)(size_t, void *) = nullptr;
+    void (*free_fn_)(void *, void *) = nullptr;
+    void *ctx_ = nullptr;
 };
 
 // One level in device memory (value type VT, low-rank storage WT).

@@ -1,5 +1,6 @@
 // GeMSLR handle, low-rank setup (Alg. 1 / Sec. 2.3), FGMRES (Sec. 4.1) and the C ABI.
 #include <chrono>
+#include <cstdio>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -604,6 +605,8 @@ gemslr_options normalized(const gemslr_options *opt) {
     for (int l = 0; l < GEMSLR_MAX_LEVELS; ++l)
         if (o.rank[l] < 0 || 2 * o.rank[l] + 1 > kMaxCols || o.rank[l] + 2 > kMaxRank)
             fail(GEMSLR_ERR_ARG, "rank out of range (0..79)");
+    if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
+        fail(GEMSLR_ERR_ARG, "dev_alloc and dev_free must be given together");
     return o;
 }
 
@@ -615,6 +618,7 @@ namespace gemslr {
 void setup_single_host(const gemslr_csr *A, const gemslr_partition *part, const gemslr_options *opt, Hierarchy &out) {
     std::unique_ptr<gemslr_ctx> h(new gemslr_ctx());
     h->opt = normalized(opt);
+    h->arena.set_allocator(h->opt.dev_alloc, h->opt.dev_free, h->opt.alloc_ctx);
     h->opt.precision = GEMSLR_PREC_FP64;
     Csr M = csr_from_abi(A);
     build_levels(M, part, &h->opt, h->host);
@@ -662,6 +666,7 @@ gemslr_status gemslr_setup(const gemslr_csr *A, const gemslr_partition *part, co
         auto t0 = std::chrono::steady_clock::now();
         std::unique_ptr<gemslr_ctx> h(new gemslr_ctx());
         h->opt = normalized(opt);
+        h->arena.set_allocator(h->opt.dev_alloc, h->opt.dev_free, h->opt.alloc_ctx);
         Csr M = csr_from_abi(A);
         build_levels(M, part, &h->opt, h->host);
         finish_setup(h.get(), true);
@@ -678,6 +683,7 @@ gemslr_status gemslr_setup_from_factors(const gemslr_csr *A, const gemslr_partit
         auto t0 = std::chrono::steady_clock::now();
         std::unique_ptr<gemslr_ctx> h(new gemslr_ctx());
         h->opt = normalized(opt);
+        h->arena.set_allocator(h->opt.dev_alloc, h->opt.dev_free, h->opt.alloc_ctx);
         Csr M = csr_from_abi(A);
         // slice levels from the partition but take every factor from f
         gemslr_options o = h->opt;
@@ -768,6 +774,139 @@ gemslr_status gemslr_export_factors(gemslr_handle h, gemslr_factors *f) {
         put_mat(H.last.L, f->last_L);
         put_mat(H.last.U, f->last_U);
     });
+}
+
+// ---- factor files (checkpoint / resume) --------------------------------------------
+// Layout (little-endian, as on the supported hosts): the 8 bytes "GEMSLRF1",
+// int64 n, int64 nlev, then per Schur level L, U, E, F as CSR records
+// (int64 nrows, ncols, nnz; int64 rowptr[nrows+1]; int32 colind[nnz];
+// double val[nnz]), int64 k, double W[(n - level_ptr[l+1]) * k],
+// double H[k * k]; then the last level's L and U records.
+}  // extern "C"
+namespace {
+constexpr char kFactorMagic[8] = {'G', 'E', 'M', 'S', 'L', 'R', 'F', '1'};
+
+struct FileCloser {
+    void operator()(FILE *f) const { if (f) fclose(f); }
+};
+using FilePtr = std::unique_ptr<FILE, FileCloser>;
+
+void write_all(FILE *f, const void *p, size_t bytes) {
+    if (bytes && fwrite(p, 1, bytes, f) != bytes) fail(GEMSLR_ERR_ARG, "writing the factor file failed");
+}
+void read_all(FILE *f, void *p, size_t bytes) {
+    if (bytes && fread(p, 1, bytes, f) != bytes) fail(GEMSLR_ERR_ARG, "factor file truncated or unreadable");
+}
+void write_csr(FILE *f, const Csr &m) {
+    const int64_t hdr[3] = {m.nrows, m.ncols, m.nnz()};
+    write_all(f, hdr, sizeof(hdr));
+    write_all(f, m.rp.data(), sizeof(int64_t) * m.rp.size());
+    write_all(f, m.ci.data(), sizeof(int32_t) * m.ci.size());
+    write_all(f, m.v.data(), sizeof(double) * m.v.size());
+}
+// Reads one CSR record into m; `limit` bounds every size read from the file.
+void read_csr(FILE *f, Csr &m, int64_t limit) {
+    int64_t hdr[3];
+    read_all(f, hdr, sizeof(hdr));
+    if (hdr[0] < 0 || hdr[1] < 0 || hdr[2] < 0 || hdr[0] > limit || hdr[1] > limit || hdr[2] > limit * limit)
+        fail(GEMSLR_ERR_ARG, "corrupt factor file (matrix sizes)");
+    m.nrows = hdr[0];
+    m.ncols = hdr[1];
+    m.rp.resize(hdr[0] + 1);
+    m.ci.resize(hdr[2]);
+    m.v.resize(hdr[2]);
+    read_all(f, m.rp.data(), sizeof(int64_t) * m.rp.size());
+    read_all(f, m.ci.data(), sizeof(int32_t) * m.ci.size());
+    read_all(f, m.v.data(), sizeof(double) * m.v.size());
+    if (m.rp[0] != 0 || m.rp[hdr[0]] != hdr[2]) fail(GEMSLR_ERR_ARG, "corrupt factor file (row pointers)");
+}
+gemslr_mat mat_view(const Csr &m) {
+    gemslr_mat v;
+    v.nrows = m.nrows;
+    v.ncols = m.ncols;
+    v.rowptr = m.rp.data();
+    v.colind = m.ci.data();
+    v.val = m.v.data();
+    return v;
+}
+}  // namespace
+extern "C" {
+
+gemslr_status gemslr_save_factors(gemslr_handle h, const char *path) {
+    return guard([&] {
+        if (!h || !path) fail(GEMSLR_ERR_ARG, "NULL argument");
+        FilePtr f(fopen(path, "wb"));
+        if (!f) fail(GEMSLR_ERR_ARG, std::string("cannot open ") + path + " for writing");
+        const Hierarchy &H = h->host;
+        write_all(f.get(), kFactorMagic, sizeof(kFactorMagic));
+        const int64_t hdr[2] = {H.n, (int64_t)H.nlev};
+        write_all(f.get(), hdr, sizeof(hdr));
+        for (const HostLevel &hl : H.lev) {
+            write_csr(f.get(), hl.L);
+            write_csr(f.get(), hl.U);
+            write_csr(f.get(), hl.E);
+            write_csr(f.get(), hl.F);
+            const int64_t k = hl.k;
+            write_all(f.get(), &k, sizeof(k));
+            write_all(f.get(), hl.W.data(), sizeof(double) * hl.W.size());
+            write_all(f.get(), hl.H.data(), sizeof(double) * hl.H.size());
+        }
+        write_csr(f.get(), H.last.L);
+        write_csr(f.get(), H.last.U);
+        if (fflush(f.get()) != 0) fail(GEMSLR_ERR_ARG, "writing the factor file failed");
+    });
+}
+
+gemslr_status gemslr_load_factors(const gemslr_csr *A, const gemslr_partition *part, const char *path,
+                                  const gemslr_options *opt, gemslr_handle *out) {
+    if (out) *out = nullptr;
+    Hierarchy H;                               // file contents, kept alive for the views below
+    std::vector<gemslr_level_factors> lf;
+    gemslr_factors fac{};
+    gemslr_status st = guard([&] {
+        if (!A || !part || !path || !out) fail(GEMSLR_ERR_ARG, "NULL argument");
+        FilePtr f(fopen(path, "rb"));
+        if (!f) fail(GEMSLR_ERR_ARG, std::string("cannot open ") + path);
+        char magic[8];
+        read_all(f.get(), magic, sizeof(magic));
+        if (std::memcmp(magic, kFactorMagic, sizeof(magic)) != 0) fail(GEMSLR_ERR_ARG, "not a GeMSLR factor file");
+        int64_t hdr[2];
+        read_all(f.get(), hdr, sizeof(hdr));
+        if (hdr[0] != A->n) fail(GEMSLR_ERR_ARG, "factor file is for another matrix size");
+        if (hdr[1] < 2 || hdr[1] > GEMSLR_MAX_LEVELS) fail(GEMSLR_ERR_ARG, "corrupt factor file (levels)");
+        const int64_t lim = std::max<int64_t>(A->n, 1);
+        H.lev.resize(hdr[1] - 1);
+        lf.resize(H.lev.size());
+        for (size_t l = 0; l < H.lev.size(); ++l) {
+            HostLevel &hl = H.lev[l];
+            read_csr(f.get(), hl.L, lim);
+            read_csr(f.get(), hl.U, lim);
+            read_csr(f.get(), hl.E, lim);
+            read_csr(f.get(), hl.F, lim);
+            int64_t k = 0;
+            read_all(f.get(), &k, sizeof(k));
+            if (k < 0 || k + 2 > kMaxRank) fail(GEMSLR_ERR_ARG, "corrupt factor file (rank)");
+            hl.W.resize((size_t)hl.E.nrows * k);
+            hl.H.resize((size_t)k * k);
+            read_all(f.get(), hl.W.data(), sizeof(double) * hl.W.size());
+            read_all(f.get(), hl.H.data(), sizeof(double) * hl.H.size());
+            lf[l].L = mat_view(hl.L);
+            lf[l].U = mat_view(hl.U);
+            lf[l].E = mat_view(hl.E);
+            lf[l].F = mat_view(hl.F);
+            lf[l].k = (int32_t)k;
+            lf[l].W = hl.W.data();
+            lf[l].H = hl.H.data();
+        }
+        read_csr(f.get(), H.last.L, lim);
+        read_csr(f.get(), H.last.U, lim);
+        fac.nlev = (int32_t)hdr[1];
+        fac.levels = lf.data();
+        fac.last_L = mat_view(H.last.L);
+        fac.last_U = mat_view(H.last.U);
+    });
+    if (st != GEMSLR_OK) return st;
+    return gemslr_setup_from_factors(A, part, &fac, opt, out);
 }
 
 gemslr_status gemslr_apply(gemslr_handle h, const double *r_dev, double *z_dev, int32_t nrhs, void *stream) {

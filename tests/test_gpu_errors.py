@@ -63,3 +63,30 @@ def test_invalid_solve_options_are_rejected(torch_cuda):
         assert lib.gemslr_last_error().decode()
     xs, info = G.solve(b, restart=20, rtol=1e-8)            # still usable
     assert info[0]["converged"]
+
+
+def test_factor_file_round_trip_and_corruption(torch_cuda, tmp_path):
+    """gemslr_save_factors / gemslr_load_factors: the reloaded handle applies the
+    same M^{-1} bit for bit (mixed precision too); a truncated file, a foreign
+    file and a file for another matrix size are rejected with ERR_ARG."""
+    torch = torch_cuda
+    from paper_2205_03224_gb300 import Gemslr, _lib, partition_geometric
+    A, xyz = gi.grid_operator((13, 11, 9), beta=0.4)
+    part = partition_geometric(A, xyz, 3, 8)
+    G = Gemslr(A, part, ilu="ilut", tau=1e-2, lfil=5, rank=5, precision="mixed")
+    path = tmp_path / "factors.bin"
+    G.save_factors(str(path))
+    G2 = Gemslr.load_factors(A, part, str(path), precision="mixed")
+    r = torch.from_numpy(gi.rhs_uniform(A.n, 5)).cuda()
+    assert torch.equal(G.apply(r), G2.apply(r))
+    data = path.read_bytes()
+    bad = tmp_path / "truncated.bin"
+    bad.write_bytes(data[: len(data) // 2])
+    foreign = tmp_path / "foreign.bin"
+    foreign.write_bytes(b"NOTGEMSL" + data[8:])
+    A2, xyz2 = gi.grid_operator((12, 11, 9), beta=0.4)
+    part2 = partition_geometric(A2, xyz2, 3, 8)
+    for (M, P, f) in ((A, part, bad), (A, part, foreign), (A2, part2, path), (A, part, tmp_path / "missing.bin")):
+        with pytest.raises(_lib.GemslrError) as e:
+            Gemslr.load_factors(M, P, str(f), precision="mixed")
+        assert e.value.status == 1
