@@ -2,7 +2,8 @@
 
 The GPU network (BF16 weights, FP32 accumulation) must reproduce the FP64
 oracle's loss and gradients at the same (BF16-rounded) weights; training
-must reduce the loss; with the stage on, FGMRES must still reach 1e-8."""
+must reduce the loss; with the stage on, FGMRES must still reach 1e-8, in
+fewer iterations than without it."""
 import numpy as np
 import pytest
 
@@ -89,6 +90,9 @@ def test_training_reduces_loss_and_solve_converges(torch_cuda, handle):
     x1, i1 = G.solve(b, restart=40, rtol=1e-8)
     res = np.linalg.norm(gi.rhs_uniform(A.n, 4) - A.to_scipy() @ x1.cpu().numpy()) / np.linalg.norm(b.cpu().numpy())
     assert i1[0]["converged"] and res <= 1e-8
+    # what the network gains: on this shifted operator the trained stage cuts the
+    # outer iterations at the same accuracy (measured 21 -> 13 on the GB300)
+    assert i1[0]["iters"] <= i0[0]["iters"] - 3, (i0[0]["iters"], i1[0]["iters"])
     G.learned_enable(False)
     x2, i2 = G.solve(b, restart=40, rtol=1e-8)
     assert i2[0]["iters"] == i0[0]["iters"]        # switching the stage off restores the method
