@@ -48,7 +48,7 @@ typedef enum {
     GEMSLR_ERR_TIMEOUT = 6,       /* a bounded device wait expired                 */
     GEMSLR_ERR_CUDA = 7,          /* CUDA runtime error                            */
     GEMSLR_ERR_NOMEM = 8,         /* host or device allocation failed              */
-    GEMSLR_ERR_UNSUPPORTED = 9    /* valid request this build does not implement   */
+    GEMSLR_ERR_UNSUPPORTED = 9    /* valid request the library does not implement  */
 } gemslr_status;
 
 /* Host CSR matrix, 0-based, columns ascending within a row. */
