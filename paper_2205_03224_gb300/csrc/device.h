@@ -45,7 +45,6 @@ void launch_couple(const LevelView<VT, WT> &lv, const double *in, VT *work, VT *
 void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t st);
 void launch_scatter(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t st);
 void launch_zero(int64_t n, double *x, cudaStream_t st);
-void launch_zero_f(int64_t n, float *x, cudaStream_t st);
 void launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *x,
                  const double *b, double *y, int lanes, cudaStream_t st, double *zcol = nullptr,
                  const KrylovCtl *ctl = nullptr);

@@ -1546,9 +1546,6 @@ void launch_scatter(int64_t n, const int32_t *perm, const double *src, double *d
 void launch_zero(int64_t n, double *x, cudaStream_t st) {
     if (n > 0) { k_set<double><<<grid_for(n, 256, 4864), 256, 0, st>>>(n, x, 0.0); count_launch(); }
 }
-void launch_zero_f(int64_t n, float *x, cudaStream_t st) {
-    if (n > 0) { k_set<float><<<grid_for(n, 256, 4864), 256, 0, st>>>(n, x, 0.0f); count_launch(); }
-}
 void launch_spmv(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *x,
                  const double *b, double *y, int lanes, cudaStream_t st, double *zcol, const KrylovCtl *ctl) {
     if (n == 0) return;
