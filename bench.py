@@ -49,14 +49,20 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2.07 * 2
 #   M^-1 kernels: (config, precision, kernel) -> DRAM bytes of a launch
 #   Krylov kernels (work grows with the step j): -> (DRAM bytes, algorithmic bytes) of the captured step
 NCU_TRAFFIC = {    # profiles/trsv_c2_apply_<precision>.md
-    ("c2", "mixed", "trsv_down_L0"): 43_782_144, ("c2", "mixed", "trsv_down_L1"): 5_065_216,
-    ("c2", "mixed", "trsv_down_L2"): 487_680, ("c2", "mixed", "trsv_last"): 170_496,
-    ("c2", "mixed", "trsv_up_L2"): 329_472, ("c2", "mixed", "trsv_up_L1"): 3_443_968,
-    ("c2", "mixed", "trsv_up_L0"): 45_622_528 + 4_352,
-    ("c2", "fp64", "trsv_down_L0"): 73_523_456 + 741_120, ("c2", "fp64", "trsv_down_L1"): 12_471_040,
-    ("c2", "fp64", "trsv_down_L2"): 1_317_632, ("c2", "fp64", "trsv_last"): 367_872,
-    ("c2", "fp64", "trsv_up_L2"): 560_128, ("c2", "fp64", "trsv_up_L1"): 4_947_968,
-    ("c2", "fp64", "trsv_up_L0"): 76_690_944 + 829_952,
+    ("c2", "mixed", "trsv_down_L0"): 43_783_168,
+    ("c2", "mixed", "trsv_down_L1"): 5_068_544,
+    ("c2", "mixed", "trsv_down_L2"): 485_888,
+    ("c2", "mixed", "trsv_last"): 170_496,
+    ("c2", "mixed", "trsv_up_L2"): 330_496,
+    ("c2", "mixed", "trsv_up_L1"): 3_444_480,
+    ("c2", "mixed", "trsv_up_L0"): 45_625_088,
+    ("c2", "fp64", "trsv_down_L0"): 73_697_536,
+    ("c2", "fp64", "trsv_down_L1"): 12_483_072,
+    ("c2", "fp64", "trsv_down_L2"): 1_318_400,
+    ("c2", "fp64", "trsv_last"): 367_360,
+    ("c2", "fp64", "trsv_up_L2"): 559_616,
+    ("c2", "fp64", "trsv_up_L1"): 4_950_528,
+    ("c2", "fp64", "trsv_up_L0"): 76_695_296,
 }
 NCU_TRAFFIC_KRYLOV = {    # profiles/krylov_c2_mixed.md, step j = 25
     ("c2", "mixed", "dgs_fix_adots"): (54_605_056 + 78_592, None),
