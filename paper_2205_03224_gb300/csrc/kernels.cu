@@ -14,11 +14,14 @@
 //   last level       k_trsv on the block-Jacobi blocks (Sec. 4.3);
 //   k_trsv   (up)    y1 = z1 - U^-1 L^-1 (F_l y2), F_l y2 formed row by row as
 //                    the right-hand side of the forward sweep.
-// FGMRES (Sec. 4.1): CSR SpMV, classical Gram-Schmidt with a second pass when
-// the first one cancels (Daniel-Gragg-Kaufman-Stewart test), Givens update of
-// the Hessenberg least-squares problem, solution update.  Reductions are
-// per-CTA partial sums finished by the last CTA in a fixed order, so results
-// are deterministic run to run.
+// FGMRES (Sec. 4.1): CSR SpMV; for a linear M^-1 delayed classical
+// Gram-Schmidt with reorthogonalisation (k_dgs_*: one reduction after each
+// product, the second pass and the previous basis vector beside M^-1), else
+// classical Gram-Schmidt with a second pass when the first one cancels
+// (Daniel-Gragg-Kaufman-Stewart test, k_gs_*); Givens update of the Hessenberg
+// least-squares problem, solution update.  Reductions are per-CTA partial sums
+// finished by the last CTA in a fixed order, so results are deterministic run
+// to run.
 #include <cstdio>
 
 #include "device.h"
