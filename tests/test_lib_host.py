@@ -62,3 +62,18 @@ def test_partition_rejects_bad_arguments(lib):
         partition_geometric(A, xyz, 3, 3)          # p not a power of two
     with pytest.raises(GemslrError):
         partition_geometric(A, xyz, 1, 4)          # needs a Schur level
+
+
+def test_binding_argument_counts_match_the_header(lib):
+    """Every entry point declared in include/gemslr.h has ctypes argument types
+    in the binding, as many as the declaration has parameters."""
+    hdr = open(os.path.join(ROOT, "include", "gemslr.h")).read()
+    code = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    decls = re.findall(r"\b(gemslr_[a-z_]+)\s*\(([^;{]*?)\)\s*;", code)
+    assert len(decls) >= 25
+    for name, args in decls:
+        args = args.strip()
+        nparam = 0 if args in ("", "void") else len(args.split(","))
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == nparam, (name, nparam, len(fn.argtypes))
