@@ -105,3 +105,40 @@ def test_fgmres_with_inner_steps_converges_on_indefinite_operator():
         assert np.linalg.norm(b - As @ x) <= 1e-8 * np.linalg.norm(b)
         its[k] = info["iters"]
     assert its[3] < its[0]
+
+
+def test_cgs2_arnoldi_with_pythagorean_norm_equals_mgs():
+    """The GPU runs the inner Arnoldi with classical Gram-Schmidt and a second
+    pass, taking h_{j+1,j} = (||w'||^2 - ||h2||^2)^(1/2) after the second
+    projection instead of a third reduction.  Restated here in numpy, it gives
+    the oracle's (modified Gram-Schmidt) inner GMRES result to rounding."""
+    As, P_ = _problem((8, 7, 6), beta=0.3, sigma=0.06)
+    M = OracleGemslr(As, P_, ilu="ilut", tau=1e-2, lfil=3, rank=6)
+    z2 = gi.rhs_uniform(M.n - M.levels[0]["e"], 15)
+    for k in (1, 4, 8):
+        beta = np.linalg.norm(z2)
+        V = [z2 / beta]
+        Z = []
+        H = np.zeros((k + 1, k))
+        steps = k
+        for j in range(k):
+            Z.append(M.precond_schur(V[j], 0))
+            w = M.s_hat(Z[j], 0)
+            w0 = np.linalg.norm(w)
+            Vj = np.column_stack(V)
+            h = Vj.T @ w
+            w = w - Vj @ h
+            h2 = Vj.T @ w
+            hn = np.sqrt(max(w @ w - h2 @ h2, 0.0))
+            H[:j + 1, j] = h + h2
+            H[j + 1, j] = hn
+            if not hn > 1e-14 * w0:
+                steps = j + 1
+                break
+            V.append((w - Vj @ h2) / hn)
+        rhs = np.zeros(steps + 1)
+        rhs[0] = beta
+        c = np.linalg.lstsq(H[:steps + 1, :steps], rhs, rcond=None)[0]
+        y2 = np.column_stack(Z[:steps]) @ c
+        ref = M.inner_gmres(z2, k)
+        assert np.allclose(y2, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max()), k
