@@ -87,3 +87,68 @@ def test_triangular_solves_match_dense():
     Ld = np.eye(n) + L.toarray()
     ref = sla.solve_triangular(U.toarray(), sla.solve_triangular(Ld, b, lower=True, unit_diagonal=True))
     assert np.allclose(lu_solve(L, U, b), ref, rtol=1e-12)
+
+
+def test_ilut_hand_worked_dual_threshold():
+    """ILUT(tau = 0.1, lfil = 1) of a 5 x 5 matrix, worked by hand from the
+    dual-threshold definition (Saad's ILUT, cited in Sec. 2.1) with the
+    scale-free measures of the oracle: a multiplier l_ik is measured by
+    |l_ik u_kk| (the entry w_k it eliminates), a U entry by |u_ij|, both
+    against tau ||a_i||_2.  The case exercises each rule so that a plausible
+    misreading changes the factors:
+      - final-row drop in U: row 0 drops u_01 = 1 < 1.122; kept, it would
+        make u_11 = 2 - 0.4 * 1 = 1.6 instead of 2;
+      - lfil selection in U: row 1 has candidates u_13 = 3 and the fill
+        u_12 = -2, keeps the larger;
+      - in-elimination drop: row 2 drops w_0 = 1 < 1.175 before it is used;
+        used, it would make u_22 = 10 - 0.1 * 5 = 9.5;
+      - keep the largest by |l_ik u_kk|, not by |l_ik|: row 3 has l_31 = 1.5
+        (measure 1.5 * 2 = 3) and l_32 = 0.4 (measure 0.4 * 10 = 4) and keeps
+        l_32; keeping the largest |l| or the smallest measure keeps l_31;
+        measuring |l_ik| in the elimination would drop both (1.5, 0.4 < 2.19)
+        and leave u_33 = 20.9;
+      - fill that appears is eliminated in turn: row 4 eliminates the fill at
+        columns 2 and 3 created by row 0 and row 2, which reaches u_44.
+    """
+    A = np.array([[10.0, 1.0, 5.0, 0.0, 0.0],
+                  [4.0, 2.0, 0.0, 3.0, 0.0],
+                  [1.0, 6.0, 10.0, 0.0, 1.0],
+                  [0.0, 3.0, 4.0, 20.9, 4.0],
+                  [5.0, 0.0, 0.0, 0.0, 10.0]])
+    # row 0: thr = 0.1 sqrt(126) = 1.122.  U candidates 1 (dropped), 5.
+    # row 1: thr = 0.1 sqrt(29) = 0.539.  k = 0: w_0 = 4 -> l_10 = 0.4;
+    #        w_2 = -0.4 * 5 = -2 (fill).  U candidates 3 (col 3), -2 (col 2):
+    #        lfil = 1 keeps col 3.  u_11 = 2.
+    # row 2: thr = 0.1 sqrt(138) = 1.175.  k = 0: w_0 = 1 < thr, dropped.
+    #        k = 1: l_21 = 6 / 2 = 3; w_3 = -3 * 3 = -9.  u_22 = 10; U
+    #        candidates -9 (col 3), 1 (col 4, < thr, dropped).
+    # row 3: thr = 0.1 sqrt(9 + 16 + 20.9^2 + 16) = 2.186.  k = 1: l_31 = 1.5,
+    #        w_3 = 20.9 - 1.5 * 3 = 16.4.  k = 2: l_32 = 0.4,
+    #        w_3 = 16.4 - 0.4 * (-9) = 20.  L keeps l_32 (measure 4 > 3).
+    #        u_33 = 20, u_34 = 4.
+    # row 4: thr = 0.1 sqrt(125) = 1.118.  k = 0: l_40 = 0.5, w_2 = -2.5
+    #        (fill).  k = 2: l_42 = -2.5 / 10 = -0.25, w_3 = -0.25 * 9 = -2.25
+    #        (fill).  k = 3: l_43 = -2.25 / 20 = -0.1125,
+    #        w_4 = 10 + 0.1125 * 4 = 10.45.  L measures 5, 2.5, 2.25: keeps l_40.
+    L_hand = np.zeros((5, 5))
+    L_hand[1, 0] = 0.4
+    L_hand[2, 1] = 3.0
+    L_hand[3, 2] = 0.4
+    L_hand[4, 0] = 0.5
+    U_hand = np.zeros((5, 5))
+    U_hand[0, 0], U_hand[0, 2] = 10.0, 5.0
+    U_hand[1, 1], U_hand[1, 3] = 2.0, 3.0
+    U_hand[2, 2], U_hand[2, 3] = 10.0, -9.0
+    U_hand[3, 3], U_hand[3, 4] = 20.0, 4.0
+    U_hand[4, 4] = 10.45
+    L, U, nc = ilut(sp.csr_matrix(A), 0.1, 1)
+    assert nc == 0
+    Ld, Ud = L.toarray(), U.toarray()
+    assert np.array_equal(Ld != 0, L_hand != 0)
+    assert np.array_equal(Ud != 0, U_hand != 0)
+    assert np.allclose(Ld, L_hand, rtol=1e-14, atol=0.0)
+    assert np.allclose(Ud, U_hand, rtol=1e-14, atol=0.0)
+    # U stores the diagonal first in each row, then ascending columns
+    for i in range(5):
+        cols = U.indices[U.indptr[i]:U.indptr[i + 1]]
+        assert cols[0] == i and np.all(np.diff(cols) > 0)
