@@ -61,11 +61,18 @@ class OracleGemslr:
     inner_steps : Alg. 2 step 9; 0 applies the standard recursion at level 0,
         k > 0 solves S_hat_0 y2 = z2 there by k steps of right-preconditioned
         GMRES (``inner_gmres``)
+
+    Attribute ``stage`` (default None): an extra correction of the deepest
+    Schur level l* = nlev - 2, a callable (z2, y2) -> y2' applied after y2 is
+    computed there and before the back-substitution with F (the learned
+    interface correction, ``oracle.learned.interface_stage``; not in the
+    paper: FGMRES tolerates a preconditioner that varies, Sec. 4.1).
     """
 
     def __init__(self, A, part, ilu="ilu0", tau=1e-3, lfil=10, rank=8, last_ilu=None,
                  arnoldi_tol=1e-2, max_cycles=20, lowrank=True, inner_steps=0):
         self.inner_steps = int(inner_steps)
+        self.stage = None
         A = sp.csr_matrix(A)
         self.n = A.shape[0]
         self.part = part
@@ -119,6 +126,8 @@ class OracleGemslr:
             y2 = self.inner_gmres(z2, self.inner_steps)          # S_hat_0 y2 = z2 by GMRES
         else:
             y2 = self.precond_schur(z2, l)                       # y2 = Solve(z2 + u2, l+1)
+        if self.stage is not None and l == self.nlev - 2:
+            y2 = self.stage(z2, y2)                              # learned correction at l*
         y1 = z1 - _ilu.lu_solve(lv["L"], lv["U"], lv["F"] @ y2)  # y1 = z1 - U^-1 L^-1 F y2
         return np.concatenate([y1, y2])
 

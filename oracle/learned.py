@@ -135,6 +135,38 @@ def schur_dense(M, l):
     return C - lv["E"].toarray() @ X
 
 
+def interface_stage(M, net, d=None):
+    """The in-apply correction of level l* = nlev - 2 as a callable for
+    ``OracleGemslr.stage``:
+
+        rho = z2 - S_hat y2,   y2' = y2 + (||rho|| / d) * net(rho / ||rho||)
+
+    with S_hat y2 = C y2 - E (U^{-1} L^{-1}) F y2 (``OracleGemslr.s_hat``, Sec. 2.4)
+    and d the mean |diagonal| of S_hat (formed densely when not given).  ``net``
+    maps a vector of the level's S sites to S values; ``cnn(params, nbr)``
+    gives the network.  rho = 0 leaves y2 unchanged."""
+    l = M.nlev - 2
+    if d is None:
+        d = float(np.mean(np.abs(np.diag(schur_dense(M, l)))))
+
+    def stage(z2, y2):
+        rho = z2 - M.s_hat(y2, l)
+        nr = float(np.linalg.norm(rho))
+        if nr == 0.0:
+            return y2
+        return y2 + (nr / d) * net(rho / nr)
+
+    return stage
+
+
+def cnn(params, nbr):
+    """The 4-layer network as a map of one site vector (S,) -> (S,)."""
+    def f(x):
+        out, _ = net_forward(params, np.asarray(x, dtype=np.float64)[None, :], nbr)
+        return out[0]
+    return f
+
+
 def level_preconditioner_dense(M, l):
     """M_S^{-1} of level l (C_l^{-1} approximated by the levels below, plus the low-rank term) as a dense matrix."""
     lv = M.levels[l]

@@ -104,3 +104,55 @@ def _has_stage(G):
         return True
     except Exception:
         return False
+
+
+def test_in_apply_stage_matches_oracle(torch_cuda):
+    """One M^{-1} application with the stage on, element by element against
+    the oracle's restatement: rho = z2 - S_hat y2 at l* = nlev - 2,
+    y2 += (||rho|| / d) net(rho / ||rho||), then the back-substitution with F.
+    Both sides use the oracle's factors and the same network (weights rounded
+    to BF16, biases to FP32, as the GPU keeps them).  The stage's own
+    contribution (application with it minus without it) must agree to FP32
+    accuracy, which a wrong sign, scale, level or site order would break."""
+    torch = torch_cuda
+    from oracle import OracleGemslr, multilevel_partition
+    from oracle.learned import cnn, interface_stage, schur_dense
+    from paper_2205_03224_gb300 import Gemslr, partition_geometric
+    A, xyz = gi.grid_operator((12, 11, 10), beta=0.0, sigma=0.05)
+    As = A.to_scipy()
+    part = partition_geometric(A, xyz, 3, 8)
+    ref_part = multilevel_partition(As, xyz, 3, 8)
+    assert np.array_equal(part["perm"], ref_part["perm"])
+    M = OracleGemslr(As, ref_part, ilu="ilut", tau=1e-3, lfil=10, rank=5)
+    G = Gemslr.from_factors(A, part, M.factors())
+    C = 8
+    G.learned_train(xyz, channels=C, npairs=16, epochs=0, batch=16, seed=3)
+    params = init_params(channels=C, seed=11)
+    for l, (W, b) in enumerate(params):
+        b[:] = 0.05 * (l + 1) * (1.0 - 2.0 * (np.arange(len(b)) % 2))
+    G.learned_params(_flat(params))
+    pr = [[_bf16(W), np.asarray(b, np.float32).astype(np.float64)] for W, b in params]
+    lstar = M.nlev - 2
+    e = M.levels[lstar]["e"]
+    nbr = site_neighbors(xyz[part["perm"][e:]])
+    d = float(np.mean(np.abs(np.diag(schur_dense(M, lstar)))))
+    info = G.learned_info()
+    assert info["sites"] == nbr.shape[0]
+    assert abs(info["dscale"] - d) <= 1e-12 * d
+    for seed in (41, 42):
+        r = gi.rhs_uniform(A.n, seed)
+        rd = torch.from_numpy(r).cuda()
+        G.learned_enable(True)
+        z_on = G.apply(rd).cpu().numpy()
+        G.learned_enable(False)
+        z_off = G.apply(rd).cpu().numpy()
+        M.stage = None
+        z0 = M.apply(r)
+        M.stage = interface_stage(M, cnn(pr, nbr), d)
+        z1 = M.apply(r)
+        M.stage = None
+        assert np.linalg.norm(z_off - z0) <= 1e-10 * np.linalg.norm(z0)
+        delta, delta_ref = z_on - z_off, z1 - z0
+        assert np.linalg.norm(delta_ref) >= 1e-3 * np.linalg.norm(z0)
+        assert np.linalg.norm(delta - delta_ref) <= 1e-4 * np.linalg.norm(delta_ref), seed
+        assert np.linalg.norm(z_on - z1) <= 1e-4 * np.linalg.norm(z1)

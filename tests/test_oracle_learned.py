@@ -6,8 +6,8 @@ import numpy as np
 
 import gemslr_inputs as gi
 from oracle import OracleGemslr, multilevel_partition
-from oracle.learned import (conv_backward, conv_forward, init_params, loss_and_grads, net_forward,
-                            schur_dense, site_neighbors, training_pairs)
+from oracle.learned import (cnn, conv_backward, conv_forward, init_params, interface_stage, loss_and_grads,
+                            net_forward, schur_dense, site_neighbors, training_pairs)
 
 
 def _sites():
@@ -125,3 +125,70 @@ def test_schur_and_training_pairs():
     W, H = lv["W"], lv["H"]
     y2 = M.solve_level(z + W @ (H @ (W.T @ z)), l + 1)
     assert np.allclose(R[0], z - S @ y2, rtol=1e-10, atol=1e-10 * np.abs(R[0]).max())
+
+
+def _two_level():
+    A, xyz = gi.grid_operator((9, 8, 6), beta=0.3, sigma=0.05)
+    As = A.to_scipy()
+    part = multilevel_partition(As, xyz, 2, 4)
+    M = OracleGemslr(As, part, ilu="ilut", tau=1e-2, lfil=3, rank=3)
+    return As, xyz, part, M
+
+
+def test_stage_with_ideal_network_solves_the_schur_system():
+    """With net(x) = d S_hat^{-1} x the stage returns y2' = y2 + S_hat^{-1}(z2 - S_hat y2)
+    = S_hat^{-1} z2 whatever y2 was.  With two levels (l* = 0 is the root) the
+    application is then the exact inverse of A~ = [[LU, F], [E, C]], the matrix
+    whose block elimination it performs (Sec. 2.3), for any incomplete factors.
+    A wrong sign, a missing ||rho|| or a d applied the wrong way round breaks it."""
+    As, xyz, part, M = _two_level()
+    S = schur_dense(M, 0)
+    d = float(np.mean(np.abs(np.diag(S))))
+    M.stage = interface_stage(M, lambda x: d * np.linalg.solve(S, x))
+    lv = M.levels[0]
+    s, e = lv["s"], lv["e"]
+    At = M.Ahat.toarray()
+    LU = (np.eye(e - s) + lv["L"].toarray()) @ lv["U"].toarray()
+    At[s:e, s:e] = LU
+    r = gi.rhs_uniform(M.n, 8)
+    z = M.apply_perm(r)
+    assert np.allclose(z, np.linalg.solve(At, r), rtol=1e-9, atol=1e-9 * np.abs(z).max())
+    M.stage = None
+    assert not np.allclose(M.apply_perm(r), z, rtol=1e-3)     # the method alone is not exact here
+
+
+def test_stage_with_zero_network_is_the_method():
+    As, xyz, part, M = _two_level()
+    r = gi.rhs_uniform(M.n, 9)
+    z0 = M.apply_perm(r)
+    M.stage = interface_stage(M, lambda x: np.zeros_like(x))
+    assert np.array_equal(M.apply_perm(r), z0)
+
+
+def test_stage_with_cnn_is_positively_homogeneous_and_changes_y():
+    """N(rho) = (||rho||/d) net(rho/||rho||) is positively homogeneous even
+    with biases, so the whole application stays homogeneous; the correction
+    only touches the level's y2 and, through F, the y1 above it."""
+    A, xyz = gi.grid_operator((9, 8, 7), beta=0.0, sigma=0.05)
+    As = A.to_scipy()
+    part = multilevel_partition(As, xyz, 3, 4)
+    M = OracleGemslr(As, part, ilu="ilut", tau=1e-2, lfil=4, rank=4)
+    e = M.levels[-1]["e"]
+    nbr = site_neighbors(xyz[part["perm"][e:]])
+    params = init_params(channels=4, seed=5)
+    for l, (W, b) in enumerate(params):
+        b[:] = 0.1 * (l + 1) * (1.0 - 2.0 * (np.arange(len(b)) % 2))
+    r = gi.rhs_uniform(M.n, 10)
+    z0 = M.apply_perm(r)
+    M.stage = interface_stage(M, cnn(params, nbr))
+    z1 = M.apply_perm(r)
+    assert np.linalg.norm(z1 - z0) > 1e-3 * np.linalg.norm(z0)
+    assert np.allclose(M.apply_perm(3.0 * r), 3.0 * z1, rtol=1e-12, atol=1e-12 * np.abs(z1).max())
+    # rows of levels above l* change only through F y2: the first level's z1 part
+    # differs, and the difference equals -(LU)^{-1} F (y2' - y2) of level 0's tail
+    from oracle.ilu import lu_solve
+    lv0 = M.levels[0]
+    dy = z1[lv0["e"]:] - z0[lv0["e"]:]
+    d1 = z1[:lv0["e"]] - z0[:lv0["e"]]
+    assert np.allclose(d1, -lu_solve(lv0["L"], lv0["U"], lv0["F"] @ dy), rtol=1e-9,
+                       atol=1e-9 * np.abs(d1).max())
