@@ -44,11 +44,14 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained) x 2.07 GHz x 2 flops.
 FP64_PEAK_GFLOPS = 152 * 2 * 2.07 * 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu --set full capture of the same workload (profiles/), with the algorithmic
-# bytes of the captured launch; an entry must be removed when its kernel changes.
+# ncu capture of the same workload, with the digest of the kernel sources at
+# capture time: an entry whose sources have changed since is reported as null
+# (the counters no longer describe the kernel that ran).
 #   M^-1 kernels: (config, precision, kernel) -> DRAM bytes of a launch
 #   Krylov kernels (work grows with the step j): -> (DRAM bytes, algorithmic bytes) of the captured step
-NCU_TRAFFIC = {    # profiles/trsv_c2_apply_<precision>.md
+TRAFFIC_SOURCES = ["kernels.cu", "kernels.cuh", "ptx.cuh", "device.cu"]
+NCU_TRAFFIC_DIGEST = "439ad4e5a5c41f9b"
+NCU_TRAFFIC = {
     ("c2", "mixed", "trsv_down_L0"): 43_783_168,
     ("c2", "mixed", "trsv_down_L1"): 5_068_544,
     ("c2", "mixed", "trsv_down_L2"): 485_888,
@@ -64,12 +67,29 @@ NCU_TRAFFIC = {    # profiles/trsv_c2_apply_<precision>.md
     ("c2", "fp64", "trsv_up_L1"): 4_950_528,
     ("c2", "fp64", "trsv_up_L0"): 76_695_296,
 }
-NCU_TRAFFIC_KRYLOV = {    # profiles/krylov_c2_mixed.md, step j = 25
+NCU_TRAFFIC_KRYLOV = {
     ("c2", "mixed", "dgs_fix_adots"): (54_605_056 + 78_592, None),
     ("c2", "mixed", "dgs_spmv_dots"): (80_561_152 + 2_375_936, None),
     ("c2", "mixed", "dgs_next"): (56_632_832 + 146_944, None),
 }
 NCU_KRYLOV_STEP = 25
+
+
+def kernel_digest():
+    """sha256 (first 16 hex digits) of the sources of the solve-phase kernels."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2205_03224_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_table():
+    """The measured traffic tables, or empty ones when the kernels changed since the capture."""
+    if NCU_TRAFFIC_DIGEST is None or NCU_TRAFFIC_DIGEST != kernel_digest():
+        return {}, {}
+    return NCU_TRAFFIC, NCU_TRAFFIC_KRYLOV
 
 
 def cfg():
@@ -145,27 +165,84 @@ def oracle_solves(nsolve):
     return times, its, t_setup
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), else what the platform module reports."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_worker(config, nsolve, barrier, queue):
+    # each process: oracle setup (untimed), wait for every process, then its timed solves
+    global CONFIG
+    CONFIG = config
+    os.environ["OMP_NUM_THREADS"] = "1"
+    try:
+        from oracle import OracleGemslr, fgmres, multilevel_partition
+        c = cfg()
+        A, xyz, b = gi.config_problem(CONFIG)
+        As = A.to_scipy()
+        part = multilevel_partition(As, xyz, c["nlev"], c["p"])
+        M = OracleGemslr(As, part, ilu=c["ilu"], tau=c["tau"], lfil=c["lfil"], rank=c["rank"])
+        barrier.wait(timeout=600)
+        t0 = time.perf_counter()
+        its = 0
+        for _ in range(nsolve):
+            x, info = fgmres(As, b, M.apply, restart=c["restart"], rtol=c["rtol"])
+            its = info["iters"]
+        queue.put((time.perf_counter() - t0, nsolve, its))
+    except Exception as exc:        # reported by the parent
+        queue.put(repr(exc))
+
+
+def oracle_all_cores(nproc, nsolve):
+    """The oracle as it stands on every host core: nproc single-threaded
+    processes (spawned, so no CUDA state is inherited) each solve the workload
+    nsolve times after a common barrier.  Returns (solves/s over the job, the
+    slowest process's seconds, iterations)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(nproc)
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker, args=(CONFIG, nsolve, barrier, queue)) for _ in range(nproc)]
+    for p in procs:
+        p.start()
+    res = [queue.get(timeout=1200) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+    bad = [r for r in res if isinstance(r, str)]
+    if bad:
+        raise RuntimeError(f"oracle worker failed: {bad[0]}")
+    slowest = max(r[0] for r in res)
+    return nproc * nsolve / slowest, slowest, res[0][2]
+
+
 def run_reference(args):
     ws, rank, _ = dist()
     if rank != 0:
         return 0
-    # one step = one complete oracle solve (about 2 s on one core); the sample
-    # is bounded (at most 1 warm-up and 20 timed solves) so the run ends in
-    # about a minute whatever K and W are asked for
-    warm, steps = min(args.warmup, 1), max(1, min(args.steps, 20))
-    times, its, t_setup = oracle_solves(warm + steps)
-    timed = times[warm:]
-    total = sum(timed)
-    value = len(timed) / total
+    # the oracle on every host core: one single-threaded process per core, each
+    # timing one or two complete solves of the workload (a bounded sample: the
+    # run ends in about a minute whatever K and W are asked for)
+    nproc = os.cpu_count() or 1
+    nper = max(1, min(args.steps, 2 * nproc) // nproc)
+    value, slowest, its = oracle_all_cores(nproc, nper)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": steps, "warmup": warm, "steps_requested": args.steps, "warmup_requested": args.warmup,
-        "ms_per_step": 1e3 * total / len(timed),
+        "steps": nproc * nper, "warmup": 0, "steps_requested": args.steps, "warmup_requested": args.warmup,
+        "ms_per_step": 1e3 * slowest / nper,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "replicas"},
-        "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
-                         "sample": f"{len(timed)} complete oracle FGMRES solves of the workload "
-                                   f"(setup {t_setup:.1f} s excluded), iterations {its[-1]}"},
+        "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": nproc, "cpu": cpu_model(),
+                         "sample": f"{nproc} single-threaded oracle processes x {nper} complete FGMRES solves of "
+                                   f"the workload after a common barrier (oracle setup excluded), "
+                                   f"{its} iterations each"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -243,13 +320,14 @@ def rooflines(prof, ab, kw, hbm, peaks, precision, nkeep=4):
     total time first: M^-1 kernels against the HBM copy peak (algorithmic
     bytes), Krylov kernels against the FP64 peak (they are bound by the FP64
     pipe on this part), with their algorithmic bandwidth beside it."""
+    traffic_m, traffic_k = traffic_table()
     out = []
     for k, (ms, cnt) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
         if k in ab:
             per = ms / cnt
             ach = ab[k] / (per * 1e-3) / 1e9
             out.append({"kernel": k, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                        "frac": ach / hbm, "traffic": NCU_TRAFFIC.get((CONFIG, precision, k)),
+                        "frac": ach / hbm, "traffic": traffic_m.get((CONFIG, precision, k)),
                         "bytes_per_launch": ab[k], "ms_per_launch": per, "share_ms": ms,
                         "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"})
         elif k in kw:
@@ -257,7 +335,7 @@ def rooflines(prof, ab, kw, hbm, peaks, precision, nkeep=4):
             per = ms / cnt
             ach = flops / (ms * 1e-3) / 1e9
             traffic = None
-            tk = NCU_TRAFFIC_KRYLOV.get((CONFIG, precision, k))
+            tk = traffic_k.get((CONFIG, precision, k))
             if tk is not None:
                 dram, alg = tk
                 ratio = dram / (alg if alg else kw["_step"][k][1])
@@ -433,9 +511,15 @@ def run_ours(args):
     }
     if rank == 0 and not args.no_cpu_baseline:
         times, oits, t_setup = oracle_solves(2)
-        line["cpu_baseline"] = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{len(times)} complete oracle FGMRES solves of the workload "
-                                          f"(oracle setup {t_setup:.1f} s excluded), {oits[-1]} iterations"}
+        nproc = os.cpu_count() or 1
+        v_all, slowest, _ = oracle_all_cores(nproc, 1)
+        line["cpu_baseline"] = {"value": v_all, "unit": UNIT, "cores": nproc, "kind": "oracle", "cpu": cpu_model(),
+                                "sample": f"{nproc} single-threaded oracle processes x 1 complete FGMRES solve of "
+                                          f"the workload after a common barrier (oracle setup excluded), "
+                                          f"{oits[-1]} iterations each",
+                                "one_core": {"value": len(times) / sum(times), "unit": UNIT, "cores": 1,
+                                             "sample": f"{len(times)} complete oracle solves in this process "
+                                                       f"(setup {t_setup:.1f} s excluded)"}}
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -570,9 +654,10 @@ def run_learned(args):
     hist = G.learned_train(xyz, channels=32, npairs=args.npairs, epochs=args.epochs, batch=64, lr=1e-3, seed=c["seed"])
     train_s = time.perf_counter() - t0
     learned = timed_solves()
-    accepted = learned["converged"] and (not plain["converged"] or learned["iterations"] < plain["iterations"])
-    if not accepted and not learned["converged"] and not plain["converged"]:
-        accepted = learned["rel_residual"] < plain["rel_residual"]
+    # kept only where it cuts the iterations to the same accuracy: both runs
+    # reach rtol and the stage needs fewer iterations (a lower residual after
+    # the iteration cap, with neither converged, does not count)
+    accepted = learned["converged"] and plain["converged"] and learned["iterations"] < plain["iterations"]
     line = {
         "metric": METRIC, "workload": "c5", "unit": "ms per FGMRES solve (maxit cap)",
         "config": {"workload": "3-D 7-pt Laplacian - 0.1 h^-2 I (indefinite) 96^3 (n=884736), 4 levels x "

@@ -203,7 +203,9 @@ gemslr_status gemslr_load_factors(const gemslr_csr *A, const gemslr_partition *p
 /*
  * z = M^{-1} r (Alg. 2) for nrhs right-hand sides in the ORIGINAL ordering:
  * z = P M_hat^{-1} P^T r.  r_dev, z_dev: n x nrhs column-major device arrays
- * (may not alias).  Asynchronous on `stream`.
+ * (may not alias).  Asynchronous on `stream`.  The device that was current
+ * when the handle was set up must be current (this applies to
+ * gemslr_apply_static and gemslr_fgmres_solve too); otherwise ARG.
  */
 gemslr_status gemslr_apply(gemslr_handle h, const double *r_dev, double *z_dev, int32_t nrhs,
                            void *stream);
@@ -305,6 +307,17 @@ void gemslr_destroy(gemslr_handle h);
 typedef struct gemslr_batch_ctx *gemslr_batch;
 gemslr_status gemslr_setup_batch(int32_t nsys, const gemslr_csr *A, const gemslr_partition *part,
                                  const gemslr_options *opt, gemslr_batch *out);
+/*
+ * Batch from factors computed elsewhere (Alg. 1 done by another program, or
+ * a checkpoint): f is an array of nsys gemslr_factors, one per system, in the
+ * layout of gemslr_setup_from_factors; nothing is factored and no Arnoldi
+ * runs, only the autotuner.  The factors are copied (caller-owned).  Errors:
+ * ARG (NULL f, a level count, shape or rank that does not match the system's
+ * partition, a rank above 64), plus those of gemslr_setup_batch.
+ */
+gemslr_status gemslr_setup_batch_from_factors(int32_t nsys, const gemslr_csr *A, const gemslr_partition *part,
+                                              const gemslr_factors *f, const gemslr_options *opt,
+                                              gemslr_batch *out);
 gemslr_status gemslr_batch_apply(gemslr_batch b, const double *r_dev, double *z_dev, int32_t nrhs,
                                  void *stream);
 gemslr_status gemslr_batch_fgmres_solve(gemslr_batch b, const double *b_dev, double *x_dev, int32_t nrhs,

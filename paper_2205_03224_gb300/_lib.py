@@ -70,7 +70,7 @@ EXPORTED = [
     "gemslr_factor_sizes", "gemslr_export_factors", "gemslr_apply", "gemslr_fgmres_solve",
     "gemslr_get_stats", "gemslr_last_error", "gemslr_destroy", "gemslr_kernel_launches",
     "gemslr_profile_enable", "gemslr_profile_reset", "gemslr_profile_read",
-    "gemslr_setup_batch", "gemslr_batch_apply", "gemslr_batch_fgmres_solve", "gemslr_batch_stats",
+    "gemslr_setup_batch", "gemslr_setup_batch_from_factors", "gemslr_batch_apply", "gemslr_batch_fgmres_solve", "gemslr_batch_stats",
     "gemslr_batch_last_error", "gemslr_batch_destroy",
     "gemslr_learned_train", "gemslr_learned_enable", "gemslr_learned_info", "gemslr_learned_params",
     "gemslr_learned_loss_grad", "gemslr_apply_static", "gemslr_selftest_wait", "gemslr_set_inner_steps",
@@ -119,6 +119,9 @@ def load():
     L.gemslr_profile_read.restype = i32
     L.gemslr_setup_batch.argtypes = [i32, ctypes.POINTER(CSR), ctypes.POINTER(Partition), ctypes.POINTER(Options),
                                      ctypes.POINTER(P)]
+    L.gemslr_setup_batch_from_factors.argtypes = [i32, ctypes.POINTER(CSR), ctypes.POINTER(Partition),
+                                                  ctypes.POINTER(Factors), ctypes.POINTER(Options),
+                                                  ctypes.POINTER(P)]
     L.gemslr_batch_apply.argtypes = [P, P, P, i32, P]
     L.gemslr_batch_fgmres_solve.argtypes = [P, P, P, i32, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), P]
     L.gemslr_batch_stats.argtypes = [P, P, i32]

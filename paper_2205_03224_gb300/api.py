@@ -80,6 +80,21 @@ def _resolve_allocator(opts):
     raise ValueError(f"unknown allocator {a!r}")
 
 
+def _factors_struct(fac, keep):
+    """gemslr_factors view of a factor dict (layout of ``oracle``'s factors()); arrays kept alive in keep."""
+    lv = fac["levels"]
+    arr = (L.LevelFactors * max(len(lv), 1))()
+    keep.append(arr)
+    for i, f in enumerate(lv):
+        W = np.asfortranarray(f["W"], dtype=np.float64)
+        H = np.asfortranarray(f["H"], dtype=np.float64)
+        keep.extend([W, H])
+        arr[i] = L.LevelFactors(L.mat_struct(f["L"], keep), L.mat_struct(f["U"], keep),
+                                L.mat_struct(f["E"], keep), L.mat_struct(f["F"], keep),
+                                W.shape[1], L.ptr(W) if W.size else None, L.ptr(H) if H.size else None)
+    return L.Factors(len(lv) + 1, arr, L.mat_struct(fac["last"]["L"], keep), L.mat_struct(fac["last"]["U"], keep))
+
+
 class Gemslr:
     """Handle of a GeMSLR preconditioner living on the current CUDA device.
 
@@ -110,16 +125,7 @@ class Gemslr:
         keep = []
         csr = L.csr_struct(A, keep)
         prt = L.partition_struct(part, keep)
-        lv = fac["levels"]
-        arr = (L.LevelFactors * max(len(lv), 1))()
-        for i, f in enumerate(lv):
-            W = np.asfortranarray(f["W"], dtype=np.float64)
-            H = np.asfortranarray(f["H"], dtype=np.float64)
-            keep.extend([W, H])
-            arr[i] = L.LevelFactors(L.mat_struct(f["L"], keep), L.mat_struct(f["U"], keep),
-                                    L.mat_struct(f["E"], keep), L.mat_struct(f["F"], keep),
-                                    W.shape[1], L.ptr(W) if W.size else None, L.ptr(H) if H.size else None)
-        fs = L.Factors(len(lv) + 1, arr, L.mat_struct(fac["last"]["L"], keep), L.mat_struct(fac["last"]["U"], keep))
+        fs = _factors_struct(fac, keep)
         alloc = _resolve_allocator(opts)
         o = options(allocator=alloc, **opts)
         h = ctypes.c_void_p()
@@ -299,6 +305,26 @@ class GemslrBatch:
         self._h = h
         self.sizes = [int(c.n) for c in csrs]
         self.nsys = n
+
+    @classmethod
+    def from_factors(cls, As, parts, facs, **opts):
+        """Batch built from given factors, one dict per system (layout of ``oracle``'s factors())."""
+        self = cls.__new__(cls)
+        self._lib = L.load()
+        keep = []
+        n = len(As)
+        csrs = (L.CSR * n)(*[L.csr_struct(A, keep) for A in As])
+        prts = (L.Partition * n)(*[L.partition_struct(p, keep) for p in parts])
+        fss = (L.Factors * n)(*[_factors_struct(f, keep) for f in facs])
+        self._alloc = _resolve_allocator(opts)
+        o = options(allocator=self._alloc, **opts)
+        h = ctypes.c_void_p()
+        L.check(self._lib.gemslr_setup_batch_from_factors(n, csrs, prts, fss, ctypes.byref(o), ctypes.byref(h)),
+                batch=True)
+        self._h = h
+        self.sizes = [int(c.n) for c in csrs]
+        self.nsys = n
+        return self
 
     def close(self):
         if getattr(self, "_h", None):

@@ -421,14 +421,18 @@ double time_ms(cudaStream_t st, const std::function<void()> &fn) {
 }  // namespace
 
 namespace gemslr {
-// Implemented with the single-system setup (solver.cu): factors + low-rank terms of one system.
+// Implemented with the single-system setup (solver.cu): factors + low-rank terms of one system,
+// or the host hierarchy of one system with every factor given.
 void setup_single_host(const gemslr_csr *A, const gemslr_partition *part, const gemslr_options *opt, Hierarchy &out);
+void hierarchy_from_factors(const gemslr_csr *A, const gemslr_partition *part, const gemslr_factors *f,
+                            const gemslr_options &opt, Hierarchy &H);
 }
 
-extern "C" {
-
-gemslr_status gemslr_setup_batch(int32_t nsys, const gemslr_csr *A, const gemslr_partition *part,
-                                 const gemslr_options *opt, gemslr_batch *out) {
+namespace {
+// Batch set-up: every system's hierarchy from the single-system set-up, or
+// (fac non-null, one gemslr_factors per system) from given factors.
+gemslr_status setup_batch(int32_t nsys, const gemslr_csr *A, const gemslr_partition *part, const gemslr_factors *fac,
+                          const gemslr_options *opt, gemslr_batch *out) {
     if (out) *out = nullptr;
     return bguard([&] {
         if (!out || nsys < 1 || !A || !part) fail(GEMSLR_ERR_ARG, "invalid batch arguments");
@@ -440,8 +444,12 @@ gemslr_status gemslr_setup_batch(int32_t nsys, const gemslr_csr *A, const gemslr
         B->nsys = nsys;
         B->sys.resize(nsys);
         B->base.assign(1, 0);
+        gemslr_options o{};
+        gemslr_default_options(&o);
+        if (opt) o = *opt;
         for (int s = 0; s < nsys; ++s) {
-            setup_single_host(&A[s], &part[s], opt, B->sys[s]);
+            if (fac) hierarchy_from_factors(&A[s], &part[s], &fac[s], o, B->sys[s]);
+            else setup_single_host(&A[s], &part[s], opt, B->sys[s]);
             if (s > 0 && B->sys[s].nlev != B->sys[0].nlev) fail(GEMSLR_ERR_PARTITION, "all systems need the same nlev");
             B->base.push_back(B->base.back() + B->sys[s].n);
         }
@@ -517,6 +525,24 @@ gemslr_status gemslr_setup_batch(int32_t nsys, const gemslr_csr *A, const gemslr
         B->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         *out = B.release();
     });
+}
+}  // namespace
+
+extern "C" {
+
+gemslr_status gemslr_setup_batch(int32_t nsys, const gemslr_csr *A, const gemslr_partition *part,
+                                 const gemslr_options *opt, gemslr_batch *out) {
+    return setup_batch(nsys, A, part, nullptr, opt, out);
+}
+
+gemslr_status gemslr_setup_batch_from_factors(int32_t nsys, const gemslr_csr *A, const gemslr_partition *part,
+                                              const gemslr_factors *f, const gemslr_options *opt,
+                                              gemslr_batch *out) {
+    if (!f) {
+        if (out) *out = nullptr;
+        return bguard([&] { fail(GEMSLR_ERR_ARG, "NULL factors"); });
+    }
+    return setup_batch(nsys, A, part, f, opt, out);
 }
 
 static void set_user_layout(gemslr_batch_ctx *B, int nrhs) {

@@ -23,6 +23,7 @@ struct LearnedHost {
 };
 
 struct gemslr_ctx {
+    int dev = -1;                  // CUDA device the handle was set up on
     Hierarchy host;
     gemslr_options opt{};
     Arena arena;
@@ -80,6 +81,16 @@ struct gemslr_ctx {
         if (err_host) cudaFreeHost(err_host);
     }
 };
+
+// The handle's device memory belongs to the device it was set up on: a call
+// made while another device is current is an argument error, not a fault.
+static void require_device(const gemslr_ctx *h) {
+    int dev = -1;
+    GEMSLR_CUDA(cudaGetDevice(&dev));
+    if (dev != h->dev)
+        fail(GEMSLR_ERR_ARG, "the handle lives on device " + std::to_string(h->dev) + " but device " +
+                                 std::to_string(dev) + " is current");
+}
 
 namespace {
 
@@ -625,6 +636,44 @@ void setup_single_host(const gemslr_csr *A, const gemslr_partition *part, const 
     finish_setup(h.get(), true);
     out = std::move(h->host);
 }
+
+// Host hierarchy whose levels are sliced from the partition (A permuted, E and
+// F formed) but whose factors all come from f: nothing is factored.
+void hierarchy_from_factors(const gemslr_csr *A, const gemslr_partition *part, const gemslr_factors *f,
+                            const gemslr_options &opt, Hierarchy &H) {
+    if (!f) fail(GEMSLR_ERR_ARG, "NULL factors");
+    Csr M = csr_from_abi(A);
+    gemslr_options o = opt;
+    o.ilu_kind = GEMSLR_ILU0;       // cheap placeholder factorisation, replaced below
+    for (int l = 0; l < GEMSLR_MAX_LEVELS; ++l) o.rank[l] = 0;
+    build_levels(M, part, &o, H);
+    if (f->nlev != H.nlev || (H.nlev > 1 && !f->levels)) fail(GEMSLR_ERR_ARG, "factor level count mismatch");
+    for (int l = 0; l < H.nlev - 1; ++l) {
+        const gemslr_level_factors &lf = f->levels[l];
+        HostLevel &hl = H.lev[l];
+        const int64_t d = hl.e - hl.s, s = H.n - hl.e;
+        hl.L = csr_from_mat(lf.L);
+        hl.U = csr_from_mat(lf.U);
+        hl.E = csr_from_mat(lf.E);
+        hl.F = csr_from_mat(lf.F);
+        if (hl.L.nrows != d || hl.U.nrows != d || hl.E.nrows != s || hl.E.ncols != d || hl.F.nrows != d ||
+            hl.F.ncols != s)
+            fail(GEMSLR_ERR_ARG, "factor shapes do not match the partition at level " + std::to_string(l));
+        if (lf.k < 0 || lf.k + 2 > kMaxRank) fail(GEMSLR_ERR_ARG, "rank out of range");
+        hl.k = lf.k;
+        hl.W.clear();
+        hl.H.clear();
+        if (lf.k > 0) {
+            if (!lf.W || !lf.H) fail(GEMSLR_ERR_ARG, "W/H missing");
+            hl.W.assign(lf.W, lf.W + (size_t)s * lf.k);
+            hl.H.assign(lf.H, lf.H + (size_t)lf.k * lf.k);
+        }
+    }
+    H.last.L = csr_from_mat(f->last_L);
+    H.last.U = csr_from_mat(f->last_U);
+    if (H.last.L.nrows != H.n - H.last.s || H.last.U.nrows != H.n - H.last.s)
+        fail(GEMSLR_ERR_ARG, "last-level factor shape mismatch");
+}
 }  // namespace gemslr
 
 extern "C" {
@@ -665,6 +714,7 @@ gemslr_status gemslr_setup(const gemslr_csr *A, const gemslr_partition *part, co
         if (!out) fail(GEMSLR_ERR_ARG, "out is NULL");
         auto t0 = std::chrono::steady_clock::now();
         std::unique_ptr<gemslr_ctx> h(new gemslr_ctx());
+        GEMSLR_CUDA(cudaGetDevice(&h->dev));
         h->opt = normalized(opt);
         h->arena.set_allocator(h->opt.dev_alloc, h->opt.dev_free, h->opt.alloc_ctx);
         Csr M = csr_from_abi(A);
@@ -682,39 +732,11 @@ gemslr_status gemslr_setup_from_factors(const gemslr_csr *A, const gemslr_partit
         if (!out || !f) fail(GEMSLR_ERR_ARG, "NULL argument");
         auto t0 = std::chrono::steady_clock::now();
         std::unique_ptr<gemslr_ctx> h(new gemslr_ctx());
+        GEMSLR_CUDA(cudaGetDevice(&h->dev));
         h->opt = normalized(opt);
         h->arena.set_allocator(h->opt.dev_alloc, h->opt.dev_free, h->opt.alloc_ctx);
-        Csr M = csr_from_abi(A);
-        // slice levels from the partition but take every factor from f
-        gemslr_options o = h->opt;
-        o.ilu_kind = GEMSLR_ILU0;       // cheap placeholder factorisation, replaced below
-        for (int l = 0; l < GEMSLR_MAX_LEVELS; ++l) o.rank[l] = 0;
-        build_levels(M, part, &o, h->host);
+        hierarchy_from_factors(A, part, f, h->opt, h->host);
         Hierarchy &H = h->host;
-        if (f->nlev != H.nlev || !f->levels) fail(GEMSLR_ERR_ARG, "factor level count mismatch");
-        for (int l = 0; l < H.nlev - 1; ++l) {
-            const gemslr_level_factors &lf = f->levels[l];
-            HostLevel &hl = H.lev[l];
-            const int64_t d = hl.e - hl.s, s = H.n - hl.e;
-            hl.L = csr_from_mat(lf.L);
-            hl.U = csr_from_mat(lf.U);
-            hl.E = csr_from_mat(lf.E);
-            hl.F = csr_from_mat(lf.F);
-            if (hl.L.nrows != d || hl.U.nrows != d || hl.E.nrows != s || hl.E.ncols != d || hl.F.nrows != d ||
-                hl.F.ncols != s)
-                fail(GEMSLR_ERR_ARG, "factor shapes do not match the partition at level " + std::to_string(l));
-            if (lf.k < 0 || lf.k + 2 > kMaxRank) fail(GEMSLR_ERR_ARG, "rank out of range");
-            hl.k = lf.k;
-            if (lf.k > 0) {
-                if (!lf.W || !lf.H) fail(GEMSLR_ERR_ARG, "W/H missing");
-                hl.W.assign(lf.W, lf.W + (size_t)s * lf.k);
-                hl.H.assign(lf.H, lf.H + (size_t)lf.k * lf.k);
-            }
-        }
-        H.last.L = csr_from_mat(f->last_L);
-        H.last.U = csr_from_mat(f->last_U);
-        if (H.last.L.nrows != H.n - H.last.s || H.last.U.nrows != H.n - H.last.s)
-            fail(GEMSLR_ERR_ARG, "last-level factor shape mismatch");
         finish_setup(h.get(), false);
         for (size_t l = 0; l < H.lev.size(); ++l) set_lowrank<double, double>(h->d64.lev[l], H.lev[l], h->arena);
         if (h->mixed) {
@@ -913,6 +935,7 @@ gemslr_status gemslr_apply(gemslr_handle h, const double *r_dev, double *z_dev, 
     return guard([&] {
         if (!h || nrhs < 0 || (nrhs > 0 && (!r_dev || !z_dev))) fail(GEMSLR_ERR_ARG, "invalid argument");
         if (r_dev == z_dev && nrhs > 0) fail(GEMSLR_ERR_ARG, "r and z must not alias");
+        require_device(h);
         cudaStream_t st = (cudaStream_t)stream;
         const int64_t n = h->host.n;
         ensure_krylov(h, 8);
@@ -931,6 +954,7 @@ gemslr_status gemslr_fgmres_solve(gemslr_handle h, const double *b_dev, double *
     gemslr_status st_ = guard([&] {
         if (!h || !opts || !info || nrhs < 0 || (nrhs > 0 && (!b_dev || !x_dev)))
             fail(GEMSLR_ERR_ARG, "invalid argument");
+        require_device(h);
         if (opts->restart < 1 || opts->maxit < 1 || !(opts->rtol > 0) || opts->ortho < 0 || opts->ortho > 1)
             fail(GEMSLR_ERR_ARG, "invalid solve options");
         cudaStream_t st = (cudaStream_t)stream;
@@ -1534,8 +1558,8 @@ extern "C" gemslr_status gemslr_apply_static(gemslr_handle h, const double *r_de
         if (n > kStaticRows)
             fail(GEMSLR_ERR_ARG, "n = " + std::to_string(n) + " exceeds the static scratch capacity of " +
                                      std::to_string(kStaticRows) + " rows; use gemslr_apply");
-        int dev = 0;
-        GEMSLR_CUDA(cudaGetDevice(&dev));
+        require_device(h);
+        const int dev = h->dev;
         if (dev < 0 || dev >= kMaxDevices) fail(GEMSLR_ERR_ARG, "device index out of range");
         double *base = nullptr;
         {

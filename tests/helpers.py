@@ -47,3 +47,20 @@ def rel_err(a, b):
     a = np.asarray(a)
     b = np.asarray(b)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def bf16(a):
+    """Round float64 -> float32 -> bfloat16 (nearest even) -> float64."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def round_w_to_bf16(M):
+    """Replace every W_l of an oracle hierarchy by its BF16-rounded copy (in place),
+    so that a mixed-precision GPU application of the same factors differs from
+    the FP64 oracle by FP32 rounding only; returns M.factors()."""
+    for lv in M.levels:
+        lv["W"] = bf16(lv["W"])
+    return M.factors()

@@ -138,3 +138,38 @@ def test_batch_splits_right_hand_sides_of_large_blocks(torch_cuda):
             zm = Gm.apply(torch.from_numpy(rv).cuda()).cpu().numpy()
             assert np.linalg.norm(z - zm) <= 1e-4 * np.linalg.norm(zm), (n, r)
         off += n * nrhs
+
+
+def test_batch_apply_matches_oracle(torch_cuda):
+    """Every (system, rhs) of a small uneven batch against the FP64 oracle
+    (Alg. 2), both sides on the oracle's factors with W rounded to BF16 (the
+    batched path keeps W in BF16): what remains is FP32 rounding of the
+    factors, vectors and sums, about 1e-6 relative, bounded at 1e-4."""
+    torch = torch_cuda
+    from oracle import OracleGemslr, multilevel_partition
+    from paper_2205_03224_gb300 import GemslrBatch, partition_geometric
+    from tests.helpers import rel_err, round_w_to_bf16
+    sy, Ms, facs = [], [], []
+    for dims, beta in gi.batch_systems(count=5, seed=13, lo=6, hi=12):
+        A, xyz = gi.grid_operator(dims, beta=beta)
+        As = A.to_scipy()
+        part = partition_geometric(A, xyz, 3, 4)
+        ref = multilevel_partition(As, xyz, 3, 4)
+        assert np.array_equal(part["perm"], ref["perm"])
+        M = OracleGemslr(As, ref, ilu="ilut", tau=1e-3, lfil=10, rank=6)
+        facs.append(round_w_to_bf16(M))
+        Ms.append(M)
+        sy.append((A, part))
+    B = GemslrBatch.from_factors([a for a, _ in sy], [p for _, p in sy], facs)
+    for nrhs in (1, 8):
+        R = _stack(sy, nrhs, 61)
+        Z = B.apply(torch.from_numpy(R).cuda(), nrhs).cpu().numpy()
+        off = 0
+        for (A, _), M in zip(sy, Ms):
+            n = A.n
+            for r in range(nrhs):
+                rv = R[off + r * n: off + (r + 1) * n]
+                z = Z[off + r * n: off + (r + 1) * n]
+                err = rel_err(z, M.apply(rv))
+                assert 0.0 < err <= 1e-4, (n, r, err)
+            off += n * nrhs

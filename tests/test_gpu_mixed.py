@@ -37,6 +37,23 @@ def test_mixed_apply_error_against_fp64_oracle(torch_cuda, name):
     assert err > 0.0          # it really ran in reduced precision
 
 
+@pytest.mark.parametrize("name", ["c1", "small3d", "shifted"])
+def test_mixed_apply_with_bf16_w_is_fp32_accurate(torch_cuda, name):
+    """With W rounded to BF16 on both sides the mixed application differs
+    from the FP64 oracle by FP32 rounding only (about 1e-6 relative)."""
+    torch = torch_cuda
+    from oracle import OracleGemslr
+    from paper_2205_03224_gb300 import Gemslr
+    from tests.helpers import CASES, round_w_to_bf16
+    dims, beta, sigma, nlev, p, ilu, tau, lfil, rank = CASES[name]
+    A, xyz, part = problem(name)
+    M = OracleGemslr(A.to_scipy(), part, ilu=ilu, tau=tau, lfil=lfil, rank=rank)
+    G = Gemslr.from_factors(A, part, round_w_to_bf16(M), precision="mixed")
+    r = gi.rhs_uniform(M.n, 22)
+    err = rel_err(G.apply(torch.from_numpy(r).cuda()).cpu().numpy(), M.apply(r))
+    assert 0.0 < err <= 1e-4, err
+
+
 @pytest.mark.parametrize("name", ["c1", "small3d", "c2"])
 def test_mixed_fgmres_reaches_1e8(torch_cuda, name):
     torch = torch_cuda
