@@ -1,4 +1,5 @@
-"""ctypes loader for the oracle's plain C loops (oracle/c/oracle_ilu.c).
+"""ctypes loader for the oracle's plain C loops (oracle/c/oracle_ilu.c and
+its complex counterpart oracle/c/oracle_ilu_z.c).
 
 Compiles the shared object with gcc on first use when it is missing or older
 than its source.  -ffp-contract=off keeps every multiply and add separately
@@ -9,14 +10,14 @@ import os
 import subprocess
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "c", "oracle_ilu.c")
+_SRCS = [os.path.join(_HERE, "c", "oracle_ilu.c"), os.path.join(_HERE, "c", "oracle_ilu_z.c")]
 _LIB = os.path.join(_HERE, "_oracle_ilu.so")
 _lib = None
 
 
 def build():
     cmd = ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c99",
-           "-o", _LIB, _SRC, "-lm"]
+           "-o", _LIB, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
 
 
@@ -34,7 +35,7 @@ class Factors(ctypes.Structure):
 def lib():
     global _lib
     if _lib is None:
-        if (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        if (not os.path.exists(_LIB)) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in _SRCS):
             build()
         L = ctypes.CDLL(_LIB)
         P = ctypes.c_void_p
@@ -44,8 +45,15 @@ def lib():
         L.oracle_ilut.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_double, ctypes.c_int64]
         L.oracle_free_factors.argtypes = [ctypes.POINTER(Factors)]
         L.oracle_free_factors.restype = None
-        for f in (L.oracle_lsolve, L.oracle_usolve):
+        for f in (L.oracle_lsolve, L.oracle_usolve, L.oracle_lsolve_z, L.oracle_usolve_z):
             f.argtypes = [ctypes.c_int64, P, P, P, P, P]
             f.restype = None
+        # complex factors: the same struct, lv/uv holding (re, im) pairs
+        L.oracle_ilu0_z.restype = ctypes.POINTER(Factors)
+        L.oracle_ilu0_z.argtypes = [ctypes.c_int64, P, P, P]
+        L.oracle_ilut_z.restype = ctypes.POINTER(Factors)
+        L.oracle_ilut_z.argtypes = [ctypes.c_int64, P, P, P, ctypes.c_double, ctypes.c_int64]
+        L.oracle_free_factors_z.argtypes = [ctypes.POINTER(Factors)]
+        L.oracle_free_factors_z.restype = None
         _lib = L
     return _lib

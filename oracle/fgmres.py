@@ -8,6 +8,12 @@ Per cycle (Saad 1993, the flexible variant; the paper's outer solver):
      Givens rotations reduce H to triangular form; |g_{j+1}| is the residual
      norm estimate; the cycle stops when |g_{j+1}| <= rtol * ||b||.
   x = x_0 + Z_j y_j with y_j = R_j^{-1} g_{1:j}; r = b - A x (true residual).
+Complex arithmetic (``cplx``: a complex preconditioner, e.g. the complex
+shift of Sec. 5.2.3, or complex b): inner products h_ij = v_i^H w and the
+complex Givens rotation [[conj(c), conj(s)], [-s, c]] with c = h_jj / d,
+s = h_{j+1,j} / d, d = sqrt(|h_jj|^2 + h_{j+1,j}^2); for real data these are
+the real formulas.  The iterate is then complex; for real A and b the real
+part of x has a residual no larger than that of x.
 Convergence is declared on the true residual ||b - A x|| <= rtol * ||b||;
 otherwise the method restarts from x.  Iterations count inner steps, capped at
 ``maxit`` (1,000 in the paper: "F").  A happy breakdown
@@ -16,11 +22,13 @@ otherwise the method restarts from x.  Iterations count inner steps, capped at
 import numpy as np
 
 
-def fgmres(A, b, apply_M, restart=50, rtol=1e-8, maxit=1000, x0=None, flexible=True):
+def fgmres(A, b, apply_M, restart=50, rtol=1e-8, maxit=1000, x0=None, flexible=True, cplx=False):
     """Returns (x, info) with info = dict(iters, restarts, converged, hist, rel_res_true)."""
-    b = np.asarray(b, dtype=np.float64)
+    cplx = bool(cplx) or np.iscomplexobj(b)
+    dt = np.complex128 if cplx else np.float64
+    b = np.asarray(b, dtype=dt)
     n = b.shape[0]
-    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    x = np.zeros(n, dtype=dt) if x0 is None else np.array(x0, dtype=dt)
     bnorm = np.linalg.norm(b)
     hist = []
     its = 0
@@ -32,12 +40,12 @@ def fgmres(A, b, apply_M, restart=50, rtol=1e-8, maxit=1000, x0=None, flexible=T
     converged = beta <= rtol * bnorm
     while not converged and its < maxit:
         m = restart
-        V = np.zeros((n, m + 1))
-        Z = np.zeros((n, m))
-        H = np.zeros((m + 1, m))
-        cs = np.zeros(m)
-        sn = np.zeros(m)
-        g = np.zeros(m + 1)
+        V = np.zeros((n, m + 1), dtype=dt)
+        Z = np.zeros((n, m), dtype=dt)
+        H = np.zeros((m + 1, m), dtype=dt)
+        cs = np.zeros(m, dtype=dt)
+        sn = np.zeros(m, dtype=dt)
+        g = np.zeros(m + 1, dtype=dt)
         g[0] = beta
         V[:, 0] = r / beta
         jdone = 0
@@ -47,28 +55,28 @@ def fgmres(A, b, apply_M, restart=50, rtol=1e-8, maxit=1000, x0=None, flexible=T
             its += 1
             wn0 = np.linalg.norm(w)
             for i in range(j + 1):                       # modified Gram-Schmidt
-                H[i, j] = V[:, i] @ w
+                H[i, j] = np.vdot(V[:, i], w) if cplx else V[:, i] @ w
                 w = w - H[i, j] * V[:, i]
             H[j + 1, j] = np.linalg.norm(w)
-            breakdown = H[j + 1, j] <= 1e-14 * wn0
+            breakdown = abs(H[j + 1, j]) <= 1e-14 * wn0
             if not breakdown:
                 V[:, j + 1] = w / H[j + 1, j]
             for i in range(j):                           # previous rotations
-                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                t = np.conj(cs[i]) * H[i, j] + np.conj(sn[i]) * H[i + 1, j]
                 H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
                 H[i, j] = t
-            den = np.hypot(H[j, j], H[j + 1, j])
+            den = np.hypot(abs(H[j, j]), abs(H[j + 1, j]))
             cs[j] = H[j, j] / den
             sn[j] = H[j + 1, j] / den
             H[j, j] = den
             H[j + 1, j] = 0.0
             g[j + 1] = -sn[j] * g[j]
-            g[j] = cs[j] * g[j]
+            g[j] = np.conj(cs[j]) * g[j]
             hist.append(abs(g[j + 1]) / bnorm)
             jdone = j + 1
             if abs(g[j + 1]) <= rtol * bnorm or breakdown or its >= maxit:
                 break
-        y = np.zeros(jdone)
+        y = np.zeros(jdone, dtype=dt)
         for i in range(jdone - 1, -1, -1):               # R y = g
             y[i] = (g[i] - H[i, i + 1:jdone] @ y[i + 1:]) / H[i, i]
         if flexible:

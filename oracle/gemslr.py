@@ -19,13 +19,16 @@ from .lowrank import correction_matrix, krylov_schur
 from .partition import level_blocks
 
 
-def _factor_blocks(B, bp, kind, tau, lfil):
-    """Incomplete LU of every diagonal block of B; block-diagonal L, U."""
+def _factor_blocks(B, bp, kind, tau, lfil, alpha=0.0):
+    """Incomplete LU of every diagonal block of B (of B_j + i alpha I when
+    alpha != 0, the complex shift of Sec. 5.2.3); block-diagonal L, U."""
     Ls, Us = [], []
     nclamp = 0
     for j in range(len(bp) - 1):
         a, b = bp[j], bp[j + 1]
         Bj = B[a:b, a:b]
+        if alpha != 0.0:
+            Bj = sp.csr_matrix(Bj, dtype=complex) + 1j * alpha * sp.eye(b - a, format="csr")
         if kind == "ilu0":
             L, U, c = _ilu.ilu0(Bj)
         elif kind == "ilut":
@@ -61,6 +64,12 @@ class OracleGemslr:
     inner_steps : Alg. 2 step 9; 0 applies the standard recursion at level 0,
         k > 0 solves S_hat_0 y2 = z2 there by k steps of right-preconditioned
         GMRES (``inner_gmres``)
+    shift : complex diagonal shift of the incomplete factorisations (Sec. 5.2.3):
+        every diagonal block of every B_l and of the last level is factored
+        as B + i alpha I with alpha = shift * sum_i |a_ii| / n (the paper uses
+        shift = 0.05); E, F and C are not shifted.  With shift != 0 the
+        factors, W, H and every vector of the application are complex, and
+        the correction is W H W^H (Sec. 2.2).
 
     Attribute ``stage`` (default None): an extra correction of the deepest
     Schur level l* = nlev - 2, a callable (z2, y2) -> y2' applied after y2 is
@@ -70,10 +79,12 @@ class OracleGemslr:
     """
 
     def __init__(self, A, part, ilu="ilu0", tau=1e-3, lfil=10, rank=8, last_ilu=None,
-                 arnoldi_tol=1e-2, max_cycles=20, lowrank=True, inner_steps=0):
+                 arnoldi_tol=1e-2, max_cycles=20, lowrank=True, inner_steps=0, shift=0.0):
         self.inner_steps = int(inner_steps)
         self.stage = None
         A = sp.csr_matrix(A)
+        self.shift = float(shift)
+        self.alpha = self.shift * float(np.abs(A.diagonal()).sum()) / A.shape[0] if A.shape[0] else 0.0
         self.n = A.shape[0]
         self.part = part
         self.perm = np.asarray(part["perm"], dtype=np.int64)
@@ -89,7 +100,7 @@ class OracleGemslr:
             s, e, bp = level_blocks(part, l)
             bp = bp - s
             B = Ah[s:e, s:e]
-            L, U, c = _factor_blocks(B, bp, ilu, tau, lfil)
+            L, U, c = _factor_blocks(B, bp, ilu, tau, lfil, self.alpha)
             self.nclamp += c
             self.levels.append(dict(s=s, e=e, bp=bp, L=L, U=U,
                                     E=Ah[e:, s:e].tocsr(), F=Ah[s:e, e:].tocsr(),
@@ -104,7 +115,7 @@ class OracleGemslr:
         self.last_s = s
         self.last_bp = bp
         self.last_C = keep
-        Lc, Uc, c = _factor_blocks(keep, bp, last_ilu or ilu, tau, lfil)
+        Lc, Uc, c = _factor_blocks(keep, bp, last_ilu or ilu, tau, lfil, self.alpha)
         self.nclamp += c
         self.last_L, self.last_U = Lc, Uc
         if lowrank:
@@ -135,7 +146,7 @@ class OracleGemslr:
         """eq. gemslr6 at level l: C_l^-1 (z2 + W_l H_l W_l^T z2), C_l^-1 the levels below."""
         lv = self.levels[l]
         W, H = lv["W"], lv["H"]
-        u2 = W @ (H @ (W.T @ z2)) if W.shape[1] else np.zeros_like(z2)
+        u2 = W @ (H @ (W.conj().T @ z2)) if W.shape[1] else np.zeros_like(z2)
         return self.solve_level(u2 + z2, l + 1)
 
     def s_hat(self, v, l):
@@ -177,11 +188,13 @@ class OracleGemslr:
 
     def apply_perm(self, r_hat):
         """M^{-1} in the multilevel ordering."""
-        return self.solve_level(np.asarray(r_hat, dtype=np.float64), 0)
+        r_hat = np.asarray(r_hat)
+        dt = np.complex128 if (self.alpha != 0.0 or np.iscomplexobj(r_hat)) else np.float64
+        return self.solve_level(r_hat.astype(dt), 0)
 
     def apply(self, r):
         """M^{-1} r in the original ordering: P (M_hat^{-1} (P^T r))."""
-        y = self.apply_perm(np.asarray(r, dtype=np.float64)[self.perm])
+        y = self.apply_perm(np.asarray(r)[self.perm])
         out = np.empty_like(y)
         out[self.perm] = y
         return out
@@ -196,7 +209,7 @@ class OracleGemslr:
         lv = self.levels[l]
         s = self.n - lv["e"]
         W, Tk, info = krylov_schur(lambda z: self.g_hat(l, z), s, lv["rank"], 1000 + l,
-                                   tol=tol, max_cycles=max_cycles)
+                                   tol=tol, max_cycles=max_cycles, complex_arith=self.alpha != 0.0)
         lv["W"] = W
         lv["T"] = Tk
         lv["H"] = correction_matrix(Tk)

@@ -21,6 +21,10 @@ Readings where the paper leaves details open (Sec. 4.2, Sec. 5 set-up):
     the basis chosen for the subspace); at most 20 cycles.
   * When s_l <= m the operator is formed densely (s_l applications to unit
     vectors) and its full real Schur form is used.
+  * Complex arithmetic (the complex-shifted factors of Sec. 5.2.3 make G_hat
+    complex): V^H w inner products and the complex Schur form H_m = Q T Q^H
+    (the form Sec. 2.2 states); values are ranked by the same score and
+    exactly k are kept (no conjugate pairs exist to keep whole).
 """
 import numpy as np
 import scipy.linalg as sla
@@ -106,12 +110,35 @@ def schur_wanted(Hm, k):
     return T, Q, keff
 
 
-def krylov_schur(op, s, k, seed, tol=1e-2, max_cycles=20, m=None):
+def schur_wanted_complex(Hm, k):
+    """Complex Schur form Hm = Q T Q^H with the k wanted values leading."""
+    m = Hm.shape[0]
+    if k >= m:
+        T, Q = sla.schur(Hm.astype(complex), output="complex")
+        return T, Q, m
+    T0, _ = sla.schur(Hm.astype(complex), output="complex")
+    theta = np.diag(T0)
+    sc = correction_score(theta)
+    order = np.lexsort((np.arange(m), -np.abs(theta), -sc))
+    sel, rest = order[:k], order[k:]
+    inside, outside = sc[sel].min(), sc[rest].max()
+    if not inside > outside:
+        raise ValueError("wanted set not separable by the correction score")
+    thr = 0.5 * (inside + outside) if np.isfinite(inside) else outside * 2.0 + 1.0
+    T, Q, sdim = sla.schur(Hm.astype(complex), output="complex", sort=lambda z: correction_score(z) > thr)
+    if sdim != k:
+        raise ValueError(f"reordered Schur form selected {sdim} values, expected {k}")
+    return T, Q, k
+
+
+def krylov_schur(op, s, k, seed, tol=1e-2, max_cycles=20, m=None, complex_arith=False):
     """W (s x keff), T_k (keff x keff) and diagnostics for the operator ``op``.
 
-    ``op`` maps an s-vector to G_hat times it.
+    ``op`` maps an s-vector to G_hat times it; complex_arith for a complex G_hat.
     """
     info = dict(cycles=0, dense=False, keff=0, ritz=np.zeros(0, dtype=complex))
+    if complex_arith:
+        return _krylov_schur_complex(op, s, k, seed, tol, max_cycles, m, info)
     if k <= 0 or s == 0:
         return np.zeros((s, 0)), np.zeros((0, 0)), info
     m = 2 * k if m is None else m
@@ -172,10 +199,72 @@ def krylov_schur(op, s, k, seed, tol=1e-2, max_cycles=20, m=None):
     raise AssertionError("unreachable")
 
 
+def _krylov_schur_complex(op, s, k, seed, tol, max_cycles, m, info):
+    """krylov_schur in complex arithmetic (same steps, V^H inner products,
+    complex Schur form)."""
+    if k <= 0 or s == 0:
+        return np.zeros((s, 0), dtype=complex), np.zeros((0, 0), dtype=complex), info
+    m = 2 * k if m is None else m
+    if s <= m:
+        G = np.zeros((s, s), dtype=complex)
+        e = np.zeros(s, dtype=complex)
+        for i in range(s):
+            e[i] = 1.0
+            G[:, i] = op(e)
+            e[i] = 0.0
+        T, Q, keff = schur_wanted_complex(G, k)
+        info.update(dense=True, keff=keff, ritz=np.diag(T)[:keff])
+        return Q[:, :keff].copy(), T[:keff, :keff].copy(), info
+    v = (2.0 * gemslr_inputs.uniform01(seed, s) - 1.0).astype(complex)
+    V = np.zeros((s, m + 1), dtype=complex)
+    Hb = np.zeros((m + 1, m), dtype=complex)
+    V[:, 0] = v / np.linalg.norm(v)
+    p = 0
+    for cycle in range(max_cycles):
+        info["cycles"] = cycle + 1
+        mm = m
+        beta = 0.0
+        for j in range(p, m):
+            w = op(V[:, j])
+            wn0 = np.linalg.norm(w)
+            h = V[:, :j + 1].conj().T @ w
+            w = w - V[:, :j + 1] @ h
+            h2 = V[:, :j + 1].conj().T @ w
+            w = w - V[:, :j + 1] @ h2
+            h = h + h2
+            beta = np.linalg.norm(w)
+            Hb[:j + 1, j] = h
+            Hb[j + 1, j] = beta
+            if beta <= 1e-14 * max(wn0, 1e-300):
+                mm = j + 1
+                beta = 0.0
+                break
+            V[:, j + 1] = w / beta
+        Hm = Hb[:mm, :mm]
+        T, Q, keff = schur_wanted_complex(Hm, k)
+        theta = np.diag(T)
+        resid = np.linalg.norm(beta * Q[mm - 1, :keff])
+        ok = resid <= tol * np.min(np.abs(theta[:keff])) or beta == 0.0
+        if ok or cycle == max_cycles - 1:
+            info.update(keff=keff, ritz=theta[:keff], converged=bool(ok), resid=resid)
+            return V[:, :mm] @ Q[:, :keff], T[:keff, :keff].copy(), info
+        Vk = V[:, :mm] @ Q[:, :keff]
+        vnext = V[:, mm].copy()
+        V[:] = 0.0
+        V[:, :keff] = Vk
+        V[:, keff] = vnext
+        bk = beta * Q[mm - 1, :keff]
+        Hb[:] = 0.0
+        Hb[:keff, :keff] = T[:keff, :keff]
+        Hb[keff, :keff] = bk
+        p = keff
+    raise AssertionError("unreachable")
+
+
 def correction_matrix(Tk):
     """H = (I - T_k)^{-1} - I, the k x k middle factor of eq. (gemslr5)."""
     k = Tk.shape[0]
     if k == 0:
-        return np.zeros((0, 0))
+        return np.zeros((0, 0), dtype=Tk.dtype)
     I = np.eye(k)
     return np.linalg.solve(I - Tk, I) - I
