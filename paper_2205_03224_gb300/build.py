@@ -49,7 +49,7 @@ def _compile(src):
         cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
                "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
     else:
-        cmd = ["g++", "-O2", "-fPIC", "-std=c++17", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC,
+        cmd = ["g++", "-O2", "-fPIC", "-pthread", "-std=c++17", "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC,
                "-I", _cuda_include(), "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -64,7 +64,7 @@ def build(force=False):
     os.makedirs(OUT_DIR, exist_ok=True)
     with ThreadPoolExecutor(max_workers=len(_sources())) as ex:
         objs = list(ex.map(_compile, _sources()))
-    cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+    cmd = [_nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

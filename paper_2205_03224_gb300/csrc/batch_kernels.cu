@@ -141,12 +141,57 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
     }
 }
 
-// z2 = b2 - E z1 on the CTA's tail rows, partial W_s^T z2, and (last CTA of
-// the system) u_s = H_s (W_s^T z2).
+// ---- BF16 tensor-core products with W (mma.sync m16n8k16, FP32 accumulation) ----------
+// The 8 right-hand sides are the n = 8 of the tile.  W is stored in BF16; the
+// FP32 vector operand is split into two BF16 terms v = hi + lo (hi = bf16(v),
+// lo = bf16(v - hi)), so that each product carries about 16 significant bits
+// of the vector (relative error ~2^-16) and W's own BF16 rounding is the only
+// reduced-precision step, as in the CUDA-core path.
+__device__ __forceinline__ uint32_t pack_bf16(float lo_elem, float hi_elem) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo_elem, hi_elem);   // .x (low 16 bits) = lo_elem
+    return *reinterpret_cast<const uint32_t *>(&p);
+}
+__device__ __forceinline__ void split_bf16(float v, float &hi, float &lo) {
+    hi = __bfloat162float(__float2bfloat16_rn(v));
+    lo = v - hi;
+}
+// D (16 x 8, FP32) += A (16 x 16, BF16, row-major fragment) * B (16 x 8, BF16, column-major fragment).
+__device__ __forceinline__ void mma_bf16_16816(float d[4], const uint32_t a[4], const uint32_t b[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// Fragment coordinates of m16n8k16 for lane = 4 * g + t (g = group 0..7, t = 0..3):
+//   A: a[0] rows g, cols 2t, 2t+1; a[1] rows g+8, cols 2t, 2t+1; a[2] row g, cols 2t+8, 2t+9;
+//      a[3] row g+8, cols 2t+8, 2t+9 (lower column in the low 16 bits);
+//   B: b[0] rows (k) 2t, 2t+1, col (n) g; b[1] rows 2t+8, 2t+9, col g;
+//   D: d[0], d[1] row g, cols 2t, 2t+1; d[2], d[3] row g+8, cols 2t, 2t+1.
+// B fragments (hi and lo) of a K-slice [kk, kk+16) of a row-major k x 8 FP32
+// matrix in shared memory (rows past kmax are zero).
+__device__ __forceinline__ void b_frag_split(const float *M8, int kk, int kmax, int lane, uint32_t bh[2],
+                                             uint32_t bl[2]) {
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int r0 = kk + 2 * t + 8 * h, r1 = r0 + 1;
+        const float v0 = r0 < kmax ? M8[r0 * R8 + g] : 0.f, v1 = r1 < kmax ? M8[r1 * R8 + g] : 0.f;
+        float h0, l0, h1, l1;
+        split_bf16(v0, h0, l0);
+        split_bf16(v1, h1, l1);
+        bh[h] = pack_bf16(h0, h1);
+        bl[h] = pack_bf16(l0, l1);
+    }
+}
+
+// z2 = b2 - E z1 on the CTA's tail rows, partial W_s^T z2 (tensor cores), and
+// (last CTA of the system) u_s = H_s (W_s^T z2).
 __global__ void __launch_bounds__(kBatchThreads)
 k_bcouple(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ work) {
     __shared__ float zs[256 * R8];
     __shared__ float ts[kBatchMaxRank * R8];
+    __shared__ float half2[kBatchMaxRank * R8];
     const int c = blockIdx.x, s = lv.cta_seg[c];
     const int64_t i0 = lv.cta_i0[c], len = lv.seg_len[s];
     const int rows = (int)min((int64_t)lv.rows_cta, len - i0);
@@ -162,16 +207,50 @@ k_bcouple(const BatchLevel lv, const double *__restrict__ in, float *__restrict_
     const int k = lv.seg_k[s];
     if (k == 0) return;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int r = lane & 7, ig = lane >> 3;
+    // partial W^T z: M = columns of W (16 per tile), K = the CTA's rows, N = 8 rhs.
+    // Warp w takes column tile w % 4 and every other K-slice (parity w / 4).
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
     const __nv_bfloat16 *Ws = lv.W + lv.seg_w0[s];
-    for (int cc = warp; cc < k; cc += nw) {
-        float acc = 0.f;
-        const __nv_bfloat16 *wc = Ws + (int64_t)cc * len + i0;
-        for (int i = ig; i < rows; i += 4) acc += __bfloat162float(wc[i]) * zs[i * R8 + r];
-        acc += __shfl_xor_sync(0xffffffffu, acc, 8);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 16);
-        if (ig == 0) lv.partial[((int64_t)c * kBatchMaxRank + cc) * R8 + r] = acc;
+    const int mt = warp & 3, par = warp >> 2;
+    const int ntile = (k + 15) / 16;
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    if (mt < ntile) {
+        const int ca = 16 * mt + g, cb = ca + 8;          // the two W columns of this lane's A rows
+        const __nv_bfloat16 z16 = __float2bfloat16_rn(0.f);
+        for (int kk = 16 * par; kk < rows; kk += 32) {
+            uint32_t a[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {                 // h = 0: K cols 2t, 2t+1; h = 1: + 8
+                const int i = kk + 2 * t + 8 * h;
+                const __nv_bfloat16 wa0 = (ca < k && i < rows) ? Ws[(int64_t)ca * len + i0 + i] : z16;
+                const __nv_bfloat16 wa1 = (ca < k && i + 1 < rows) ? Ws[(int64_t)ca * len + i0 + i + 1] : z16;
+                const __nv_bfloat16 wb0 = (cb < k && i < rows) ? Ws[(int64_t)cb * len + i0 + i] : z16;
+                const __nv_bfloat16 wb1 = (cb < k && i + 1 < rows) ? Ws[(int64_t)cb * len + i0 + i + 1] : z16;
+                a[2 * h] = (uint32_t)__bfloat16_as_ushort(wa0) | ((uint32_t)__bfloat16_as_ushort(wa1) << 16);
+                a[2 * h + 1] = (uint32_t)__bfloat16_as_ushort(wb0) | ((uint32_t)__bfloat16_as_ushort(wb1) << 16);
+            }
+            uint32_t bh[2], bl[2];
+            b_frag_split(zs, kk, rows, lane, bh, bl);
+            mma_bf16_16816(d, a, bh);
+            mma_bf16_16816(d, a, bl);
+        }
+    }
+    // the two K-parities of a column tile are added in a fixed order
+    if (par == 1 && mt < ntile) {
+        half2[(16 * mt + g) * R8 + 2 * t] = d[0];
+        half2[(16 * mt + g) * R8 + 2 * t + 1] = d[1];
+        half2[(16 * mt + g + 8) * R8 + 2 * t] = d[2];
+        half2[(16 * mt + g + 8) * R8 + 2 * t + 1] = d[3];
+    }
+    __syncthreads();
+    if (par == 0 && mt < ntile) {
+        const int rr[4] = {16 * mt + g, 16 * mt + g, 16 * mt + g + 8, 16 * mt + g + 8};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int cc = rr[q], col = 2 * t + (q & 1);
+            if (cc < k) lv.partial[((int64_t)c * kBatchMaxRank + cc) * R8 + col] = d[q] + half2[cc * R8 + col];
+        }
     }
     const int ca = lv.seg_cta0[s], cb = lv.seg_cta0[s + 1];
     if (!last_of(&lv.seg_counter[s], (unsigned)(cb - ca))) return;
@@ -186,13 +265,14 @@ k_bcouple(const BatchLevel lv, const double *__restrict__ in, float *__restrict_
     for (int idx = threadIdx.x; idx < k * R8; idx += blockDim.x) {
         const int cc = idx / R8, rr = idx % R8;
         float acc = 0.f;
-        for (int d = 0; d < k; ++d) acc += Hs[cc + (int64_t)d * k] * ts[d * R8 + rr];
+        for (int d2 = 0; d2 < k; ++d2) acc += Hs[cc + (int64_t)d2 * k] * ts[d2 * R8 + rr];
         lv.u[((int64_t)s * kBatchMaxRank + cc) * R8 + rr] = acc;
     }
     if (threadIdx.x == 0) lv.seg_counter[s] = 0u;
 }
 
-// work[tail] += W_s u_s
+// work[tail] += W_s u_s (tensor cores: M = 16 tail rows per tile, K = the rank,
+// N = 8 rhs; each warp takes every eighth row tile).
 __global__ void __launch_bounds__(kBatchThreads)
 k_blowrank(const BatchLevel lv, float *__restrict__ work) {
     __shared__ float us[kBatchMaxRank * R8];
@@ -205,11 +285,37 @@ k_blowrank(const BatchLevel lv, float *__restrict__ work) {
     __syncthreads();
     const __nv_bfloat16 *Ws = lv.W + lv.seg_w0[s];
     const int64_t g0 = lv.seg_r0[s] + i0;
-    for (int idx = threadIdx.x; idx < rows * R8; idx += blockDim.x) {
-        const int i = idx / R8, r = idx % R8;
-        float acc = 0.f;
-        for (int cc = 0; cc < k; ++cc) acc += __bfloat162float(Ws[(int64_t)cc * len + i0 + i]) * us[cc * R8 + r];
-        work[(g0 + i) * R8 + r] += acc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const __nv_bfloat16 z16 = __float2bfloat16_rn(0.f);
+    for (int rt = warp; 16 * rt < rows; rt += nw) {
+        const int ra = 16 * rt + g, rb = ra + 8;          // this lane's two A rows
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int kk = 0; kk < k; kk += 16) {
+            uint32_t a[4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {                 // K cols 2t, 2t+1 (+ 8 for h = 1)
+                const int cc = kk + 2 * t + 8 * h;
+                const __nv_bfloat16 wa0 = (ra < rows && cc < k) ? Ws[(int64_t)cc * len + i0 + ra] : z16;
+                const __nv_bfloat16 wa1 = (ra < rows && cc + 1 < k) ? Ws[(int64_t)(cc + 1) * len + i0 + ra] : z16;
+                const __nv_bfloat16 wb0 = (rb < rows && cc < k) ? Ws[(int64_t)cc * len + i0 + rb] : z16;
+                const __nv_bfloat16 wb1 = (rb < rows && cc + 1 < k) ? Ws[(int64_t)(cc + 1) * len + i0 + rb] : z16;
+                a[2 * h] = (uint32_t)__bfloat16_as_ushort(wa0) | ((uint32_t)__bfloat16_as_ushort(wa1) << 16);
+                a[2 * h + 1] = (uint32_t)__bfloat16_as_ushort(wb0) | ((uint32_t)__bfloat16_as_ushort(wb1) << 16);
+            }
+            uint32_t bh[2], bl[2];
+            b_frag_split(us, kk, k, lane, bh, bl);
+            mma_bf16_16816(d, a, bh);
+            mma_bf16_16816(d, a, bl);
+        }
+        if (ra < rows) {
+            work[(g0 + ra) * R8 + 2 * t] += d[0];
+            work[(g0 + ra) * R8 + 2 * t + 1] += d[1];
+        }
+        if (rb < rows) {
+            work[(g0 + rb) * R8 + 2 * t] += d[2];
+            work[(g0 + rb) * R8 + 2 * t + 1] += d[3];
+        }
     }
 }
 

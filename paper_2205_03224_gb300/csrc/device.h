@@ -214,6 +214,8 @@ void net_backward(NetDev &net, int N, const float *x0, float *const zs[4], float
                   float *gbuf0, float *gbuf1, float *part, int nchunk, cudaStream_t st);
 void net_adam(NetDev &net, float lr, cudaStream_t st);
 void net_sync_bf16(NetDev &net, cudaStream_t st);
+// Shared-memory limits of the tensor-core convolutions (once per device, before any capture).
+void net_kernels_init();
 void launch_uniform(uint64_t seed, int64_t count, double *out, cudaStream_t st);
 void launch_dgemm(int M, int N, int K, const double *A, const double *B, double *C, cudaStream_t st);
 void launch_scale_pairs(int S, int count, const double *R, const double *T, double d, float *X, float *Y,

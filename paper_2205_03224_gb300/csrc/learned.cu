@@ -141,6 +141,224 @@ k_conv_bwd_w(int NS, int S, int Cin, int Cout, const float *__restrict__ x, cons
     }
 }
 
+// ---- tensor-core convolutions (BF16 mma.sync m16n8k16, FP32 accumulation) ----------------
+// For the C -> C layers (C >= 8).  Every tap is a small GEMM over gathered
+// rows: forward Y[s, co] += X[nbr(s, t), :] W_t, data gradient
+// dX[u, ci] += dY[nbr(u, 26 - t), :] W_t^T, weight gradient
+// dW_t[ci, co] += X[nbr(s, t), ci]^T dY[s, co].  The weights are BF16 as in
+// the CUDA-core kernels; an FP32 activation or gradient operand is split into
+// two BF16 terms (v = hi + lo, hi = bf16(v)), so that the products keep about
+// 16 significant bits of it (weight gradients: hi*hi + hi*lo + lo*hi).
+// Fragment coordinates of m16n8k16 (lane = 4 g + q):
+//   A: a[0] (row g, cols 2q, 2q+1), a[1] (row g+8, same cols), a[2] (row g, cols 2q+8, 2q+9),
+//      a[3] (row g+8, cols 2q+8, 2q+9); B: b[0] (rows 2q, 2q+1, col g), b[1] (rows 2q+8, 2q+9, col g);
+//   D: d[0], d[1] (row g, cols 2q, 2q+1), d[2], d[3] (row g+8, same cols).
+constexpr int kConvTcWarps = 4;                 // 16-site tiles per CTA (forward, data gradient)
+
+__device__ __forceinline__ uint32_t bf16_pair(float lo_elem, float hi_elem) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo_elem, hi_elem);
+    return *reinterpret_cast<const uint32_t *>(&p);
+}
+__device__ __forceinline__ void split2(float v0, float v1, uint32_t &hi, uint32_t &lo) {
+    const float h0 = __bfloat162float(__float2bfloat16_rn(v0)), h1 = __bfloat162float(__float2bfloat16_rn(v1));
+    hi = bf16_pair(h0, h1);
+    lo = bf16_pair(v0 - h0, v1 - h1);
+}
+__device__ __forceinline__ void mma16816(float d[4], const uint32_t a[4], const uint32_t b0, const uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// Two BF16 weights w[i0], w[i1] (element indices, out-of-range as zero) packed low/high.
+__device__ __forceinline__ uint32_t w_pair(const __nv_bfloat16 *w, bool ok0, int i0, bool ok1, int i1) {
+    const uint32_t lo = ok0 ? (uint32_t)__bfloat16_as_ushort(w[i0]) : 0u;
+    const uint32_t hi = ok1 ? (uint32_t)__bfloat16_as_ushort(w[i1]) : 0u;
+    return lo | (hi << 16);
+}
+
+// z = b + sum_t X[nbr(s, t)] W_t (h = relu(z) when relu); grid (ceil(S / 64), N),
+// kConvTcWarps warps, dynamic shared memory 27 * Cin * Cout BF16 (all taps).
+__global__ void __launch_bounds__(32 * kConvTcWarps)
+k_conv_fwd_tc(int S, int Cin, int Cout, const float *__restrict__ x, const __nv_bfloat16 *__restrict__ W,
+              const float *__restrict__ b, const int32_t *__restrict__ nbr, float *__restrict__ z,
+              float *__restrict__ h, int relu) {
+    extern __shared__ __align__(16) unsigned char conv_smem[];
+    __nv_bfloat16 *Ws = reinterpret_cast<__nv_bfloat16 *>(conv_smem);
+    const int nw = 27 * Cin * Cout;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) Ws[i] = W[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
+    const int n = blockIdx.y;
+    const int sa = (blockIdx.x * kConvTcWarps + warp) * 16 + g, sb = sa + 8;
+    const float *xn = x + (int64_t)n * S * Cin;
+    const int ntn = (Cout + 7) / 8;                  // n-tiles of 8 output channels (<= 4)
+    float d[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+        const int c0 = nt * 8 + 2 * q;
+        d[nt][0] = d[nt][2] = (c0 < Cout) ? b[c0] : 0.f;
+        d[nt][1] = d[nt][3] = (c0 + 1 < Cout) ? b[c0 + 1] : 0.f;
+    }
+    for (int t = 0; t < 27; ++t) {
+        const int src_a = sa < S ? nbr[sa * 27 + t] : -1, src_b = sb < S ? nbr[sb * 27 + t] : -1;
+        for (int kk = 0; kk < Cin; kk += 16) {
+            uint32_t ah[4], al[4];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {             // K columns 2q, 2q+1 (+8)
+                const int ci = kk + 2 * q + 8 * hh;
+                const float xa0 = (src_a >= 0 && ci < Cin) ? xn[(int64_t)src_a * Cin + ci] : 0.f;
+                const float xa1 = (src_a >= 0 && ci + 1 < Cin) ? xn[(int64_t)src_a * Cin + ci + 1] : 0.f;
+                const float xb0 = (src_b >= 0 && ci < Cin) ? xn[(int64_t)src_b * Cin + ci] : 0.f;
+                const float xb1 = (src_b >= 0 && ci + 1 < Cin) ? xn[(int64_t)src_b * Cin + ci + 1] : 0.f;
+                split2(xa0, xa1, ah[2 * hh], al[2 * hh]);
+                split2(xb0, xb1, ah[2 * hh + 1], al[2 * hh + 1]);
+            }
+            const __nv_bfloat16 *wt = Ws + t * Cin * Cout;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                if (nt >= ntn) break;
+                const int co = nt * 8 + g;
+                const int r0 = kk + 2 * q, r1 = r0 + 8;   // K rows (input channels) of b[0], b[1]
+                const bool okc = co < Cout;
+                const uint32_t b0 = w_pair(wt, okc && r0 < Cin, r0 * Cout + co, okc && r0 + 1 < Cin, (r0 + 1) * Cout + co);
+                const uint32_t b1 = w_pair(wt, okc && r1 < Cin, r1 * Cout + co, okc && r1 + 1 < Cin, (r1 + 1) * Cout + co);
+                mma16816(d[nt], ah, b0, b1);
+                mma16816(d[nt], al, b0, b1);
+            }
+        }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+        if (nt >= ntn) break;
+        const int c0 = nt * 8 + 2 * q;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int s = e < 2 ? sa : sb, co = c0 + (e & 1);
+            if (s < S && co < Cout) {
+                const int64_t o = ((int64_t)n * S + s) * Cout + co;
+                z[o] = d[nt][e];
+                if (h) h[o] = relu ? fmaxf(d[nt][e], 0.f) : d[nt][e];
+            }
+        }
+    }
+}
+
+// dx[n, u, ci] = sum_t sum_co W[t, ci, co] dy[n, nbr[u, 26 - t], co]; layout as k_conv_fwd_tc.
+__global__ void __launch_bounds__(32 * kConvTcWarps)
+k_conv_bwd_data_tc(int S, int Cin, int Cout, const float *__restrict__ dy, const __nv_bfloat16 *__restrict__ W,
+                   const int32_t *__restrict__ nbr, float *__restrict__ dx) {
+    extern __shared__ __align__(16) unsigned char conv_smem[];
+    __nv_bfloat16 *Ws = reinterpret_cast<__nv_bfloat16 *>(conv_smem);
+    const int nw = 27 * Cin * Cout;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) Ws[i] = W[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
+    const int n = blockIdx.y;
+    const int ua = (blockIdx.x * kConvTcWarps + warp) * 16 + g, ub = ua + 8;
+    const float *gn = dy + (int64_t)n * S * Cout;
+    const int ntn = (Cin + 7) / 8;
+    float d[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) d[nt][e] = 0.f;
+    for (int t = 0; t < 27; ++t) {
+        const int sa = ua < S ? nbr[ua * 27 + (26 - t)] : -1, sb = ub < S ? nbr[ub * 27 + (26 - t)] : -1;
+        for (int kk = 0; kk < Cout; kk += 16) {
+            uint32_t ah[4], al[4];
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {             // K columns (output channels) 2q, 2q+1 (+8)
+                const int co = kk + 2 * q + 8 * hh;
+                const float ga0 = (sa >= 0 && co < Cout) ? gn[(int64_t)sa * Cout + co] : 0.f;
+                const float ga1 = (sa >= 0 && co + 1 < Cout) ? gn[(int64_t)sa * Cout + co + 1] : 0.f;
+                const float gb0 = (sb >= 0 && co < Cout) ? gn[(int64_t)sb * Cout + co] : 0.f;
+                const float gb1 = (sb >= 0 && co + 1 < Cout) ? gn[(int64_t)sb * Cout + co + 1] : 0.f;
+                split2(ga0, ga1, ah[2 * hh], al[2 * hh]);
+                split2(gb0, gb1, ah[2 * hh + 1], al[2 * hh + 1]);
+            }
+            const __nv_bfloat16 *wt = Ws + t * Cin * Cout;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                if (nt >= ntn) break;
+                const int ci = nt * 8 + g;                // B column (n) = input channel
+                const int r0 = kk + 2 * q, r1 = r0 + 8;   // B rows (k) = output channels
+                const bool okc = ci < Cin;
+                const uint32_t b0 = w_pair(wt, okc && r0 < Cout, ci * Cout + r0, okc && r0 + 1 < Cout, ci * Cout + r0 + 1);
+                const uint32_t b1 = w_pair(wt, okc && r1 < Cout, ci * Cout + r1, okc && r1 + 1 < Cout, ci * Cout + r1 + 1);
+                mma16816(d[nt], ah, b0, b1);
+                mma16816(d[nt], al, b0, b1);
+            }
+        }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+        if (nt >= ntn) break;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int u = e < 2 ? ua : ub, ci = nt * 8 + 2 * q + (e & 1);
+            if (u < S && ci < Cin) dx[((int64_t)n * S + u) * Cin + ci] = d[nt][e];
+        }
+    }
+}
+
+// part[chunk][t][ci][co] = sum over the chunk's rows (n, s) of x[n, nbr[s, t], ci] dy[n, s, co]
+// (grid (27, nchunk), 8 warps: warp w takes input-channel tile w & 1 (16 channels) and
+// output-channel tile w >> 1 (8 channels); rows staged 32 at a time).
+__global__ void __launch_bounds__(256)
+k_conv_bwd_w_tc(int NS, int S, int Cin, int Cout, const float *__restrict__ x, const float *__restrict__ dy,
+                const int32_t *__restrict__ nbr, int rows_per_chunk, float *__restrict__ part) {
+    __shared__ float xs[32][kMaxCh + 1];
+    __shared__ float gs[32][kMaxCh + 1];
+    const int t = blockIdx.x, chunk = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
+    const int mt = warp & 1, nt = warp >> 1;
+    const bool live = 16 * mt < Cin && 8 * nt < Cout;
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    const int r0 = chunk * rows_per_chunk, r1 = min(NS, r0 + rows_per_chunk);
+    for (int rb = r0; rb < r1; rb += 32) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 32 * kMaxCh; i += blockDim.x) {
+            const int rr = i / kMaxCh, c = i % kMaxCh;
+            const int row = rb + rr;
+            float xv = 0.f, gv = 0.f;
+            if (row < r1) {
+                const int n = row / S, s = row % S;
+                const int src = nbr[s * 27 + t];
+                if (c < Cin && src >= 0) xv = x[((int64_t)n * S + src) * Cin + c];
+                if (c < Cout) gv = dy[(int64_t)row * Cout + c];
+            }
+            xs[rr][c] = xv;
+            gs[rr][c] = gv;
+        }
+        __syncthreads();
+        if (!live) continue;
+#pragma unroll
+        for (int kk = 0; kk < 32; kk += 16) {
+            uint32_t ah[4], al[4], bh[2], bl[2];
+            const int ca = 16 * mt + g, cb = ca + 8;      // A rows (m) = input channels
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {             // A columns (k) = rows kk + 2q (+8)
+                const int rr = kk + 2 * q + 8 * hh;
+                split2(xs[rr][ca], xs[rr + 1][ca], ah[2 * hh], al[2 * hh]);
+                split2(xs[rr][cb], xs[rr + 1][cb], ah[2 * hh + 1], al[2 * hh + 1]);
+                const int co = 8 * nt + g;                // B column (n) = output channel
+                split2(gs[rr][co], gs[rr + 1][co], bh[hh], bl[hh]);
+            }
+            mma16816(d, ah, bh[0], bh[1]);
+            mma16816(d, ah, bl[0], bl[1]);
+            mma16816(d, al, bh[0], bh[1]);
+        }
+    }
+    if (!live) return;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int ci = 16 * mt + g + (e < 2 ? 0 : 8), co = 8 * nt + 2 * q + (e & 1);
+        if (ci < Cin && co < Cout) part[(((int64_t)chunk * 27 + t) * Cin + ci) * Cout + co] = d[e];
+    }
+}
+
 // gW = sum over chunks (fixed order); gb[co] = sum over rows of dy.
 __global__ void k_conv_reduce(int nchunk, int nw, const float *__restrict__ part, float *__restrict__ gW) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -339,13 +557,27 @@ __global__ void k_copy_vec(int64_t n, const VT *__restrict__ src, VT *__restrict
 }  // namespace
 
 // ---- host: network passes ----------------------------------------------------------------------
+// Tensor cores for the C -> C layers (both channel counts >= 8).
+static bool conv_tc(const NetDev &net, int l) { return net.cin[l] >= 8 && net.cout[l] >= 8; }
+static size_t conv_tc_smem(const NetDev &net, int l) { return (size_t)27 * net.cin[l] * net.cout[l] * 2; }
+
+static void launch_conv_fwd(const NetDev &net, int l, int N, const float *in, float *z, float *h, int relu,
+                            cudaStream_t st) {
+    if (conv_tc(net, l)) {
+        const int sites = 16 * kConvTcWarps;
+        k_conv_fwd_tc<<<dim3((net.S + sites - 1) / sites, N), 32 * kConvTcWarps, conv_tc_smem(net, l), st>>>(
+            net.S, net.cin[l], net.cout[l], in, net.Wb[l], net.b[l], net.nbr, z, h, relu);
+    } else {
+        dim3 grid((net.S + kConvSitesPerCta - 1) / kConvSitesPerCta, N), block(32, 8);
+        k_conv_fwd<<<grid, block, 0, st>>>(net.S, net.cin[l], net.cout[l], in, net.Wb[l], net.b[l], net.nbr, z, h, relu);
+    }
+    count_launch();
+}
+
 void net_forward(NetDev &net, int N, const float *x0, float *const zs[4], float *const hs[3], cudaStream_t st) {
     const float *in = x0;
     for (int l = 0; l < kNetLayers; ++l) {
-        dim3 grid((net.S + kConvSitesPerCta - 1) / kConvSitesPerCta, N), block(32, 8);
-        k_conv_fwd<<<grid, block, 0, st>>>(net.S, net.cin[l], net.cout[l], in, net.Wb[l], net.b[l], net.nbr, zs[l],
-                                           l < 3 ? hs[l] : nullptr, l < 3 ? 1 : 0);
-        count_launch();
+        launch_conv_fwd(net, l, N, in, zs[l], l < 3 ? hs[l] : nullptr, l < 3 ? 1 : 0, st);
         if (l < 3) in = hs[l];
     }
 }
@@ -363,15 +595,26 @@ void net_backward(NetDev &net, int N, const float *x0, float *const zs[4], float
         }
         const float *inp = l == 0 ? x0 : hs[l - 1];
         const int nw = 27 * net.cin[l] * net.cout[l];
-        k_conv_bwd_w<<<dim3(27, nchunk), dim3(32, 8), 0, st>>>(NS, net.S, net.cin[l], net.cout[l], inp, g, net.nbr,
-                                                             rows, part);
+        if (conv_tc(net, l))
+            k_conv_bwd_w_tc<<<dim3(27, nchunk), 256, 0, st>>>(NS, net.S, net.cin[l], net.cout[l], inp, g, net.nbr,
+                                                              rows, part);
+        else
+            k_conv_bwd_w<<<dim3(27, nchunk), dim3(32, 8), 0, st>>>(NS, net.S, net.cin[l], net.cout[l], inp, g, net.nbr,
+                                                                 rows, part);
         k_conv_reduce<<<(nw + 255) / 256, 256, 0, st>>>(nchunk, nw, part, net.gW[l]);
         k_bias_grad<<<net.cout[l], 256, 0, st>>>(NS, net.cout[l], g, net.gb[l]);
         count_launch(3);
         if (l > 0) {
             float *dx = (g == gbuf0) ? gbuf1 : gbuf0;
-            dim3 grid((net.S + kConvSitesPerCta - 1) / kConvSitesPerCta, N), block(32, 8);
-            k_conv_bwd_data<<<grid, block, 0, st>>>(net.S, net.cin[l], net.cout[l], g, net.Wb[l], net.nbr, dx);
+            if (conv_tc(net, l)) {
+                const int sites = 16 * kConvTcWarps;
+                k_conv_bwd_data_tc<<<dim3((net.S + sites - 1) / sites, N), 32 * kConvTcWarps,
+                                     conv_tc_smem(net, l), st>>>(net.S, net.cin[l], net.cout[l], g, net.Wb[l], net.nbr,
+                                                                 dx);
+            } else {
+                dim3 grid((net.S + kConvSitesPerCta - 1) / kConvSitesPerCta, N), block(32, 8);
+                k_conv_bwd_data<<<grid, block, 0, st>>>(net.S, net.cin[l], net.cout[l], g, net.Wb[l], net.nbr, dx);
+            }
             count_launch();
             g = dx;
         }
@@ -388,6 +631,12 @@ void net_adam(NetDev &net, float lr, cudaStream_t st) {
         k_adam<<<1, 256, 0, st>>>(net.cout[l], net.b[l], net.gb[l], net.mb[l], net.vb[l], nullptr, lr, b1, b2, c1, c2);
         count_launch(2);
     }
+}
+
+void net_kernels_init() {
+    const int bytes = 27 * kMaxCh * kMaxCh * 2;          // all taps of a 32 -> 32 layer in BF16
+    GEMSLR_CUDA(cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    GEMSLR_CUDA(cudaFuncSetAttribute(k_conv_bwd_data_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
 }
 
 void net_sync_bf16(NetDev &net, cudaStream_t st) {
@@ -437,14 +686,11 @@ void learned_rho_and_update(const LearnedStage<VT> &L, int64_t e, VT *work, cuda
     float *bufs[2] = {L.act1, L.act2};
     for (int l = 0; l < kNetLayers; ++l) {
         float *o = bufs[l & 1];
-        dim3 grid((net.S + kConvSitesPerCta - 1) / kConvSitesPerCta, 1), block(32, 8);
-        k_conv_fwd<<<grid, block, 0, st>>>(net.S, net.cin[l], net.cout[l], in, net.Wb[l], net.b[l], net.nbr, o,
-                                           nullptr, 0);
+        launch_conv_fwd(net, l, 1, in, o, nullptr, 0, st);
         if (l < 3) {
             k_relu_mask<<<(net.S * net.cout[l] + 255) / 256, 256, 0, st>>>((int64_t)net.S * net.cout[l], o, o);
             count_launch();
         }
-        count_launch();
         in = o;
     }
     (void)zs;

@@ -4,8 +4,11 @@
 // last-level blocks (Sec. 2.3, Sec. 4.3), and level-set analysis of the
 // triangular factors for the GPU substitutions.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <exception>
 #include <numeric>
+#include <thread>
 
 #include "internal.h"
 
@@ -293,18 +296,44 @@ std::vector<int32_t> wavefronts_upper(const Csr &U, int64_t r0, int64_t r1) {
 }
 
 // ---- hierarchy ------------------------------------------------------------
+// The diagonal blocks of a level are independent (Sec. 4.2), so they are
+// factored by a pool of host threads (blocks handed out in turn); the factors
+// are appended in block order, so the result does not depend on the threads.
 static void factor_level(const Csr &B, const std::vector<int64_t> &bp, const gemslr_options *opt,
                          Csr &L, Csr &U, int64_t &clamped) {
     const int64_t n = B.nrows;
+    const size_t nb = bp.size() - 1;
+    std::vector<Csr> Ls(nb), Us(nb);
+    std::vector<int64_t> cl(nb, 0);
+    std::vector<std::exception_ptr> err(nb);
+    std::atomic<size_t> next{0};
+    std::atomic<bool> failed{false};
+    auto work = [&] {
+        for (size_t j; !failed.load() && (j = next.fetch_add(1)) < nb;) {
+            try {
+                Csr Bj = submatrix(B, bp[j], bp[j + 1], bp[j], bp[j + 1]);
+                if (opt->ilu_kind == GEMSLR_ILU0) cl[j] = factor_ilu0(Bj, Ls[j], Us[j]);
+                else cl[j] = factor_ilut(Bj, opt->ilut_tau, opt->ilut_lfil, Ls[j], Us[j]);
+            } catch (...) {
+                err[j] = std::current_exception();
+                failed = true;
+            }
+        }
+    };
+    const size_t hw = std::max<unsigned>(1u, std::thread::hardware_concurrency());
+    const size_t nt = std::min<size_t>(nb, std::min<size_t>(hw, 32));
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < nt; ++t) pool.emplace_back(work);
+    work();
+    for (auto &th : pool) th.join();
+    for (auto &e : err)
+        if (e) std::rethrow_exception(e);
     L = Csr();
     U = Csr();
-    for (size_t j = 0; j + 1 < bp.size(); ++j) {
-        Csr Bj = submatrix(B, bp[j], bp[j + 1], bp[j], bp[j + 1]);
-        Csr Lj, Uj;
-        if (opt->ilu_kind == GEMSLR_ILU0) clamped += factor_ilu0(Bj, Lj, Uj);
-        else clamped += factor_ilut(Bj, opt->ilut_tau, opt->ilut_lfil, Lj, Uj);
-        append_block(L, Lj, bp[j]);
-        append_block(U, Uj, bp[j]);
+    for (size_t j = 0; j < nb; ++j) {
+        append_block(L, Ls[j], bp[j]);
+        append_block(U, Us[j], bp[j]);
+        clamped += cl[j];
     }
     L.nrows = L.ncols = U.nrows = U.ncols = n;
 }

@@ -1302,6 +1302,7 @@ void learned_init(gemslr_ctx *h, LearnedHost &Lh, const int32_t *coords, int cha
         net.nparams += nw + dims[l + 1];
     }
     net.adam_t = 0;
+    net_kernels_init();
     net_sync_bf16(net, nullptr);
     // in-apply buffers for both precisions
     const HostLevel &hl = H.lev[Lh.lstar];
