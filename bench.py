@@ -520,6 +520,10 @@ def run_ours(args):
                                 "one_core": {"value": len(times) / sum(times), "unit": UNIT, "cores": 1,
                                              "sample": f"{len(times)} complete oracle solves in this process "
                                                        f"(setup {t_setup:.1f} s excluded)"}}
+    if rank == 0 and CONFIG == "c2" and not args.no_other_configs:
+        # the other configurations, measured by the same run: the batched
+        # systems (solves/s) and the indefinite 128^3 operator (per iteration)
+        line["other_configs"] = {"c4_batched": batch_measure(3, 1), "c3_indefinite": indefinite_measure(200)}
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -527,11 +531,10 @@ def run_ours(args):
     return 0
 
 
-def run_batch(args):
-    """c4: 96 uneven convection-diffusion systems x 8 right-hand sides, one batched solve per step."""
+def batch_measure(steps, warmup):
+    """c4: 96 uneven convection-diffusion systems x 8 right-hand sides; batched
+    FGMRES solves (CUDA events) and batched M^-1 applications per second."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2205_03224_gb300 import GemslrBatch, partition_geometric
     from paper_2205_03224_gb300 import _lib
     c = gi.CONFIGS["c4"]
@@ -549,14 +552,14 @@ def run_batch(args):
                                     axis=1).T.ravel() for s, A in enumerate(As)])
     b_dev = torch.from_numpy(bvec).cuda()
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         x, info = B.solve(b_dev, nrhs, restart=c["restart"], rtol=c["rtol"])
-    clocks = Clocks(0)
+    clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     torch.cuda.synchronize()
     l0 = _lib.kernel_launches()
     ms = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -567,7 +570,6 @@ def run_batch(args):
     torch.cuda.synchronize()
     launches = _lib.kernel_launches() - l0
     clk = clocks.stop()
-    # batched M^-1 applications per second
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     for _ in range(3):
@@ -590,24 +592,80 @@ def run_batch(args):
     npairs = len(As) * nrhs
     total_ms = sum(ms)
     st = B.stats()
-    line = {
-        "metric": METRIC, "value": npairs * args.steps / (total_ms / 1e3), "unit": "solves/s (FGMRES to 1e-8, all systems x rhs)",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/bf16 M^-1 + f64 FGMRES",
-        "data": "synthetic",
-        "config": {"workload": f"{len(As)} 3-D conv-diff systems, sides U[16,48], beta U[0,0.5], {nrhs} rhs each, "
-                               f"{c['nlev']} levels x {c['p']} subdomains, ILUT(1e-3,10), rank {c['rank']}, "
-                               f"FGMRES({c['restart']}) to 1e-8, seed {c['seed']}",
-                   "rows_total": int(sum(A.n for A in As)), "parallelism": "single"},
-        "time_to_solution_ms": total_ms / args.steps, "max_iterations": max(i["iters"] for i in info),
+    B.close()
+    return {
+        "workload": f"{len(As)} 3-D conv-diff systems, sides U[16,48], beta U[0,0.5], {nrhs} rhs each, "
+                    f"{c['nlev']} levels x {c['p']} subdomains, ILUT(1e-3,10), rank {c['rank']}, "
+                    f"FGMRES({c['restart']}) to 1e-8, seed {c['seed']}",
+        "rows_total": int(sum(A.n for A in As)), "solves_per_s": npairs * steps / (total_ms / 1e3),
+        "unit": "solves/s (FGMRES to 1e-8, all systems x rhs)", "steps": steps, "warmup": warmup,
+        "time_to_solution_ms": total_ms / steps, "max_iterations": max(i["iters"] for i in info),
         "mean_iterations": float(np.mean([i["iters"] for i in info])), "worst_rel_residual": worst,
+        "all_converged": bool(all(i["converged"] for i in info)),
         "batched_applies_per_s": 1e3 / apply_ms, "rhs_applies_per_s": npairs * 1e3 / apply_ms,
         "setup_s": setup_s, "autotune": {"rows_couple": st["rows_couple"], "rows_krylov": st["rows_krylov"],
                                          "tune_ms": st["tune_ms"]},
         "gpu_launches": int(launches), "clocks": clk,
     }
+
+
+def run_batch(args):
+    """c4 alone: one batched solve per step."""
+    import __graft_entry__
+    __graft_entry__.build()
+    d = batch_measure(args.steps, args.warmup)
+    line = {
+        "metric": METRIC, "value": d["solves_per_s"], "unit": d["unit"],
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": d["time_to_solution_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/bf16 M^-1 + f64 FGMRES",
+        "data": "synthetic", "config": {"workload": d["workload"], "rows_total": d["rows_total"], "parallelism": "single"},
+    }
+    line.update({k: v for k, v in d.items() if k not in ("workload", "rows_total", "unit", "steps", "warmup")})
     print(json.dumps(line))
     return 0
+
+
+def indefinite_measure(maxit):
+    """c3: 128^3 shifted (indefinite) Laplacian, mixed precision, FGMRES(60)
+    for ``maxit`` iterations (it does not reach 1e-8 with this method and
+    these settings): set-up, time per iteration, residual reached, M^-1
+    applications per second."""
+    import torch
+    from paper_2205_03224_gb300 import Gemslr, partition_geometric
+    c = gi.CONFIGS["c3"]
+    A, xyz, b = gi.config_problem("c3")
+    part = partition_geometric(A, xyz, c["nlev"], c["p"])
+    t0 = time.perf_counter()
+    G = Gemslr(A, part, ilu=c["ilu"], tau=c["tau"], lfil=c["lfil"], rank=c["rank"], precision="mixed")
+    setup_s = time.perf_counter() - t0
+    b_dev = torch.from_numpy(b).cuda()
+    stream = torch.cuda.current_stream()
+    G.solve(b_dev, restart=c["restart"], rtol=c["rtol"], maxit=20, check=False)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    x, info = G.solve(b_dev, restart=c["restart"], rtol=c["rtol"], maxit=maxit, check=False)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    res = float(np.linalg.norm(b - A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(b))
+    r_dev = torch.from_numpy(gi.rhs_uniform(A.n, 7)).cuda()
+    for _ in range(3):
+        G.apply(r_dev)
+    e0.record(stream)
+    for _ in range(20):
+        G.apply(r_dev)
+    e1.record(stream)
+    e1.synchronize()
+    apply_ms = e0.elapsed_time(e1) / 20
+    st = G.stats()
+    G.close()
+    return {"workload": "3-D 7-pt Laplacian - 0.05 h^-2 I (indefinite) 128^3 (n=2097152), 4 levels x 64 subdomains, "
+                        "ILUT(1e-3,10), rank 64, mixed (FP32 factors, BF16 W), FGMRES(60)",
+            "setup_s": setup_s, "iterations": info[0]["iters"], "converged": bool(info[0]["converged"]),
+            "rel_residual": res, "ms_per_iteration": ms / max(1, info[0]["iters"]), "apply_ms": apply_ms,
+            "applies_per_s": 1e3 / apply_ms, "bytes_per_apply": st["bytes_per_apply"],
+            "apply_gbs": st["bytes_per_apply"] / (apply_ms * 1e-3) / 1e9}
 
 
 def run_learned(args):
@@ -685,6 +743,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="mixed runs: skip timing the plain FP64 GPU path beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="default line: skip the batched (c4) and indefinite (c3) measurements")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2 (default line), c3: 128^3 shifted (mixed), c4: batched systems, c5: learned stage")
     ap.add_argument("--maxit", type=int, default=1000)

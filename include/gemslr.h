@@ -78,8 +78,11 @@ typedef struct {
 
 /* Precision of the preconditioner application (FGMRES is FP64 in both). */
 enum { GEMSLR_PREC_FP64 = 0, GEMSLR_PREC_MIXED = 1 };
-/* Incomplete factorisation of the diagonal blocks. */
-enum { GEMSLR_ILU0 = 0, GEMSLR_ILUT = 1 };
+/* Incomplete factorisation of the diagonal blocks: ILU(0) or ILUT on the host
+ * (blocks on a pool of host threads), or ILU(0) on the GPU (level-scheduled,
+ * one CTA per block; factors bit-identical to GEMSLR_ILU0; every row of A
+ * needs its diagonal entry, else ARG). */
+enum { GEMSLR_ILU0 = 0, GEMSLR_ILUT = 1, GEMSLR_ILU0_DEVICE = 2 };
 
 typedef struct {
     int32_t ilu_kind;             /* GEMSLR_ILU0 or GEMSLR_ILUT                     */

@@ -84,6 +84,9 @@ struct Hierarchy {
     int64_t nclamp = 0;
 };
 
+// ILU(0) of the diagonal blocks of a level matrix on the current device (ilu_device.cu).
+void factor_level_ilu0_device(const Csr &B, const std::vector<int64_t> &bp, Csr &L, Csr &U, int64_t &clamped);
+
 // Build the hierarchy without the low-rank terms (permute, slice, factor).
 void build_levels(const Csr &A, const gemslr_partition *part, const gemslr_options *opt,
                   Hierarchy &h);

@@ -301,6 +301,10 @@ std::vector<int32_t> wavefronts_upper(const Csr &U, int64_t r0, int64_t r1) {
 // are appended in block order, so the result does not depend on the threads.
 static void factor_level(const Csr &B, const std::vector<int64_t> &bp, const gemslr_options *opt,
                          Csr &L, Csr &U, int64_t &clamped) {
+    if (opt->ilu_kind == GEMSLR_ILU0_DEVICE) {
+        factor_level_ilu0_device(B, bp, L, U, clamped);
+        return;
+    }
     const int64_t n = B.nrows;
     const size_t nb = bp.size() - 1;
     std::vector<Csr> Ls(nb), Us(nb);

@@ -610,7 +610,8 @@ gemslr_options normalized(const gemslr_options *opt) {
     gemslr_options o;
     gemslr_default_options(&o);
     if (opt) o = *opt;
-    if (o.ilu_kind != GEMSLR_ILU0 && o.ilu_kind != GEMSLR_ILUT) fail(GEMSLR_ERR_ARG, "unknown ilu_kind");
+    if (o.ilu_kind != GEMSLR_ILU0 && o.ilu_kind != GEMSLR_ILUT && o.ilu_kind != GEMSLR_ILU0_DEVICE)
+        fail(GEMSLR_ERR_ARG, "unknown ilu_kind");
     if (o.precision != GEMSLR_PREC_FP64 && o.precision != GEMSLR_PREC_MIXED) fail(GEMSLR_ERR_ARG, "unknown precision");
     if (o.ilut_tau < 0) fail(GEMSLR_ERR_ARG, "ilut_tau must be >= 0");
     for (int l = 0; l < GEMSLR_MAX_LEVELS; ++l)
