@@ -15,7 +15,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import ilu as _ilu
-from .lowrank import correction_matrix, krylov_schur
+from .lowrank import correction_matrix, krylov_schur, randomized_schur
 from .partition import level_blocks
 
 
@@ -70,6 +70,9 @@ class OracleGemslr:
         shift = 0.05); E, F and C are not shifted.  With shift != 0 the
         factors, W, H and every vector of the application are complex, and
         the correction is W H W^H (Sec. 2.2).
+    lowrank : "arnoldi" (thick-restart Krylov-Schur, the default) or
+        "randomized" (``randomized_schur``: subspace iteration on a random
+        block with ``power`` passes, Sec. 6); False skips the corrections.
 
     Attribute ``stage`` (default None): an extra correction of the deepest
     Schur level l* = nlev - 2, a callable (z2, y2) -> y2' applied after y2 is
@@ -79,7 +82,7 @@ class OracleGemslr:
     """
 
     def __init__(self, A, part, ilu="ilu0", tau=1e-3, lfil=10, rank=8, last_ilu=None,
-                 arnoldi_tol=1e-2, max_cycles=20, lowrank=True, inner_steps=0, shift=0.0):
+                 arnoldi_tol=1e-2, max_cycles=20, lowrank=True, inner_steps=0, shift=0.0, power=1):
         self.inner_steps = int(inner_steps)
         self.stage = None
         A = sp.csr_matrix(A)
@@ -118,6 +121,8 @@ class OracleGemslr:
         Lc, Uc, c = _factor_blocks(keep, bp, last_ilu or ilu, tau, lfil, self.alpha)
         self.nclamp += c
         self.last_L, self.last_U = Lc, Uc
+        self.lowrank_method = "randomized" if lowrank == "randomized" else "arnoldi"
+        self.power = int(power)
         if lowrank:
             # bottom-up (Sec. 4.2): level l needs the apply of every level > l
             for l in range(nsch - 1, -1, -1):
@@ -208,8 +213,13 @@ class OracleGemslr:
     def build_lowrank(self, l, tol=1e-2, max_cycles=20):
         lv = self.levels[l]
         s = self.n - lv["e"]
-        W, Tk, info = krylov_schur(lambda z: self.g_hat(l, z), s, lv["rank"], 1000 + l,
-                                   tol=tol, max_cycles=max_cycles, complex_arith=self.alpha != 0.0)
+        if self.lowrank_method == "randomized":
+            if self.alpha != 0.0:
+                raise ValueError("the randomized set-up is real only")
+            W, Tk, info = randomized_schur(lambda z: self.g_hat(l, z), s, lv["rank"], 1000 + l, power=self.power)
+        else:
+            W, Tk, info = krylov_schur(lambda z: self.g_hat(l, z), s, lv["rank"], 1000 + l,
+                                       tol=tol, max_cycles=max_cycles, complex_arith=self.alpha != 0.0)
         lv["W"] = W
         lv["T"] = Tk
         lv["H"] = correction_matrix(Tk)

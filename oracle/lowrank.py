@@ -261,6 +261,53 @@ def _krylov_schur_complex(op, s, k, seed, tol, max_cycles, m, info):
     raise AssertionError("unreachable")
 
 
+def randomized_schur(op, s, k, seed, oversample=None, power=1):
+    """W (s x keff), T_k and diagnostics from a randomized block method instead
+    of the thick-restart Arnoldi (Sec. 6 names block and randomized variants
+    as future work for the set-up):
+
+      1. Omega: s x b, b = k + oversample (oversample defaults to k), entries
+         2u - 1 with u the splitmix64(seed) stream, column after column;
+      2. Y = G_hat Omega, then ``power`` times: Q = orth(Y), Y = G_hat Q
+         (subspace iteration);
+      3. Q = orth(Y) (reduced QR), Z = G_hat Q, Rayleigh quotient B = Q^T Z;
+      4. B = U T U^T (real Schur form) with the wanted values leading
+         (``schur_wanted``, same ranking and pair rule as the Arnoldi);
+         W = Q U[:, :keff], T_k = T[:keff, :keff].
+
+    G_hat W = Z U[:, :keff], so the residual ||G_hat W - W T_k|| is reported
+    without further products.  When s <= b the operator is formed densely as
+    in ``krylov_schur``."""
+    info = dict(dense=False, keff=0, ritz=np.zeros(0, dtype=complex), products=0)
+    if k <= 0 or s == 0:
+        return np.zeros((s, 0)), np.zeros((0, 0)), info
+    b = k + (k if oversample is None else int(oversample))
+    if s <= b:
+        W, Tk, i2 = krylov_schur(op, s, k, seed, m=b)
+        info.update(dense=True, keff=i2["keff"], ritz=i2["ritz"], products=s)
+        return W, Tk, info
+    u = gemslr_inputs.uniform01(seed, s * b)
+    Omega = (2.0 * u - 1.0).reshape(b, s).T
+
+    def apply_block(X):
+        info["products"] += X.shape[1]
+        return np.column_stack([op(X[:, c]) for c in range(X.shape[1])])
+
+    Y = apply_block(Omega)
+    for _ in range(int(power)):
+        Q, _ = np.linalg.qr(Y)
+        Y = apply_block(Q)
+    Q, _ = np.linalg.qr(Y)
+    Z = apply_block(Q)
+    B = Q.T @ Z
+    T, U, keff = schur_wanted(B, k)
+    W = Q @ U[:, :keff]
+    Tk = T[:keff, :keff].copy()
+    resid = np.linalg.norm(Z @ U[:, :keff] - W @ Tk)
+    info.update(keff=keff, ritz=block_eigs(T)[:keff], resid=resid)
+    return W, Tk, info
+
+
 def correction_matrix(Tk):
     """H = (I - T_k)^{-1} - I, the k x k middle factor of eq. (gemslr5)."""
     k = Tk.shape[0]

@@ -185,3 +185,49 @@ def test_wanted_selection_never_splits_a_pair():
     Hm2 = np.diag([0.9, 0.1, 0.2])
     T, Q, keff = schur_wanted(Hm2, 1)
     assert keff == 1 and np.isclose(T[0, 0], 0.9)
+
+
+def test_randomized_schur_recovers_an_exact_low_rank_operator():
+    """An operator of rank r <= b: the random block's range is its range, so the
+    Rayleigh quotient holds its nonzero eigenvalues exactly and W spans an
+    invariant subspace (G W = W T_k to rounding)."""
+    from oracle.lowrank import randomized_schur
+    rng = np.random.default_rng(11)
+    s, r = 300, 6
+    X = np.linalg.qr(rng.standard_normal((s, r)))[0]
+    Yb = rng.standard_normal((s, r))
+    D = np.diag([0.9, 0.8, -0.7, 0.6, 0.5, 0.4])
+    G = X @ D @ (Yb.T @ X) @ np.linalg.inv(Yb.T @ X) @ X.T       # rank r, eigenvalues diag(D) and 0
+    W, Tk, info = randomized_schur(lambda z: G @ z, s, r, 5, oversample=4, power=0)
+    assert W.shape == (s, r) and np.allclose(W.T @ W, np.eye(r), atol=1e-12)
+    assert np.linalg.norm(G @ W - W @ Tk) <= 1e-10
+    ev = np.sort(np.linalg.eigvals(Tk).real)
+    assert np.allclose(ev, np.sort(np.diag(D)), atol=1e-10)
+    assert info["products"] == 2 * (r + 4)
+
+
+def test_randomized_schur_agrees_with_arnoldi_on_the_dominant_values():
+    """On G_hat of a hierarchy the subspace iteration finds the same leading
+    Ritz values as the thick-restart Arnoldi to the Arnoldi's own accuracy
+    (two digits), and the correction is exact at full rank like the Arnoldi's."""
+    from oracle.lowrank import krylov_schur, randomized_schur
+    A, xyz = gi.grid_operator((10, 9, 8), beta=0.2)
+    As = A.to_scipy()
+    part = multilevel_partition(As, xyz, 3, 4)
+    M = OracleGemslr(As, part, ilu="ilut", tau=1e-2, lfil=4, rank=5, lowrank=False)
+    lv = M.levels[0]
+    s = M.n - lv["e"]
+    op = lambda z: M.g_hat(0, z)           # noqa: E731
+    _, _, ia = krylov_schur(op, s, 5, 1000, tol=1e-6, max_cycles=50)
+    _, _, ir = randomized_schur(op, s, 5, 1000, oversample=10, power=3)
+    ta = np.sort_complex(ia["ritz"])
+    tr = np.sort_complex(ir["ritz"])
+    assert len(ta) == len(tr)
+    assert np.allclose(tr, ta, rtol=1e-2, atol=1e-3)
+    # full rank: the randomized set-up reproduces the exact inverse of A~ (T5)
+    A2, xyz2 = gi.grid_operator((8, 7), beta=0.3)
+    A2s = A2.to_scipy()
+    part2 = multilevel_partition(A2s, xyz2, 2, 2, p_last=1)
+    Mr = OracleGemslr(A2s, part2, ilu="exact", rank=10 ** 6, lowrank="randomized")
+    r = gi.rhs_uniform(A2.n, 3)
+    assert np.allclose(Mr.apply(r), np.linalg.solve(A2s.toarray(), r), rtol=1e-8)
