@@ -104,9 +104,18 @@ typedef struct {
     void *(*dev_alloc)(size_t bytes, void *alloc_ctx);
     void (*dev_free)(void *ptr, void *alloc_ctx);
     void *alloc_ctx;
+    /* Set-up of the low-rank corrections: GEMSLR_LOWRANK_ARNOLDI (thick-restart
+     * Krylov-Schur, Sec. 4.2; the default) or GEMSLR_LOWRANK_RANDOMIZED (the
+     * block / randomized variant that Sec. 6 names as future work: subspace
+     * iteration on a seeded random s x 2k block with lowrank_power passes,
+     * then Rayleigh-Ritz with the same selection of the wanted values). */
+    int32_t lowrank_method;
+    int32_t lowrank_power;        /* subspace-iteration passes (randomized; 1)   */
 } gemslr_options;
+enum { GEMSLR_LOWRANK_ARNOLDI = 0, GEMSLR_LOWRANK_RANDOMIZED = 1 };
 
-/* Fill *opt with the defaults: ILUT(1e-3, 10), rank 0, FP64, 1e-2, 20 cycles. */
+/* Fill *opt with the defaults: ILUT(1e-3, 10), rank 0, FP64, 1e-2, 20 cycles,
+ * Arnoldi set-up of the corrections (1 pass when randomized is chosen). */
 void gemslr_default_options(gemslr_options *opt);
 
 /*

@@ -33,7 +33,8 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 class Options(ctypes.Structure):
     _fields_ = [("ilu_kind", i32), ("ilut_tau", f64), ("ilut_lfil", i32), ("rank", i32 * MAX_LEVELS),
                 ("precision", i32), ("arnoldi_tol", f64), ("arnoldi_max_cycles", i32),
-                ("strict_pivots", i32), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", P)]
+                ("strict_pivots", i32), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", P),
+                ("lowrank_method", i32), ("lowrank_power", i32)]
 
 
 class Mat(ctypes.Structure):

@@ -51,8 +51,9 @@ def torch_allocator():
 
 
 def options(ilu="ilut", tau=1e-3, lfil=10, rank=0, precision="fp64", arnoldi_tol=1e-2, max_cycles=20,
-            strict_pivots=False, allocator=None):
-    """gemslr_options; allocator: None (cudaMalloc) or a (dev_alloc, dev_free) pair of callbacks."""
+            strict_pivots=False, allocator=None, lowrank="arnoldi", power=1):
+    """gemslr_options; allocator: None (cudaMalloc) or a (dev_alloc, dev_free) pair of callbacks;
+    lowrank: "arnoldi" or "randomized" set-up of the corrections (power: subspace-iteration passes)."""
     o = L.Options()
     L.load().gemslr_default_options(ctypes.byref(o))
     o.ilu_kind = {"ilu0": 0, "ilut": 1, "ilu0_device": 2}[ilu]
@@ -65,6 +66,8 @@ def options(ilu="ilut", tau=1e-3, lfil=10, rank=0, precision="fp64", arnoldi_tol
     o.arnoldi_tol = arnoldi_tol
     o.arnoldi_max_cycles = max_cycles
     o.strict_pivots = 1 if strict_pivots else 0
+    o.lowrank_method = {"arnoldi": 0, "randomized": 1}[lowrank]
+    o.lowrank_power = int(power)
     if allocator is not None:
         o.dev_alloc, o.dev_free = allocator
     return o

@@ -103,6 +103,8 @@ void launch_step_end_g(KrylovCtl *ctl, cudaGraphConditionalHandle h, cudaStream_
 void launch_cycle_end_g(KrylovCtl *ctl, const double *n2r, cudaGraphConditionalHandle h, cudaStream_t st);
 void launch_basis_rotate(int64_t len, const double *V, int64_t ldv, int mm, const double *Q, int kk, double *out,
                          cudaStream_t st);
+// B = V^T Z (b x b, column-major) for s x b column-major V, Z (lowrank_rand.cu).
+void launch_gram(int64_t s, int b, const double *V, const double *Z, double *B, cudaStream_t st);
 
 // ---- host-side conversions and the chunk layout of the substitutions ---------------
 template <typename T> inline T cast_to(double v);

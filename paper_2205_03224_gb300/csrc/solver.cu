@@ -212,6 +212,83 @@ std::vector<double> start_vector(uint64_t seed, int64_t s) {
 // Cycle m = 2k; the wanted subspace is kept on restart; converged when
 // ||beta * Q[m-1, :k]||_2 <= tol * min |theta_i| (every Ritz value to ~two
 // digits, Sec. 5 set-up); s_l <= m: dense G_hat and its full Schur form.
+std::vector<double> splitmix_uniform01(uint64_t seed, int64_t count);
+
+// Randomized block set-up of level l's correction (Sec. 6 future work): an
+// s x b block (b = 2k) of 2u - 1 from splitmix64(1000 + l), column after
+// column; Y = G_hat Omega and lowrank_power passes of Q = orth(Y),
+// Y = G_hat Q; Q = orth(Y) by classical Gram-Schmidt with a second pass (the
+// Arnoldi's kernels, column by column); Z = G_hat Q and B = Q^T Z; the wanted
+// part of B's Schur form gives W = Q U_k and H (same selection as the
+// Arnoldi).  A column that Gram-Schmidt annihilates ends the block early.
+void build_lowrank_randomized(gemslr_ctx *h, int l, int k, int b, cudaStream_t st) {
+    HostLevel &hl = h->host.lev[l];
+    const int64_t s = h->host.n - hl.e;
+    double *V = (double *)h->arena.alloc(8 * (size_t)s * (b + 1));
+    double *Y = (double *)h->arena.alloc(8 * (size_t)s * b);
+    double *w = (double *)h->arena.alloc(8 * (size_t)s);
+    double *Hd = (double *)h->arena.alloc(8 * (size_t)(b + 1) * b);
+    double *Bd = (double *)h->arena.alloc(8 * (size_t)b * b);
+    double *Qd = (double *)h->arena.alloc(8 * (size_t)b * (k + 2));
+    double *W2 = (double *)h->arena.alloc(8 * (size_t)s * (k + 2));
+    {
+        std::vector<double> u = splitmix_uniform01(1000 + (uint64_t)l, s * b);
+        for (double &x : u) x = 2.0 * x - 1.0;
+        GEMSLR_CUDA(cudaMemcpyAsync(V, u.data(), 8 * (size_t)s * b, cudaMemcpyHostToDevice, st));
+    }
+    int bb = b;                                      // columns of the current orthonormal block
+    auto apply_block = [&](const double *X, int cols) {
+        for (int c = 0; c < cols; ++c) g_hat(h, l, X + (size_t)c * s, Y + (size_t)c * s, st);
+    };
+    // Q = orth(Y[:, :cols]) into V; returns the number of columns kept
+    auto orth = [&](int cols) {
+        launch_norm2(s, Y, h->partial, h->counter, h->n2, h->red_grid, st);
+        launch_scale_by_norm(s, Y, h->n2, V, st);
+        KrylovCtl c{};
+        c.j = 0;
+        c.m = cols;
+        c.givens = 0;
+        c.force_reorth = 1;
+        c.maxit = 1 << 30;
+        *h->ctl_host = c;
+        write_ctl(h, st);
+        GEMSLR_CUDA(cudaMemsetAsync(Hd, 0, 8 * (size_t)(b + 1) * b, st));
+        for (int j = 1; j < cols; ++j) {
+            GEMSLR_CUDA(cudaMemcpyAsync(w, Y + (size_t)j * s, 8 * s, cudaMemcpyDeviceToDevice, st));
+            launch_gs_dots(s, V, s, w, h->partial, h->counter, h->ctl, Hd, nullptr, nullptr, nullptr, h->h2,
+                           h->red_grid, st);
+            launch_gs_sub(s, V, s, w, h->partial, h->counter, h->ctl, Hd, nullptr, nullptr, nullptr, h->h2,
+                          h->red_grid, st);
+            launch_gs_sub2(s, V, s, w, h->h2, h->partial, h->counter, h->ctl, Hd, nullptr, nullptr, nullptr,
+                           h->red_grid, st);
+            launch_gs_scale(s, V, s, w, h->ctl, nullptr, st);
+            launch_gs_next(h->ctl, st);
+            read_ctl(h, st);
+            if (h->ctl_host->breakdown) return j;    // column j lies in the span of the ones before
+        }
+        return cols;
+    };
+    apply_block(V, bb);
+    for (int it = 0; it < h->opt.lowrank_power; ++it) {
+        bb = orth(bb);
+        apply_block(V, bb);
+    }
+    bb = orth(bb);
+    apply_block(V, bb);                              // Z = G_hat Q (in Y)
+    launch_gram(s, bb, V, Y, Bd, st);
+    std::vector<double> B((size_t)bb * bb), Q, Tk, tre, tim;
+    GEMSLR_CUDA(cudaMemcpyAsync(B.data(), Bd, 8 * B.size(), cudaMemcpyDeviceToHost, st));
+    GEMSLR_CUDA(cudaStreamSynchronize(st));
+    const int keff = schur_wanted(B, bb, std::min(k, bb), Q, Tk, tre, tim);
+    GEMSLR_CUDA(cudaMemcpyAsync(Qd, Q.data(), 8 * (size_t)bb * keff, cudaMemcpyHostToDevice, st));
+    launch_basis_rotate(s, V, s, bb, Qd, keff, W2, st);
+    hl.k = keff;
+    hl.W.resize((size_t)s * keff);
+    GEMSLR_CUDA(cudaMemcpyAsync(hl.W.data(), W2, 8 * (size_t)s * keff, cudaMemcpyDeviceToHost, st));
+    GEMSLR_CUDA(cudaStreamSynchronize(st));
+    hl.H = correction_matrix(Tk, keff);
+}
+
 void build_lowrank(gemslr_ctx *h, int l, cudaStream_t st) {
     HostLevel &hl = h->host.lev[l];
     const int64_t s = h->host.n - hl.e;
@@ -240,6 +317,10 @@ void build_lowrank(gemslr_ctx *h, int l, cudaStream_t st) {
         return;
     }
     if (m + 1 > kMaxCols) fail(GEMSLR_ERR_ARG, "rank too large for the Arnoldi workspace");
+    if (h->opt.lowrank_method == GEMSLR_LOWRANK_RANDOMIZED) {
+        build_lowrank_randomized(h, l, k, m, st);
+        return;
+    }
     double *V = (double *)h->arena.alloc(8 * (size_t)s * (m + 1));
     double *W2 = (double *)h->arena.alloc(8 * (size_t)s * (k + 2));
     double *w = (double *)h->arena.alloc(8 * (size_t)s);
@@ -619,6 +700,9 @@ gemslr_options normalized(const gemslr_options *opt) {
             fail(GEMSLR_ERR_ARG, "rank out of range (0..79)");
     if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
         fail(GEMSLR_ERR_ARG, "dev_alloc and dev_free must be given together");
+    if (o.lowrank_method != GEMSLR_LOWRANK_ARNOLDI && o.lowrank_method != GEMSLR_LOWRANK_RANDOMIZED)
+        fail(GEMSLR_ERR_ARG, "unknown lowrank_method");
+    if (o.lowrank_power < 0 || o.lowrank_power > 16) fail(GEMSLR_ERR_ARG, "lowrank_power must be in 0..16");
     return o;
 }
 
@@ -688,6 +772,8 @@ void gemslr_default_options(gemslr_options *opt) {
     opt->precision = GEMSLR_PREC_FP64;
     opt->arnoldi_tol = 1e-2;
     opt->arnoldi_max_cycles = 20;
+    opt->lowrank_method = GEMSLR_LOWRANK_ARNOLDI;
+    opt->lowrank_power = 1;
 }
 
 const char *gemslr_last_error(void) { return g_last_error.c_str(); }

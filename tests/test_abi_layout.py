@@ -16,7 +16,8 @@ STRUCTS = {
     "gemslr_csr": ("CSR", ["n", "rowptr", "colind", "val"]),
     "gemslr_partition": ("Partition", ["nlev", "perm", "level_ptr", "nblk", "block_ptr"]),
     "gemslr_options": ("Options", ["ilu_kind", "ilut_tau", "ilut_lfil", "rank", "precision", "arnoldi_tol",
-                                   "arnoldi_max_cycles", "strict_pivots", "dev_alloc", "dev_free", "alloc_ctx"]),
+                                   "arnoldi_max_cycles", "strict_pivots", "dev_alloc", "dev_free", "alloc_ctx",
+                                   "lowrank_method", "lowrank_power"]),
     "gemslr_mat": ("Mat", ["nrows", "ncols", "rowptr", "colind", "val"]),
     "gemslr_level_factors": ("LevelFactors", ["L", "U", "E", "F", "k", "W", "H"]),
     "gemslr_factors": ("Factors", ["nlev", "levels", "last_L", "last_U"]),

@@ -160,3 +160,30 @@ def test_maxit_reports_not_converged(torch_cuda):
     nan[3] = float("nan")
     xn, infon = G.solve(nan, restart=5, rtol=1e-8, check=False)
     assert infon[0]["status"] == "ERR_NAN"
+
+
+@pytest.mark.parametrize("name", ["small3d", "c1"])
+def test_randomized_setup_matches_oracle(torch_cuda, name):
+    """The randomized block set-up (subspace iteration on the same seeded
+    block, Rayleigh-Ritz) computed on the GPU gives the oracle's corrections as
+    operators (W H W^T is basis-independent, Sec. 2.2), and FGMRES with it takes
+    the oracle's iteration count to +-1."""
+    torch = torch_cuda
+    from oracle import OracleGemslr
+    from paper_2205_03224_gb300 import Gemslr
+    from tests.helpers import CASES
+    A, xyz, part = problem(name)
+    dims, beta, sigma, nlev, p, ilu, tau, lfil, rank = CASES[name]
+    M = OracleGemslr(A.to_scipy(), part, ilu=ilu, tau=tau, lfil=lfil, rank=rank, lowrank="randomized", power=1)
+    G = Gemslr(A, part, **lib_opts(name), lowrank="randomized", power=1)
+    f, ref = G.export_factors(), M.factors()
+    for lf, rf in zip(f["levels"], ref["levels"]):
+        W, H, Wr, Hr = lf["W"], lf["H"], rf["W"], rf["H"]
+        assert W.shape == Wr.shape
+        P = np.stack([gi.rhs_uniform(W.shape[0], q) for q in range(3)], axis=1)
+        assert rel_err(W @ (H @ (W.T @ P)), Wr @ (Hr @ (Wr.T @ P))) <= 1e-6
+    b = gi.rhs_uniform(A.n, 1)
+    As = A.to_scipy()
+    _, info_ref = fgmres(As, b, M.apply, restart=RESTART[name], rtol=1e-8)
+    x, info = G.solve(torch.from_numpy(b).cuda(), restart=RESTART[name], rtol=1e-8)
+    assert info[0]["converged"] and abs(info[0]["iters"] - info_ref["iters"]) <= 1
