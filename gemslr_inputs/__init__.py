@@ -143,18 +143,19 @@ def batch_systems(count=96, seed=3, lo=16, hi=48):
 
 
 # The five workloads: operator, partition shape, factor kind, rank, solver.
-# nlev counts the Schur levels plus the last (block-Jacobi) level.
+# nlev counts the Schur levels plus the last (block-Jacobi) level; local_from:
+# the first level whose blocks take the local multicolour order (None: none).
 CONFIGS = {
     "c1": dict(kind="2d", N=32, beta=0.0, sigma=0.0, nlev=2, p=4, ilu="ilu0",
                tau=0.0, lfil=0, rank=8, restart=30, rtol=1e-8, seed=0),
     "c2": dict(kind="3d", N=64, beta=0.1, sigma=0.0, nlev=4, p=64, ilu="ilut",
-               tau=1e-3, lfil=10, rank=32, restart=50, rtol=1e-8, seed=1),
+               tau=1e-3, lfil=10, rank=32, restart=50, rtol=1e-8, seed=1, local_from=1),
     "c3": dict(kind="3d", N=128, beta=0.0, sigma=0.05, nlev=4, p=64, ilu="ilut",
-               tau=1e-3, lfil=10, rank=64, restart=60, rtol=1e-8, seed=2),
+               tau=1e-3, lfil=10, rank=64, restart=60, rtol=1e-8, seed=2, local_from=1),
     "c4": dict(kind="batch", count=96, nlev=3, p=8, ilu="ilut", tau=1e-3, lfil=10,
                rank=16, restart=50, rtol=1e-8, seed=3, nrhs=8),
     "c5": dict(kind="3d", N=96, beta=0.0, sigma=0.1, nlev=4, p=64, ilu="ilut",
-               tau=1e-3, lfil=10, rank=32, restart=60, rtol=1e-8, seed=4),
+               tau=1e-3, lfil=10, rank=32, restart=60, rtol=1e-8, seed=4, local_from=1),
 }
 
 

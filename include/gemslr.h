@@ -132,6 +132,23 @@ gemslr_status gemslr_partition_geometric(const gemslr_csr *A, const int32_t *coo
                                          int64_t *block_ptr);
 
 /*
+ * Local order inside the diagonal blocks (Sec. 3.2: each B_l may be permuted
+ * locally, the multilevel structure unchanged).  For every block of the
+ * levels first_level .. nlev-1 (the last level included), the block's entries
+ * of part->perm are sorted stably by the colour key 8 t + c of their vertex,
+ * t = (floor(x/2) mod 2) + 2 (floor(y/2) mod 2) + 4 (floor(z/2) mod 2) the
+ * colour of its 2 x 2 x 2 tile and c = (x mod 2) + 2 (y mod 2) + 4 (z mod 2)
+ * its point colour (coords: n x 3 int32 grid coordinates, row-major).  Each
+ * class is an independent set of a 5- or 7-point stencil, so the blocks'
+ * triangular factors get fewer, wider wavefronts.  perm_out (n, caller-owned)
+ * receives the new permutation and may be part->perm itself; level_ptr, nblk
+ * and block_ptr stay valid.  Errors: ARG (NULL, first_level outside
+ * 0..nlev), PARTITION (inconsistent offsets).
+ */
+gemslr_status gemslr_local_order(int64_t n, const int32_t *coords, const gemslr_partition *part,
+                                 int32_t first_level, int32_t *perm_out);
+
+/*
  * Setup (Alg. 1): permute A, factor every diagonal block of every B_l and of
  * the last level, then bottom-up (Sec. 4.2) compute the rank-k_l correction
  * W_l [(I - R_l)^{-1} - I] W_l^T from thick-restart Arnoldi on

@@ -11,7 +11,7 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 library and never imports it; the only shared module is ``gemslr_inputs``,
 which generates the seeded synthetic problems.
 """
-from .partition import multilevel_partition, rcm_order, check_partition  # noqa: F401
+from .partition import multilevel_partition, rcm_order, check_partition, local_order  # noqa: F401
 from .ilu import ilu0, ilut  # noqa: F401
 from .gemslr import OracleGemslr  # noqa: F401
 from .fgmres import fgmres  # noqa: F401

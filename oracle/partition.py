@@ -151,6 +151,37 @@ def multilevel_partition(A, coords, nlev, p, p_last=None):
                 block_ptr=np.array(block_ptr, dtype=np.int64))
 
 
+def local_order(part, coords, first_level):
+    """Local order inside the diagonal blocks (Sec. 3.2: each B_l may be permuted
+    locally) of the levels first_level .. nlev-1.
+
+    Reading: the vertices of a block are grouped into the 64 classes given by
+    the parity of their 2 x 2 x 2 tile (floor(x/2), floor(y/2), floor(z/2) mod 2:
+    tile colour t = tx + 2 ty + 4 tz) and the parity of the point itself (point
+    colour c = px + 2 py + 4 pz); the classes are taken in the order of
+    8 t + c, and inside a class the vertices keep their order.  Returns a copy
+    of ``part`` with the new perm."""
+    coords = np.asarray(coords, dtype=np.int64)
+    perm = np.array(part["perm"], copy=True)
+    nlev = len(part["nblk"])
+    for l in range(first_level, nlev):
+        _, _, bp = level_blocks(part, l)
+        for j in range(len(bp) - 1):
+            a, b = int(bp[j]), int(bp[j + 1])
+            verts = perm[a:b]
+            c = coords[verts]
+            tile = ((c[:, 0] // 2) % 2) + 2 * ((c[:, 1] // 2) % 2) + 4 * ((c[:, 2] // 2) % 2)
+            point = (c[:, 0] % 2) + 2 * (c[:, 1] % 2) + 4 * (c[:, 2] % 2)
+            classes = 8 * tile + point
+            out = []
+            for k in range(64):                       # class after class, original order inside
+                out.extend(verts[classes == k].tolist())
+            perm[a:b] = out
+    res = dict(part)
+    res["perm"] = perm
+    return res
+
+
 def level_blocks(part, l):
     """(start, stop) offsets of level l and its block offsets (absolute)."""
     nblk = part["nblk"]

@@ -3,4 +3,4 @@
 The compute path is the CUDA library ``libgemslr.so`` (C ABI in
 ``include/gemslr.h``); this package only marshals arguments to it.
 """
-from .api import Gemslr, GemslrBatch, partition_geometric  # noqa: F401
+from .api import Gemslr, GemslrBatch, local_order, partition_geometric  # noqa: F401

@@ -67,7 +67,7 @@ STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_PARTITION", 3: "ERR_ZERO_PIVOT", 4: "ER
           5: "ERR_NAN", 6: "ERR_TIMEOUT", 7: "ERR_CUDA", 8: "ERR_NOMEM", 9: "ERR_UNSUPPORTED"}
 
 EXPORTED = [
-    "gemslr_default_options", "gemslr_partition_geometric", "gemslr_setup", "gemslr_setup_from_factors",
+    "gemslr_default_options", "gemslr_partition_geometric", "gemslr_local_order", "gemslr_setup", "gemslr_setup_from_factors",
     "gemslr_factor_sizes", "gemslr_export_factors", "gemslr_apply", "gemslr_fgmres_solve",
     "gemslr_get_stats", "gemslr_last_error", "gemslr_destroy", "gemslr_kernel_launches",
     "gemslr_profile_enable", "gemslr_profile_reset", "gemslr_profile_read",
@@ -98,6 +98,7 @@ def load():
     L.gemslr_default_options.argtypes = [ctypes.POINTER(Options)]
     L.gemslr_default_options.restype = None
     L.gemslr_partition_geometric.argtypes = [ctypes.POINTER(CSR), P, i32, i32, i32, P, P, P, P]
+    L.gemslr_local_order.argtypes = [i64, P, ctypes.POINTER(Partition), i32, P]
     L.gemslr_setup.argtypes = [ctypes.POINTER(CSR), ctypes.POINTER(Partition), ctypes.POINTER(Options), ctypes.POINTER(P)]
     L.gemslr_setup_from_factors.argtypes = [ctypes.POINTER(CSR), ctypes.POINTER(Partition),
                                             ctypes.POINTER(Factors), ctypes.POINTER(Options), ctypes.POINTER(P)]

@@ -11,8 +11,11 @@ def _stream(torch):
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def partition_geometric(A, coords, nlev, p, p_last=None):
-    """Multilevel partition (Alg. 3) computed by the library; returns a dict of arrays."""
+def partition_geometric(A, coords, nlev, p, p_last=None, local_from=None):
+    """Multilevel partition (Alg. 3) computed by the library; returns a dict of arrays.
+
+    local_from: if given, the blocks of levels local_from .. nlev-1 are then put in
+    the library's local multicolour order (``local_order``)."""
     lib = L.load()
     keep = []
     csr = L.csr_struct(A, keep)
@@ -25,7 +28,22 @@ def partition_geometric(A, coords, nlev, p, p_last=None):
     block_ptr = np.zeros((nlev - 1) * (p + 1) + p_last + 1, dtype=np.int64)
     L.check(lib.gemslr_partition_geometric(ctypes.byref(csr), L.ptr(coords), nlev, p, p_last, L.ptr(perm),
                                            L.ptr(level_ptr), L.ptr(nblk), L.ptr(block_ptr)))
-    return dict(perm=perm, level_ptr=level_ptr, nblk=nblk, block_ptr=block_ptr)
+    part = dict(perm=perm, level_ptr=level_ptr, nblk=nblk, block_ptr=block_ptr)
+    if local_from is not None:
+        part = local_order(part, coords, local_from)
+    return part
+
+
+def local_order(part, coords, first_level):
+    """The library's local multicolour order inside the blocks of levels first_level on (Sec. 3.2)."""
+    lib = L.load()
+    keep = []
+    n = len(part["perm"])
+    coords = np.ascontiguousarray(coords, dtype=np.int32).reshape(n, 3)
+    prt = L.partition_struct(part, keep)
+    out = np.zeros(n, dtype=np.int32)
+    L.check(lib.gemslr_local_order(n, L.ptr(coords), ctypes.byref(prt), int(first_level), L.ptr(out)))
+    return dict(part, perm=out)
 
 
 def torch_allocator():

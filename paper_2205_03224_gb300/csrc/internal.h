@@ -45,6 +45,9 @@ std::vector<int32_t> wavefronts_lower(const Csr &L, int64_t r0, int64_t r1);
 std::vector<int32_t> wavefronts_upper(const Csr &U, int64_t r0, int64_t r1);
 
 // ---- partitioner (partition.cpp) ------------------------------------------
+void local_order(const int32_t *coords, int64_t n, const std::vector<int64_t> &level_ptr,
+                 const std::vector<int32_t> &nblk, const std::vector<int64_t> &block_ptr, int first,
+                 std::vector<int32_t> &perm);
 void partition_geometric(const Csr &A, const int32_t *coords, int nlev, int p, int p_last,
                          std::vector<int32_t> &perm, std::vector<int64_t> &level_ptr,
                          std::vector<int32_t> &nblk, std::vector<int64_t> &block_ptr);

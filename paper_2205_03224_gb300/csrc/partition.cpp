@@ -169,4 +169,36 @@ void partition_geometric(const Csr &A, const int32_t *coords, int nlev, int p, i
     nblk.push_back(p_last);
 }
 
+// Local order inside the blocks of levels first .. nlev-1 (Sec. 3.2: each B_l
+// may be permuted locally).  A block's vertices are sorted stably by the
+// colour key 8 t + c, with t = (floor(x/2) mod 2) + 2 (floor(y/2) mod 2) +
+// 4 (floor(z/2) mod 2) the colour of the vertex's 2 x 2 x 2 tile and
+// c = (x mod 2) + 2 (y mod 2) + 4 (z mod 2) its point colour.  Two vertices of
+// one class differ by an even amount in every coordinate, so no class holds
+// two 7-point (or 5-point) neighbours: the classes are independent sets,
+// which shortens the wavefronts of the blocks' triangular factors.
+void local_order(const int32_t *coords, int64_t n, const std::vector<int64_t> &level_ptr,
+                 const std::vector<int32_t> &nblk, const std::vector<int64_t> &block_ptr, int first,
+                 std::vector<int32_t> &perm) {
+    const int nlev = (int)nblk.size();
+    if (first < 0 || first > nlev) fail(GEMSLR_ERR_ARG, "local order: first level out of range");
+    auto key = [&](int32_t v) {
+        const int32_t x = coords[3 * (int64_t)v], y = coords[3 * (int64_t)v + 1], z = coords[3 * (int64_t)v + 2];
+        const int t = ((x >> 1) & 1) + 2 * ((y >> 1) & 1) + 4 * ((z >> 1) & 1);
+        const int c = (x & 1) + 2 * (y & 1) + 4 * (z & 1);
+        return 8 * t + c;
+    };
+    int64_t off = 0;
+    for (int l = 0; l < nlev; ++l) {
+        for (int j = 0; j < nblk[l]; ++j) {
+            if (l < first) continue;
+            const int64_t a = level_ptr[l] + block_ptr[off + j], b = level_ptr[l] + block_ptr[off + j + 1];
+            if (a < 0 || b > n || a > b) fail(GEMSLR_ERR_PARTITION, "local order: block out of range");
+            std::stable_sort(perm.begin() + a, perm.begin() + b,
+                             [&](int32_t u, int32_t v) { return key(u) < key(v); });
+        }
+        off += nblk[l] + 1;
+    }
+}
+
 }  // namespace gemslr

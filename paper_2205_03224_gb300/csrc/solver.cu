@@ -794,6 +794,26 @@ gemslr_status gemslr_partition_geometric(const gemslr_csr *A, const int32_t *coo
     });
 }
 
+gemslr_status gemslr_local_order(int64_t n, const int32_t *coords, const gemslr_partition *part, int32_t first_level,
+                                 int32_t *perm_out) {
+    return guard([&] {
+        if (n < 0 || !coords || !part || !perm_out || !part->perm || !part->level_ptr || !part->nblk ||
+            !part->block_ptr || part->nlev < 1)
+            fail(GEMSLR_ERR_ARG, "NULL argument or empty partition");
+        std::vector<int32_t> pv(part->perm, part->perm + n), nb(part->nblk, part->nblk + part->nlev);
+        std::vector<int64_t> lp(part->level_ptr, part->level_ptr + part->nlev + 1);
+        int64_t nbp = 0;
+        for (int32_t v : nb) {
+            if (v < 1) fail(GEMSLR_ERR_PARTITION, "every level needs at least one block");
+            nbp += v + 1;
+        }
+        std::vector<int64_t> bp(part->block_ptr, part->block_ptr + nbp);
+        if (lp[0] != 0 || lp.back() != n) fail(GEMSLR_ERR_PARTITION, "level_ptr must run from 0 to n");
+        local_order(coords, n, lp, nb, bp, first_level, pv);
+        std::copy(pv.begin(), pv.end(), perm_out);
+    });
+}
+
 gemslr_status gemslr_setup(const gemslr_csr *A, const gemslr_partition *part, const gemslr_options *opt,
                            gemslr_handle *out) {
     if (out) *out = nullptr;

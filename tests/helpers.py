@@ -4,7 +4,7 @@ import functools
 import numpy as np
 
 import gemslr_inputs as gi
-from oracle import OracleGemslr, multilevel_partition
+from oracle import OracleGemslr, local_order, multilevel_partition
 
 CASES = {
     # name: (dims, beta, sigma, nlev, p, ilu, tau, lfil, rank)
@@ -15,6 +15,8 @@ CASES = {
     "tinyparts": ((6, 5, 4), 0.3, 0.0, 3, 16, "ilu0", 0.0, 0, 3),
     "bigblock": ((240, 240), 0.5, 0.0, 2, 2, "ilu0", 0.0, 0, 4),
     "c2": ((64, 64, 64), 0.1, 0.0, 4, 64, "ilut", 1e-3, 10, 32),
+    # the benchmarked 64^3 workload: interface levels in the local multicolour order
+    "c2local": ((64, 64, 64), 0.1, 0.0, 4, 64, "ilut", 1e-3, 10, 32),
     # indefinite (shift 0.1 h^-2): the DGKS test skips the second Gram-Schmidt
     # pass at step 7 of the first cycle, every other step takes it
     "indef24": ((24, 24, 24), 0.0, 0.1, 4, 8, "ilut", 1e-3, 10, 8),
@@ -23,11 +25,16 @@ CASES = {
 }
 
 
+LOCAL_FROM = {"c2local": 1}
+
+
 @functools.lru_cache(maxsize=None)
 def problem(name):
     dims, beta, sigma, nlev, p, ilu, tau, lfil, rank = CASES[name]
     A, xyz = gi.grid_operator(dims, beta=beta, sigma=sigma)
     part = multilevel_partition(A.to_scipy(), xyz, nlev, p)
+    if name in LOCAL_FROM:
+        part = local_order(part, xyz, LOCAL_FROM[name])
     return A, xyz, part
 
 

@@ -30,7 +30,7 @@ def _lib_from_oracle(name):
     return Gemslr.from_factors(A, part, M.factors()), M
 
 
-@pytest.mark.parametrize("name", ["c1", "small3d", "shifted", "rank0", "tinyparts", "bigblock", "c2"])
+@pytest.mark.parametrize("name", ["c1", "small3d", "shifted", "rank0", "tinyparts", "bigblock", "c2", "c2local"])
 def test_apply_matches_oracle(torch_cuda, name):
     torch = torch_cuda
     G, M = _lib_from_oracle(name)

@@ -23,7 +23,7 @@ def torch_cuda():
     return torch
 
 
-@pytest.mark.parametrize("name", ["c1", "small3d", "shifted", "c2"])
+@pytest.mark.parametrize("name", ["c1", "small3d", "shifted", "c2", "c2local"])
 def test_mixed_apply_error_against_fp64_oracle(torch_cuda, name):
     torch = torch_cuda
     from paper_2205_03224_gb300 import Gemslr
@@ -54,13 +54,13 @@ def test_mixed_apply_with_bf16_w_is_fp32_accurate(torch_cuda, name):
     assert 0.0 < err <= 1e-4, err
 
 
-@pytest.mark.parametrize("name", ["c1", "small3d", "c2"])
+@pytest.mark.parametrize("name", ["c1", "small3d", "c2", "c2local"])
 def test_mixed_fgmres_reaches_1e8(torch_cuda, name):
     torch = torch_cuda
     from paper_2205_03224_gb300 import Gemslr
     A, xyz, part = problem(name)
     M = oracle_hierarchy(name)
-    restart = {"c1": 30, "small3d": 20, "c2": 50}[name]
+    restart = {"c1": 30, "small3d": 20, "c2": 50, "c2local": 50}[name]
     b = gi.rhs_uniform(M.n, 1)
     _, info_ref = fgmres(A.to_scipy(), b, M.apply, restart=restart, rtol=1e-8)
     G = Gemslr.from_factors(A, part, M.factors(), precision="mixed")

@@ -17,11 +17,11 @@ def torch_cuda():
     return torch
 
 
-RESTART = {"c1": 30, "small3d": 20, "shifted": 30, "c2": 50}
+RESTART = {"c1": 30, "small3d": 20, "shifted": 30, "c2": 50, "c2local": 50}
 
 
 @pytest.mark.parametrize("ortho", ["auto", "cgs2"])
-@pytest.mark.parametrize("name", ["c1", "small3d", "shifted", "c2"])
+@pytest.mark.parametrize("name", ["c1", "small3d", "shifted", "c2", "c2local"])
 def test_fgmres_matches_oracle_iterations(torch_cuda, name, ortho):
     torch = torch_cuda
     from paper_2205_03224_gb300 import Gemslr

@@ -106,3 +106,57 @@ def test_c2_level_sizes():
     s, e, bp = level_blocks(P, 0)
     d = np.diff(bp)
     assert d.min() == 15**3 and d.max() == 16**3
+
+
+def test_local_order_keeps_blocks_and_separates_neighbours():
+    """The local order (Sec. 3.2) only permutes inside the blocks of the chosen
+    levels; inside a block the colour key never decreases and equal keys keep
+    their original order; two vertices of one class are never neighbours in
+    the stencil graph (brute force), so each class is an independent set."""
+    from oracle.partition import level_blocks, local_order
+    A, xyz = gi.grid_operator((11, 9, 7), beta=0.3)
+    As = A.to_scipy()
+    part = multilevel_partition(As, xyz, 4, 8)
+    loc = local_order(part, xyz, 1)
+    check_partition(As, loc)
+    G = (abs(As) + abs(As.T)).tocsr()
+    c = np.asarray(xyz, dtype=np.int64)
+    key = 8 * (((c[:, 0] // 2) % 2) + 2 * ((c[:, 1] // 2) % 2) + 4 * ((c[:, 2] // 2) % 2)) + \
+        (c[:, 0] % 2) + 2 * (c[:, 1] % 2) + 4 * (c[:, 2] % 2)
+    for l in range(4):
+        _, _, bp = level_blocks(part, l)
+        for j in range(len(bp) - 1):
+            a, b = bp[j], bp[j + 1]
+            old, new = part["perm"][a:b], loc["perm"][a:b]
+            assert sorted(old) == sorted(new)
+            if l == 0:
+                assert np.array_equal(old, new)            # level 0 untouched
+                continue
+            k = key[new]
+            assert np.all(np.diff(k) >= 0)
+            pos = {v: i for i, v in enumerate(old)}
+            for cls in np.unique(k):
+                members = new[k == cls]
+                assert all(pos[members[i]] < pos[members[i + 1]] for i in range(len(members) - 1))
+                ms = set(members.tolist())
+                for v in members:
+                    nb = G.indices[G.indptr[v]:G.indptr[v + 1]]
+                    assert not any(u in ms and u != v for u in nb)
+
+
+def test_library_local_order_equals_oracle():
+    pytest = __import__("pytest")
+    try:
+        from paper_2205_03224_gb300 import local_order as lib_local_order, partition_geometric
+        from paper_2205_03224_gb300 import _lib
+        _lib.load()
+    except (ImportError, OSError):
+        pytest.skip("library not built")
+    from oracle.partition import local_order
+    for dims, nlev, p in (((13, 11, 9), 3, 8), ((20, 17), 3, 4), ((16, 16, 16), 4, 8)):
+        A, xyz = gi.grid_operator(dims, beta=0.2)
+        part = partition_geometric(A, xyz, nlev, p)
+        for first in (0, 1, nlev - 1):
+            ref = local_order(part, xyz, first)
+            got = lib_local_order(part, xyz, first)
+            assert np.array_equal(ref["perm"], got["perm"]), (dims, first)
