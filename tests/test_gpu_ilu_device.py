@@ -49,3 +49,14 @@ def test_device_ilu0_factors_match_oracle_and_solve(torch_cuda):
     x, info = G.solve(torch.from_numpy(b).cuda(), restart=30, rtol=1e-8)
     res = np.linalg.norm(b - A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(b)
     assert info[0]["converged"] and res <= 1e-8
+
+
+def test_device_ilu0_mixed_application_equals_host_ilu0(torch_cuda):
+    """Identical factors give the identical mixed-precision application."""
+    torch = torch_cuda
+    from paper_2205_03224_gb300 import Gemslr
+    A, xyz, part = problem("tinyparts")
+    r = torch.from_numpy(gi.rhs_uniform(A.n, 5)).cuda()
+    zh = Gemslr(A, part, ilu="ilu0", rank=3, precision="mixed").apply(r)
+    zd = Gemslr(A, part, ilu="ilu0_device", rank=3, precision="mixed").apply(r)
+    assert torch.equal(zh, zd)

@@ -187,3 +187,31 @@ def test_randomized_setup_matches_oracle(torch_cuda, name):
     _, info_ref = fgmres(As, b, M.apply, restart=RESTART[name], rtol=1e-8)
     x, info = G.solve(torch.from_numpy(b).cuda(), restart=RESTART[name], rtol=1e-8)
     assert info[0]["converged"] and abs(info[0]["iters"] - info_ref["iters"]) <= 1
+
+
+def test_randomized_setup_mixed_and_local_order_2d(torch_cuda):
+    """The randomized set-up with the mixed-precision application, and the
+    local multicolour order on a 2-D problem (every level), both solve to 1e-8;
+    the locally ordered 2-D application matches the oracle on the same order."""
+    torch = torch_cuda
+    from oracle import OracleGemslr, local_order, multilevel_partition
+    from paper_2205_03224_gb300 import Gemslr, partition_geometric
+    A, xyz, part = problem("small3d")
+    b = gi.rhs_uniform(A.n, 3)
+    G = Gemslr(A, part, **lib_opts("small3d"), lowrank="randomized", power=2, precision="mixed")
+    x, info = G.solve(torch.from_numpy(b).cuda(), restart=20, rtol=1e-8)
+    res = np.linalg.norm(b - A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert info[0]["converged"] and res <= 1e-8
+    A2, xyz2 = gi.laplace2d(40)
+    A2s = A2.to_scipy()
+    part2 = partition_geometric(A2, xyz2, 3, 4, local_from=0)
+    ref2 = local_order(multilevel_partition(A2s, xyz2, 3, 4), xyz2, 0)
+    assert np.array_equal(part2["perm"], ref2["perm"])
+    M = OracleGemslr(A2s, ref2, ilu="ilut", tau=1e-3, lfil=10, rank=6)
+    G2 = Gemslr.from_factors(A2, part2, M.factors())
+    r = gi.rhs_uniform(A2.n, 4)
+    assert rel_err(G2.apply(torch.from_numpy(r).cuda()).cpu().numpy(), M.apply(r)) <= 1e-10
+    b2 = gi.rhs_uniform(A2.n, 1)
+    _, info_ref = fgmres(A2s, b2, M.apply, restart=30, rtol=1e-8)
+    x2, info2 = G2.solve(torch.from_numpy(b2).cuda(), restart=30, rtol=1e-8)
+    assert info2[0]["converged"] and abs(info2[0]["iters"] - info_ref["iters"]) <= 1

@@ -77,3 +77,27 @@ def test_binding_argument_counts_match_the_header(lib):
         fn = getattr(lib, name)
         assert fn.argtypes is not None, name
         assert len(fn.argtypes) == nparam, (name, nparam, len(fn.argtypes))
+
+
+def test_local_order_and_batch_from_factors_reject_bad_arguments(lib):
+    """Argument errors of the host-only entry points are reported before any
+    device work: a NULL permutation or an out-of-range first level for the
+    local order, NULL factors for the batch set-up from factors."""
+    from paper_2205_03224_gb300 import _lib, local_order, partition_geometric
+    from paper_2205_03224_gb300._lib import GemslrError
+    A, xyz = gi.grid_operator((9, 7, 6), beta=0.3)
+    part = partition_geometric(A, xyz, 3, 4)
+    with pytest.raises(GemslrError):
+        local_order(part, xyz, 4)                  # first level past nlev
+    keep = []
+    prt = _lib.partition_struct(part, keep)
+    st = lib.gemslr_local_order(A.n, _lib.ptr(np.ascontiguousarray(xyz, dtype=np.int32)), ctypes.byref(prt), 1,
+                                None)
+    assert _lib.STATUS[st] == "ERR_ARG"
+    csr = _lib.csr_struct(A, keep)
+    h = ctypes.c_void_p()
+    st = lib.gemslr_setup_batch_from_factors(1, ctypes.byref(csr), ctypes.byref(prt), None, None, ctypes.byref(h))
+    assert _lib.STATUS[st] == "ERR_ARG" and not h.value
+    # the identity case: first level = nlev leaves the permutation unchanged
+    same = local_order(part, xyz, 3)
+    assert np.array_equal(same["perm"], part["perm"])
