@@ -53,20 +53,20 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2.07 * 2
 TRAFFIC_SOURCES = ["kernels.cu", "kernels.cuh", "ptx.cuh", "device.cu"]
 NCU_TRAFFIC_DIGEST = "439ad4e5a5c41f9b"
 NCU_TRAFFIC = {
-    ("c2", "mixed", "trsv_down_L0"): 43_783_168,
-    ("c2", "mixed", "trsv_down_L1"): 5_068_544,
-    ("c2", "mixed", "trsv_down_L2"): 485_888,
-    ("c2", "mixed", "trsv_last"): 170_496,
-    ("c2", "mixed", "trsv_up_L2"): 330_496,
-    ("c2", "mixed", "trsv_up_L1"): 3_444_480,
-    ("c2", "mixed", "trsv_up_L0"): 45_625_088,
-    ("c2", "fp64", "trsv_down_L0"): 73_697_536,
-    ("c2", "fp64", "trsv_down_L1"): 12_483_072,
-    ("c2", "fp64", "trsv_down_L2"): 1_318_400,
-    ("c2", "fp64", "trsv_last"): 367_360,
-    ("c2", "fp64", "trsv_up_L2"): 559_616,
-    ("c2", "fp64", "trsv_up_L1"): 4_950_528,
-    ("c2", "fp64", "trsv_up_L0"): 76_695_296,
+    ("c2", "mixed", "trsv_down_L0"): 43_782_912,
+    ("c2", "mixed", "trsv_down_L1"): 6_459_392,
+    ("c2", "mixed", "trsv_down_L2"): 439_296,
+    ("c2", "mixed", "trsv_last"): 146_944,
+    ("c2", "mixed", "trsv_up_L2"): 284_416,
+    ("c2", "mixed", "trsv_up_L1"): 4_819_712,
+    ("c2", "mixed", "trsv_up_L0"): 45_624_320,
+    ("c2", "fp64", "trsv_down_L0"): 73_890_816,
+    ("c2", "fp64", "trsv_down_L1"): 15_527_168,
+    ("c2", "fp64", "trsv_down_L2"): 1_221_888,
+    ("c2", "fp64", "trsv_last"): 342_016,
+    ("c2", "fp64", "trsv_up_L2"): 463_104,
+    ("c2", "fp64", "trsv_up_L1"): 7_985_408,
+    ("c2", "fp64", "trsv_up_L0"): 76_709_888,
 }
 NCU_TRAFFIC_KRYLOV = {
     ("c2", "mixed", "dgs_fix_adots"): (54_605_056 + 78_592, None),
