@@ -111,11 +111,23 @@ typedef struct {
      * then Rayleigh-Ritz with the same selection of the wanted values). */
     int32_t lowrank_method;
     int32_t lowrank_power;        /* subspace-iteration passes (randomized; 1)   */
+    /* Complex diagonal shift of the incomplete factorisations (Sec. 5.2.3, the
+     * paper's Helmholtz experiments use 0.05): with shift != 0 every diagonal
+     * block of every B_l and of the last level is factored as B + i alpha I,
+     * alpha = shift * sum_i |a_ii| / n (E, F and C are not shifted), the
+     * corrections come from the Arnoldi in complex arithmetic (W H W^H, complex
+     * Schur form), and the handle is complex: gemslr_zapply and
+     * gemslr_zfgmres_solve apply and solve in complex FP64; the real entry
+     * points refuse it (ARG).  A complex handle needs precision FP64,
+     * ilu_kind ILU0 or ILUT and the Arnoldi set-up, else UNSUPPORTED.  0: the
+     * real method (the default). */
+    double shift;
 } gemslr_options;
 enum { GEMSLR_LOWRANK_ARNOLDI = 0, GEMSLR_LOWRANK_RANDOMIZED = 1 };
 
 /* Fill *opt with the defaults: ILUT(1e-3, 10), rank 0, FP64, 1e-2, 20 cycles,
- * Arnoldi set-up of the corrections (1 pass when randomized is chosen). */
+ * Arnoldi set-up of the corrections (1 pass when randomized is chosen), no
+ * complex shift. */
 void gemslr_default_options(gemslr_options *opt);
 
 /*
@@ -181,25 +193,33 @@ typedef struct {
     int32_t k;
     const double *W;
     const double *H;
+    /* Complex factors (the complex shift, Sec. 5.2.3): imaginary parts of
+     * L.val, U.val (nnz each), W (s x k) and H (k x k), same layouts; NULL: 0.
+     * Factors with any imaginary part make a complex handle. */
+    const double *L_im, *U_im, *W_im, *H_im;
 } gemslr_level_factors;
 
 typedef struct {
     int32_t nlev;
     const gemslr_level_factors *levels;   /* nlev - 1 Schur levels              */
     gemslr_mat last_L, last_U;            /* last level, block diagonal         */
+    const double *last_L_im, *last_U_im;  /* imaginary parts (NULL: 0)          */
 } gemslr_factors;
 
 /*
  * Build a handle from factors computed elsewhere (checkpoint/resume, or a
  * reference computation): nothing is factored, the permuted A is still
- * formed for the FGMRES products.  Same errors as gemslr_setup.
+ * formed for the FGMRES products.  Factors with imaginary parts give a
+ * complex handle (FP64 only).  Same errors as gemslr_setup.
  */
 gemslr_status gemslr_setup_from_factors(const gemslr_csr *A, const gemslr_partition *part,
                                         const gemslr_factors *f, const gemslr_options *opt,
                                         gemslr_handle *out);
 
 /*
- * Sizes of the handle's factors (for gemslr_export_factors buffers):
+ * Sizes of the handle's factors (for gemslr_export_factors buffers; a complex
+ * handle exports its imaginary parts into the *_im buffers, which must then
+ * all be given, and cannot be saved to a factor file: UNSUPPORTED):
  * counts[0] = nlev; then per Schur level l, 9 entries starting at 1 + 9*l:
  * nnz(L), nnz(U), nnz(E), nnz(F), k, d_l, s_l, level_ptr[l], level_ptr[l+1];
  * then nnz(last_L), nnz(last_U), size of the last level.  ncounts must be at
@@ -294,6 +314,24 @@ typedef struct {
 gemslr_status gemslr_fgmres_solve(gemslr_handle h, const double *b_dev, double *x_dev,
                                   int32_t nrhs, const gemslr_solve_opts *opts,
                                   gemslr_solve_info *info, void *stream);
+
+/*
+ * Complex application and solve (handles set up with a complex shift, or from
+ * complex factors; Sec. 5.2.3): the same operations as gemslr_apply and
+ * gemslr_fgmres_solve in complex FP64.  Vectors are n x nrhs column-major
+ * arrays of complex values stored as (re, im) double pairs (the C99
+ * double _Complex layout), in the original ordering.  gemslr_zapply:
+ * z = M^{-1} r, asynchronous on `stream`, r and z may not alias.
+ * gemslr_zfgmres_solve: restarted right-preconditioned FGMRES(m) (Sec. 4.1)
+ * with x_0 = 0, inner products v^H w, classical Gram-Schmidt with a second
+ * pass, complex Givens rotations; stops on the true residual
+ * ||b - A x|| <= rtol ||b||.  opts->ortho is ignored.  Synchronises `stream`.
+ * Errors: ARG (a real handle, NULL or invalid arguments, another device
+ * current), NOT_CONVERGED (info filled), NAN, CUDA, TIMEOUT.
+ */
+gemslr_status gemslr_zapply(gemslr_handle h, const double *r_dev, double *z_dev, int32_t nrhs, void *stream);
+gemslr_status gemslr_zfgmres_solve(gemslr_handle h, const double *b_dev, double *x_dev, int32_t nrhs,
+                                   const gemslr_solve_opts *opts, gemslr_solve_info *info, void *stream);
 
 /*
  * Statistics: out[0..] = n, nlev, nclamped pivots, nnz(A), nnz of all

@@ -34,7 +34,7 @@ class Options(ctypes.Structure):
     _fields_ = [("ilu_kind", i32), ("ilut_tau", f64), ("ilut_lfil", i32), ("rank", i32 * MAX_LEVELS),
                 ("precision", i32), ("arnoldi_tol", f64), ("arnoldi_max_cycles", i32),
                 ("strict_pivots", i32), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ctx", P),
-                ("lowrank_method", i32), ("lowrank_power", i32)]
+                ("lowrank_method", i32), ("lowrank_power", i32), ("shift", f64)]
 
 
 class Mat(ctypes.Structure):
@@ -42,11 +42,13 @@ class Mat(ctypes.Structure):
 
 
 class LevelFactors(ctypes.Structure):
-    _fields_ = [("L", Mat), ("U", Mat), ("E", Mat), ("F", Mat), ("k", i32), ("W", P), ("H", P)]
+    _fields_ = [("L", Mat), ("U", Mat), ("E", Mat), ("F", Mat), ("k", i32), ("W", P), ("H", P),
+                ("L_im", P), ("U_im", P), ("W_im", P), ("H_im", P)]
 
 
 class Factors(ctypes.Structure):
-    _fields_ = [("nlev", i32), ("levels", ctypes.POINTER(LevelFactors)), ("last_L", Mat), ("last_U", Mat)]
+    _fields_ = [("nlev", i32), ("levels", ctypes.POINTER(LevelFactors)), ("last_L", Mat), ("last_U", Mat),
+                ("last_L_im", P), ("last_U_im", P)]
 
 
 class LearnedOpts(ctypes.Structure):
@@ -75,7 +77,7 @@ EXPORTED = [
     "gemslr_batch_last_error", "gemslr_batch_destroy",
     "gemslr_learned_train", "gemslr_learned_enable", "gemslr_learned_info", "gemslr_learned_params",
     "gemslr_learned_loss_grad", "gemslr_apply_static", "gemslr_selftest_wait", "gemslr_set_inner_steps",
-    "gemslr_save_factors", "gemslr_load_factors",
+    "gemslr_save_factors", "gemslr_load_factors", "gemslr_zapply", "gemslr_zfgmres_solve",
 ]
 
 _lib = None
@@ -106,6 +108,8 @@ def load():
     L.gemslr_export_factors.argtypes = [P, ctypes.POINTER(Factors)]
     L.gemslr_apply.argtypes = [P, P, P, i32, P]
     L.gemslr_fgmres_solve.argtypes = [P, P, P, i32, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), P]
+    L.gemslr_zapply.argtypes = [P, P, P, i32, P]
+    L.gemslr_zfgmres_solve.argtypes = [P, P, P, i32, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), P]
     L.gemslr_get_stats.argtypes = [P, P, i32]
     L.gemslr_last_error.restype = ctypes.c_char_p
     L.gemslr_last_error.argtypes = []
@@ -185,15 +189,25 @@ def partition_struct(part, keep):
 
 
 def mat_struct(M, keep):
-    """gemslr_mat from a scipy CSR matrix."""
+    """gemslr_mat from a scipy CSR matrix (real)."""
+    return mat_struct_z(M, keep)[0]
+
+
+def mat_struct_z(M, keep):
+    """(gemslr_mat, imaginary parts or None) from a scipy CSR matrix, real or complex."""
     import scipy.sparse as sp
     M = sp.csr_matrix(M)
     M.sort_indices()
     rp = np.ascontiguousarray(M.indptr, dtype=np.int64)
     ci = np.ascontiguousarray(M.indices, dtype=np.int32)
-    v = np.ascontiguousarray(M.data, dtype=np.float64)
+    v = np.ascontiguousarray(M.data.real, dtype=np.float64)
     keep.extend([rp, ci, v])
-    return Mat(M.shape[0], M.shape[1], ptr(rp), ptr(ci), ptr(v))
+    im = None
+    if np.iscomplexobj(M.data):
+        vi = np.ascontiguousarray(M.data.imag, dtype=np.float64)
+        keep.append(vi)
+        im = ptr(vi)
+    return Mat(M.shape[0], M.shape[1], ptr(rp), ptr(ci), ptr(v)), im
 
 
 def kernel_launches():

@@ -69,9 +69,10 @@ def torch_allocator():
 
 
 def options(ilu="ilut", tau=1e-3, lfil=10, rank=0, precision="fp64", arnoldi_tol=1e-2, max_cycles=20,
-            strict_pivots=False, allocator=None, lowrank="arnoldi", power=1):
+            strict_pivots=False, allocator=None, lowrank="arnoldi", power=1, shift=0.0):
     """gemslr_options; allocator: None (cudaMalloc) or a (dev_alloc, dev_free) pair of callbacks;
-    lowrank: "arnoldi" or "randomized" set-up of the corrections (power: subspace-iteration passes)."""
+    lowrank: "arnoldi" or "randomized" set-up of the corrections (power: subspace-iteration passes);
+    shift: complex diagonal shift of the factorisations (0: the real method)."""
     o = L.Options()
     L.load().gemslr_default_options(ctypes.byref(o))
     o.ilu_kind = {"ilu0": 0, "ilut": 1, "ilu0_device": 2}[ilu]
@@ -86,6 +87,7 @@ def options(ilu="ilut", tau=1e-3, lfil=10, rank=0, precision="fp64", arnoldi_tol
     o.strict_pivots = 1 if strict_pivots else 0
     o.lowrank_method = {"arnoldi": 0, "randomized": 1}[lowrank]
     o.lowrank_power = int(power)
+    o.shift = float(shift)
     if allocator is not None:
         o.dev_alloc, o.dev_free = allocator
     return o
@@ -102,18 +104,37 @@ def _resolve_allocator(opts):
 
 
 def _factors_struct(fac, keep):
-    """gemslr_factors view of a factor dict (layout of ``oracle``'s factors()); arrays kept alive in keep."""
+    """gemslr_factors view of a factor dict (layout of ``oracle``'s factors()); arrays kept alive in keep.
+    Complex factors (the complex shift) pass their imaginary parts separately."""
     lv = fac["levels"]
     arr = (L.LevelFactors * max(len(lv), 1))()
     keep.append(arr)
+
+    def parts(X):
+        X = np.asarray(X)
+        re = np.asfortranarray(X.real, dtype=np.float64)
+        im = np.asfortranarray(X.imag, dtype=np.float64) if np.iscomplexobj(X) else None
+        keep.extend([re, im])
+        return re, im
+
     for i, f in enumerate(lv):
-        W = np.asfortranarray(f["W"], dtype=np.float64)
-        H = np.asfortranarray(f["H"], dtype=np.float64)
-        keep.extend([W, H])
-        arr[i] = L.LevelFactors(L.mat_struct(f["L"], keep), L.mat_struct(f["U"], keep),
-                                L.mat_struct(f["E"], keep), L.mat_struct(f["F"], keep),
-                                W.shape[1], L.ptr(W) if W.size else None, L.ptr(H) if H.size else None)
-    return L.Factors(len(lv) + 1, arr, L.mat_struct(fac["last"]["L"], keep), L.mat_struct(fac["last"]["U"], keep))
+        W, Wi = parts(f["W"])
+        H, Hi = parts(f["H"])
+        Lm, Li = L.mat_struct_z(f["L"], keep)
+        Um, Ui = L.mat_struct_z(f["U"], keep)
+        arr[i] = L.LevelFactors(Lm, Um, L.mat_struct(f["E"], keep), L.mat_struct(f["F"], keep),
+                                W.shape[1], L.ptr(W) if W.size else None, L.ptr(H) if H.size else None,
+                                Li, Ui, L.ptr(Wi) if Wi is not None and Wi.size else None,
+                                L.ptr(Hi) if Hi is not None and Hi.size else None)
+    lL, lLi = L.mat_struct_z(fac["last"]["L"], keep)
+    lU, lUi = L.mat_struct_z(fac["last"]["U"], keep)
+    return L.Factors(len(lv) + 1, arr, lL, lU, lLi, lUi)
+
+
+def _is_complex_factors(fac):
+    import scipy.sparse as sp
+    mats = [f[k] for f in fac["levels"] for k in ("L", "U", "W", "H")] + [fac["last"]["L"], fac["last"]["U"]]
+    return any(np.iscomplexobj(m.data if sp.issparse(m) else np.asarray(m)) for m in mats)
 
 
 class Gemslr:
@@ -122,10 +143,12 @@ class Gemslr:
     Device memory comes from PyTorch's caching allocator unless allocator=None
     (then the library calls cudaMalloc itself)."""
 
-    def __init__(self, A, part, _handle=None, _alloc=None, **opts):
+    def __init__(self, A, part, _handle=None, _alloc=None, _complex=False, **opts):
         self._lib = L.load()
         self.n = int(len(part["perm"]))
         self.nlev = int(len(part["nblk"]))
+        # complex handle (complex shift, Sec. 5.2.3): apply/solve take complex128 tensors
+        self.complex = bool(_complex) or float(opts.get("shift", 0.0)) != 0.0
         if _handle is not None:
             self._h = _handle
             self._alloc = _alloc
@@ -152,7 +175,7 @@ class Gemslr:
         h = ctypes.c_void_p()
         L.check(lib.gemslr_setup_from_factors(ctypes.byref(csr), ctypes.byref(prt), ctypes.byref(fs),
                                               ctypes.byref(o), ctypes.byref(h)))
-        return cls(A, part, _handle=h, _alloc=alloc)
+        return cls(A, part, _handle=h, _alloc=alloc, _complex=_is_complex_factors(fac))
 
     def save_factors(self, path):
         """Write every factor of the handle to `path` (checkpoint of the set-up)."""
@@ -184,28 +207,35 @@ class Gemslr:
             pass
 
     def apply(self, r):
-        """z = M^{-1} r for a CUDA float64 tensor r of shape (n,) or (n, nrhs) column-major."""
+        """z = M^{-1} r for a CUDA float64 tensor r of shape (n,) or (n, nrhs) column-major
+        (complex128 for a complex handle)."""
         import torch
+        if self.complex:
+            r = r.to(torch.complex128)
         r = r.contiguous() if r.dim() == 1 else r.t().contiguous().t()
         z = torch.empty_like(r)
         nrhs = 1 if r.dim() == 1 else r.shape[1]
-        L.check(self._lib.gemslr_apply(self._h, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr()),
-                                       nrhs, _stream(torch)))
+        fn = self._lib.gemslr_zapply if self.complex else self._lib.gemslr_apply
+        L.check(fn(self._h, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr()), nrhs, _stream(torch)))
         return z
 
     def solve(self, b, restart=50, rtol=1e-8, maxit=1000, check=True, ortho="auto"):
         """FGMRES(restart) on A x = b; returns (x, [info dict per right-hand side]).
 
         ortho: "auto" (delayed reorthogonalisation where M^{-1} is linear) or
-        "cgs2" (classical Gram-Schmidt with a selective second pass)."""
+        "cgs2" (classical Gram-Schmidt with a selective second pass).  A complex handle solves in
+        complex arithmetic (b and x complex128; ortho is ignored)."""
         import torch
+        if self.complex:
+            b = b.to(torch.complex128)
         b = b.contiguous() if b.dim() == 1 else b.t().contiguous().t()
         x = torch.empty_like(b)
         nrhs = 1 if b.dim() == 1 else b.shape[1]
         so = L.SolveOpts(restart, maxit, rtol, {"auto": 0, "cgs2": 1}[ortho])
         info = (L.SolveInfo * nrhs)()
-        st = self._lib.gemslr_fgmres_solve(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
-                                           nrhs, ctypes.byref(so), info, _stream(torch))
+        fn = self._lib.gemslr_zfgmres_solve if self.complex else self._lib.gemslr_fgmres_solve
+        st = fn(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nrhs, ctypes.byref(so), info,
+                _stream(torch))
         infos = [dict(iters=i.iters, restarts=i.restarts, converged=bool(i.converged), reorth=i.reorth,
                       rel_res_est=i.rel_res_est, rel_res_true=i.rel_res_true, t_total_ms=i.t_total_ms,
                       status=L.STATUS.get(st, st)) for i in info]
@@ -270,12 +300,18 @@ class Gemslr:
         L.check(self._lib.gemslr_factor_sizes(self._h, L.ptr(counts), len(counts)))
         keep = []
 
+        cx = self.complex
+
         def mk(nrows, ncols, nnz):
             rp = np.zeros(nrows + 1, dtype=np.int64)
             ci = np.zeros(max(nnz, 1), dtype=np.int32)
             v = np.zeros(max(nnz, 1), dtype=np.float64)
-            keep.append((rp, ci, v, nrows, ncols, nnz))
+            vi = np.zeros(max(nnz, 1), dtype=np.float64)
+            keep.append((rp, ci, v, nrows, ncols, nnz, vi))
             return L.Mat(nrows, ncols, L.ptr(rp), L.ptr(ci), L.ptr(v)), len(keep) - 1
+
+        def im(i):
+            return L.ptr(keep[i][6]) if cx else None
 
         arr = (L.LevelFactors * max(nl - 1, 1))()
         meta = []
@@ -288,24 +324,31 @@ class Gemslr:
             mF, iF = mk(d, s, nF)
             W = np.zeros((s, max(k, 1)), dtype=np.float64, order="F")
             H = np.zeros((max(k, 1), max(k, 1)), dtype=np.float64, order="F")
-            arr[l] = L.LevelFactors(mL, mU, mE, mF, k, L.ptr(W), L.ptr(H))
-            meta.append((iL, iU, iE, iF, W, H, k, int(c[7]), int(c[8])))
+            Wi = np.zeros_like(W)
+            Hi = np.zeros_like(H)
+            arr[l] = L.LevelFactors(mL, mU, mE, mF, k, L.ptr(W), L.ptr(H), im(iL), im(iU),
+                                    L.ptr(Wi) if cx else None, L.ptr(Hi) if cx else None)
+            meta.append((iL, iU, iE, iF, W, H, Wi, Hi, k, int(c[7]), int(c[8])))
         c = counts[1 + 9 * (nl - 1):]
         nLl, nUl, sl = int(c[0]), int(c[1]), int(c[2])
         mLl, iLl = mk(sl, sl, nLl)
         mUl, iUl = mk(sl, sl, nUl)
-        fs = L.Factors(nl, arr, mLl, mUl)
+        fs = L.Factors(nl, arr, mLl, mUl, im(iLl), im(iUl))
         L.check(self._lib.gemslr_export_factors(self._h, ctypes.byref(fs)))
 
-        def tocsr(i):
-            rp, ci, v, nr, nc, nnz = keep[i]
-            return sp.csr_matrix((v[:nnz], ci[:nnz], rp), shape=(nr, nc))
+        def tocsr(i, imag=False):
+            rp, ci, v, nr, nc, nnz, vi = keep[i]
+            vals = v[:nnz] + 1j * vi[:nnz] if imag and cx else v[:nnz]
+            return sp.csr_matrix((vals, ci[:nnz], rp), shape=(nr, nc))
+
+        def dense(X, Xi, r, c):
+            return np.array(X[:r, :c] + 1j * Xi[:r, :c]) if cx else np.array(X[:r, :c])
 
         levels = []
-        for (iL, iU, iE, iF, W, H, k, s0, e0) in meta:
-            levels.append(dict(s=s0, e=e0, L=tocsr(iL), U=tocsr(iU), E=tocsr(iE), F=tocsr(iF),
-                               W=np.array(W[:, :k]), H=np.array(H[:k, :k])))
-        return dict(levels=levels, last=dict(L=tocsr(iLl), U=tocsr(iUl)))
+        for (iL, iU, iE, iF, W, H, Wi, Hi, k, s0, e0) in meta:
+            levels.append(dict(s=s0, e=e0, L=tocsr(iL, True), U=tocsr(iU, True), E=tocsr(iE), F=tocsr(iF),
+                               W=dense(W, Wi, W.shape[0], k), H=dense(H, Hi, k, k)))
+        return dict(levels=levels, last=dict(L=tocsr(iLl, True), U=tocsr(iUl, True)))
 
 
 class GemslrBatch:

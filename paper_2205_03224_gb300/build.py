@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libgemslr.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels.cu", "device.cu", "solver.cu", "batch_kernels.cu", "batch.cu", "learned.cu", "inner.cu",
-              "ilu_device.cu", "lowrank_rand.cu"]
+              "ilu_device.cu", "lowrank_rand.cu", "complex.cu"]
 CPP_SOURCES = ["setup.cpp", "partition.cpp", "schur.cpp"]
 
 

@@ -447,9 +447,11 @@ gemslr_status setup_batch(int32_t nsys, const gemslr_csr *A, const gemslr_partit
         gemslr_options o{};
         gemslr_default_options(&o);
         if (opt) o = *opt;
+        if (o.shift != 0.0) fail(GEMSLR_ERR_UNSUPPORTED, "the batched path is real (no complex shift)");
         for (int s = 0; s < nsys; ++s) {
             if (fac) hierarchy_from_factors(&A[s], &part[s], &fac[s], o, B->sys[s]);
             else setup_single_host(&A[s], &part[s], opt, B->sys[s]);
+            if (B->sys[s].cplx) fail(GEMSLR_ERR_UNSUPPORTED, "the batched path is real (complex factors given)");
             if (s > 0 && B->sys[s].nlev != B->sys[0].nlev) fail(GEMSLR_ERR_PARTITION, "all systems need the same nlev");
             B->base.push_back(B->base.back() + B->sys[s].n);
         }

@@ -1,5 +1,6 @@
 // Device layout of the GeMSLR hierarchy and the application of M^{-1} (Alg. 2).
 #include <algorithm>
+#include <complex>
 #include <atomic>
 #include <cstring>
 #include <mutex>
@@ -144,13 +145,23 @@ void validate_tri(const Csr &T, const std::vector<int64_t> &bp, bool upper) {
                 if (c < bp[b] || c >= bp[b + 1]) fail(GEMSLR_ERR_ARG, "factor entry outside its diagonal block");
                 if (!upper && c >= i) fail(GEMSLR_ERR_ARG, "L must be strictly lower triangular");
                 if (upper && c < i) fail(GEMSLR_ERR_ARG, "U must be upper triangular");
-                if (upper && c == i) diag = T.v[p] != 0.0;
+                if (upper && c == i) diag = T.v[p] != 0.0 || (!T.vi.empty() && T.vi[p] != 0.0);
             }
             if (upper && !diag) fail(GEMSLR_ERR_ARG, "U needs a nonzero diagonal");
         }
 }
 
 size_t pad16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Entry p of a factor (and the reciprocal of a diagonal entry) in the value
+// type of the substitution; complex factors keep their imaginary parts in vi.
+template <typename VT> VT entry_at(const Csr &T, int64_t p) { return cast_to<VT>(T.v[p]); }
+template <> zc entry_at<zc>(const Csr &T, int64_t p) { return zc(T.v[p], T.vi.empty() ? 0.0 : T.vi[p]); }
+template <typename VT> VT inv_entry(const Csr &T, int64_t p) { return cast_to<VT>(1.0 / T.v[p]); }
+template <> zc inv_entry<zc>(const Csr &T, int64_t p) {
+    const std::complex<double> r = 1.0 / std::complex<double>(T.v[p], T.vi.empty() ? 0.0 : T.vi[p]);
+    return zc(r.real(), r.imag());
+}
 
 }  // namespace
 
@@ -216,12 +227,12 @@ void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, Chun
                 int64_t q = 0;
                 for (int64_t pp = T.rp[i]; pp < T.rp[i + 1]; ++pp) {
                     if (T.ci[pp] == i) {
-                        if (upper) dd[t] = cast_to<VT>(1.0 / T.v[pp]);
+                        if (upper) dd[t] = inv_entry<VT>(T, pp);
                         continue;
                     }
                     const int64_t e = LanesPerRow<VT>::value == 1 ? q * n + t : ((q >> 2) * n + t) * 4 + (q & 3);
                     cc[e] = (int32_t)(T.ci[pp] - r0);
-                    vv[e] = cast_to<VT>(T.v[pp]);
+                    vv[e] = entry_at<VT>(T, pp);
                     ++q;
                 }
             }
@@ -274,6 +285,7 @@ void build_chunks(const Csr &L, const Csr &U, const std::vector<int64_t> &bp, Ch
 template void build_chunks<float>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<float> &, int, int);
 template void build_chunks<double>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<double> &, int,
                                    int);
+template void build_chunks<zc>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<zc> &, int, int);
 
 namespace {
 
@@ -338,6 +350,21 @@ void set_lowrank(DevLevel<VT, WT> &d, const HostLevel &hl, Arena &a) {
     if (hl.k > 0) {
         d.view.W = a.upload(convert<WT>(hl.W));
         d.view.H = a.upload(convert<VT>(hl.H));
+    }
+}
+
+// complex W, H: real parts in W, H and imaginary parts in Wi, Hi (empty: real)
+template <>
+void set_lowrank<zc, zc>(DevLevel<zc, zc> &d, const HostLevel &hl, Arena &a) {
+    d.view.k = hl.k;
+    if (hl.k > 0) {
+        auto pack = [](const std::vector<double> &re, const std::vector<double> &im) {
+            std::vector<zc> z(re.size());
+            for (size_t i = 0; i < re.size(); ++i) z[i] = zc(re[i], im.empty() ? 0.0 : im[i]);
+            return z;
+        };
+        d.view.W = a.upload(pack(hl.W, hl.Wi));
+        d.view.H = a.upload(pack(hl.H, hl.Hi));
     }
 }
 
@@ -409,7 +436,7 @@ void setup_inner(const Hierarchy &h, Arena &a, DevHierarchy<VT, WT> &d, int k, i
 // k GMRES steps on S_hat_0 y2 = z2 (inner.cu) whose preconditioner is the
 // level-0 correction plus the levels below, y1 = z1 - U^-1 L^-1 F y2.
 template <typename VT, typename WT>
-void apply_root_inner(DevHierarchy<VT, WT> &d, const double *in, VT *work, double *out_final, cudaStream_t st) {
+void apply_root_inner(DevHierarchy<VT, WT> &d, const IoT<VT> *in, VT *work, IoT<VT> *out_final, cudaStream_t st) {
     DevLevel<VT, WT> &L0 = d.lev[0];
     DevInner<VT> &I = d.inner;
     const InnerView<VT> &iv = I.iv;
@@ -468,23 +495,26 @@ void apply_root_inner(DevHierarchy<VT, WT> &d, const double *in, VT *work, doubl
 }
 
 template <typename VT, typename WT>
-void apply_levels(DevHierarchy<VT, WT> &d, int from, const double *in, VT *work, double *out_final,
+void apply_levels(DevHierarchy<VT, WT> &d, int from, const IoT<VT> *in, VT *work, IoT<VT> *out_final,
                   cudaStream_t st, const PendingLowRank<VT, WT> &pend0) {
     const int nl = (int)d.lev.size();
-    if (from == 0 && nl >= 1 && d.inner.k > 0) {
-        apply_root_inner<VT, WT>(d, in, work, out_final, st);
-        return;
+    constexpr bool kReal = !IsComplex<VT>::value;   // the complex hierarchy has neither inner steps nor a learned stage
+    if constexpr (kReal) {
+        if (from == 0 && nl >= 1 && d.inner.k > 0) {
+            apply_root_inner<VT, WT>(d, in, work, out_final, st);
+            return;
+        }
     }
     static const char *kDown[] = {"trsv_down_L0", "trsv_down_L1", "trsv_down_L2", "trsv_down_L3", "trsv_down_L4+"};
     static const char *kUp[] = {"trsv_up_L0", "trsv_up_L1", "trsv_up_L2", "trsv_up_L3", "trsv_up_L4+"};
     static const char *kCouple[] = {"couple_EWt_L0", "couple_EWt_L1", "couple_EWt_L2", "couple_EWt_L3", "couple_EWt_L4+"};
     // learned correction at the deepest Schur level (active only when that level is part of this application)
-    const bool learn = d.learned && d.learned->enabled && nl >= 1 && from <= nl - 1;
+    const bool learn = kReal && d.learned && d.learned->enabled && nl >= 1 && from <= nl - 1;
     // W_l u_l of the level before is added where its tail rows are first read
     PendingLowRank<VT, WT> pend = pend0;
     for (int l = from; l < nl; ++l) {
         DevLevel<VT, WT> &L = d.lev[l];
-        const double *src = (l == from) ? in : nullptr;
+        const IoT<VT> *src = (l == from) ? in : nullptr;
         {
             ProfScope ps(kDown[std::min(l, 4)], st);
             launch_trsv<VT, WT>(L.view, 0, L.smem_rows, src, work, nullptr, d.scratch, st, pend);
@@ -493,7 +523,8 @@ void apply_levels(DevHierarchy<VT, WT> &d, int from, const double *in, VT *work,
             ProfScope ps(kCouple[std::min(l, 4)], st);
             launch_couple<VT, WT>(L.view, src, work, d.partial, d.counter, d.u, st, pend);
         }
-        if (learn && l == nl - 1) learned_save<VT>(*d.learned, L.view.e, work, st);   // z2 of level l*
+        if constexpr (kReal)
+            if (learn && l == nl - 1) learned_save<VT>(*d.learned, L.view.e, work, st);   // z2 of level l*
         pend = PendingLowRank<VT, WT>();
         if (L.view.k > 0 && L.view.stail > 0) {
             pend.W = L.view.W;
@@ -508,7 +539,7 @@ void apply_levels(DevHierarchy<VT, WT> &d, int from, const double *in, VT *work,
         launch_trsv<VT, WT>(d.last.view, 0, d.last.smem_rows, from == nl ? in : nullptr, work,
                             learn ? nullptr : out_final, d.scratch, st, pend);
     }
-    if (learn) {
+    if constexpr (kReal) if (learn) {
         // S_hat y2 = C y2 - E (LU)^{-1} F y2 on a scratch vector, then y2 += N(rho)
         ProfScope ps("learned_stage", st);
         DevLevel<VT, WT> &L = d.lev[nl - 1];
@@ -544,6 +575,9 @@ void apply_hierarchy<float, __nv_bfloat16>(DevHierarchy<float, __nv_bfloat16> &d
 template void upload_hierarchy<double, double>(const Hierarchy &, Arena &, DevHierarchy<double, double> &, int);
 template void upload_hierarchy<float, __nv_bfloat16>(const Hierarchy &, Arena &,
                                                      DevHierarchy<float, __nv_bfloat16> &, int);
+template void upload_hierarchy<zc, zc>(const Hierarchy &, Arena &, DevHierarchy<zc, zc> &, int);
+template void apply_levels<zc, zc>(DevHierarchy<zc, zc> &, int, const zc *, zc *, zc *, cudaStream_t,
+                                   const PendingLowRank<zc, zc> &);
 template void set_lowrank<double, double>(DevLevel<double, double> &, const HostLevel &, Arena &);
 template void apply_levels<double, double>(DevHierarchy<double, double> &, int, const double *, double *, double *,
                                            cudaStream_t, const PendingLowRank<double, double> &);

@@ -35,12 +35,12 @@ uint64_t launches_total();
 // ---- launchers (kernels.cu) --------------------------------------------------
 // pl: the previous level's pending W u (MODE 0 only; default: none).
 template <typename VT, typename WT>
-void launch_trsv(const LevelView<VT, WT> &lv, int mode, int smem_rows, const double *in, VT *work,
-                 double *out_final, VT *scratch, cudaStream_t st,
+void launch_trsv(const LevelView<VT, WT> &lv, int mode, int smem_rows, const IoT<VT> *in, VT *work,
+                 IoT<VT> *out_final, VT *scratch, cudaStream_t st,
                  const PendingLowRank<VT, WT> &pl = PendingLowRank<VT, WT>());
 template <typename VT, typename WT> void set_trsv_smem_limit(int bytes);
 template <typename VT, typename WT>
-void launch_couple(const LevelView<VT, WT> &lv, const double *in, VT *work, VT *partial, unsigned *counter,
+void launch_couple(const LevelView<VT, WT> &lv, const IoT<VT> *in, VT *work, VT *partial, unsigned *counter,
                    VT *u, cudaStream_t st, const PendingLowRank<VT, WT> &pl = PendingLowRank<VT, WT>());
 void launch_gather(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t st);
 void launch_scatter(int64_t n, const int32_t *perm, const double *src, double *dst, cudaStream_t st);
@@ -111,6 +111,7 @@ template <typename T> inline T cast_to(double v);
 template <> inline double cast_to<double>(double v) { return v; }
 template <> inline float cast_to<float>(double v) { return (float)v; }
 template <> inline __nv_bfloat16 cast_to<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
+template <> inline zc cast_to<zc>(double v) { return zc(v); }
 template <typename T> inline std::vector<T> convert(const std::vector<double> &x) {
     std::vector<T> y(x.size());
     for (size_t i = 0; i < x.size(); ++i) y[i] = cast_to<T>(x[i]);
@@ -224,6 +225,20 @@ void launch_scale_pairs(int S, int count, const double *R, const double *T, doub
                         cudaStream_t st);
 void launch_loss(int S, int N, const float *out, const float *tgt, float *dout, float *loss, cudaStream_t st);
 
+// ---- complex-shifted hierarchy (complex.cu, Sec. 5.2.3) -----------------------------
+// Device copy of a complex host hierarchy with its Krylov workspace; the
+// low-rank terms are built on the device (bottom-up) when compute_lowrank.
+struct ZState;
+ZState *z_create(Hierarchy &h, Arena &a, const gemslr_options &opt, const int64_t *A_rp, const int32_t *A_ci,
+                 const double *A_v, const int32_t *perm, int smem_limit, int sms, bool compute_lowrank);
+void z_destroy(ZState *z);
+void z_wavefronts(const ZState *z, int l, int &wl, int &wu);   // l = nlev - 1: the last level
+// z = M^{-1} r, complex vectors in the original ordering (nrhs columns of n)
+void z_apply(ZState *z, const zc *r, zc *out, int32_t nrhs, cudaStream_t st);
+// complex FGMRES for one right-hand side; msg receives the reason of a non-OK status
+gemslr_status z_solve(ZState *z, const zc *b, zc *x, const gemslr_solve_opts &o, gemslr_solve_info &inf,
+                      std::string &msg, cudaStream_t st);
+
 // Build the device copy of a host hierarchy.
 template <typename VT, typename WT>
 void upload_hierarchy(const Hierarchy &h, Arena &arena, DevHierarchy<VT, WT> &d, int smem_limit_bytes);
@@ -239,7 +254,7 @@ void set_lowrank(DevLevel<VT, WT> &d, const HostLevel &hl, Arena &a);
 // W u term to add to the right-hand side of level `from` (from > 0).  With
 // from == 0 and inner steps set, the root level runs Alg. 2 step 9.
 template <typename VT, typename WT>
-void apply_levels(DevHierarchy<VT, WT> &d, int from, const double *in, VT *work, double *out_final,
+void apply_levels(DevHierarchy<VT, WT> &d, int from, const IoT<VT> *in, VT *work, IoT<VT> *out_final,
                   cudaStream_t st, const PendingLowRank<VT, WT> &pend0 = PendingLowRank<VT, WT>());
 
 // Allocate (once) and switch on the inner GMRES with k steps (k = 0: off).

@@ -1,6 +1,7 @@
 // Internal types of the GB300 GeMSLR library (host side).
 #pragma once
 
+#include <complex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -15,6 +16,7 @@ struct Csr {
     std::vector<int64_t> rp{0};
     std::vector<int32_t> ci;
     std::vector<double> v;
+    std::vector<double> vi;          // imaginary parts (complex factors); empty: real
     int64_t nnz() const { return (int64_t)ci.size(); }
 };
 
@@ -62,6 +64,13 @@ int schur_wanted(const std::vector<double> &Hm, int m, int k, std::vector<double
                  std::vector<double> &theta_im);
 // H = (I - Tk)^{-1} - I (k x k, column-major), partial pivoting LU.
 std::vector<double> correction_matrix(const std::vector<double> &Tk, int k);
+// Complex counterparts (complex-shifted hierarchy, Sec. 5.2.3): complex Schur
+// form of a general complex m x m Hm, the k wanted values (same ranking, no
+// pairs) leading; Q (m x k) and the upper triangular Tk (k x k), column-major.
+int schur_wanted_z(const std::vector<std::complex<double>> &Hm, int m, int k,
+                   std::vector<std::complex<double>> &Q, std::vector<std::complex<double>> &Tk,
+                   std::vector<std::complex<double>> &theta);
+std::vector<std::complex<double>> correction_matrix_z(const std::vector<std::complex<double>> &Tk, int k);
 
 // ---- host description of the hierarchy -------------------------------------
 struct HostLevel {
@@ -74,6 +83,7 @@ struct HostLevel {
     int rank_req = 0;
     std::vector<double> W;           // (n - e) x k, column-major
     std::vector<double> H;           // k x k, column-major
+    std::vector<double> Wi, Hi;      // imaginary parts of W and H (complex hierarchy); empty: real
 };
 
 struct Hierarchy {
@@ -85,6 +95,10 @@ struct Hierarchy {
     std::vector<HostLevel> lev;      // nlev - 1 Schur levels
     HostLevel last;                  // s, e = n, bp, L, U
     int64_t nclamp = 0;
+    // complex diagonal shift of the factored blocks (Sec. 5.2.3): B + i alpha I;
+    // with cplx the factors, W and H carry imaginary parts and M^{-1} is complex
+    double alpha = 0.0;
+    bool cplx = false;
 };
 
 // ILU(0) of the diagonal blocks of a level matrix on the current device (ilu_device.cu).

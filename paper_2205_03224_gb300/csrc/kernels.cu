@@ -37,6 +37,10 @@ template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v
 
 template <typename VT, typename WT> __device__ __forceinline__ VT wval(WT w) { return (VT)to_f(w); }
 template <> __device__ __forceinline__ double wval<double, double>(double w) { return w; }
+template <> __device__ __forceinline__ zc wval<zc, zc>(zc w) { return w; }
+// an entry of W^H (the correction is W H W^H; for real data W^T)
+template <typename VT, typename WT> __device__ __forceinline__ VT wval_h(WT w) { return wval<VT, WT>(w); }
+template <> __device__ __forceinline__ zc wval_h<zc, zc>(zc w) { return conj(w); }
 
 // Row g's share of the previous level's W u (see PendingLowRank): sixteen
 // columns at a time with all their loads issued first (columns past k load
@@ -53,7 +57,7 @@ __device__ __forceinline__ VT pending_row(const PendingLowRank<VT, WT> &pl, int6
         for (int q = 0; q < 16; ++q) {
             const int c = min(c0 + q, pl.k - 1);
             wv[q] = w[(int64_t)c * pl.ld];
-            uv[q] = c0 + q < pl.k ? __ldcg(pl.u + c) : (VT)0;
+            uv[q] = c0 + q < pl.k ? ldcg(pl.u + c) : (VT)0;
         }
 #pragma unroll
         for (int q = 0; q < 16; q += 2) {
@@ -77,8 +81,8 @@ __device__ __forceinline__ VT pending_row(const PendingLowRank<VT, WT> &pl, int6
 // MODE 1: right-hand side F y2 (gathered from work's tail); work[rows] -= result.
 template <typename VT, typename WT, int MODE, bool SMEM, int NE>
 __global__ void __launch_bounds__(kTrsvThreads2)
-k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict__ work,
-       double *__restrict__ out_final, VT *__restrict__ scratch, const PendingLowRank<VT, WT> pl) {
+k_trsv(const LevelView<VT, WT> lv, const IoT<VT> *__restrict__ in, VT *__restrict__ work,
+       IoT<VT> *__restrict__ out_final, VT *__restrict__ scratch, const PendingLowRank<VT, WT> pl) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *ring = smem;
     // FP32: kGroupChunks chunks per copy, one per consumer warp; FP64: one
@@ -165,7 +169,7 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
         for (int i = ct; i < nr; i += NC) xs[i] = mine[i] + pending_row<VT, WT>(pl, lv.s + r0 + i);
     } else if (in || SMEM) {
         // eight independent loads in flight per thread
-        const double *src_d = in ? in + lv.s + r0 : nullptr;
+        const IoT<VT> *src_d = in ? in + lv.s + r0 : nullptr;
         for (int i0 = ct; i0 < nr; i0 += 8 * NC) {
             VT v[8];
 #pragma unroll
@@ -216,8 +220,8 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
                             acc += vals[e] * xs[cols[e]];
                         }
                     }
-                    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-                    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                    acc += shfl_xor(acc, 1);
+                    acc += shfl_xor(acc, 2);
                     if (active && sub == 0) {
                         const int row = rows[t];
                         VT y = xs[row] - acc;
@@ -240,14 +244,15 @@ k_trsv(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict
         VT y = xs[i];
         if (MODE == 1) y = mine[i] - y;
         if (SMEM || MODE == 1) mine[i] = y;
-        if (out_final) out_final[lv.s + r0 + i] = (double)y;
+        if (out_final) out_final[lv.s + r0 + i] = (IoT<VT>)y;
     }
 }
 
-// z2 = b2 - E z1 on rows [row0, row1) of the tail, then partial W^T z2.
+// z2 = b2 - E z1 on rows [row0, row1) of the tail, then partial W^T z2 (W^H z2
+// for the complex hierarchy).
 template <typename VT, typename WT>
 __global__ void __launch_bounds__(kCoupleRows)
-k_couple(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restrict__ work,
+k_couple(const LevelView<VT, WT> lv, const IoT<VT> *__restrict__ in, VT *__restrict__ work,
          VT *__restrict__ partial, unsigned *__restrict__ counter, VT *u_out,
          const PendingLowRank<VT, WT> pl) {
     __shared__ VT zs[kCoupleRows];
@@ -300,7 +305,7 @@ k_couple(const LevelView<VT, WT> lv, const double *__restrict__ in, VT *__restri
         for (int u = 0; u < 4; ++u) {
             acc[u] = 0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) acc[u] += wval<VT, WT>(wv[u][q]) * zs[lane + 32 * q];   // zs = 0 past i1
+            for (int q = 0; q < 8; ++q) acc[u] += wval_h<VT, WT>(wv[u][q]) * zs[lane + 32 * q];   // zs = 0 past i1
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -1455,8 +1460,8 @@ static int grid_for(int64_t n, int threads, int cap) {
 }
 
 template <typename VT, typename WT>
-void launch_trsv(const LevelView<VT, WT> &lv, int mode, int smem_rows, const double *in, VT *work,
-                 double *out_final, VT *scratch, cudaStream_t st, const PendingLowRank<VT, WT> &pl) {
+void launch_trsv(const LevelView<VT, WT> &lv, int mode, int smem_rows, const IoT<VT> *in, VT *work,
+                 IoT<VT> *out_final, VT *scratch, cudaStream_t st, const PendingLowRank<VT, WT> &pl) {
     if (lv.nblk == 0) return;
     const bool smem = smem_rows > 0;
     const size_t bytes = kRingBytes + (smem ? (size_t)smem_rows * sizeof(VT) : 0);
@@ -1518,7 +1523,7 @@ void set_trsv_smem_limit(int bytes) {
 }
 
 template <typename VT, typename WT>
-void launch_couple(const LevelView<VT, WT> &lv, const double *in, VT *work, VT *partial, unsigned *counter,
+void launch_couple(const LevelView<VT, WT> &lv, const IoT<VT> *in, VT *work, VT *partial, unsigned *counter,
                    VT *u, cudaStream_t st, const PendingLowRank<VT, WT> &pl) {
     if (lv.stail == 0) return;
     const int grid = (int)((lv.stail + kCoupleRows - 1) / kCoupleRows);
@@ -1531,11 +1536,16 @@ template void launch_trsv<double, double>(const LevelView<double, double> &, int
 template void launch_trsv<float, __nv_bfloat16>(const LevelView<float, __nv_bfloat16> &, int, int, const double *,
                                                 float *, double *, float *, cudaStream_t,
                                                 const PendingLowRank<float, __nv_bfloat16> &);
+template void launch_trsv<zc, zc>(const LevelView<zc, zc> &, int, int, const zc *, zc *, zc *, zc *, cudaStream_t,
+                                  const PendingLowRank<zc, zc> &);
 template void set_trsv_smem_limit<double, double>(int);
+template void set_trsv_smem_limit<zc, zc>(int);
 template void set_trsv_smem_limit<float, __nv_bfloat16>(int);
 template void launch_couple<double, double>(const LevelView<double, double> &, const double *, double *, double *,
                                             unsigned *, double *, cudaStream_t,
                                             const PendingLowRank<double, double> &);
+template void launch_couple<zc, zc>(const LevelView<zc, zc> &, const zc *, zc *, zc *, unsigned *, zc *, cudaStream_t,
+                                    const PendingLowRank<zc, zc> &);
 template void launch_couple<float, __nv_bfloat16>(const LevelView<float, __nv_bfloat16> &, const double *, float *,
                                                   float *, unsigned *, float *, cudaStream_t,
                                                   const PendingLowRank<float, __nv_bfloat16> &);

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include "zcomplex.cuh"
+
 namespace gemslr {
 
 constexpr int kTrsvThreads = 512;

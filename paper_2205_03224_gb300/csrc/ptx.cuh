@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.cuh"
+#include "zcomplex.cuh"
 
 namespace gemslr {
 namespace {
@@ -15,7 +16,7 @@ namespace {
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
     return v;
 }
 
@@ -45,7 +46,7 @@ __device__ void reduce_columns(const T *partial, int nparts, int ncols1, T *out)
 #pragma unroll
                 for (int q = 0; q < RP; ++q) {
                     const int p = p0 + q * 32 + lane;
-                    v[u][q] = (c < ncols1 && p < nparts) ? __ldcg(partial + (int64_t)c * nparts + p) : (T)0;
+                    v[u][q] = (c < ncols1 && p < nparts) ? ldcg(partial + (int64_t)c * nparts + p) : (T)0;
                 }
             }
 #pragma unroll

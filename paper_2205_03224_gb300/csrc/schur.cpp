@@ -158,6 +158,46 @@ double score(cplx t) {
     return den == 0.0 ? INFINITY : std::abs(t) / den;
 }
 
+// Complex Householder reduction to upper Hessenberg form: T <- P T P with
+// P = I - 2 v v^H / (v^H v) per column (P Hermitian and unitary), Z <- Z P.
+void complex_hessenberg(CMat &T, CMat &Z) {
+    const int m = T.m;
+    std::vector<cplx> v(m);
+    for (int k = 0; k + 2 < m; ++k) {
+        double nx = 0.0;
+        for (int i = k + 1; i < m; ++i) nx += std::norm(T(i, k));
+        nx = std::sqrt(nx);
+        if (nx == 0.0) continue;
+        const cplx x0 = T(k + 1, k);
+        const cplx phase = std::abs(x0) == 0.0 ? cplx(1.0) : x0 / std::abs(x0);
+        const cplx alpha = -phase * nx;
+        std::fill(v.begin(), v.end(), cplx(0.0));
+        for (int i = k + 1; i < m; ++i) v[i] = T(i, k);
+        v[k + 1] -= alpha;
+        double nv = 0.0;
+        for (int i = k + 1; i < m; ++i) nv += std::norm(v[i]);
+        if (nv == 0.0) continue;
+        const double f = 2.0 / nv;
+        for (int j = 0; j < m; ++j) {          // rows: T <- P T
+            cplx d = 0.0;
+            for (int i = k + 1; i < m; ++i) d += std::conj(v[i]) * T(i, j);
+            d *= f;
+            for (int i = k + 1; i < m; ++i) T(i, j) -= v[i] * d;
+        }
+        for (int i = 0; i < m; ++i) {          // columns: T <- T P, Z <- Z P
+            cplx d = 0.0, e = 0.0;
+            for (int j = k + 1; j < m; ++j) { d += T(i, j) * v[j]; e += Z(i, j) * v[j]; }
+            d *= f;
+            e *= f;
+            for (int j = k + 1; j < m; ++j) {
+                T(i, j) -= d * std::conj(v[j]);
+                Z(i, j) -= e * std::conj(v[j]);
+            }
+        }
+        for (int i = k + 2; i < m; ++i) T(i, k) = 0.0;
+    }
+}
+
 }  // namespace
 
 int schur_wanted(const std::vector<double> &Hm, int m, int k, std::vector<double> &Q,
@@ -271,6 +311,86 @@ int schur_wanted(const std::vector<double> &Hm, int m, int k, std::vector<double
             Tk[a + (size_t)b * keff] = d;
         }
     return keff;
+}
+
+// Complex counterpart (complex-shifted hierarchy): complex Schur form of a
+// general m x m Hm (Householder Hessenberg, then the complex QR above), the
+// same ranking of the Ritz values, exactly k kept (no conjugate pairs to keep
+// whole), moved to the front by adjacent swaps; Q = Z[:, :k] is already an
+// orthonormal basis of the wanted invariant subspace and Tk = T[:k, :k].
+int schur_wanted_z(const std::vector<cplx> &Hm, int m, int k, std::vector<cplx> &Q, std::vector<cplx> &Tk,
+                   std::vector<cplx> &theta) {
+    k = std::min(k, m);
+    CMat T(m), Z(m);
+    T.a = Hm;
+    for (int i = 0; i < m; ++i) Z(i, i) = 1.0;
+    complex_hessenberg(T, Z);
+    complex_schur(T, Z);
+    std::vector<int> ord(m);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::vector<cplx> th(m);
+    for (int i = 0; i < m; ++i) th[i] = T(i, i);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+        const double sa = score(th[a]), sb = score(th[b]);
+        if (sa != sb) return sa > sb;
+        const double ma = std::abs(th[a]), mb = std::abs(th[b]);
+        if (ma != mb) return ma > mb;
+        return a < b;
+    });
+    std::vector<int> at(m), who(m);
+    std::iota(at.begin(), at.end(), 0);
+    std::iota(who.begin(), who.end(), 0);
+    for (int t = 0; t < k; ++t) {
+        for (int p = at[ord[t]] - 1; p >= t; --p) {
+            swap_adjacent(T, Z, p);
+            std::swap(who[p], who[p + 1]);
+            at[who[p]] = p;
+            at[who[p + 1]] = p + 1;
+        }
+    }
+    Q.assign((size_t)m * k, 0.0);
+    for (int t = 0; t < k; ++t)
+        for (int i = 0; i < m; ++i) Q[i + (size_t)t * m] = Z(i, t);
+    Tk.assign((size_t)k * k, 0.0);
+    theta.resize(k);
+    for (int b = 0; b < k; ++b) {
+        theta[b] = T(b, b);
+        for (int a = 0; a <= b; ++a) Tk[a + (size_t)b * k] = T(a, b);
+    }
+    return k;
+}
+
+std::vector<cplx> correction_matrix_z(const std::vector<cplx> &Tk, int k) {
+    // (I - Tk)^{-1} - I by Gaussian elimination with partial pivoting (moduli)
+    std::vector<cplx> M((size_t)k * k), X((size_t)k * k, 0.0);
+    for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i) M[i + (size_t)j * k] = (i == j ? cplx(1.0) : cplx(0.0)) - Tk[i + (size_t)j * k];
+    for (int i = 0; i < k; ++i) X[i + (size_t)i * k] = 1.0;
+    for (int c = 0; c < k; ++c) {
+        int piv = c;
+        for (int i = c + 1; i < k; ++i)
+            if (std::abs(M[i + (size_t)c * k]) > std::abs(M[piv + (size_t)c * k])) piv = i;
+        if (M[piv + (size_t)c * k] == cplx(0.0)) fail(GEMSLR_ERR_NOT_CONVERGED, "I - T_k is singular");
+        if (piv != c)
+            for (int j = 0; j < k; ++j) {
+                std::swap(M[c + (size_t)j * k], M[piv + (size_t)j * k]);
+                std::swap(X[c + (size_t)j * k], X[piv + (size_t)j * k]);
+            }
+        for (int i = c + 1; i < k; ++i) {
+            const cplx f = M[i + (size_t)c * k] / M[c + (size_t)c * k];
+            if (f == cplx(0.0)) continue;
+            for (int j = c; j < k; ++j) M[i + (size_t)j * k] -= f * M[c + (size_t)j * k];
+            for (int j = 0; j < k; ++j) X[i + (size_t)j * k] -= f * X[c + (size_t)j * k];
+        }
+    }
+    for (int j = 0; j < k; ++j)
+        for (int i = k - 1; i >= 0; --i) {
+            cplx s = X[i + (size_t)j * k];
+            for (int t = i + 1; t < k; ++t) s -= M[i + (size_t)t * k] * X[t + (size_t)j * k];
+            X[i + (size_t)j * k] = s / M[i + (size_t)i * k];
+        }
+    for (int i = 0; i < k; ++i) X[i + (size_t)i * k] -= 1.0;
+    return X;
 }
 
 std::vector<double> correction_matrix(const std::vector<double> &Tk, int k) {

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <complex>
 #include <exception>
 #include <numeric>
 #include <thread>
@@ -129,6 +130,7 @@ void append_block(Csr &dst, const Csr &blk, int64_t off) {
         for (int64_t p = blk.rp[i]; p < blk.rp[i + 1]; ++p) {
             dst.ci.push_back((int32_t)(blk.ci[p] + off));
             dst.v.push_back(blk.v[p]);
+            if (!blk.vi.empty()) dst.vi.push_back(blk.vi[p]);
         }
         dst.rp.push_back((int64_t)dst.ci.size());
     }
@@ -137,9 +139,23 @@ void append_block(Csr &dst, const Csr &blk, int64_t off) {
 }
 
 // ---- incomplete factorisations ---------------------------------------------
+// The factorisations are written once for a scalar S: double, or
+// std::complex<double> for the complex-shifted blocks B + i alpha I of
+// Sec. 5.2.3 (values in v, imaginary parts in vi).  Every magnitude is the
+// modulus |.|.
+using zd = std::complex<double>;
+
+template <typename S> S value_of(const Csr &B, int64_t p);
+template <> double value_of<double>(const Csr &B, int64_t p) { return B.v[p]; }
+template <> zd value_of<zd>(const Csr &B, int64_t p) { return zd(B.v[p], B.vi.empty() ? 0.0 : B.vi[p]); }
+static void push_value(Csr &M, double x) { M.v.push_back(x); }
+static void push_value(Csr &M, zd x) { M.v.push_back(x.real()); M.vi.push_back(x.imag()); }
+static double sq(double x) { return x * x; }
+static double sq(zd x) { return x.real() * x.real() + x.imag() * x.imag(); }
+
 // Pivot rule for the (undiscussed) small-pivot case: |u_ii| below
 // 1e-12*||a_i||_2 is replaced by sign(u_ii)*1e-12*||a_i||_2 (+ for zero);
-// an all-zero row gets 1.
+// an all-zero row gets 1.  A complex pivot keeps its phase.
 static double guard_pivot(double u, double rownorm, int64_t &count) {
     if (rownorm == 0.0) {
         if (u == 0.0) { ++count; return 1.0; }
@@ -149,10 +165,20 @@ static double guard_pivot(double u, double rownorm, int64_t &count) {
     if (std::fabs(u) < floor_) { ++count; return u < 0.0 ? -floor_ : floor_; }
     return u;
 }
+static zd guard_pivot(zd u, double rownorm, int64_t &count) {
+    if (rownorm == 0.0) {
+        if (u == 0.0) { ++count; return 1.0; }
+        return u;
+    }
+    const double floor_ = 1e-12 * rownorm, a = std::abs(u);
+    if (a < floor_) { ++count; return u == 0.0 ? zd(floor_) : u * (floor_ / a); }
+    return u;
+}
 
+template <typename S>
 static double norm2_row(const Csr &B, int64_t i) {
     double acc = 0.0;
-    for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p) acc += B.v[p] * B.v[p];
+    for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p) acc += sq(value_of<S>(B, p));
     return std::sqrt(acc);
 }
 
@@ -161,41 +187,43 @@ static void reset_factor(Csr &M, int64_t n) {
     M.rp.assign(1, 0);
     M.ci.clear();
     M.v.clear();
+    M.vi.clear();
 }
 
 // ILU(0): elimination restricted to the pattern of B, rows top to bottom,
 // multipliers in ascending column order (IKJ form).
-int64_t factor_ilu0(const Csr &B, Csr &L, Csr &U) {
+template <typename S>
+static int64_t ilu0_impl(const Csr &B, Csr &L, Csr &U) {
     const int64_t n = B.nrows;
     reset_factor(L, n);
     reset_factor(U, n);
-    std::vector<double> row(n, 0.0), piv(n, 0.0);
+    std::vector<S> row(n, S(0.0)), piv(n, S(0.0));
     std::vector<int64_t> stamp(n, -1);
     int64_t clamped = 0;
     for (int64_t i = 0; i < n; ++i) {
-        for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p) { row[B.ci[p]] = B.v[p]; stamp[B.ci[p]] = i; }
+        for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p) { row[B.ci[p]] = value_of<S>(B, p); stamp[B.ci[p]] = i; }
         for (int64_t p = B.rp[i]; p < B.rp[i + 1] && B.ci[p] < i; ++p) {
             const int32_t k = B.ci[p];
             row[k] = row[k] / piv[k];
-            const double lik = row[k];
+            const S lik = row[k];
             for (int64_t q = U.rp[k] + 1; q < U.rp[k + 1]; ++q) {   // skip u_kk (first)
                 const int32_t j = U.ci[q];
-                if (stamp[j] == i) row[j] -= lik * U.v[q];
+                if (stamp[j] == i) row[j] -= lik * value_of<S>(U, q);
             }
         }
         bool diag = false;
         for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p) diag |= (B.ci[p] == i);
-        const double d = guard_pivot(diag ? row[i] : 0.0, norm2_row(B, i), clamped);
+        const S d = guard_pivot(diag ? row[i] : S(0.0), norm2_row<S>(B, i), clamped);
         piv[i] = d;
         for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p)
-            if (B.ci[p] < i) { L.ci.push_back(B.ci[p]); L.v.push_back(row[B.ci[p]]); }
+            if (B.ci[p] < i) { L.ci.push_back(B.ci[p]); push_value(L, row[B.ci[p]]); }
         U.ci.push_back((int32_t)i);
-        U.v.push_back(d);
+        push_value(U, d);
         for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p)
-            if (B.ci[p] > i) { U.ci.push_back(B.ci[p]); U.v.push_back(row[B.ci[p]]); }
+            if (B.ci[p] > i) { U.ci.push_back(B.ci[p]); push_value(U, row[B.ci[p]]); }
         L.rp.push_back((int64_t)L.ci.size());
         U.rp.push_back((int64_t)U.ci.size());
-        for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p) row[B.ci[p]] = 0.0;
+        for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p) row[B.ci[p]] = S(0.0);
     }
     return clamped;
 }
@@ -204,18 +232,18 @@ int64_t factor_ilu0(const Csr &B, Csr &L, Csr &U) {
 // of the row being reduced (scale-independent reading): a multiplier l_ik by
 // |l_ik * u_kk|, a U entry by |u_ij|; threshold tau*||a_i||_2; then the lfil
 // largest of each part are kept (ties: lower column), the diagonal always.
-int64_t factor_ilut(const Csr &B, double tau, int lfil, Csr &L, Csr &U) {
+template <typename S>
+static int64_t ilut_impl(const Csr &B, double tau, int lfil, Csr &L, Csr &U) {
     const int64_t n = B.nrows;
     reset_factor(L, n);
     reset_factor(U, n);
-    std::vector<double> row(n, 0.0), piv(n, 0.0);
+    std::vector<S> row(n, S(0.0)), piv(n, S(0.0));
     std::vector<char> present(n, 0), eliminated(n, 0);
     std::vector<int32_t> cols;
     struct Cand { int32_t c; double mag; };
     std::vector<Cand> cand;
     auto by_size = [](const Cand &a, const Cand &b) {
-        const double x = std::fabs(a.mag), y = std::fabs(b.mag);
-        if (x != y) return x > y;
+        if (a.mag != b.mag) return a.mag > b.mag;
         return a.c < b.c;
     };
     auto by_col = [](const Cand &a, const Cand &b) { return a.c < b.c; };
@@ -223,53 +251,92 @@ int64_t factor_ilut(const Csr &B, double tau, int lfil, Csr &L, Csr &U) {
     for (int64_t i = 0; i < n; ++i) {
         cols.clear();
         for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p) {
-            row[B.ci[p]] = B.v[p];
+            row[B.ci[p]] = value_of<S>(B, p);
             if (!present[B.ci[p]]) { present[B.ci[p]] = 1; cols.push_back(B.ci[p]); }
         }
-        const double thr = tau * norm2_row(B, i);
+        const double thr = tau * norm2_row<S>(B, i);
         while (true) {   // smallest not-yet-eliminated column below the diagonal
             int32_t k = -1;
             for (int32_t c : cols)
                 if (c < i && !eliminated[c] && (k < 0 || c < k)) k = c;
             if (k < 0) break;
             eliminated[k] = 1;
-            if (std::fabs(row[k]) < thr) { row[k] = 0.0; continue; }
+            if (std::abs(row[k]) < thr) { row[k] = S(0.0); continue; }
             row[k] = row[k] / piv[k];
-            const double lik = row[k];
+            const S lik = row[k];
             for (int64_t q = U.rp[k] + 1; q < U.rp[k + 1]; ++q) {
                 const int32_t j = U.ci[q];
-                if (!present[j]) { present[j] = 1; row[j] = 0.0; cols.push_back(j); }
-                row[j] -= lik * U.v[q];
+                if (!present[j]) { present[j] = 1; row[j] = S(0.0); cols.push_back(j); }
+                row[j] -= lik * value_of<S>(U, q);
             }
         }
         cand.clear();
         for (int32_t c : cols)
-            if (c < i && row[c] != 0.0 && std::fabs(row[c] * piv[c]) >= thr)
-                cand.push_back({c, row[c] * piv[c]});
+            if (c < i && row[c] != S(0.0) && std::abs(row[c] * piv[c]) >= thr)
+                cand.push_back({c, std::abs(row[c] * piv[c])});
         if (lfil >= 0 && (int64_t)cand.size() > lfil) {
             std::sort(cand.begin(), cand.end(), by_size);
             cand.resize(lfil);
         }
         std::sort(cand.begin(), cand.end(), by_col);
-        for (auto &e : cand) { L.ci.push_back(e.c); L.v.push_back(row[e.c]); }
-        const double d = guard_pivot(present[i] ? row[i] : 0.0, norm2_row(B, i), clamped);
+        for (auto &e : cand) { L.ci.push_back(e.c); push_value(L, row[e.c]); }
+        const S d = guard_pivot(present[i] ? row[i] : S(0.0), norm2_row<S>(B, i), clamped);
         piv[i] = d;
         U.ci.push_back((int32_t)i);
-        U.v.push_back(d);
+        push_value(U, d);
         cand.clear();
         for (int32_t c : cols)
-            if (c > i && row[c] != 0.0 && std::fabs(row[c]) >= thr) cand.push_back({c, row[c]});
+            if (c > i && row[c] != S(0.0) && std::abs(row[c]) >= thr) cand.push_back({c, std::abs(row[c])});
         if (lfil >= 0 && (int64_t)cand.size() > lfil) {
             std::sort(cand.begin(), cand.end(), by_size);
             cand.resize(lfil);
         }
         std::sort(cand.begin(), cand.end(), by_col);
-        for (auto &e : cand) { U.ci.push_back(e.c); U.v.push_back(row[e.c]); }
+        for (auto &e : cand) { U.ci.push_back(e.c); push_value(U, row[e.c]); }
         L.rp.push_back((int64_t)L.ci.size());
         U.rp.push_back((int64_t)U.ci.size());
-        for (int32_t c : cols) { row[c] = 0.0; present[c] = 0; eliminated[c] = 0; }
+        for (int32_t c : cols) { row[c] = S(0.0); present[c] = 0; eliminated[c] = 0; }
     }
     return clamped;
+}
+
+int64_t factor_ilu0(const Csr &B, Csr &L, Csr &U) {
+    return B.vi.empty() ? ilu0_impl<double>(B, L, U) : ilu0_impl<zd>(B, L, U);
+}
+
+int64_t factor_ilut(const Csr &B, double tau, int lfil, Csr &L, Csr &U) {
+    return B.vi.empty() ? ilut_impl<double>(B, tau, lfil, L, U) : ilut_impl<zd>(B, tau, lfil, L, U);
+}
+
+// B + i alpha I of one block (Sec. 5.2.3): imaginary parts alpha on the
+// diagonal (an entry is inserted where the pattern has none), 0 elsewhere.
+static Csr shifted_block(const Csr &B, double alpha) {
+    Csr S;
+    S.nrows = B.nrows;
+    S.ncols = B.ncols;
+    S.rp.assign(1, 0);
+    for (int64_t i = 0; i < B.nrows; ++i) {
+        bool diag = false;
+        for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p) {
+            if (!diag && B.ci[p] > i) {
+                S.ci.push_back((int32_t)i);
+                S.v.push_back(0.0);
+                S.vi.push_back(alpha);
+                diag = true;
+            }
+            S.ci.push_back(B.ci[p]);
+            S.v.push_back(B.v[p]);
+            S.vi.push_back(B.ci[p] == i ? alpha : 0.0);
+            diag |= (B.ci[p] == i);
+        }
+        if (!diag) {
+            S.ci.push_back((int32_t)i);
+            S.v.push_back(0.0);
+            S.vi.push_back(alpha);
+        }
+        S.rp.push_back((int64_t)S.ci.size());
+    }
+    return S;
 }
 
 // ---- level sets ------------------------------------------------------------
@@ -299,9 +366,10 @@ std::vector<int32_t> wavefronts_upper(const Csr &U, int64_t r0, int64_t r1) {
 // The diagonal blocks of a level are independent (Sec. 4.2), so they are
 // factored by a pool of host threads (blocks handed out in turn); the factors
 // are appended in block order, so the result does not depend on the threads.
-static void factor_level(const Csr &B, const std::vector<int64_t> &bp, const gemslr_options *opt,
+static void factor_level(const Csr &B, const std::vector<int64_t> &bp, const gemslr_options *opt, double alpha,
                          Csr &L, Csr &U, int64_t &clamped) {
     if (opt->ilu_kind == GEMSLR_ILU0_DEVICE) {
+        if (alpha != 0.0) fail(GEMSLR_ERR_UNSUPPORTED, "the complex shift needs a host factorisation (ILU0 or ILUT)");
         factor_level_ilu0_device(B, bp, L, U, clamped);
         return;
     }
@@ -316,6 +384,7 @@ static void factor_level(const Csr &B, const std::vector<int64_t> &bp, const gem
         for (size_t j; !failed.load() && (j = next.fetch_add(1)) < nb;) {
             try {
                 Csr Bj = submatrix(B, bp[j], bp[j + 1], bp[j], bp[j + 1]);
+                if (alpha != 0.0) Bj = shifted_block(Bj, alpha);
                 if (opt->ilu_kind == GEMSLR_ILU0) cl[j] = factor_ilu0(Bj, Ls[j], Us[j]);
                 else cl[j] = factor_ilut(Bj, opt->ilut_tau, opt->ilut_lfil, Ls[j], Us[j]);
             } catch (...) {
@@ -376,6 +445,15 @@ static void read_partition(const gemslr_partition *part, int64_t n, Hierarchy &h
 void build_levels(const Csr &A, const gemslr_partition *part, const gemslr_options *opt,
                   Hierarchy &h) {
     h.n = A.nrows;
+    h.cplx = opt->shift != 0.0;
+    h.alpha = 0.0;
+    if (h.cplx) {   // alpha = shift * sum_i |a_ii| / n (Sec. 5.2.3)
+        double sd = 0.0;
+        for (int64_t i = 0; i < A.nrows; ++i)
+            for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p)
+                if (A.ci[p] == i) sd += std::fabs(A.v[p]);
+        h.alpha = A.nrows ? opt->shift * sd / (double)A.nrows : 0.0;
+    }
     std::vector<std::vector<int64_t>> bps;
     read_partition(part, h.n, h, bps);
     h.Ahat = permute_sym(A, h.perm);
@@ -391,7 +469,7 @@ void build_levels(const Csr &A, const gemslr_partition *part, const gemslr_optio
             fail(GEMSLR_ERR_PARTITION, "level " + std::to_string(l) + ": diagonal blocks are coupled");
         lv.E = submatrix(h.Ahat, lv.e, n, lv.s, lv.e);
         lv.F = submatrix(h.Ahat, lv.s, lv.e, lv.e, n);
-        factor_level(B, lv.bp, opt, lv.L, lv.U, h.nclamp);
+        factor_level(B, lv.bp, opt, h.alpha, lv.L, lv.U, h.nclamp);
         lv.rank_req = opt->rank[l];
     }
     HostLevel &la = h.last;
@@ -399,7 +477,7 @@ void build_levels(const Csr &A, const gemslr_partition *part, const gemslr_optio
     la.e = n;
     la.bp = bps[h.nlev - 1];
     Csr C = block_diag_part(submatrix(h.Ahat, la.s, n, la.s, n), la.bp);
-    factor_level(C, la.bp, opt, la.L, la.U, h.nclamp);
+    factor_level(C, la.bp, opt, h.alpha, la.L, la.U, h.nclamp);
     if (opt->strict_pivots && h.nclamp > 0)
         fail(GEMSLR_ERR_ZERO_PIVOT, std::to_string(h.nclamp) + " pivots were clamped");
 }

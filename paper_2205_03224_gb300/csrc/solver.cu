@@ -66,8 +66,10 @@ struct gemslr_ctx {
     bool graph_failed = false;
     uint64_t graph_k_top = 0, graph_k_cycle = 0, graph_k_step = 0;
     LearnedHost *learned = nullptr;
+    ZState *z = nullptr;           // complex hierarchy and its Krylov workspace (complex shift)
     ~gemslr_ctx() {
         delete learned;
+        z_destroy(z);
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (graph) cudaGraphDestroy(graph);
         if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -90,6 +92,11 @@ static void require_device(const gemslr_ctx *h) {
     if (dev != h->dev)
         fail(GEMSLR_ERR_ARG, "the handle lives on device " + std::to_string(h->dev) + " but device " +
                                  std::to_string(dev) + " is current");
+}
+
+// The real entry points refuse a complex handle and the complex ones a real one.
+static void require_real(const gemslr_ctx *h) {
+    if (h->host.cplx) fail(GEMSLR_ERR_ARG, "complex handle (complex shift): use gemslr_zapply / gemslr_zfgmres_solve");
 }
 
 namespace {
@@ -413,6 +420,12 @@ void finish_setup(gemslr_ctx *h, bool compute_lowrank) {
     h->zeros = (double *)h->arena.alloc(8 * std::max<int64_t>(n, 1));
     GEMSLR_CUDA(cudaMemset(h->zeros, 0, 8 * std::max<int64_t>(n, 1)));
     const int limit = smem_optin();
+    if (h->host.cplx) {            // complex shift (Sec. 5.2.3): complex hierarchy only
+        ensure_krylov(h, 8);
+        h->z = z_create(h->host, h->arena, h->opt, h->A_rp, h->A_ci, h->A_v, h->perm, limit, sm_count(),
+                        compute_lowrank);
+        return;
+    }
     upload_hierarchy<double, double>(h->host, h->arena, h->d64, limit);
     ensure_krylov(h, 8);
     if (compute_lowrank) {
@@ -703,6 +716,10 @@ gemslr_options normalized(const gemslr_options *opt) {
     if (o.lowrank_method != GEMSLR_LOWRANK_ARNOLDI && o.lowrank_method != GEMSLR_LOWRANK_RANDOMIZED)
         fail(GEMSLR_ERR_ARG, "unknown lowrank_method");
     if (o.lowrank_power < 0 || o.lowrank_power > 16) fail(GEMSLR_ERR_ARG, "lowrank_power must be in 0..16");
+    if (!std::isfinite(o.shift)) fail(GEMSLR_ERR_ARG, "shift must be finite");
+    if (o.shift != 0.0 && (o.precision != GEMSLR_PREC_FP64 || o.lowrank_method != GEMSLR_LOWRANK_ARNOLDI ||
+                           o.ilu_kind == GEMSLR_ILU0_DEVICE))
+        fail(GEMSLR_ERR_UNSUPPORTED, "the complex shift needs FP64, a host ILU and the Arnoldi set-up");
     return o;
 }
 
@@ -730,8 +747,15 @@ void hierarchy_from_factors(const gemslr_csr *A, const gemslr_partition *part, c
     Csr M = csr_from_abi(A);
     gemslr_options o = opt;
     o.ilu_kind = GEMSLR_ILU0;       // cheap placeholder factorisation, replaced below
+    o.shift = 0.0;
     for (int l = 0; l < GEMSLR_MAX_LEVELS; ++l) o.rank[l] = 0;
     build_levels(M, part, &o, H);
+    // imaginary parts (complex factors): copied into vi / Wi / Hi, NULL: none
+    auto imag = [&H](Csr &T, const double *im) {
+        if (!im) return;
+        T.vi.assign(im, im + T.nnz());
+        H.cplx = true;
+    };
     if (f->nlev != H.nlev || (H.nlev > 1 && !f->levels)) fail(GEMSLR_ERR_ARG, "factor level count mismatch");
     for (int l = 0; l < H.nlev - 1; ++l) {
         const gemslr_level_factors &lf = f->levels[l];
@@ -752,10 +776,18 @@ void hierarchy_from_factors(const gemslr_csr *A, const gemslr_partition *part, c
             if (!lf.W || !lf.H) fail(GEMSLR_ERR_ARG, "W/H missing");
             hl.W.assign(lf.W, lf.W + (size_t)s * lf.k);
             hl.H.assign(lf.H, lf.H + (size_t)lf.k * lf.k);
+            hl.Wi.clear();
+            hl.Hi.clear();
+            if (lf.W_im) { hl.Wi.assign(lf.W_im, lf.W_im + (size_t)s * lf.k); H.cplx = true; }
+            if (lf.H_im) { hl.Hi.assign(lf.H_im, lf.H_im + (size_t)lf.k * lf.k); H.cplx = true; }
         }
+        imag(hl.L, lf.L_im);
+        imag(hl.U, lf.U_im);
     }
     H.last.L = csr_from_mat(f->last_L);
     H.last.U = csr_from_mat(f->last_U);
+    imag(H.last.L, f->last_L_im);
+    imag(H.last.U, f->last_U_im);
     if (H.last.L.nrows != H.n - H.last.s || H.last.U.nrows != H.n - H.last.s)
         fail(GEMSLR_ERR_ARG, "last-level factor shape mismatch");
 }
@@ -774,6 +806,7 @@ void gemslr_default_options(gemslr_options *opt) {
     opt->arnoldi_max_cycles = 20;
     opt->lowrank_method = GEMSLR_LOWRANK_ARNOLDI;
     opt->lowrank_power = 1;
+    opt->shift = 0.0;
 }
 
 const char *gemslr_last_error(void) { return g_last_error.c_str(); }
@@ -844,7 +877,14 @@ gemslr_status gemslr_setup_from_factors(const gemslr_csr *A, const gemslr_partit
         h->arena.set_allocator(h->opt.dev_alloc, h->opt.dev_free, h->opt.alloc_ctx);
         hierarchy_from_factors(A, part, f, h->opt, h->host);
         Hierarchy &H = h->host;
+        if (H.cplx && h->opt.precision != GEMSLR_PREC_FP64)
+            fail(GEMSLR_ERR_UNSUPPORTED, "complex factors need precision FP64");
         finish_setup(h.get(), false);
+        if (H.cplx) {
+            h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            *out = h.release();
+            return;
+        }
         for (size_t l = 0; l < H.lev.size(); ++l) set_lowrank<double, double>(h->d64.lev[l], H.lev[l], h->arena);
         if (h->mixed) {
             // rebuild the mixed hierarchy now that W/H are attached
@@ -886,6 +926,13 @@ gemslr_status gemslr_export_factors(gemslr_handle h, gemslr_factors *f) {
         if (!h || !f || !f->levels) fail(GEMSLR_ERR_ARG, "NULL argument");
         const Hierarchy &H = h->host;
         if (f->nlev != H.nlev) fail(GEMSLR_ERR_ARG, "nlev mismatch");
+        // imaginary parts of a complex handle (zeros where a factor has none)
+        auto put_im = [&H](const std::vector<double> &im, size_t count, const double *dst) {
+            if (!H.cplx) return;
+            if (!dst && count > 0) fail(GEMSLR_ERR_ARG, "complex handle: NULL imaginary-part buffer");
+            double *d = const_cast<double *>(dst);
+            for (size_t i = 0; i < count; ++i) d[i] = im.empty() ? 0.0 : im[i];
+        };
         for (size_t l = 0; l < H.lev.size(); ++l) {
             const HostLevel &hl = H.lev[l];
             const gemslr_level_factors &lf = f->levels[l];
@@ -893,15 +940,21 @@ gemslr_status gemslr_export_factors(gemslr_handle h, gemslr_factors *f) {
             put_mat(hl.U, lf.U);
             put_mat(hl.E, lf.E);
             put_mat(hl.F, lf.F);
+            put_im(hl.L.vi, (size_t)hl.L.nnz(), lf.L_im);
+            put_im(hl.U.vi, (size_t)hl.U.nnz(), lf.U_im);
             const_cast<gemslr_level_factors &>(lf).k = hl.k;
             if (hl.k > 0) {
                 if (!lf.W || !lf.H) fail(GEMSLR_ERR_ARG, "NULL W/H buffer");
                 std::copy(hl.W.begin(), hl.W.end(), const_cast<double *>(lf.W));
                 std::copy(hl.H.begin(), hl.H.end(), const_cast<double *>(lf.H));
+                put_im(hl.Wi, hl.W.size(), lf.W_im);
+                put_im(hl.Hi, hl.H.size(), lf.H_im);
             }
         }
         put_mat(H.last.L, f->last_L);
         put_mat(H.last.U, f->last_U);
+        put_im(H.last.L.vi, (size_t)H.last.L.nnz(), f->last_L_im);
+        put_im(H.last.U.vi, (size_t)H.last.U.nnz(), f->last_U_im);
     });
 }
 
@@ -964,6 +1017,7 @@ extern "C" {
 gemslr_status gemslr_save_factors(gemslr_handle h, const char *path) {
     return guard([&] {
         if (!h || !path) fail(GEMSLR_ERR_ARG, "NULL argument");
+        if (h->host.cplx) fail(GEMSLR_ERR_UNSUPPORTED, "a complex handle cannot be saved");
         FilePtr f(fopen(path, "wb"));
         if (!f) fail(GEMSLR_ERR_ARG, std::string("cannot open ") + path + " for writing");
         const Hierarchy &H = h->host;
@@ -1043,6 +1097,7 @@ gemslr_status gemslr_apply(gemslr_handle h, const double *r_dev, double *z_dev, 
         if (!h || nrhs < 0 || (nrhs > 0 && (!r_dev || !z_dev))) fail(GEMSLR_ERR_ARG, "invalid argument");
         if (r_dev == z_dev && nrhs > 0) fail(GEMSLR_ERR_ARG, "r and z must not alias");
         require_device(h);
+        require_real(h);
         cudaStream_t st = (cudaStream_t)stream;
         const int64_t n = h->host.n;
         ensure_krylov(h, 8);
@@ -1062,6 +1117,7 @@ gemslr_status gemslr_fgmres_solve(gemslr_handle h, const double *b_dev, double *
         if (!h || !opts || !info || nrhs < 0 || (nrhs > 0 && (!b_dev || !x_dev)))
             fail(GEMSLR_ERR_ARG, "invalid argument");
         require_device(h);
+        require_real(h);
         if (opts->restart < 1 || opts->maxit < 1 || !(opts->rtol > 0) || opts->ortho < 0 || opts->ortho > 1)
             fail(GEMSLR_ERR_ARG, "invalid solve options");
         cudaStream_t st = (cudaStream_t)stream;
@@ -1137,6 +1193,41 @@ gemslr_status gemslr_fgmres_solve(gemslr_handle h, const double *b_dev, double *
     return st_ != GEMSLR_OK ? st_ : worst;
 }
 
+gemslr_status gemslr_zapply(gemslr_handle h, const double *r_dev, double *z_dev, int32_t nrhs, void *stream) {
+    return guard([&] {
+        if (!h || nrhs < 0 || (nrhs > 0 && (!r_dev || !z_dev))) fail(GEMSLR_ERR_ARG, "invalid argument");
+        if (r_dev == z_dev && nrhs > 0) fail(GEMSLR_ERR_ARG, "r and z must not alias");
+        require_device(h);
+        if (!h->host.cplx) fail(GEMSLR_ERR_ARG, "real handle: use gemslr_apply");
+        z_apply(h->z, reinterpret_cast<const zc *>(r_dev), reinterpret_cast<zc *>(z_dev), nrhs,
+                (cudaStream_t)stream);
+    });
+}
+
+gemslr_status gemslr_zfgmres_solve(gemslr_handle h, const double *b_dev, double *x_dev, int32_t nrhs,
+                                   const gemslr_solve_opts *opts, gemslr_solve_info *info, void *stream) {
+    gemslr_status worst = GEMSLR_OK;
+    gemslr_status st_ = guard([&] {
+        if (!h || !opts || !info || nrhs < 0 || (nrhs > 0 && (!b_dev || !x_dev)))
+            fail(GEMSLR_ERR_ARG, "invalid argument");
+        require_device(h);
+        if (!h->host.cplx) fail(GEMSLR_ERR_ARG, "real handle: use gemslr_fgmres_solve");
+        if (opts->restart < 1 || opts->maxit < 1 || !(opts->rtol > 0)) fail(GEMSLR_ERR_ARG, "invalid solve options");
+        const int64_t n = h->host.n;
+        for (int c = 0; c < nrhs; ++c) {
+            std::string msg;
+            const gemslr_status s = z_solve(h->z, reinterpret_cast<const zc *>(b_dev) + (size_t)c * n,
+                                            reinterpret_cast<zc *>(x_dev) + (size_t)c * n, *opts, info[c], msg,
+                                            (cudaStream_t)stream);
+            if (s != GEMSLR_OK && worst == GEMSLR_OK) {
+                worst = s;
+                g_last_error = msg;
+            }
+        }
+    });
+    return st_ != GEMSLR_OK ? st_ : worst;
+}
+
 gemslr_status gemslr_get_stats(gemslr_handle h, double *out, int32_t nout) {
     return guard([&] {
         if (!h || !out) fail(GEMSLR_ERR_ARG, "NULL argument");
@@ -1153,7 +1244,8 @@ gemslr_status gemslr_get_stats(gemslr_handle h, double *out, int32_t nout) {
         out[3] = (double)H.Ahat.nnz();
         out[4] = (double)nnzf;
         // algorithmic bytes of one application (values, indices, vectors, W)
-        const double sv = h->mixed ? 4.0 : 8.0, sw = h->mixed ? 2.0 : 8.0, si = 4.0;
+        const double sv = H.cplx ? 16.0 : (h->mixed ? 4.0 : 8.0), sw = H.cplx ? 16.0 : (h->mixed ? 2.0 : 8.0),
+                     si = 4.0;
         double bytes = 0.0;
         for (auto &l : H.lev) {
             const double d = (double)(l.e - l.s), s = (double)(H.n - l.e);
@@ -1163,7 +1255,7 @@ gemslr_status gemslr_get_stats(gemslr_handle h, double *out, int32_t nout) {
             bytes += (8.0 * d + 6.0 * s) * sv;
         }
         bytes += (H.last.L.nnz() + H.last.U.nnz()) * (sv + si) + 2.0 * (H.n - H.last.s) * sv;
-        bytes += 2.0 * H.n * 8.0;
+        bytes += 2.0 * H.n * (H.cplx ? 16.0 : 8.0);
         out[5] = bytes;
         out[6] = h->setup_ms;
         out[7] = (double)h->arena.bytes();
@@ -1171,14 +1263,21 @@ gemslr_status gemslr_get_stats(gemslr_handle h, double *out, int32_t nout) {
             double *o = out + 8 + 6 * l;
             if (l + 1 < H.nlev) {
                 const HostLevel &hl = H.lev[l];
-                const auto &dl = h->d64.lev[l];
                 o[0] = (double)(hl.e - hl.s); o[1] = (double)(H.n - hl.e); o[2] = hl.k;
-                o[3] = (double)(hl.L.nnz() + hl.U.nnz()); o[4] = dl.nwf_L; o[5] = dl.nwf_U;
+                o[3] = (double)(hl.L.nnz() + hl.U.nnz());
             } else {
                 o[0] = (double)(H.n - H.last.s);
                 o[3] = (double)(H.last.L.nnz() + H.last.U.nnz());
-                o[4] = h->d64.last.nwf_L; o[5] = h->d64.last.nwf_U;
             }
+            int wl = 0, wu = 0;
+            if (H.cplx) z_wavefronts(h->z, l, wl, wu);
+            else {
+                const auto &dl = l + 1 < H.nlev ? h->d64.lev[l] : h->d64.last;
+                wl = dl.nwf_L;
+                wu = dl.nwf_U;
+            }
+            o[4] = wl;
+            o[5] = wu;
         }
     });
 }
@@ -1472,6 +1571,7 @@ gemslr_status gemslr_learned_train(gemslr_handle h, const int32_t *coords, const
                                    double *loss_history) {
     return guard([&] {
         if (!h || !coords || !o) fail(GEMSLR_ERR_ARG, "NULL argument");
+        require_real(h);
         if (h->d64.inner.k > 0 || h->d32.inner.k > 0)
             fail(GEMSLR_ERR_ARG, "inner steps and the learned stage are exclusive");
         if (o->npairs < 1 || o->epochs < 0 || o->batch < 1 || !(o->lr > 0)) fail(GEMSLR_ERR_ARG, "invalid learned options");
@@ -1539,6 +1639,7 @@ gemslr_status gemslr_learned_train(gemslr_handle h, const int32_t *coords, const
 gemslr_status gemslr_set_inner_steps(gemslr_handle h, int32_t steps) {
     return guard([&] {
         if (!h || steps < 0 || steps > kMaxInner) fail(GEMSLR_ERR_ARG, "inner steps must be in [0, 8]");
+        require_real(h);
         if (steps > 0 && h->host.lev.empty()) fail(GEMSLR_ERR_ARG, "inner steps need a Schur level");
         const bool learned = (h->d64.learned && h->d64.learned->enabled) || (h->d32.learned && h->d32.learned->enabled);
         if (steps > 0 && learned) fail(GEMSLR_ERR_ARG, "inner steps and the learned stage are exclusive");
@@ -1667,6 +1768,7 @@ extern "C" gemslr_status gemslr_apply_static(gemslr_handle h, const double *r_de
             fail(GEMSLR_ERR_ARG, "n = " + std::to_string(n) + " exceeds the static scratch capacity of " +
                                      std::to_string(kStaticRows) + " rows; use gemslr_apply");
         require_device(h);
+        require_real(h);
         const int dev = h->dev;
         if (dev < 0 || dev >= kMaxDevices) fail(GEMSLR_ERR_ARG, "device index out of range");
         double *base = nullptr;

@@ -71,3 +71,16 @@ def round_w_to_bf16(M):
     for lv in M.levels:
         lv["W"] = bf16(lv["W"])
     return M.factors()
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_hierarchy_z(name, shift):
+    """Oracle hierarchy of a case with the complex diagonal shift (Sec. 5.2.3)."""
+    dims, beta, sigma, nlev, p, ilu, tau, lfil, rank = CASES[name]
+    A, xyz, part = problem(name)
+    return OracleGemslr(A.to_scipy(), part, ilu=ilu, tau=tau, lfil=lfil, rank=rank, shift=shift)
+
+
+def rhs_complex(n, seed):
+    """Seeded complex right-hand side: real and imaginary parts U[-1, 1)."""
+    return gi.rhs_uniform(n, seed) + 1j * gi.rhs_uniform(n, seed + 1000)

@@ -17,10 +17,10 @@ STRUCTS = {
     "gemslr_partition": ("Partition", ["nlev", "perm", "level_ptr", "nblk", "block_ptr"]),
     "gemslr_options": ("Options", ["ilu_kind", "ilut_tau", "ilut_lfil", "rank", "precision", "arnoldi_tol",
                                    "arnoldi_max_cycles", "strict_pivots", "dev_alloc", "dev_free", "alloc_ctx",
-                                   "lowrank_method", "lowrank_power"]),
+                                   "lowrank_method", "lowrank_power", "shift"]),
     "gemslr_mat": ("Mat", ["nrows", "ncols", "rowptr", "colind", "val"]),
-    "gemslr_level_factors": ("LevelFactors", ["L", "U", "E", "F", "k", "W", "H"]),
-    "gemslr_factors": ("Factors", ["nlev", "levels", "last_L", "last_U"]),
+    "gemslr_level_factors": ("LevelFactors", ["L", "U", "E", "F", "k", "W", "H", "L_im", "U_im", "W_im", "H_im"]),
+    "gemslr_factors": ("Factors", ["nlev", "levels", "last_L", "last_U", "last_L_im", "last_U_im"]),
     "gemslr_solve_opts": ("SolveOpts", ["restart", "maxit", "rtol", "ortho"]),
     "gemslr_solve_info": ("SolveInfo", ["iters", "restarts", "converged", "reorth", "rel_res_est", "rel_res_true",
                                         "t_total_ms"]),
