@@ -528,7 +528,8 @@ def run_ours(args):
     if rank == 0 and CONFIG == "c2" and not args.no_other_configs:
         # the other configurations, measured by the same run: the batched
         # systems (solves/s) and the indefinite 128^3 operator (per iteration)
-        line["other_configs"] = {"c4_batched": batch_measure(3, 1), "c3_indefinite": indefinite_measure(200)}
+        line["other_configs"] = {"c4_batched": batch_measure(3, 1), "c3_indefinite": indefinite_measure(200),
+                                 "c3_complex_shift": complex_measure(60)}
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -673,6 +674,67 @@ def indefinite_measure(maxit):
             "apply_gbs": st["bytes_per_apply"] / (apply_ms * 1e-3) / 1e9}
 
 
+def complex_measure(maxit):
+    """The complex diagonal shift (Sec. 5.2.3, shift 0.05): every diagonal block
+    factored as B + i alpha I, complex W H W^H, M^-1 and FGMRES in complex FP64.
+    (a) the c3 operator (128^3, -0.05 h^-2): set-up, time per FGMRES(60)
+    iteration over ``maxit`` iterations, residual reached, M^-1 applications;
+    (b) the same family at 48^3: time to 1e-8 with the complex shift against
+    the real FP64 path on the same operator and partition."""
+    import torch
+    from paper_2205_03224_gb300 import Gemslr, partition_geometric
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    c = gi.CONFIGS["c3"]
+    A, xyz, b = gi.config_problem("c3")
+    part = partition_geometric(A, xyz, c["nlev"], c["p"], local_from=c.get("local_from"))
+    t0 = time.perf_counter()
+    G = Gemslr(A, part, ilu=c["ilu"], tau=c["tau"], lfil=c["lfil"], rank=c["rank"], shift=0.05)
+    setup_s = time.perf_counter() - t0
+    b_dev = torch.from_numpy(b).cuda()
+    G.solve(b_dev, restart=c["restart"], rtol=c["rtol"], maxit=5, check=False)
+    (x, info), ms = timed(lambda: G.solve(b_dev, restart=c["restart"], rtol=c["rtol"], maxit=maxit, check=False))
+    res = float(np.linalg.norm(b - A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(b))
+    r_dev = torch.from_numpy(gi.rhs_uniform(A.n, 7)).cuda().to(torch.complex128)
+    for _ in range(3):
+        G.apply(r_dev)
+    _, apply_ms = timed(lambda: [G.apply(r_dev) for _ in range(10)])
+    apply_ms /= 10
+    st = G.stats()
+    G.close()
+    big = {"workload": "3-D 7-pt Laplacian - 0.05 h^-2 I (indefinite) 128^3 (n=2097152), 4 levels x 64 subdomains, "
+                       "ILUT(1e-3,10) of B + i alpha I, alpha = 0.05 mean |a_ii|, rank 64, complex FP64, FGMRES(60)",
+           "setup_s": setup_s, "iterations": info[0]["iters"], "converged": bool(info[0]["converged"]),
+           "rel_residual": res, "ms_per_iteration": ms / max(1, info[0]["iters"]), "apply_ms": apply_ms,
+           "applies_per_s": 1e3 / apply_ms, "bytes_per_apply": st["bytes_per_apply"],
+           "apply_gbs": st["bytes_per_apply"] / (apply_ms * 1e-3) / 1e9}
+    A2, xyz2 = gi.grid_operator((48, 48, 48), beta=0.0, sigma=0.05)
+    b2 = gi.rhs_uniform(A2.n, 2)
+    part2 = partition_geometric(A2, xyz2, 4, 64, local_from=1)
+    b2_dev = torch.from_numpy(b2).cuda()
+    small = {"workload": "3-D 7-pt Laplacian - 0.05 h^-2 I 48^3 (n=110592), 4 levels x 64 subdomains, ILUT(1e-3,10), "
+                         "rank 32, FGMRES(60) to 1e-8, b~U[-1,1) seed 2"}
+    for key, shift in (("complex_shift_0.05", 0.05), ("real_fp64", 0.0)):
+        G2 = Gemslr(A2, part2, ilu="ilut", tau=1e-3, lfil=10, rank=32, shift=shift)
+        G2.solve(b2_dev, restart=60, rtol=1e-8, maxit=1000, check=False)
+        (x2, inf2), ms2 = timed(lambda: G2.solve(b2_dev, restart=60, rtol=1e-8, maxit=1000, check=False))
+        r2 = float(np.linalg.norm(b2 - A2.to_scipy() @ x2.cpu().numpy()) / np.linalg.norm(b2))
+        small[key] = {"time_to_solution_ms": ms2, "iterations": inf2[0]["iters"],
+                      "converged": bool(inf2[0]["converged"]), "rel_residual": r2,
+                      "ms_per_iteration": ms2 / max(1, inf2[0]["iters"])}
+        G2.close()
+    return {"c3_operator": big, "n48": small}
+
+
 def run_learned(args):
     """c5: 96^3 shifted (indefinite) operator; FGMRES(60) with and without the learned stage."""
     import torch
@@ -749,7 +811,7 @@ def main():
                     help="mixed runs: skip timing the plain FP64 GPU path beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-configs", action="store_true",
-                    help="default line: skip the batched (c4) and indefinite (c3) measurements")
+                    help="default line: skip the batched (c4), indefinite (c3) and complex-shift measurements")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2 (default line), c3: 128^3 shifted (mixed), c4: batched systems, c5: learned stage")
     ap.add_argument("--maxit", type=int, default=1000)

@@ -202,7 +202,7 @@ void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, Chun
             const int64_t maxlen = nlen[R[start] - r0];
             int64_t n = 0;
             while (start + n < R.size() && n < max_rows &&
-                   chunk_bytes<VT>(n + 1, maxlen, upper) <= (size_t)kStageBytes)
+                   chunk_bytes<VT>(n + 1, maxlen, upper) <= (size_t)StageBytesOf<VT>::value)
                 ++n;
             if (n == 0) fail(GEMSLR_ERR_UNSUPPORTED, "a factor row has too many entries for the staged substitution");
             const size_t bytes = chunk_bytes<VT>(n, maxlen, upper);

@@ -87,7 +87,8 @@ k_trsv(const LevelView<VT, WT> lv, const IoT<VT> *__restrict__ in, VT *__restric
     unsigned char *ring = smem;
     // FP32: kGroupChunks chunks per copy, one per consumer warp; FP64: one
     constexpr int CPG = LanesPerRow<VT>::value == 1 ? kGroupChunks : 1;
-    constexpr int kSlots = kRingData / (CPG * kStageBytes);
+    constexpr int SB = StageBytesOf<VT>::value;
+    constexpr int kSlots = kRingData / (CPG * SB);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + kRingData);
     uint64_t *empty = full + kSlots;
     uint64_t *cbar = empty + kSlots;
@@ -113,7 +114,7 @@ k_trsv(const LevelView<VT, WT> lv, const IoT<VT> *__restrict__ in, VT *__restric
     __syncthreads();
 
     if (warp == kConsumerWarps) {            // producer warp
-        produce_chunks<CPG>(lv.C.data, lv.C.off, c0, c1, ring, full, empty, abort_flag, lv.err, lane);
+        produce_chunks<CPG, SB>(lv.C.data, lv.C.off, c0, c1, ring, full, empty, abort_flag, lv.err, lane);
         return;
     }
 
@@ -193,7 +194,7 @@ k_trsv(const LevelView<VT, WT> lv, const IoT<VT> *__restrict__ in, VT *__restric
         const unsigned char *base = nullptr;
         for (int c = c0; c < c1; ++c) {
             const int k = c - c0;
-            base = aborted ? nullptr : next_chunk<VT, CPG>(ring, full, abort_flag, k, base);
+            base = aborted ? nullptr : next_chunk<VT, CPG, SB>(ring, full, abort_flag, k, base);
             if (!aborted && !base) {
                 aborted = true;
                 *abort_flag = 1;
@@ -230,7 +231,7 @@ k_trsv(const LevelView<VT, WT> lv, const IoT<VT> *__restrict__ in, VT *__restric
                     }
                 }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[chunk_slot<CPG>(k)]);
+                if (lane == 0) mbar_arrive(&empty[chunk_slot<CPG, SB>(k)]);
             }
             consumer_barrier();
         }

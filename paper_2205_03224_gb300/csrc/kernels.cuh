@@ -48,6 +48,10 @@ constexpr int kTrsvThreads2 = 32 * (kConsumerWarps + 1);
 constexpr int kRingBytes = kRingData + 2 * kMaxSlots * 8 + 64;   // ring + mbarriers + flags
 template <typename VT> struct LanesPerRow { static constexpr int value = 4; };
 template <> struct LanesPerRow<float> { static constexpr int value = 1; };
+// Largest chunk of a value type: complex chunks (16-byte values) are twice as
+// large, so that a typical wavefront still fits in one chunk (one hand-off).
+template <typename VT> struct StageBytesOf { static constexpr int value = kStageBytes; };
+template <> struct StageBytesOf<zc> { static constexpr int value = 2 * kStageBytes; };
 
 struct ChunkView {
     const unsigned char *data;

@@ -153,11 +153,11 @@ __device__ __forceinline__ bool wait_bounded(uint64_t *bar, unsigned parity, vol
 // waits on a global load of its own size; lane 0 issues the copies.  On an
 // expired wait the CTA's abort flag and the device error word are set.
 // Before returning, lane 0 waits for the copies still in flight.
-template <int CPG>
+template <int CPG, int SB = kStageBytes>
 __device__ __forceinline__ void produce_chunks(const unsigned char *data, const int64_t *off, int c0, int c1,
                                                unsigned char *ring, uint64_t *full, uint64_t *empty,
                                                volatile int *abort_flag, int32_t *err, int lane) {
-    constexpr int kGroups = kRingData / (CPG * kStageBytes), kGroupBytes = CPG * kStageBytes;
+    constexpr int kGroups = kRingData / (CPG * SB), kGroupBytes = CPG * SB;
     const int ngroup = (c1 - c0 + CPG - 1) / CPG;
     auto group_range = [&](int g, int64_t &a, int64_t &b) {
         a = off[c0 + CPG * g];
@@ -218,10 +218,10 @@ __device__ __forceinline__ int chunk_size(const int *hdr) {
 // Wait until chunk k (block-relative) is in shared memory and return it: its
 // group of CPG chunks is in slot (k / CPG) % kGroups, after the chunks
 // before it.
-template <typename VT, int CPG>
+template <typename VT, int CPG, int SB = kStageBytes>
 __device__ __forceinline__ const unsigned char *wait_chunk(const unsigned char *ring, uint64_t *full,
                                                            volatile int *abort_flag, int k) {
-    constexpr int kGroups = kRingData / (CPG * kStageBytes), kGroupBytes = CPG * kStageBytes;
+    constexpr int kGroups = kRingData / (CPG * SB), kGroupBytes = CPG * SB;
     const int g = k / CPG, slot = g % kGroups;
     if (!poll_bounded(&full[slot], (g / kGroups) & 1, abort_flag)) return nullptr;
     const unsigned char *p = ring + (size_t)slot * kGroupBytes;
@@ -231,20 +231,20 @@ __device__ __forceinline__ const unsigned char *wait_chunk(const unsigned char *
 
 // For consumers that take the chunks in order: chunk k follows chunk k-1
 // (at prev) in the same group, else it starts a group that must be waited for.
-template <typename VT, int CPG>
+template <typename VT, int CPG, int SB = kStageBytes>
 __device__ __forceinline__ const unsigned char *next_chunk(const unsigned char *ring, uint64_t *full,
                                                            volatile int *abort_flag, int k,
                                                            const unsigned char *prev) {
-    constexpr int kGroups = kRingData / (CPG * kStageBytes), kGroupBytes = CPG * kStageBytes;
+    constexpr int kGroups = kRingData / (CPG * SB), kGroupBytes = CPG * SB;
     if (k % CPG != 0) return prev + chunk_size<VT>(reinterpret_cast<const int *>(prev));
     const int g = k / CPG, slot = g % kGroups;
     if (!poll_bounded(&full[slot], (g / kGroups) & 1, abort_flag)) return nullptr;
     return ring + (size_t)slot * kGroupBytes;
 }
 
-// Ring slot of chunk k for CPG chunks per copy.
-template <int CPG>
-__device__ __forceinline__ int chunk_slot(int k) { return (k / CPG) % (kRingData / (CPG * kStageBytes)); }
+// Ring slot of chunk k for CPG chunks of at most SB bytes per copy.
+template <int CPG, int SB = kStageBytes>
+__device__ __forceinline__ int chunk_slot(int k) { return (k / CPG) % (kRingData / (CPG * SB)); }
 
 // Registers holding one row slot of a chunk (lane-per-row layout): NE entry
 // slots (the launch picks NE >= the level's longest row where it can; longer

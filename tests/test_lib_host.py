@@ -40,6 +40,7 @@ def test_default_options(lib):
     lib.gemslr_default_options(ctypes.byref(o))
     assert o.ilu_kind == 1 and o.ilut_tau == 1e-3 and o.ilut_lfil == 10
     assert o.arnoldi_tol == 1e-2 and o.arnoldi_max_cycles == 20 and o.precision == 0
+    assert o.shift == 0.0 and o.lowrank_method == 0 and o.lowrank_power == 1
 
 
 @pytest.mark.parametrize("case", [("2d", (32, 32), 0.0, 2, 4), ("3d", (9, 7, 6), 0.3, 3, 4),
@@ -101,3 +102,15 @@ def test_local_order_and_batch_from_factors_reject_bad_arguments(lib):
     # the identity case: first level = nlev leaves the permutation unchanged
     same = local_order(part, xyz, 3)
     assert np.array_equal(same["perm"], part["perm"])
+
+
+def test_complex_entry_points_reject_bad_arguments(lib):
+    """The complex application and solve report argument errors before any
+    device work (NULL handle, NULL vectors, negative nrhs)."""
+    from paper_2205_03224_gb300 import _lib
+    so = _lib.SolveOpts(30, 100, 1e-8, 0)
+    info = (_lib.SolveInfo * 1)()
+    assert _lib.STATUS[lib.gemslr_zapply(None, None, None, 1, None)] == "ERR_ARG"
+    assert _lib.STATUS[lib.gemslr_zapply(None, None, None, -1, None)] == "ERR_ARG"
+    assert _lib.STATUS[lib.gemslr_zfgmres_solve(None, None, None, 1, ctypes.byref(so), info, None)] == "ERR_ARG"
+    assert _lib.STATUS[lib.gemslr_zfgmres_solve(None, None, None, 1, None, info, None)] == "ERR_ARG"
