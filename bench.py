@@ -735,6 +735,56 @@ def complex_measure(maxit):
     return {"c3_operator": big, "n48": small}
 
 
+def run_complex(args):
+    """c2 with the complex diagonal shift 0.05 (Sec. 5.2.3): complex-shifted
+    block ILU, complex W H W^H, complex FP64 M^-1 and FGMRES; one JSON line
+    (time to 1e-8 per solve, M^-1 applications inside an NVTX range
+    "applies")."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2205_03224_gb300 import Gemslr, partition_geometric
+    c = gi.CONFIGS["c2"]
+    A, xyz, b = gi.config_problem("c2")
+    part = partition_geometric(A, xyz, c["nlev"], c["p"], local_from=c.get("local_from"))
+    t0 = time.perf_counter()
+    G = Gemslr(A, part, ilu=c["ilu"], tau=c["tau"], lfil=c["lfil"], rank=c["rank"], shift=0.05)
+    setup_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    b_dev = torch.from_numpy(b).cuda()
+    ms, x, info = solve_timing(G, b_dev, c, args.steps, args.warmup, flush, stream)
+    res = float(np.linalg.norm(b - A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(b))
+    r_dev = torch.from_numpy(gi.rhs_uniform(A.n, 7)).cuda().to(torch.complex128)
+    for _ in range(3):
+        G.apply(r_dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("applies")
+    e0.record(stream)
+    for _ in range(10):
+        G.apply(r_dev)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.nvtx.range_pop()
+    apply_ms = e0.elapsed_time(e1) / 10
+    st = G.stats()
+    total = sum(ms)
+    line = {
+        "metric": METRIC, "value": 1e3 * len(ms) / total, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total / len(ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("ILUT(1e-3,10)", "ILUT(1e-3,10) of B + i alpha I (shift 0.05)"),
+                   "precision": "complex fp64", "parallelism": "single",
+                   "l2": "256 MB buffer written between solves"},
+        "iterations": info[0]["iters"], "converged": bool(info[0]["converged"]), "final_rel_residual": res,
+        "setup_s": setup_s, "apply_ms": apply_ms, "bytes_per_apply": st["bytes_per_apply"],
+        "apply_gbs": st["bytes_per_apply"] / (apply_ms * 1e-3) / 1e9,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_learned(args):
     """c5: 96^3 shifted (indefinite) operator; FGMRES(60) with and without the learned stage."""
     import torch
@@ -812,8 +862,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other-configs", action="store_true",
                     help="default line: skip the batched (c4), indefinite (c3) and complex-shift measurements")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
-                    help="c2 (default line), c3: 128^3 shifted (mixed), c4: batched systems, c5: learned stage")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "c2z"],
+                    help="c2 (default line), c3: 128^3 shifted (mixed), c4: batched systems, c5: learned stage, "
+                         "c2z: c2 with the complex shift 0.05 (complex FP64)")
     ap.add_argument("--maxit", type=int, default=1000)
     ap.add_argument("--npairs", type=int, default=20000)
     ap.add_argument("--epochs", type=int, default=8)
@@ -826,6 +877,8 @@ def main():
         return run_batch(args)
     if args.workload == "c5":
         return run_learned(args)
+    if args.workload == "c2z":
+        return run_complex(args)
     if args.workload == "c3":
         global CONFIG, WORKLOAD
         CONFIG = "c3"
