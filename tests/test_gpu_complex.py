@@ -34,7 +34,8 @@ def _lib_from_oracle(name, shift=SHIFT):
     return Gemslr.from_factors(A, part, M.factors()), M
 
 
-@pytest.mark.parametrize("name", ["c1", "small3d", "shifted", "tinyparts", "bigblock", "indef24"])
+# c2local: the full 64^3 workload of `bench.py --workload c2z`, in its launch configuration
+@pytest.mark.parametrize("name", ["c1", "small3d", "shifted", "tinyparts", "bigblock", "indef24", "c2local"])
 def test_complex_apply_matches_oracle(torch_cuda, name):
     torch = torch_cuda
     G, M = _lib_from_oracle(name)
@@ -101,16 +102,17 @@ def test_complex_library_setup_matches_oracle_factors(torch_cuda, name):
         assert np.array_equal(a.indices, b.indices) and np.allclose(a.data, b.data, rtol=1e-12, atol=0)
 
 
-@pytest.mark.parametrize("name", ["c1", "small3d", "shifted", "indef24"])
+@pytest.mark.parametrize("name", ["c1", "small3d", "shifted", "indef24", "c2local"])
 def test_complex_fgmres_matches_oracle(torch_cuda, name):
     torch = torch_cuda
     A, xyz, part = problem(name)
     G, M = _lib_from_oracle(name)
     As = A.to_scipy()
     b = gi.rhs_uniform(M.n, 1)
-    x_ref, info_ref = fgmres(As, b, M.apply, restart=30, rtol=1e-8, cplx=True)
+    restart = 50 if name == "c2local" else 30
+    x_ref, info_ref = fgmres(As, b, M.apply, restart=restart, rtol=1e-8, cplx=True)
     assert info_ref["converged"]
-    x, info = G.solve(torch.from_numpy(b).cuda(), restart=30, rtol=1e-8)
+    x, info = G.solve(torch.from_numpy(b).cuda(), restart=restart, rtol=1e-8)
     x = x.cpu().numpy()
     assert np.iscomplexobj(x)
     assert info[0]["converged"]
