@@ -111,6 +111,9 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
             const int t = warp * per + rr;
             if (rr < per && t < nrow) {
                 const int row = rows[t], len = lens[t];
+                // stored values are -t_ij (L) and -u_ij/u_ii (U): x_row d + sum v x,
+                // x_row's load overlapping the chains
+                const float self = xs[row * RPC + r], d = upper ? dinv[t] : 1.f;
                 float a0 = 0.f, a1 = 0.f;
                 int q = 0;
                 for (; q + 1 < len; q += 2) {
@@ -118,9 +121,7 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
                     a1 += vals[(q + 1) * nrow + t] * xs[cols[(q + 1) * nrow + t] * RPC + r];
                 }
                 if (q < len) a0 += vals[q * nrow + t] * xs[cols[q * nrow + t] * RPC + r];
-                float y = xs[row * RPC + r] - (a0 + a1);
-                if (upper) y *= dinv[t];
-                xs[row * RPC + r] = y;
+                xs[row * RPC + r] = fmaf(self, d, a0 + a1);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[chunk_slot<CPG>(k)]);

@@ -162,6 +162,15 @@ template <> zc inv_entry<zc>(const Csr &T, int64_t p) {
     const std::complex<double> r = 1.0 / std::complex<double>(T.v[p], T.vi.empty() ? 0.0 : T.vi[p]);
     return zc(r.real(), r.imag());
 }
+// The stored value of an off-diagonal entry: -t_ij (L, pdiag < 0) or
+// -u_ij / u_ii (U, u_ii at pdiag), formed in FP64 and rounded once.
+template <typename VT> VT stored_entry(const Csr &T, int64_t p, int64_t pdiag) {
+    return cast_to<VT>(pdiag < 0 ? -T.v[p] : -(T.v[p] * (1.0 / T.v[pdiag])));
+}
+template <> zc stored_entry<zc>(const Csr &T, int64_t p, int64_t pdiag) {
+    const zc v = entry_at<zc>(T, p);
+    return pdiag < 0 ? -v : -(v * inv_entry<zc>(T, pdiag));
+}
 
 }  // namespace
 
@@ -220,19 +229,23 @@ void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, Chun
             int32_t *rr = hdr + 4, *ll = rr + pr, *cc = ll + pr;
             VT *vv = reinterpret_cast<VT *>(reinterpret_cast<unsigned char *>(cc) + pad16((size_t)(S * n) * 4));
             VT *dd = reinterpret_cast<VT *>(reinterpret_cast<unsigned char *>(vv) + pad16((size_t)(S * n) * sizeof(VT)));
+            // the chunks store -t_ij (L) and -u_ij / u_ii (U), so that a row is
+            // x_i (times 1/u_ii) plus one sum of products (see kernels.cuh)
             for (int64_t t = 0; t < n; ++t) {
                 const int64_t i = R[start + t];
                 rr[t] = (int32_t)(i - r0);
                 ll[t] = (int32_t)nlen[i - r0];
+                int64_t pdiag = -1;
+                if (upper)
+                    for (int64_t pp = T.rp[i]; pp < T.rp[i + 1]; ++pp)
+                        if (T.ci[pp] == i) pdiag = pp;
+                if (upper) dd[t] = inv_entry<VT>(T, pdiag);
                 int64_t q = 0;
                 for (int64_t pp = T.rp[i]; pp < T.rp[i + 1]; ++pp) {
-                    if (T.ci[pp] == i) {
-                        if (upper) dd[t] = inv_entry<VT>(T, pp);
-                        continue;
-                    }
+                    if (T.ci[pp] == i) continue;
                     const int64_t e = LanesPerRow<VT>::value == 1 ? q * n + t : ((q >> 2) * n + t) * 4 + (q & 3);
                     cc[e] = (int32_t)(T.ci[pp] - r0);
-                    vv[e] = entry_at<VT>(T, pp);
+                    vv[e] = stored_entry<VT>(T, pp, pdiag);
                     ++q;
                 }
             }

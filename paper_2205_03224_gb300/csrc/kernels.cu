@@ -209,26 +209,44 @@ k_trsv(const LevelView<VT, WT> lv, const IoT<VT> *__restrict__ in, VT *__restric
                 const VT *vals = reinterpret_cast<const VT *>(cols + (size_t)S * nrow);
                 const int per = (nrow + kConsumerWarps - 1) / kConsumerWarps;   // rows of this warp (<= 8)
                 if (warp * per < nrow) {                                       // idle warps skip the FP64 work
+                    // x_row = x_row d + sum_j v_j x_j with v_j = -t_row,j (d = 1, L) or
+                    // -u_row,j / u_row,row (d = 1 / u_row,row, U): the padded slots hold
+                    // column 0 and value 0, so every lane loads its first four entries
+                    // unconditionally, all loads before the arithmetic, and adds them in
+                    // two short chains (dependent FP64 operations are slow on this part);
+                    // inactive lanes read row slot 0 and their sums are discarded
                     const int t = warp * per + r;
                     const bool active = r < per && t < nrow;
-                    const int len = active ? lens[t] : 0;
+                    const int tt = active ? t : 0;
                     const int kq = S >> 2;
-                    VT acc = 0;
-                    for (int kk = 0; kk < kq; ++kk) {
-                        const int q = 4 * kk + sub;
-                        if (q < len) {
-                            const int e = (kk * nrow + t) * 4 + sub;
-                            acc += vals[e] * xs[cols[e]];
-                        }
+                    const int row = rows[tt];
+                    int cq[4];
+                    VT vq[4], xq[4];
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {                            // slots past S: column 0, value 0
+                        const int e = (kk * nrow + tt) * 4 + sub;
+                        cq[kk] = kk < kq ? cols[e] : 0;
+                        vq[kk] = kk < kq ? vals[e] : (VT)0;
                     }
+                    VT a0 = 0;
+                    if (sub == 0) {
+                        a0 = xs[row];
+                        if (upper) a0 *= vals[(size_t)S * nrow + tt];          // dinv follows vals
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) xq[kk] = xs[cq[kk]];
+                    VT a1 = vq[1] * xq[1];
+                    a0 += vq[0] * xq[0];
+                    a1 += vq[3] * xq[3];
+                    a0 += vq[2] * xq[2];
+                    for (int kk = 4; kk < kq; ++kk) {                          // rows of more than 16 entries
+                        const int e = (kk * nrow + tt) * 4 + sub;
+                        a0 += vals[e] * xs[cols[e]];
+                    }
+                    VT acc = a0 + a1;
                     acc += shfl_xor(acc, 1);
                     acc += shfl_xor(acc, 2);
-                    if (active && sub == 0) {
-                        const int row = rows[t];
-                        VT y = xs[row] - acc;
-                        if (upper) y *= vals[(size_t)S * nrow + t];     // dinv follows vals
-                        xs[row] = y;
-                    }
+                    if (active && sub == 0) xs[row] = acc;
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[chunk_slot<CPG, SB>(k)]);

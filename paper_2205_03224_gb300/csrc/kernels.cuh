@@ -26,7 +26,9 @@ constexpr int kMaxCols = 160;     // Krylov columns per Gram-Schmidt pass (m + 1
 //   int32 rows[pad4(nrows)]           block-local row of every slot
 //   int32 lens[pad4(nrows)]           entries of every slot
 //   int32 cols[pad4(S*nrows)]         block-local columns
-//   VT    vals[S*nrows] padded to 16 bytes
+//   VT    vals[S*nrows] padded to 16 bytes: -t_ij in L chunks, -u_ij/u_ii in
+//         U chunks (formed in FP64, rounded once), so that a row is
+//         x_i = x_i * d_i + sum_j vals_ij x_j with d_i = 1 (L) or 1/u_ii (U)
 //   VT    dinv[nrows]  padded to 16 bytes (U chunks: 1/u_ii)
 // Entry q of row slot t sits at
 //   FP32 (one lane per row, S = maxlen):          q*nrows + t

@@ -298,7 +298,8 @@ __device__ __forceinline__ void fetch_row(const unsigned char *p, int lane, RowR
     }
 }
 
-// x_row = (x_row - sum_q val_q x_col_q) * dinv for this lane's row slot.
+// x_row = x_row * dinv + sum_q val_q x_col_q for this lane's row slot (the
+// values are stored negated and, in U chunks, divided by u_row,row).
 template <typename VT, int NE>
 __device__ __forceinline__ void solve_row(const RowRegs<VT, NE> &R, VT *xs, int lane) {
     static_assert(NE % 2 == 0, "two partial sums");
@@ -306,7 +307,7 @@ __device__ __forceinline__ void solve_row(const RowRegs<VT, NE> &R, VT *xs, int 
 #pragma unroll
     for (int q = 0; q < NE; ++q)            // padded slots: x_0 * 0
         xv[q] = *reinterpret_cast<const VT *>(reinterpret_cast<const unsigned char *>(xs) + R.col[q]);
-    const VT self = xs[R.row];
+    const VT self = xs[R.row];                 // loaded with the gathers, used after the chains
     VT a0 = 0, a1 = 0;
 #pragma unroll
     for (int q = 0; q < NE; q += 2) {
@@ -320,7 +321,7 @@ __device__ __forceinline__ void solve_row(const RowRegs<VT, NE> &R, VT *xs, int 
         const VT *vals = reinterpret_cast<const VT *>(cols + ((ne + 3) & ~3));
         for (int q = NE; q < R.len; ++q) a0 += vals[q * R.nrow + lane] * xs[cols[q * R.nrow + lane]];
     }
-    if (R.active) xs[R.row] = (self - (a0 + a1)) * R.dinv;
+    if (R.active) xs[R.row] = fmaf(self, R.dinv, a0 + a1);
 }
 
 // Named barriers 2 .. 1+kConsumerWarps hand the sweep from one consumer warp
