@@ -128,6 +128,45 @@ class OracleGemslr:
             for l in range(nsch - 1, -1, -1):
                 self.build_lowrank(l, arnoldi_tol, max_cycles)
 
+    @classmethod
+    def from_factors(cls, A, part, fac):
+        """A hierarchy whose factors are given, in the layout of ``factors()``
+        (L, U, E, F, W, H per Schur level, L, U of the last level): nothing is
+        factored, so Alg. 2 can be applied to factors computed elsewhere (the
+        permutation and the level slices still come from A and the partition)."""
+        self = cls.__new__(cls)
+        self.inner_steps = 0
+        self.stage = None
+        A = sp.csr_matrix(A)
+        self.n = A.shape[0]
+        self.part = part
+        self.perm = np.asarray(part["perm"], dtype=np.int64)
+        self.nlev = len(part["nblk"])
+        Ah = A[self.perm][:, self.perm].tocsr()
+        Ah.sort_indices()
+        self.Ahat = Ah
+        cplx = any(np.iscomplexobj(f[k].data if sp.issparse(f[k]) else np.asarray(f[k]))
+                   for f in fac["levels"] for k in ("L", "U", "W", "H"))
+        self.shift = 0.0
+        self.alpha = 1.0 if cplx else 0.0      # only its being nonzero matters (complex arithmetic)
+        self.levels = []
+        self.nclamp = 0
+        for l, f in enumerate(fac["levels"]):
+            s, e, bp = level_blocks(part, l)
+            W = np.asarray(f["W"])
+            self.levels.append(dict(s=s, e=e, bp=bp - s, L=sp.csr_matrix(f["L"]), U=sp.csr_matrix(f["U"]),
+                                    E=Ah[e:, s:e].tocsr(), F=Ah[s:e, e:].tocsr(), W=W,
+                                    H=np.asarray(f["H"]), rank=W.shape[1], info=None))
+        s, e, bp = level_blocks(part, self.nlev - 1)
+        self.last_s = s
+        self.last_bp = bp - s
+        self.last_C = None
+        self.last_L = sp.csr_matrix(fac["last"]["L"])
+        self.last_U = sp.csr_matrix(fac["last"]["U"])
+        self.lowrank_method = "given"
+        self.power = 1
+        return self
+
     # ---- pieces of Alg. 2 -------------------------------------------------
     def solve_level(self, r, l):
         """pGeMSLRSolve(r, l) on the tail vector r (length n - level_ptr[l])."""

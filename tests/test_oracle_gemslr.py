@@ -231,3 +231,21 @@ def test_randomized_schur_agrees_with_arnoldi_on_the_dominant_values():
     Mr = OracleGemslr(A2s, part2, ilu="exact", rank=10 ** 6, lowrank="randomized")
     r = gi.rhs_uniform(A2.n, 3)
     assert np.allclose(Mr.apply(r), np.linalg.solve(A2s.toarray(), r), rtol=1e-8)
+
+
+@pytest.mark.parametrize("shift", [0.0, 0.05])
+def test_hierarchy_from_given_factors_is_the_same_operator(shift):
+    """OracleGemslr.from_factors rebuilds Alg. 2 from given factors only: fed
+    the factors of an oracle set-up it applies the same M^-1, bit for bit, in
+    real and in complex arithmetic; fed altered factors it follows them."""
+    As, P = _problem()
+    M = OracleGemslr(As, P, ilu="ilut", tau=1e-2, lfil=4, rank=3, shift=shift)
+    fac = M.factors()
+    M2 = OracleGemslr.from_factors(As, P, fac)
+    for seed in (1, 2):
+        r = gi.rhs_uniform(As.shape[0], seed)
+        assert np.array_equal(M2.apply(r), M.apply(r))
+    fac["levels"][0]["H"] = 2.0 * fac["levels"][0]["H"]      # a different correction is followed
+    M3 = OracleGemslr.from_factors(As, P, fac)
+    r = gi.rhs_uniform(As.shape[0], 3)
+    assert not np.allclose(M3.apply(r), M.apply(r))
