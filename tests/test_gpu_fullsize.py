@@ -78,3 +78,41 @@ def test_full_size_mixed_apply_matches_oracle_with_bf16_w(torch_cuda):
     err = rel_err(z, z_ref)
     assert 0.0 < err <= 1e-5, err          # measured on the GB300: 6.8e-8
     G.close()
+
+
+def test_full_size_batched_apply_matches_oracle(torch_cuda):
+    """The batched workload at full size (96 uneven convection-diffusion systems,
+    sides 16..48, 8 right-hand sides each, the c4 bench line's launch
+    configuration): every system's hierarchy from the library's own set-up,
+    batched through gemslr_setup_batch_from_factors, against the oracle on the
+    same factors with W rounded to BF16, for the first and the last
+    right-hand side of every system (FP32 rounding only)."""
+    torch = torch_cuda
+    from paper_2205_03224_gb300 import Gemslr, GemslrBatch, partition_geometric
+    c = gi.CONFIGS["c4"]
+    As, parts, facs, Ms = [], [], [], []
+    for dims, beta in gi.batch_systems(count=c["count"], seed=c["seed"]):
+        A, xyz = gi.grid_operator(dims, beta=beta)
+        part = partition_geometric(A, xyz, c["nlev"], c["p"])
+        G = Gemslr(A, part, ilu=c["ilu"], tau=c["tau"], lfil=c["lfil"], rank=c["rank"])
+        fac = G.export_factors()
+        G.close()
+        As.append(A)
+        parts.append(part)
+        facs.append(fac)
+        Ms.append(OracleGemslr.from_factors(A.to_scipy(), part, _with_bf16_w(fac)))
+    B = GemslrBatch.from_factors(As, parts, facs)
+    nrhs = c["nrhs"]
+    R = np.concatenate([np.stack([gi.rhs_uniform(A.n, 7000 + 10 * s + r) for r in range(nrhs)], axis=1).T.ravel()
+                        for s, A in enumerate(As)])
+    Z = B.apply(torch.from_numpy(R).cuda(), nrhs).cpu().numpy()
+    off = 0
+    for A, M in zip(As, Ms):
+        n = A.n
+        for r in (0, nrhs - 1):
+            rv = R[off + r * n: off + (r + 1) * n]
+            err = rel_err(Z[off + r * n: off + (r + 1) * n], M.apply(rv))
+            assert 0.0 < err <= 1e-4, (n, r, err)
+        off += n * nrhs
+    assert off == R.size
+    B.close()
