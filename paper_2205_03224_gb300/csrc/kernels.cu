@@ -829,7 +829,10 @@ k_gs_sub2(int64_t len, const double *__restrict__ V, int64_t ldv, double *__rest
 __global__ void k_gs_scale(int64_t len, double *__restrict__ V, int64_t ldv, const double *__restrict__ w,
                            const KrylovCtl *ctl, double *__restrict__ vcopy) {
     if (!ctl->reorth || ctl->stop || ctl->breakdown) return;
-    const double inv = 1.0 / ctl->beta;
+    __shared__ double sc;
+    if (threadIdx.x == 0) sc = 1.0 / ctl->beta;               // once per CTA
+    __syncthreads();
+    const double inv = sc;
     double *vn = V + (int64_t)(ctl->j + 1) * ldv;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
         const double x = w[i] * inv;
@@ -1198,14 +1201,21 @@ __global__ void __launch_bounds__(256)
 k_dgs_next(int64_t len, double *__restrict__ V, int64_t ldv, double *vt, const double *__restrict__ w,
            const KrylovCtl *ctl, DgsBufs B) {
     __shared__ double cf[kMaxCols];
+    __shared__ double sc[2];
     const int j = ctl->j;
-    const double nu = ctl->nu, bt = ctl->btil;
-    const bool next = !ctl->breakdown && bt > 0.0;
-    const double inv_nu = 1.0 / nu;
-    const double cj = __ldcg(B.coef + j) * inv_nu;
+    const bool next = !ctl->breakdown && ctl->btil > 0.0;
+    // the step's scalars once per CTA: an FP64 division is a long sequence on
+    // the slow FP64 pipe, and this grid has a thread per row
+    if (threadIdx.x == 0) {
+        const double nu = ctl->nu, inv_nu = 1.0 / nu;
+        sc[0] = __ldcg(B.coef + j) * inv_nu;
+        sc[1] = next ? inv_nu / ctl->btil : 0.0;
+    }
+    __syncthreads();
+    const double cj = sc[0];
     for (int c = threadIdx.x; c < j; c += blockDim.x) cf[c] = fma(-__ldcg(B.a + c), cj, __ldcg(B.coef + c));
     __syncthreads();
-    const double inv_nb = next ? 1.0 / (nu * bt) : 0.0;
+    const double inv_nb = sc[1];
     double *vj = V + (int64_t)j * ldv;
     const int64_t st = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += st) {
@@ -1263,11 +1273,13 @@ k_dgs_fix_adots(int64_t len, double *V, int64_t ldv, const double *vt, double *p
 __global__ void __launch_bounds__(256)
 k_dgs_fix(int64_t len, double *__restrict__ V, int64_t ldv, const KrylovCtl *ctl, DgsBufs B, int off) {
     __shared__ double as[kMaxCols];
+    __shared__ double sc;
     const int jp = ctl->j + off;
     if (jp < 0) return;
     for (int c = threadIdx.x; c < jp; c += blockDim.x) as[c] = __ldcg(B.a + c);
+    if (threadIdx.x == 0) sc = 1.0 / ctl->nu;                 // once per CTA (a thread per row)
     __syncthreads();
-    const double inv_nu = 1.0 / ctl->nu;
+    const double inv_nu = sc;
     double *vj = V + (int64_t)jp * ldv;
     const int64_t st = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += st)
@@ -1373,7 +1385,10 @@ k_norm2(int64_t len, const double *__restrict__ x, double *partial, unsigned *co
 // v = x * (1 / sqrt(*n2))
 __global__ void k_scale_by_norm(int64_t len, const double *__restrict__ x, const double *n2, double *__restrict__ v,
                                 double *__restrict__ vcopy) {
-    const double inv = 1.0 / sqrt(*n2);
+    __shared__ double sc;
+    if (threadIdx.x == 0) sc = 1.0 / sqrt(*n2);               // once per CTA
+    __syncthreads();
+    const double inv = sc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
         v[i] = x[i] * inv;
         if (vcopy) vcopy[i] = x[i] * inv;
