@@ -51,27 +51,27 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2.07 * 2
 #   M^-1 kernels: (config, precision, kernel) -> DRAM bytes of a launch
 #   Krylov kernels (work grows with the step j): -> (DRAM bytes, algorithmic bytes) of the captured step
 TRAFFIC_SOURCES = ["kernels.cu", "kernels.cuh", "ptx.cuh", "device.cu"]
-NCU_TRAFFIC_DIGEST = "e5523be7757c0aaa"
+NCU_TRAFFIC_DIGEST = "e86613e42846e538"
 NCU_TRAFFIC = {
-    ("c2", "mixed", "trsv_down_L0"): 43_782_912,
-    ("c2", "mixed", "trsv_down_L1"): 6_460_160,
-    ("c2", "mixed", "trsv_down_L2"): 438_528,
-    ("c2", "mixed", "trsv_last"): 146_688,
-    ("c2", "mixed", "trsv_up_L2"): 282_624,
-    ("c2", "mixed", "trsv_up_L1"): 4_818_944,
-    ("c2", "mixed", "trsv_up_L0"): 45_650_688,
-    ("c2", "fp64", "trsv_down_L0"): 73_525_760 + 396_288,
-    ("c2", "fp64", "trsv_down_L1"): 15_524_608,
-    ("c2", "fp64", "trsv_down_L2"): 1_223_168,
+    ("c2", "mixed", "trsv_down_L0"): 43_783_424,
+    ("c2", "mixed", "trsv_down_L1"): 6_459_392,
+    ("c2", "mixed", "trsv_down_L2"): 439_552,
+    ("c2", "mixed", "trsv_last"): 146_944,
+    ("c2", "mixed", "trsv_up_L2"): 281_856,
+    ("c2", "mixed", "trsv_up_L1"): 4_819_456,
+    ("c2", "mixed", "trsv_up_L0"): 45_624_320,
+    ("c2", "fp64", "trsv_down_L0"): 73_524_736 + 365_568,
+    ("c2", "fp64", "trsv_down_L1"): 15_523_584,
+    ("c2", "fp64", "trsv_down_L2"): 1_220_352,
     ("c2", "fp64", "trsv_last"): 341_504,
     ("c2", "fp64", "trsv_up_L2"): 462_592,
-    ("c2", "fp64", "trsv_up_L1"): 7_984_128,
-    ("c2", "fp64", "trsv_up_L0"): 76_693_248 + 8_704,
+    ("c2", "fp64", "trsv_up_L1"): 7_985_408,
+    ("c2", "fp64", "trsv_up_L0"): 76_728_576 + 8_704,
 }
 NCU_TRAFFIC_KRYLOV = {
-    ("c2", "mixed", "dgs_fix_adots"): (54_606_336 + 164_096, None),
-    ("c2", "mixed", "dgs_spmv_dots"): (80_556_800 + 2_968_064, None),
-    ("c2", "mixed", "dgs_next"): (56_632_576 + 61_440, None),
+    ("c2", "mixed", "dgs_fix_adots"): (54_605_312 + 107_008, None),
+    ("c2", "mixed", "dgs_spmv_dots"): (80_557_312 + 2_799_616, None),
+    ("c2", "mixed", "dgs_next"): (56_635_136 + 97_280, None),
 }
 NCU_KRYLOV_STEP = 25
 

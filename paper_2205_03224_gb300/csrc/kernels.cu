@@ -233,12 +233,25 @@ k_trsv(const LevelView<VT, WT> lv, const IoT<VT> *__restrict__ in, VT *__restric
                         a0 = xs[row];
                         if (upper) a0 *= vals[(size_t)S * nrow + tt];          // dinv follows vals
                     }
+                    VT a1 = 0;
+                    if constexpr (IsComplex<VT>::value) {
+                        // a complex product is four FP64 FMAs: skip the slots past kq
+                        // (uniform over the chunk)
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) xq[kk] = xs[cq[kk]];
-                    VT a1 = vq[1] * xq[1];
-                    a0 += vq[0] * xq[0];
-                    a1 += vq[3] * xq[3];
-                    a0 += vq[2] * xq[2];
+                        for (int kk = 0; kk < 4; ++kk) xq[kk] = kk < kq ? xs[cq[kk]] : (VT)0;
+                        if (kq > 0) a0 += vq[0] * xq[0];
+                        if (kq > 1) a1 = vq[1] * xq[1];
+                        if (kq > 2) a0 += vq[2] * xq[2];
+                        if (kq > 3) a1 += vq[3] * xq[3];
+                    } else {
+                        // FP64: all four slots, no branches (padded slots add 0 * x_0)
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) xq[kk] = xs[cq[kk]];
+                        a1 = vq[1] * xq[1];
+                        a0 += vq[0] * xq[0];
+                        a1 += vq[3] * xq[3];
+                        a0 += vq[2] * xq[2];
+                    }
                     for (int kk = 4; kk < kq; ++kk) {                          // rows of more than 16 entries
                         const int e = (kk * nrow + tt) * 4 + sub;
                         a0 += vals[e] * xs[cols[e]];
