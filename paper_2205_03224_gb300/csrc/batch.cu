@@ -133,7 +133,7 @@ void build_batch_level(gemslr_batch_ctx *B, int l, bool last, int rows_cta, BLev
         const HostLevel &hl = last ? h.last : h.lev[l];
         const int64_t bs = B->base[s];
         ChunkHost<float> cs;
-        build_chunks<float>(hl.L, hl.U, hl.bp, cs, kBatchChunkRows, 1);
+        build_chunks<float>(hl.L, hl.U, hl.bp, cs, kBatchChunkRows, 1, kStageBytes);
         // append chunk data with offsets shifted
         const int64_t doff = (int64_t)ch.data.size();
         const int64_t coff = (int64_t)ch.off.size() - 1;

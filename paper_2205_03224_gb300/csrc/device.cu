@@ -189,7 +189,7 @@ size_t chunk_bytes(int64_t nrows, int64_t maxlen, bool upper) {
 // Append the chunks of one triangular factor of block [r0, r1) (see kernels.cuh).
 template <typename VT>
 void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, ChunkHost<VT> &out, int &maxwf,
-                          int max_rows) {
+                          int max_rows, int stage_bytes) {
     std::vector<int32_t> lev = upper ? wavefronts_upper(T, r0, r1) : wavefronts_lower(T, r0, r1);
     int nw = 0;
     for (int32_t x : lev) nw = std::max(nw, x + 1);
@@ -211,7 +211,7 @@ void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, Chun
             const int64_t maxlen = nlen[R[start] - r0];
             int64_t n = 0;
             while (start + n < R.size() && n < max_rows &&
-                   chunk_bytes<VT>(n + 1, maxlen, upper) <= (size_t)StageBytesOf<VT>::value)
+                   chunk_bytes<VT>(n + 1, maxlen, upper) <= (size_t)stage_bytes)
                 ++n;
             if (n == 0) fail(GEMSLR_ERR_UNSUPPORTED, "a factor row has too many entries for the staged substitution");
             const size_t bytes = chunk_bytes<VT>(n, maxlen, upper);
@@ -263,29 +263,28 @@ void append_factor_chunks(const Csr &T, int64_t r0, int64_t r1, bool upper, Chun
 
 template <typename VT>
 void build_chunks(const Csr &L, const Csr &U, const std::vector<int64_t> &bp, ChunkHost<VT> &out, int max_rows,
-                  int max_slices) {
+                  int max_slices, int stage_bytes) {
+    if (max_slices < 1 || max_slices > kMaxSlices) fail(GEMSLR_ERR_ARG, "slices per chunk out of range");
     validate_tri(L, bp, false);
     validate_tri(U, bp, true);
     for (size_t b = 0; b + 1 < bp.size(); ++b) {
         const size_t first = out.off.size() - 1;
-        append_factor_chunks<VT>(L, bp[b], bp[b + 1], false, out, out.maxwf_L, max_rows);
-        append_factor_chunks<VT>(U, bp[b], bp[b + 1], true, out, out.maxwf_U, max_rows);
+        append_factor_chunks<VT>(L, bp[b], bp[b + 1], false, out, out.maxwf_L, max_rows, stage_bytes);
+        append_factor_chunks<VT>(U, bp[b], bp[b + 1], true, out, out.maxwf_U, max_rows, stage_bytes);
         if (max_slices >= 2) {
-            // pair consecutive slices into one chunk (<= kStageBytes) by dropping the
-            // boundary between them; the first slice's header says one follows
+            // join up to max_slices consecutive slices into one chunk (<= stage_bytes)
+            // by dropping the boundaries between them; the header of every slice but
+            // the chunk's last says that another one follows
             std::vector<int64_t> keep(out.off.begin(), out.off.begin() + (int64_t)first + 1);
             size_t c = first;
             const size_t last = out.off.size() - 1;
             while (c < last) {
-                const int64_t a0 = out.off[c], a1 = out.off[c + 1];
-                if (c + 1 < last && out.off[c + 2] - a0 <= (int64_t)kStageBytes) {
-                    reinterpret_cast<int32_t *>(out.data.data() + a0)[3] = 1;
-                    keep.push_back(out.off[c + 2]);
-                    c += 2;
-                } else {
-                    keep.push_back(a1);
-                    c += 1;
-                }
+                const int64_t a0 = out.off[c];
+                size_t e = c + 1;                    // slices [c, e) form the chunk
+                while (e < last && (int)(e + 1 - c) <= max_slices && out.off[e + 1] - a0 <= (int64_t)stage_bytes) ++e;
+                for (size_t t = c; t + 1 < e; ++t) reinterpret_cast<int32_t *>(out.data.data() + out.off[t])[3] = 1;
+                keep.push_back(out.off[e]);
+                c = e;
             }
             out.off.swap(keep);
         }
@@ -295,10 +294,11 @@ void build_chunks(const Csr &L, const Csr &U, const std::vector<int64_t> &bp, Ch
 }
 
 
-template void build_chunks<float>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<float> &, int, int);
+template void build_chunks<float>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<float> &, int, int,
+                                  int);
 template void build_chunks<double>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<double> &, int,
-                                   int);
-template void build_chunks<zc>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<zc> &, int, int);
+                                   int, int);
+template void build_chunks<zc>(const Csr &, const Csr &, const std::vector<int64_t> &, ChunkHost<zc> &, int, int, int);
 
 namespace {
 
@@ -315,7 +315,8 @@ void upload_level(const HostLevel &hl, int64_t n, bool schur, Arena &a, DevLevel
     for (size_t b = 0; b + 1 < hl.bp.size(); ++b) maxrows = std::max(maxrows, hl.bp[b + 1] - hl.bp[b]);
     d.smem_rows = (kRingBytes + maxrows * (int64_t)sizeof(VT) <= smem_limit) ? (int)maxrows : 0;
     ChunkHost<VT> ch;
-    build_chunks<VT>(hl.L, hl.U, hl.bp, ch, kChunkRows, LanesPerRow<VT>::value == 1 ? 2 : 1);
+    build_chunks<VT>(hl.L, hl.U, hl.bp, ch, kChunkRows, LanesPerRow<VT>::value == 1 ? kMaxSlices : 1,
+                     StageBytesOf<VT>::value);
     v.C.data = a.upload(ch.data);
     v.C.off = a.upload(ch.off);
     v.C.blk_chunk = a.upload(ch.blk_chunk);

@@ -128,11 +128,11 @@ struct ChunkHost {
 };
 
 // Chunks (layout in kernels.cuh) of the block-diagonal factors L, U of one
-// level: slices of at most max_rows row slots, up to max_slices (1 or 2)
-// consecutive slices per chunk.
+// level: slices of at most max_rows row slots, up to max_slices (1 ..
+// kMaxSlices) consecutive slices per chunk of at most stage_bytes.
 template <typename VT>
 void build_chunks(const Csr &L, const Csr &U, const std::vector<int64_t> &bp, ChunkHost<VT> &out, int max_rows,
-                  int max_slices);
+                  int max_slices, int stage_bytes);
 
 // ---- device memory arena ------------------------------------------------------------
 class Arena {

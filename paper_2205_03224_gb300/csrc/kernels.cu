@@ -187,7 +187,7 @@ k_trsv(const LevelView<VT, WT> lv, const IoT<VT> *__restrict__ in, VT *__restric
     if constexpr (LanesPerRow<VT>::value == 1) {
         // FP32: the consumer warps take the chunks in turn, one lane per row,
         // each loading its next chunk into registers while the others work.
-        consume_chunks_round_robin<VT, NE>(ring, full, empty, abort_flag, c1 - c0, xs, warp, lane);
+        consume_chunks_round_robin<VT, NE, SB>(ring, full, empty, abort_flag, c1 - c0, xs, warp, lane);
     } else {
         bool aborted = false;
         const int r = lane >> 2, sub = lane & 3;

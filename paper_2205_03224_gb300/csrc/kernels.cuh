@@ -18,11 +18,12 @@ constexpr int kMaxCols = 160;     // Krylov columns per Gram-Schmidt pass (m + 1
 // Triangular factors of one level as a sequence of "chunks" per block: the L
 // chunks of a block in wavefront (level-set) order, then its U chunks.  A
 // chunk holds <= kChunkRows independent rows of one wavefront and is one
-// contiguous, 16-byte aligned byte range of <= kStageBytes:
+// contiguous, 16-byte aligned byte range of <= StageBytesOf<VT> bytes:
 //   int32 {nrows, S, upper, more}     S = entry slots per row; more = 1 when
-//                                     a second slice of the same layout follows
-//                                     in the same chunk (FP32: two consecutive
-//                                     wavefront slices per chunk when they fit)
+//                                     another slice of the same layout follows
+//                                     in the same chunk (FP32: up to kMaxSlices
+//                                     consecutive wavefront slices per chunk
+//                                     when they fit)
 //   int32 rows[pad4(nrows)]           block-local row of every slot
 //   int32 lens[pad4(nrows)]           entries of every slot
 //   int32 cols[pad4(S*nrows)]         block-local columns
@@ -36,7 +37,7 @@ constexpr int kMaxCols = 160;     // Krylov columns per Gram-Schmidt pass (m + 1
 // so a warp always reads consecutive addresses.  The chunks of a block move
 // into a shared-memory ring of kRingData bytes CPG at a time: group g (chunks
 // CPG*g onwards, contiguous in global memory) is one bulk copy into ring slot
-// g % (kRingData / (CPG*kStageBytes)), and a chunk is found in its slot by
+// g % (kRingData / (CPG*StageBytesOf<VT>)), and a chunk is found in its slot by
 // skipping the chunks before it (their sizes follow from their headers).
 // The FP32 substitutions move kGroupChunks chunks per copy (one per consumer
 // warp); the FP64 and batched ones, whose warps share every chunk, move one.
@@ -54,6 +55,11 @@ template <> struct LanesPerRow<float> { static constexpr int value = 1; };
 // large, so that a typical wavefront still fits in one chunk (one hand-off).
 template <typename VT> struct StageBytesOf { static constexpr int value = kStageBytes; };
 template <> struct StageBytesOf<zc> { static constexpr int value = 2 * kStageBytes; };
+// FP32 chunks (single system) hold up to kMaxSlices consecutive wavefront
+// slices in 8 KB, so that a consumer warp hands the sweep on once per four
+// wavefronts (a hand-off costs more than a slice solved by the same warp).
+template <> struct StageBytesOf<float> { static constexpr int value = 2 * kStageBytes; };
+constexpr int kMaxSlices = 4;
 
 struct ChunkView {
     const unsigned char *data;

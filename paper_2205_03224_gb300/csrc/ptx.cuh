@@ -201,8 +201,8 @@ __device__ __forceinline__ void produce_chunks(const unsigned char *data, const 
             wait_bounded(&full[g % kGroups], (g / kGroups) & 1, nullptr);
 }
 
-// Bytes of one slice, and of one chunk (a slice and, when its header says
-// so, the slice after it); see kernels.cuh.
+// Bytes of one slice, and of one chunk (a slice and, while their headers say
+// so, the slices after it); see kernels.cuh.
 template <typename VT>
 __device__ __forceinline__ int slice_size(const int *hdr) {
     const int nrow = hdr[0], S = hdr[1], pr = (nrow + 3) & ~3, ne = S * nrow;
@@ -211,8 +211,13 @@ __device__ __forceinline__ int slice_size(const int *hdr) {
 }
 template <typename VT>
 __device__ __forceinline__ int chunk_size(const int *hdr) {
-    const int a = slice_size<VT>(hdr);
-    return hdr[3] ? a + slice_size<VT>(hdr + a / 4) : a;
+    int a = 0;
+    for (int t = 0; t < kMaxSlices; ++t) {
+        const int *h = hdr + a / 4;
+        a += slice_size<VT>(h);
+        if (!h[3]) break;
+    }
+    return a;
 }
 
 // Wait until chunk k (block-relative) is in shared memory and return it: its
@@ -335,42 +340,68 @@ __device__ __forceinline__ void handoff_signal(int next_warp) {
 
 // Lane-per-row substitutions (FP32).  Chunk k belongs to consumer warp
 // k % kConsumerWarps (one chunk of every group).  A warp loads its next
-// chunk (one or two slices: consecutive wavefronts) into registers while the
-// other warps work, then waits for the previous chunk's warp, gathers x,
-// computes its rows (the second slice after a __syncwarp), stores them and
-// hands on; the barrier orders the stores before the next warp's gathers.  Every warp runs the same sequence of waits and
-// signals whatever happens (an expired wait only skips the arithmetic), so
-// the hand-off chain always completes.
-template <typename VT, int NE>
+// chunk (one to kMaxSlices slices: consecutive wavefronts) into registers
+// while the other warps work, then waits for the previous chunk's warp,
+// gathers x, computes its rows (each later slice after a __syncwarp), stores
+// them and hands on; the barrier orders the stores before the next warp's
+// gathers.  Every warp runs the same sequence of waits and signals whatever
+// happens (an expired wait only skips the arithmetic), so the hand-off chain
+// always completes.
+template <typename VT, int NE, int SB>
 __device__ void consume_chunks_round_robin(const unsigned char *ring, uint64_t *full, uint64_t *empty,
                                            volatile int *abort_flag, int nchunk, VT *xs, int warp, int lane) {
     static_assert(kConsumerWarps == kGroupChunks, "one chunk of every group per consumer warp");
+    static_assert(kMaxSlices == 4, "four slice registers");
     constexpr int NW = kConsumerWarps;
     bool ok = true;
     for (int k = warp; k < nchunk; k += NW) {
-        RowRegs<VT, NE> R, R2;
-        const unsigned char *p = ok ? wait_chunk<VT, kGroupChunks>(ring, full, abort_flag, k) : nullptr;
+        RowRegs<VT, NE> R0, R1, R2, R3;
+        const unsigned char *p = ok ? wait_chunk<VT, kGroupChunks, SB>(ring, full, abort_flag, k) : nullptr;
         ok = p != nullptr;
         if (!ok && lane == 0) *abort_flag = 1;
-        bool two = false;
+        int ns = 0;                             // slices of the chunk (uniform over the warp)
         if (ok) {
-            fetch_row<VT, NE>(p, lane, R);
-            two = reinterpret_cast<const int *>(p)[3] != 0;
-            if (two) fetch_row<VT, NE>(p + slice_size<VT>(reinterpret_cast<const int *>(p)), lane, R2);
+            const unsigned char *q = p;
+            fetch_row<VT, NE>(q, lane, R0);
+            ns = 1;
+            if (reinterpret_cast<const int *>(q)[3]) {
+                q += slice_size<VT>(reinterpret_cast<const int *>(q));
+                fetch_row<VT, NE>(q, lane, R1);
+                ns = 2;
+                if (reinterpret_cast<const int *>(q)[3]) {
+                    q += slice_size<VT>(reinterpret_cast<const int *>(q));
+                    fetch_row<VT, NE>(q, lane, R2);
+                    ns = 3;
+                    if (reinterpret_cast<const int *>(q)[3]) {
+                        q += slice_size<VT>(reinterpret_cast<const int *>(q));
+                        fetch_row<VT, NE>(q, lane, R3);
+                        ns = 4;
+                    }
+                }
+            }
         }
         const bool go = ok && !*abort_flag;     // read before the wait, off the critical path
         if (k > 0) handoff_wait(warp);
         if (go) {
-            solve_row<VT, NE>(R, xs, lane);
-            if (two) {
-                __syncwarp();                   // the first slice's rows before the second's gathers
+            // each slice's rows are stored before the next slice's gathers
+            solve_row<VT, NE>(R0, xs, lane);
+            if (ns > 1) {
+                __syncwarp();
+                solve_row<VT, NE>(R1, xs, lane);
+            }
+            if (ns > 2) {
+                __syncwarp();
                 solve_row<VT, NE>(R2, xs, lane);
+            }
+            if (ns > 3) {
+                __syncwarp();
+                solve_row<VT, NE>(R3, xs, lane);
             }
         }
         // bar.arrive orders each lane's own stores before the next warp's gathers
         if (k + 1 < nchunk) handoff_signal((warp + 1) % NW);
         __syncwarp();                           // every lane is done with the staged chunk
-        if (ok && lane == 0) mbar_arrive(&empty[chunk_slot<kGroupChunks>(k)]);
+        if (ok && lane == 0) mbar_arrive(&empty[chunk_slot<kGroupChunks, SB>(k)]);
     }
 }
 
