@@ -51,27 +51,27 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2.07 * 2
 #   M^-1 kernels: (config, precision, kernel) -> DRAM bytes of a launch
 #   Krylov kernels (work grows with the step j): -> (DRAM bytes, algorithmic bytes) of the captured step
 TRAFFIC_SOURCES = ["kernels.cu", "kernels.cuh", "ptx.cuh", "device.cu"]
-NCU_TRAFFIC_DIGEST = "e86613e42846e538"
+NCU_TRAFFIC_DIGEST = "916bf152ac449417"
 NCU_TRAFFIC = {
-    ("c2", "mixed", "trsv_down_L0"): 43_783_424,
-    ("c2", "mixed", "trsv_down_L1"): 6_459_392,
-    ("c2", "mixed", "trsv_down_L2"): 439_552,
-    ("c2", "mixed", "trsv_last"): 146_944,
-    ("c2", "mixed", "trsv_up_L2"): 281_856,
-    ("c2", "mixed", "trsv_up_L1"): 4_819_456,
-    ("c2", "mixed", "trsv_up_L0"): 45_624_320,
-    ("c2", "fp64", "trsv_down_L0"): 73_524_736 + 365_568,
-    ("c2", "fp64", "trsv_down_L1"): 15_523_584,
-    ("c2", "fp64", "trsv_down_L2"): 1_220_352,
-    ("c2", "fp64", "trsv_last"): 341_504,
+    ("c2", "mixed", "trsv_down_L0"): 43_714_560,
+    ("c2", "mixed", "trsv_down_L1"): 6_465_280,
+    ("c2", "mixed", "trsv_down_L2"): 449_536,
+    ("c2", "mixed", "trsv_last"): 158_208,
+    ("c2", "mixed", "trsv_up_L2"): 292_352,
+    ("c2", "mixed", "trsv_up_L1"): 4_825_344,
+    ("c2", "mixed", "trsv_up_L0"): 45_555_200,
+    ("c2", "fp64", "trsv_down_L0"): 73_524_736 + 430_336,
+    ("c2", "fp64", "trsv_down_L1"): 15_524_608,
+    ("c2", "fp64", "trsv_down_L2"): 1_221_376,
+    ("c2", "fp64", "trsv_last"): 341_760,
     ("c2", "fp64", "trsv_up_L2"): 462_592,
-    ("c2", "fp64", "trsv_up_L1"): 7_985_408,
-    ("c2", "fp64", "trsv_up_L0"): 76_728_576 + 8_704,
+    ("c2", "fp64", "trsv_up_L1"): 7_983_360,
+    ("c2", "fp64", "trsv_up_L0"): 76_710_400 + 49_408,
 }
 NCU_TRAFFIC_KRYLOV = {
-    ("c2", "mixed", "dgs_fix_adots"): (54_605_312 + 107_008, None),
-    ("c2", "mixed", "dgs_spmv_dots"): (80_557_312 + 2_799_616, None),
-    ("c2", "mixed", "dgs_next"): (56_635_136 + 97_280, None),
+    ("c2", "mixed", "dgs_fix_adots"): (54_606_080 + 174_080, None),
+    ("c2", "mixed", "dgs_spmv_dots"): (80_565_248 + 2_691_840, None),
+    ("c2", "mixed", "dgs_next"): (56_636_672 + 102_656, None),
 }
 NCU_KRYLOV_STEP = 25
 
