@@ -20,6 +20,10 @@ CASES = {
     # indefinite (shift 0.1 h^-2): the DGKS test skips the second Gram-Schmidt
     # pass at step 7 of the first cycle, every other step takes it
     "indef24": ((24, 24, 24), 0.0, 0.1, 4, 8, "ilut", 1e-3, 10, 8),
+    # the indefinite operators of the 128^3 and 96^3 workloads (shifts -0.05 h^-2
+    # and -0.1 h^-2) at a size the oracle solves in seconds
+    "indef32a": ((32, 32, 32), 0.0, 0.05, 4, 8, "ilut", 1e-3, 10, 32),
+    "indef32b": ((32, 32, 32), 0.0, 0.1, 4, 8, "ilut", 1e-3, 10, 32),
     # a 5-unknown root Schur system: 8 inner GMRES steps end in a happy breakdown
     "tiny2d": ((9, 5), 0.3, 0.0, 2, 2, "ilu0", 0.0, 0, 2),
 }
