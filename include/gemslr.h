@@ -79,13 +79,16 @@ typedef struct {
 /* Precision of the preconditioner application (FGMRES is FP64 in both). */
 enum { GEMSLR_PREC_FP64 = 0, GEMSLR_PREC_MIXED = 1 };
 /* Incomplete factorisation of the diagonal blocks: ILU(0) or ILUT on the host
- * (blocks on a pool of host threads), or ILU(0) on the GPU (level-scheduled,
+ * (blocks on a pool of host threads), ILU(0) on the GPU (level-scheduled,
  * one CTA per block; factors bit-identical to GEMSLR_ILU0; every row of A
- * needs its diagonal entry, else ARG). */
-enum { GEMSLR_ILU0 = 0, GEMSLR_ILUT = 1, GEMSLR_ILU0_DEVICE = 2 };
+ * needs its diagonal entry, else ARG), or ILUT on the GPU (one warp per
+ * block, the block's rows in order since the fill depends on the values;
+ * factors bit-identical to GEMSLR_ILUT; needs 0 <= ilut_lfil <= 64, else
+ * ARG). */
+enum { GEMSLR_ILU0 = 0, GEMSLR_ILUT = 1, GEMSLR_ILU0_DEVICE = 2, GEMSLR_ILUT_DEVICE = 3 };
 
 typedef struct {
-    int32_t ilu_kind;             /* GEMSLR_ILU0 or GEMSLR_ILUT                     */
+    int32_t ilu_kind;             /* GEMSLR_ILU0, _ILUT, _ILU0_DEVICE, _ILUT_DEVICE */
     double ilut_tau;              /* ILUT drop tolerance (relative to ||a_i||_2)    */
     int32_t ilut_lfil;            /* ILUT fill per row in L and in U (<0: no cap)   */
     int32_t rank[GEMSLR_MAX_LEVELS]; /* k_l per Schur level (0 = no correction)     */
@@ -118,8 +121,8 @@ typedef struct {
      * corrections come from the Arnoldi in complex arithmetic (W H W^H, complex
      * Schur form), and the handle is complex: gemslr_zapply and
      * gemslr_zfgmres_solve apply and solve in complex FP64; the real entry
-     * points refuse it (ARG).  A complex handle needs precision FP64,
-     * ilu_kind ILU0 or ILUT and the Arnoldi set-up, else UNSUPPORTED.  0: the
+     * points refuse it (ARG).  A complex handle needs precision FP64, a host
+     * ilu_kind (ILU0 or ILUT) and the Arnoldi set-up, else UNSUPPORTED.  0: the
      * real method (the default). */
     double shift;
 } gemslr_options;

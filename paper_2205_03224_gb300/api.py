@@ -75,7 +75,7 @@ def options(ilu="ilut", tau=1e-3, lfil=10, rank=0, precision="fp64", arnoldi_tol
     shift: complex diagonal shift of the factorisations (0: the real method)."""
     o = L.Options()
     L.load().gemslr_default_options(ctypes.byref(o))
-    o.ilu_kind = {"ilu0": 0, "ilut": 1, "ilu0_device": 2}[ilu]
+    o.ilu_kind = {"ilu0": 0, "ilut": 1, "ilu0_device": 2, "ilut_device": 3}[ilu]
     o.ilut_tau = tau
     o.ilut_lfil = lfil
     ranks = list(rank) if np.ndim(rank) else [int(rank)] * L.MAX_LEVELS

@@ -103,6 +103,11 @@ struct Hierarchy {
 
 // ILU(0) of the diagonal blocks of a level matrix on the current device (ilu_device.cu).
 void factor_level_ilu0_device(const Csr &B, const std::vector<int64_t> &bp, Csr &L, Csr &U, int64_t &clamped);
+// ILUT(tau, lfil) of the diagonal blocks of a level matrix on the current device
+// (one warp per block, rows in order; bit-identical to factor_ilut; 0 <= lfil <= 64).
+// false: a row was too wide for the kernel and nothing was written.
+bool factor_level_ilut_device(const Csr &B, const std::vector<int64_t> &bp, double tau, int lfil, Csr &L, Csr &U,
+                              int64_t &clamped);
 
 // Build the hierarchy without the low-rank terms (permute, slice, factor).
 void build_levels(const Csr &A, const gemslr_partition *part, const gemslr_options *opt,

@@ -368,10 +368,14 @@ std::vector<int32_t> wavefronts_upper(const Csr &U, int64_t r0, int64_t r1) {
 // are appended in block order, so the result does not depend on the threads.
 static void factor_level(const Csr &B, const std::vector<int64_t> &bp, const gemslr_options *opt, double alpha,
                          Csr &L, Csr &U, int64_t &clamped) {
-    if (opt->ilu_kind == GEMSLR_ILU0_DEVICE) {
+    if (opt->ilu_kind == GEMSLR_ILU0_DEVICE || opt->ilu_kind == GEMSLR_ILUT_DEVICE) {
         if (alpha != 0.0) fail(GEMSLR_ERR_UNSUPPORTED, "the complex shift needs a host factorisation (ILU0 or ILUT)");
-        factor_level_ilu0_device(B, bp, L, U, clamped);
-        return;
+        if (opt->ilu_kind == GEMSLR_ILU0_DEVICE) {
+            factor_level_ilu0_device(B, bp, L, U, clamped);
+            return;
+        }
+        // a row too wide for the device kernel: the host ILUT below (same factors)
+        if (factor_level_ilut_device(B, bp, opt->ilut_tau, opt->ilut_lfil, L, U, clamped)) return;
     }
     const int64_t n = B.nrows;
     const size_t nb = bp.size() - 1;
@@ -385,7 +389,8 @@ static void factor_level(const Csr &B, const std::vector<int64_t> &bp, const gem
             try {
                 Csr Bj = submatrix(B, bp[j], bp[j + 1], bp[j], bp[j + 1]);
                 if (alpha != 0.0) Bj = shifted_block(Bj, alpha);
-                if (opt->ilu_kind == GEMSLR_ILU0) cl[j] = factor_ilu0(Bj, Ls[j], Us[j]);
+                if (opt->ilu_kind == GEMSLR_ILU0 || opt->ilu_kind == GEMSLR_ILU0_DEVICE)
+                    cl[j] = factor_ilu0(Bj, Ls[j], Us[j]);
                 else cl[j] = factor_ilut(Bj, opt->ilut_tau, opt->ilut_lfil, Ls[j], Us[j]);
             } catch (...) {
                 err[j] = std::current_exception();

@@ -704,8 +704,11 @@ gemslr_options normalized(const gemslr_options *opt) {
     gemslr_options o;
     gemslr_default_options(&o);
     if (opt) o = *opt;
-    if (o.ilu_kind != GEMSLR_ILU0 && o.ilu_kind != GEMSLR_ILUT && o.ilu_kind != GEMSLR_ILU0_DEVICE)
+    if (o.ilu_kind != GEMSLR_ILU0 && o.ilu_kind != GEMSLR_ILUT && o.ilu_kind != GEMSLR_ILU0_DEVICE &&
+        o.ilu_kind != GEMSLR_ILUT_DEVICE)
         fail(GEMSLR_ERR_ARG, "unknown ilu_kind");
+    if (o.ilu_kind == GEMSLR_ILUT_DEVICE && (o.ilut_lfil < 0 || o.ilut_lfil > 64))
+        fail(GEMSLR_ERR_ARG, "device ILUT needs 0 <= ilut_lfil <= 64");
     if (o.precision != GEMSLR_PREC_FP64 && o.precision != GEMSLR_PREC_MIXED) fail(GEMSLR_ERR_ARG, "unknown precision");
     if (o.ilut_tau < 0) fail(GEMSLR_ERR_ARG, "ilut_tau must be >= 0");
     for (int l = 0; l < GEMSLR_MAX_LEVELS; ++l)
@@ -718,7 +721,7 @@ gemslr_options normalized(const gemslr_options *opt) {
     if (o.lowrank_power < 0 || o.lowrank_power > 16) fail(GEMSLR_ERR_ARG, "lowrank_power must be in 0..16");
     if (!std::isfinite(o.shift)) fail(GEMSLR_ERR_ARG, "shift must be finite");
     if (o.shift != 0.0 && (o.precision != GEMSLR_PREC_FP64 || o.lowrank_method != GEMSLR_LOWRANK_ARNOLDI ||
-                           o.ilu_kind == GEMSLR_ILU0_DEVICE))
+                           o.ilu_kind == GEMSLR_ILU0_DEVICE || o.ilu_kind == GEMSLR_ILUT_DEVICE))
         fail(GEMSLR_ERR_UNSUPPORTED, "the complex shift needs FP64, a host ILU and the Arnoldi set-up");
     return o;
 }

@@ -60,3 +60,59 @@ def test_device_ilu0_mixed_application_equals_host_ilu0(torch_cuda):
     zh = Gemslr(A, part, ilu="ilu0", rank=3, precision="mixed").apply(r)
     zd = Gemslr(A, part, ilu="ilu0_device", rank=3, precision="mixed").apply(r)
     assert torch.equal(zh, zd)
+
+
+# ILUT on the GPU: the block's rows in order (fill depends on the values), one
+# warp per block; the factors must be bit-identical to the host ILUT, whose
+# dual-threshold selection is pinned against a hand-worked case and checked
+# against the oracle's ILUT (test_oracle_ilu, test_gpu_solve).
+ILUT_CASES = [("small3d", 1e-2, 5), ("shifted", 1e-3, 10), ("indef24", 1e-3, 10), ("c2local", 1e-3, 10),
+              ("tinyparts", 1e-2, 2), ("bigblock", 1e-3, 10), ("shifted", 0.0, 0), ("small3d", 0.0, 40)]
+
+
+@pytest.mark.parametrize("name,tau,lfil", ILUT_CASES)
+def test_device_ilut_equals_host_ilut(torch_cuda, name, tau, lfil):
+    from paper_2205_03224_gb300 import Gemslr
+    A, xyz, part = problem(name)
+    Gh = Gemslr(A, part, ilu="ilut", tau=tau, lfil=lfil, rank=0)
+    Gd = Gemslr(A, part, ilu="ilut_device", tau=tau, lfil=lfil, rank=0)
+    fh, fd = Gh.export_factors(), Gd.export_factors()
+    pairs = [(a[k], b[k]) for a, b in zip(fh["levels"], fd["levels"]) for k in ("L", "U")]
+    pairs += [(fh["last"][k], fd["last"][k]) for k in ("L", "U")]
+    for a, b in pairs:
+        assert np.array_equal(a.indptr, b.indptr) and np.array_equal(a.indices, b.indices)
+        assert np.array_equal(a.data, b.data)          # bit-identical
+    assert Gh.stats()["nclamp"] == Gd.stats()["nclamp"]
+
+
+def test_device_ilut_matches_oracle_and_solves(torch_cuda):
+    """The library set-up with the device ILUT: L and U entrywise equal to the
+    oracle's ILUT (1e-12), and FGMRES reaches 1e-8."""
+    torch = torch_cuda
+    from paper_2205_03224_gb300 import Gemslr
+    from tests.helpers import lib_opts
+    A, xyz, part = problem("shifted")
+    M = oracle_hierarchy("shifted")
+    opts = lib_opts("shifted")
+    opts["ilu"] = "ilut_device"
+    G = Gemslr(A, part, **opts)
+    f, ref = G.export_factors(), M.factors()
+    for lf, rf in zip(f["levels"], ref["levels"]):
+        for key in ("L", "U"):
+            assert np.array_equal(lf[key].indices, rf[key].indices)
+            assert np.allclose(lf[key].data, rf[key].data, rtol=1e-12, atol=0.0)
+    b = gi.rhs_uniform(A.n, 2)
+    x, info = G.solve(torch.from_numpy(b).cuda(), restart=30, rtol=1e-8)
+    res = np.linalg.norm(b - A.to_scipy() @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert info[0]["converged"] and res <= 1e-8
+
+
+def test_device_ilut_rejects_unbounded_fill(torch_cuda):
+    from paper_2205_03224_gb300 import Gemslr
+    from paper_2205_03224_gb300._lib import GemslrError
+    A, xyz, part = problem("small3d")
+    for lfil in (-1, 65):
+        with pytest.raises(GemslrError, match="ERR_ARG"):
+            Gemslr(A, part, ilu="ilut_device", tau=1e-3, lfil=lfil, rank=0)
+    with pytest.raises(GemslrError, match="ERR_UNSUPPORTED"):
+        Gemslr(A, part, ilu="ilut_device", tau=1e-3, lfil=10, rank=2, shift=0.05)
