@@ -5,12 +5,15 @@
 // graph with conditional WHILE nodes.  The preconditioner is FP32 (W in BF16
 // with FP32 accumulation); the Krylov vectors, least-squares problems and
 // residuals are FP64.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <exception>
 #include <memory>
+#include <thread>
 
 #include "batch.cuh"
 #include "device.h"
@@ -448,9 +451,37 @@ gemslr_status setup_batch(int32_t nsys, const gemslr_csr *A, const gemslr_partit
         gemslr_default_options(&o);
         if (opt) o = *opt;
         if (o.shift != 0.0) fail(GEMSLR_ERR_UNSUPPORTED, "the batched path is real (no complex shift)");
+        if (fac) {
+            for (int s = 0; s < nsys; ++s) hierarchy_from_factors(&A[s], &part[s], &fac[s], o, B->sys[s]);
+        } else {
+            // the systems' own set-ups (host ILUT, the Arnoldi on the GPU with a host
+            // round trip per step) on a few host threads, so that their round trips
+            // overlap; the first failure in system order is reported
+            int dev = 0;
+            GEMSLR_CUDA(cudaGetDevice(&dev));
+            std::vector<std::exception_ptr> err(nsys);
+            std::atomic<int> next{0};
+            std::atomic<bool> failed{false};
+            auto work = [&] {
+                for (int s; !failed.load() && (s = next.fetch_add(1)) < nsys;) {
+                    try {
+                        GEMSLR_CUDA(cudaSetDevice(dev));
+                        setup_single_host(&A[s], &part[s], opt, B->sys[s]);
+                    } catch (...) {
+                        err[s] = std::current_exception();
+                        failed = true;
+                    }
+                }
+            };
+            const int nt = std::min(nsys, 8);
+            std::vector<std::thread> pool;
+            for (int t = 1; t < nt; ++t) pool.emplace_back(work);
+            work();
+            for (auto &th : pool) th.join();
+            for (auto &e : err)
+                if (e) std::rethrow_exception(e);
+        }
         for (int s = 0; s < nsys; ++s) {
-            if (fac) hierarchy_from_factors(&A[s], &part[s], &fac[s], o, B->sys[s]);
-            else setup_single_host(&A[s], &part[s], opt, B->sys[s]);
             if (B->sys[s].cplx) fail(GEMSLR_ERR_UNSUPPORTED, "the batched path is real (complex factors given)");
             if (s > 0 && B->sys[s].nlev != B->sys[0].nlev) fail(GEMSLR_ERR_PARTITION, "all systems need the same nlev");
             B->base.push_back(B->base.back() + B->sys[s].n);

@@ -408,7 +408,9 @@ void build_lowrank(gemslr_ctx *h, int l, cudaStream_t st) {
 }
 
 void finish_setup(gemslr_ctx *h, bool compute_lowrank) {
-    cudaStream_t st = nullptr;
+    // this host thread's own stream: set-ups of several systems on several
+    // threads (the batched set-up) overlap their per-step host round trips
+    cudaStream_t st = cudaStreamPerThread;
     const int64_t n = h->host.n;
     const Csr &A = h->host.Ahat;
     h->A_rp = h->arena.upload(A.rp);
