@@ -116,3 +116,32 @@ def test_device_ilut_rejects_unbounded_fill(torch_cuda):
             Gemslr(A, part, ilu="ilut_device", tau=1e-3, lfil=lfil, rank=0)
     with pytest.raises(GemslrError, match="ERR_UNSUPPORTED"):
         Gemslr(A, part, ilu="ilut_device", tau=1e-3, lfil=10, rank=2, shift=0.05)
+
+
+def test_device_ilut_falls_back_to_the_host_for_wide_rows(torch_cuda):
+    """A row touching more columns than the device kernel holds (a dense
+    650-row diagonal block) sends its level to the host ILUT: the factors are
+    still those of the host ILUT, and the solve converges."""
+    torch = torch_cuda
+    import scipy.sparse as sp
+    from paper_2205_03224_gb300 import Gemslr
+    n0, n1 = 650, 50
+    n = n0 + n1
+    rng = np.random.default_rng(7)
+    D = rng.uniform(-1.0, 1.0, (n, n))
+    D += np.diag(np.abs(D).sum(axis=1) + 1.0)           # diagonally dominant, dense
+    A = sp.csr_matrix(D)
+    part = dict(perm=np.arange(n, dtype=np.int32), level_ptr=np.array([0, n0, n], dtype=np.int64),
+                nblk=np.array([1, 1], dtype=np.int32), block_ptr=np.array([0, n0, 0, n1], dtype=np.int64))
+    Gh = Gemslr(A, part, ilu="ilut", tau=1e-2, lfil=20, rank=0)
+    Gd = Gemslr(A, part, ilu="ilut_device", tau=1e-2, lfil=20, rank=0)
+    fh, fd = Gh.export_factors(), Gd.export_factors()
+    pairs = [(a[k], b[k]) for a, b in zip(fh["levels"], fd["levels"]) for k in ("L", "U")]
+    pairs += [(fh["last"][k], fd["last"][k]) for k in ("L", "U")]
+    for a, b in pairs:
+        assert np.array_equal(a.indptr, b.indptr) and np.array_equal(a.indices, b.indices)
+        assert np.array_equal(a.data, b.data)
+    b = rng.uniform(-1.0, 1.0, n)
+    x, info = Gd.solve(torch.from_numpy(b).cuda(), restart=30, rtol=1e-8)
+    assert info[0]["converged"]
+    assert np.linalg.norm(b - A @ x.cpu().numpy()) / np.linalg.norm(b) <= 1e-8
