@@ -315,18 +315,10 @@ std::vector<double> imag_part(const std::vector<std::complex<double>> &x) {
     return r;
 }
 
-// splitmix64 uniform doubles in [-1, 1) (the seeded Arnoldi start vector, real).
+// 2u - 1 from splitmix64(seed): the seeded Arnoldi start vector (real).
 std::vector<double> start_vector_z(uint64_t seed, int64_t s) {
-    std::vector<double> v(s);
-    uint64_t state = seed;
-    for (int64_t i = 0; i < s; ++i) {
-        state += 0x9E3779B97F4A7C15ull;
-        uint64_t x = state;
-        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-        x ^= x >> 31;
-        v[i] = 2.0 * ((double)(x >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
-    }
+    std::vector<double> v = splitmix_uniform01(seed, s);
+    for (double &x : v) x = 2.0 * x - 1.0;
     return v;
 }
 

@@ -27,6 +27,10 @@ struct Error {
 };
 [[noreturn]] void fail(gemslr_status st, const std::string &msg);
 
+// u in [0, 1) from splitmix64(seed): the first `count` outputs' top 53 bits
+// (the seeded start vectors and random blocks of the set-up; setup.cpp).
+std::vector<double> splitmix_uniform01(uint64_t seed, int64_t count);
+
 // ---- sparse utilities (setup.cpp) ----------------------------------------
 Csr csr_from_abi(const gemslr_csr *A);
 Csr csr_from_mat(const gemslr_mat &m);

@@ -17,6 +17,20 @@ namespace gemslr {
 
 void fail(gemslr_status st, const std::string &msg) { throw Error{st, msg}; }
 
+std::vector<double> splitmix_uniform01(uint64_t seed, int64_t count) {
+    std::vector<double> v(count);
+    uint64_t state = seed;
+    for (int64_t i = 0; i < count; ++i) {
+        state += 0x9E3779B97F4A7C15ull;
+        uint64_t z = state;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        v[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    }
+    return v;
+}
+
 Csr csr_from_abi(const gemslr_csr *A) {
     if (!A || A->n < 0 || (A->n > 0 && (!A->rowptr || !A->colind || !A->val)))
         fail(GEMSLR_ERR_ARG, "invalid CSR matrix");

@@ -199,18 +199,10 @@ double read_scalar(gemslr_ctx *h, const double *dev, cudaStream_t st) {
     return h->n2_host[0];
 }
 
-// splitmix64 uniform doubles in [-1, 1) (the seeded Arnoldi start vector).
+// 2u - 1 from splitmix64(seed): the seeded Arnoldi start vector.
 std::vector<double> start_vector(uint64_t seed, int64_t s) {
-    std::vector<double> v(s);
-    uint64_t state = seed;
-    for (int64_t i = 0; i < s; ++i) {
-        state += 0x9E3779B97F4A7C15ull;
-        uint64_t z = state;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        z ^= z >> 31;
-        v[i] = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
-    }
+    std::vector<double> v = splitmix_uniform01(seed, s);
+    for (double &x : v) x = 2.0 * x - 1.0;
     return v;
 }
 
@@ -219,7 +211,6 @@ std::vector<double> start_vector(uint64_t seed, int64_t s) {
 // Cycle m = 2k; the wanted subspace is kept on restart; converged when
 // ||beta * Q[m-1, :k]||_2 <= tol * min |theta_i| (every Ritz value to ~two
 // digits, Sec. 5 set-up); s_l <= m: dense G_hat and its full Schur form.
-std::vector<double> splitmix_uniform01(uint64_t seed, int64_t count);
 
 // Randomized block set-up of level l's correction (Sec. 6 future work): an
 // s x b block (b = 2k) of 2u - 1 from splitmix64(1000 + l), column after
@@ -1436,20 +1427,6 @@ void dense_inverse(std::vector<double> &A, int64_t n) {
         }
     }
     A.swap(Inv);
-}
-
-std::vector<double> splitmix_uniform01(uint64_t seed, int64_t count) {
-    std::vector<double> v(count);
-    uint64_t state = seed;
-    for (int64_t i = 0; i < count; ++i) {
-        state += 0x9E3779B97F4A7C15ull;
-        uint64_t z = state;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        z ^= z >> 31;
-        v[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0);
-    }
-    return v;
 }
 
 // Sites of level l*'s tail, neighbour table, weights (seeded He initialisation).
