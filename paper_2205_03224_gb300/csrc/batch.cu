@@ -5,6 +5,7 @@
 // graph with conditional WHILE nodes.  The preconditioner is FP32 (W in BF16
 // with FP32 accumulation); the Krylov vectors, least-squares problems and
 // residuals are FP64.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -188,6 +189,15 @@ void build_batch_level(gemslr_batch_ctx *B, int l, bool last, int rows_cta, BLev
     Arena &a = B->arena;
     BatchLevel &v = out.v;
     v.nblk = (int32_t)blk_r0.size();
+    // CTAs are dispatched in index order and a block's time grows with its
+    // chunk count (one consumer barrier per chunk): the blocks with the most
+    // chunks go first, so that no long block starts in the last wave
+    std::vector<int32_t> order(v.nblk);
+    for (int32_t j = 0; j < v.nblk; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return ch.blk_chunk[x + 1] - ch.blk_chunk[x] > ch.blk_chunk[y + 1] - ch.blk_chunk[y];
+    });
+    v.order = a.upload(order);
     v.blk_r0 = a.upload(blk_r0);
     v.blk_nr = a.upload(blk_nr);
     v.blk_f0 = a.upload(blk_f0);

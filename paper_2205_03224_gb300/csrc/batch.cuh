@@ -21,6 +21,7 @@ constexpr int kBatchThreads = 256;
 // One stage level of the batch: the level-l blocks of every system.
 struct BatchLevel {
     int32_t nblk;
+    const int32_t *order;      // nblk: block of CTA group g (most chunks first)
     const int64_t *blk_r0;     // first batch row of every block
     const int32_t *blk_nr;     // rows of every block
     const int64_t *blk_f0;     // first row of the block in the level's F

@@ -49,7 +49,7 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
     uint64_t *empty = full + kSlots;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + kSlots + 1);
     float *xs_smem = reinterpret_cast<float *>(smem + kRingBytes);
-    const int b = blockIdx.x / kSplit;
+    const int b = lv.order[blockIdx.x / kSplit];
     const int rhs0 = RPC * (blockIdx.x % kSplit);
     const int64_t r0 = lv.blk_r0[b];
     const int nr = lv.blk_nr[b];
