@@ -22,6 +22,10 @@ constexpr int kBatchThreads = 256;
 struct BatchLevel {
     int32_t nblk;
     const int32_t *order;      // nblk: block of CTA group g (most chunks first)
+    const int32_t *blk_sys;    // nblk: system of every block
+    // inside a batched solve: nsys flags, 0 when every pair of the system has
+    // stopped stepping (its CTAs then return at once); nullptr: apply everything
+    const int32_t *live;
     const int64_t *blk_r0;     // first batch row of every block
     const int32_t *blk_nr;     // rows of every block
     const int64_t *blk_f0;     // first row of the block in the level's F
@@ -73,6 +77,7 @@ struct BatchKrylov {
     int32_t *maxit;
     int32_t *active;           // pair not yet converged / failed
     int32_t *run;              // pair still stepping in the current cycle
+    int32_t *sys_run;          // nsys: some pair of the system still stepping
     int32_t *jdone;            // columns of the pair's current cycle
     int32_t *conv, *bad, *its, *restarts;
     double *tol;               // rtol * ||b_p||

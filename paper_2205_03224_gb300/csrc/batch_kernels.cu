@@ -50,6 +50,7 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
     volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + kSlots + 1);
     float *xs_smem = reinterpret_cast<float *>(smem + kRingBytes);
     const int b = lv.order[blockIdx.x / kSplit];
+    if (lv.live && !lv.live[lv.blk_sys[b]]) return;          // the whole CTA
     const int rhs0 = RPC * (blockIdx.x % kSplit);
     const int64_t r0 = lv.blk_r0[b];
     const int nr = lv.blk_nr[b];
@@ -194,6 +195,7 @@ k_bcouple(const BatchLevel lv, const double *__restrict__ in, float *__restrict_
     __shared__ float ts[kBatchMaxRank * R8];
     __shared__ float half2[kBatchMaxRank * R8];
     const int c = blockIdx.x, s = lv.cta_seg[c];
+    if (lv.live && !lv.live[s]) return;                       // every CTA of the system
     const int64_t i0 = lv.cta_i0[c], len = lv.seg_len[s];
     const int rows = (int)min((int64_t)lv.rows_cta, len - i0);
     const int64_t g0 = lv.seg_r0[s] + i0, e0 = lv.seg_e0[s] + i0;
@@ -279,7 +281,7 @@ k_blowrank(const BatchLevel lv, float *__restrict__ work) {
     __shared__ float us[kBatchMaxRank * R8];
     const int c = blockIdx.x, s = lv.cta_seg[c];
     const int k = lv.seg_k[s];
-    if (k == 0) return;
+    if (k == 0 || (lv.live && !lv.live[s])) return;
     const int64_t i0 = lv.cta_i0[c], len = lv.seg_len[s];
     const int rows = (int)min((int64_t)lv.rows_cta, len - i0);
     for (int idx = threadIdx.x; idx < k * R8; idx += blockDim.x) us[idx] = lv.u[(int64_t)s * kBatchMaxRank * R8 + idx];
@@ -426,6 +428,7 @@ k_bgs(int pass, const BatchSegs S, BatchKrylov K, double *__restrict__ V, int64_
     __shared__ double hs[R8][kMaxCols];
     __shared__ double out[(kMaxCols + 1) * R8];
     const int c = blockIdx.x, s = S.cta_sys[c];
+    if (!K.sys_run[s]) return;                                // every CTA of the system
     const int64_t r0 = S.cta_r0[c], r1 = S.cta_r1[c];
     const int j = *K.j, ncols = j + 1;
     if (pass == 2) {
@@ -480,6 +483,7 @@ k_bgs_subnorm(const BatchSegs S, BatchKrylov K, const double *__restrict__ V, in
     __shared__ double hs[R8][kMaxCols];
     __shared__ double out[R8];
     const int c = blockIdx.x, s = S.cta_sys[c];
+    if (!K.sys_run[s]) return;
     const int64_t r0 = S.cta_r0[c], r1 = S.cta_r1[c];
     const int j = *K.j, ncols = j + 1;
     for (int idx = threadIdx.x; idx < R8 * ncols; idx += blockDim.x) {
@@ -523,6 +527,7 @@ k_bgs_final(const BatchSegs S, BatchKrylov K, double *__restrict__ V, int64_t ld
             double *__restrict__ vin) {
     __shared__ double inv[R8];
     const int c = blockIdx.x, s = S.cta_sys[c];
+    if (!K.sys_run[s]) return;
     const int64_t r0 = S.cta_r0[c], r1 = S.cta_r1[c];
     const int j = *K.j;
     if (threadIdx.x < R8) {
@@ -573,6 +578,15 @@ __global__ void k_binit(BatchKrylov K, double rtol, int maxit) {
 }
 
 // Cycle start: g_p = (||r_p||, 0, ...), pairs still active run; V[:,0] = r_p / ||r_p||.
+// sys_run[s] = some pair of system s still steps (one block; K.run final).
+__device__ void sys_flags(const BatchKrylov &K) {
+    for (int s = threadIdx.x; s < K.npair / R8; s += blockDim.x) {
+        int any = 0;
+        for (int r = 0; r < R8; ++r) any |= K.run[s * R8 + r];
+        K.sys_run[s] = any;
+    }
+}
+
 __global__ void k_bcycle_start(BatchKrylov K, cudaGraphConditionalHandle inner, int use_cond) {
     __shared__ int anyrun;
     if (threadIdx.x == 0) anyrun = 0;
@@ -586,6 +600,7 @@ __global__ void k_bcycle_start(BatchKrylov K, cudaGraphConditionalHandle inner, 
         if (K.active[p]) anyrun = 1;
     }
     __syncthreads();
+    sys_flags(K);
     if (threadIdx.x == 0) {
         *K.j = 0;
         K.any[0] = anyrun;
@@ -617,6 +632,7 @@ __global__ void k_bstep_end(BatchKrylov K, cudaGraphConditionalHandle inner, int
     __syncthreads();
     for (int p = threadIdx.x; p < K.npair; p += blockDim.x)
         if (K.run[p]) anyrun = 1;
+    sys_flags(K);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (anyrun) *K.j += 1;

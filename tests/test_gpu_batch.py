@@ -112,6 +112,24 @@ def test_batch_zero_rhs_and_single_system_iterations(torch_cuda, batch):
     assert abs(inf1[0]["iters"] - info[1 * nrhs + 0]["iters"]) <= 2
 
 
+def test_batch_host_loop_equals_graph(torch_cuda, batch, monkeypatch):
+    """GEMSLR_SOLVE_GRAPH=0 drives the same kernels from the host (for
+    profilers): the iterates are bit-identical to the graph's, with restarts."""
+    torch = torch_cuda
+    sy, B = batch
+    nrhs = 4
+    b = torch.from_numpy(_stack(sy, nrhs, 31)).cuda()
+    Xg, ig = B.solve(b, nrhs, restart=1, rtol=1e-8)
+    monkeypatch.setenv("GEMSLR_SOLVE_GRAPH", "0")
+    Xh, ih = B.solve(b, nrhs, restart=1, rtol=1e-8)
+    monkeypatch.delenv("GEMSLR_SOLVE_GRAPH")
+    assert torch.equal(Xg, Xh)
+    assert [(i["iters"], i["restarts"], i["converged"]) for i in ig] == \
+        [(i["iters"], i["restarts"], i["converged"]) for i in ih]
+    summary = [(i["iters"], i["restarts"]) for i in ig]
+    assert max(i["restarts"] for i in ig) >= 1 and all(i["converged"] for i in ig), summary
+
+
 def test_batch_splits_right_hand_sides_of_large_blocks(torch_cuda):
     """Blocks whose vector for 8 right-hand sides does not fit in shared
     memory are handled by several CTAs with fewer right-hand sides each; the
