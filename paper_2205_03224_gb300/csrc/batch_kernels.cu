@@ -323,6 +323,16 @@ k_blowrank(const BatchLevel lv, float *__restrict__ work) {
 }
 
 // ---- Krylov kernels (FP64, per (system, rhs) pair) ---------------------------------
+constexpr int kGsTile = 16;                  // rows of a Gram-Schmidt tile
+constexpr int kGsThreads = kGsTile * R8;     // one thread per tile element
+
+// Dynamic shared memory of a Gram-Schmidt pass for restart length m.
+size_t bgs_smem_bytes(int pass, int m) {
+    const size_t m1 = (size_t)m + 1;
+    (void)pass;
+    return (R8 * m1 + kGsThreads + std::max<size_t>(m1 * R8, kGsThreads)) * sizeof(double);
+}
+
 // y = A x or y = b - A x over the batch (block-diagonal A, batch columns);
 // zcol: copy x into column *j of zcol (leading dimension ld).
 __global__ void __launch_bounds__(256)
@@ -420,67 +430,111 @@ __device__ void bgivens(const BatchKrylov &K, int p, int j) {
 }
 }  // namespace
 
-// Gram-Schmidt pass 1 (pass == 1): h1 = V^T w.  Pass 2: w -= V h1, then
-// h2 = V^T w and ||w||^2; the finisher adds h2, forms beta by Pythagoras and
-// updates the pair's Givens rotations.
-__global__ void __launch_bounds__(256)
-k_bgs(int pass, const BatchSegs S, BatchKrylov K, double *__restrict__ V, int64_t ldv, double *__restrict__ w) {
-    __shared__ double hs[R8][kMaxCols];
-    __shared__ double out[(kMaxCols + 1) * R8];
+// Gram-Schmidt passes over tiles of kGsTile rows x 8 right-hand sides, one
+// element per thread.  Pass 1: h1 = V^T w.  Pass 2: w -= V h1, then h2 = V^T w
+// on the same tile, whose V values the CTA has just read: that second read
+// hits in L1/L2 (the resident tiles of all CTAs take a few tens of MB), so V
+// comes from DRAM once per pass without a shared-memory copy, and the small
+// shared-memory footprint keeps many CTAs resident to hide the latency.  The
+// dot products go to (column, rhs) pairs, split over row classes while there
+// are fewer pairs than threads; every item adds its tile sums in shared
+// memory.  The finisher of pass 1 stores h1; that of pass 2 adds h2 to the
+// Hessenberg column and keeps h2 for the subtraction that follows.
+template <int PASS>
+__global__ void __launch_bounds__(kGsThreads)
+k_bgs(const BatchSegs S, BatchKrylov K, const double *__restrict__ V, int64_t ldv, double *__restrict__ w) {
+    extern __shared__ __align__(16) double gsm[];
+    const int m1 = K.m + 1;
+    double *hs = gsm;                           // R8 x m1: h1 of every rhs (pass 2)
+    double *xs = hs + R8 * m1;                  // the tile of w
+    double *acc = xs + kGsThreads;              // max(m1 * R8, kGsThreads) items
     const int c = blockIdx.x, s = S.cta_sys[c];
-    if (!K.sys_run[s]) return;                                // every CTA of the system
+    if (!K.sys_run[s]) return;                  // every CTA of the system
     const int64_t r0 = S.cta_r0[c], r1 = S.cta_r1[c];
     const int j = *K.j, ncols = j + 1;
-    if (pass == 2) {
-        for (int idx = threadIdx.x; idx < R8 * ncols; idx += blockDim.x) {
+    const int t = threadIdx.x;
+    const int npairs = ncols * R8;
+    const int rs = npairs >= kGsThreads ? 1 : kGsThreads / npairs;   // row classes per pair
+    const int items = npairs * rs;
+    for (int q = t; q < items; q += kGsThreads) acc[q] = 0.0;
+    if (PASS == 2)
+        for (int idx = t; idx < R8 * ncols; idx += kGsThreads) {
             const int rr = idx / ncols, cc = idx % ncols;
-            hs[rr][cc] = K.hbuf[(int64_t)(s * R8 + rr) * kMaxCols + cc];
+            hs[rr * m1 + cc] = K.hbuf[(int64_t)(s * R8 + rr) * kMaxCols + cc];
+        }
+    for (int64_t g0 = r0; g0 < r1; g0 += kGsTile) {
+        const int nrow = (int)min((int64_t)kGsTile, r1 - g0);
+        __syncthreads();                        // the previous tile's readers are done
+        const int64_t idx = g0 * R8 + t;
+        if (t < nrow * R8) {
+            if (PASS == 1) {
+                xs[t] = w[idx];
+            } else {
+                const double *h = hs + (t & 7) * m1;
+                double x0 = w[idx], x1 = 0.0;
+                int cc = 0;
+                for (; cc + 1 < ncols; cc += 2) {
+                    x0 -= V[(int64_t)cc * ldv + idx] * h[cc];
+                    x1 -= V[(int64_t)(cc + 1) * ldv + idx] * h[cc + 1];
+                }
+                if (cc < ncols) x0 -= V[(int64_t)cc * ldv + idx] * h[cc];
+                const double x = x0 + x1;
+                w[idx] = x;
+                xs[t] = x;
+            }
         }
         __syncthreads();
-        for (int64_t idx = r0 * R8 + threadIdx.x; idx < r1 * R8; idx += blockDim.x) {
-            const int rr = (int)(idx % R8);
-            double x = w[idx];
-            for (int cc = 0; cc < ncols; ++cc) x -= V[(int64_t)cc * ldv + idx] * hs[rr][cc];
-            w[idx] = x;
+        for (int q = t; q < items; q += kGsThreads) {
+            const int pr = q % npairs, part = q / npairs;
+            const int rr = pr & 7;
+            const double *vp = V + (int64_t)(pr >> 3) * ldv + g0 * R8 + rr;
+            double a0 = 0.0, a1 = 0.0;
+            int i = part;
+#pragma unroll 4
+            for (; i + rs < nrow; i += 2 * rs) {
+                a0 += vp[(int64_t)i * R8] * xs[i * R8 + rr];
+                a1 += vp[(int64_t)(i + rs) * R8] * xs[(i + rs) * R8 + rr];
+            }
+            if (i < nrow) a0 += vp[(int64_t)i * R8] * xs[i * R8 + rr];
+            acc[q] += a0 + a1;
         }
-        __syncthreads();
     }
-    bdots_block(V, ldv, ncols, pass == 2, w, r0, r1, K.partial + (int64_t)c * (kMaxCols + 1) * R8);
+    __syncthreads();
+    double *part_out = K.partial + (int64_t)c * (kMaxCols + 1) * R8;
+    for (int pr = t; pr < npairs; pr += kGsThreads) {
+        double sum = 0.0;
+        for (int p2 = 0; p2 < rs; ++p2) sum += acc[pr + p2 * npairs];
+        part_out[pr] = sum;
+    }
     const int ca = S.sys_cta0[s], cb = S.sys_cta0[s + 1];
     if (!last_of(&S.sys_counter[s], (unsigned)(cb - ca))) return;
-    const int ntot = ncols + (pass == 2 ? 1 : 0);
-    bdots_finish(K.partial, ca, cb, ntot, out);
-    if (threadIdx.x < R8) {
-        const int rr = threadIdx.x, p = s * R8 + rr;
-        const int m1 = K.m + 1;
+    double *out = acc;                          // ncols x R8 sums of the system
+    bdots_finish(K.partial, ca, cb, ncols, out);
+    if (t < R8) {
+        const int p = s * R8 + t;
         double *hcol = K.H + (int64_t)p * m1 * K.m + (int64_t)j * m1;
         if (K.run[p]) {
-            if (pass == 1) {
-                for (int cc = 0; cc < ncols; ++cc) {
-                    hcol[cc] = out[cc * R8 + rr];
-                    K.hbuf[(int64_t)p * kMaxCols + cc] = out[cc * R8 + rr];
-                }
-            } else {
-                for (int cc = 0; cc < ncols; ++cc) {
-                    const double h2 = out[cc * R8 + rr];
-                    hcol[cc] += h2;
-                    K.hbuf[(int64_t)p * kMaxCols + cc] = h2;
-                }
+            for (int cc = 0; cc < ncols; ++cc) {
+                const double h = out[cc * R8 + t];
+                if (PASS == 1) hcol[cc] = h;
+                else hcol[cc] += h;
+                K.hbuf[(int64_t)p * kMaxCols + cc] = h;
             }
-        } else if (pass == 2) {
+        } else if (PASS == 2) {
             for (int cc = 0; cc < ncols; ++cc) K.hbuf[(int64_t)p * kMaxCols + cc] = 0.0;
             K.beta[p] = 0.0;
         }
     }
-    if (threadIdx.x == 0) S.sys_counter[s] = 0u;
+    if (t == 0) S.sys_counter[s] = 0u;
 }
 
-// w -= V h2 and an explicit ||w_p||^2 per pair (Pythagoras would lose all
-// accuracy to cancellation after the second pass); the per-system finisher
-// sets beta_p and the pair's Givens update.
+// w -= V h2 with ||w_p||^2 summed on the way (an explicit norm: Pythagoras
+// would lose all accuracy to cancellation after the second pass); the
+// per-system finisher sets beta_p and the pair's Givens update.
 __global__ void __launch_bounds__(256)
 k_bgs_subnorm(const BatchSegs S, BatchKrylov K, const double *__restrict__ V, int64_t ldv, double *__restrict__ w) {
     __shared__ double hs[R8][kMaxCols];
+    __shared__ double red[8][R8];
     __shared__ double out[R8];
     const int c = blockIdx.x, s = S.cta_sys[c];
     if (!K.sys_run[s]) return;
@@ -491,14 +545,30 @@ k_bgs_subnorm(const BatchSegs S, BatchKrylov K, const double *__restrict__ V, in
         hs[rr][cc] = K.hbuf[(int64_t)(s * R8 + rr) * kMaxCols + cc];
     }
     __syncthreads();
+    const int rr = threadIdx.x & 7;             // r0 * 8 and the stride are multiples of 8
+    double sq = 0.0;
     for (int64_t idx = r0 * R8 + threadIdx.x; idx < r1 * R8; idx += blockDim.x) {
-        const int rr = (int)(idx % R8);
-        double x = w[idx];
-        for (int cc = 0; cc < ncols; ++cc) x -= V[(int64_t)cc * ldv + idx] * hs[rr][cc];
+        double x0 = w[idx], x1 = 0.0;
+        int cc = 0;
+        for (; cc + 1 < ncols; cc += 2) {
+            x0 -= V[(int64_t)cc * ldv + idx] * hs[rr][cc];
+            x1 -= V[(int64_t)(cc + 1) * ldv + idx] * hs[rr][cc + 1];
+        }
+        if (cc < ncols) x0 -= V[(int64_t)cc * ldv + idx] * hs[rr][cc];
+        const double x = x0 + x1;
         w[idx] = x;
+        sq += x * x;
     }
+    sq += __shfl_xor_sync(0xffffffffu, sq, 8);
+    sq += __shfl_xor_sync(0xffffffffu, sq, 16);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane < R8) red[warp][lane] = sq;
     __syncthreads();
-    bdots_block(nullptr, 0, 0, true, w, r0, r1, K.partial + (int64_t)c * (kMaxCols + 1) * R8);
+    if (threadIdx.x < R8) {
+        double sum = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) sum += red[q][threadIdx.x];
+        K.partial[(int64_t)c * (kMaxCols + 1) * R8 + threadIdx.x] = sum;
+    }
     const int ca = S.sys_cta0[s], cb = S.sys_cta0[s + 1];
     if (!last_of(&S.sys_counter[s], (unsigned)(cb - ca))) return;
     bdots_finish(K.partial, ca, cb, 1, out);
@@ -796,7 +866,17 @@ void launch_bspmv(int64_t nrows, const int64_t *rp, const int32_t *ci, const dou
 }
 void launch_bgs(int pass, const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, double *w,
                 cudaStream_t st) {
-    k_bgs<<<S.ncta, 256, 0, st>>>(pass, S, K, V, ldv, w);
+    static bool attr = false;                   // once: room for the longest restart
+    if (!attr) {
+        GEMSLR_CUDA(cudaFuncSetAttribute(k_bgs<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bgs_smem_bytes(1, kMaxCols - 1)));
+        GEMSLR_CUDA(cudaFuncSetAttribute(k_bgs<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bgs_smem_bytes(2, kMaxCols - 1)));
+        attr = true;
+    }
+    const size_t smem = bgs_smem_bytes(pass, K.m);
+    if (pass == 1) k_bgs<1><<<S.ncta, kGsThreads, smem, st>>>(S, K, V, ldv, w);
+    else k_bgs<2><<<S.ncta, kGsThreads, smem, st>>>(S, K, V, ldv, w);
     count_launch();
 }
 void launch_bgs_subnorm(const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, double *w,
