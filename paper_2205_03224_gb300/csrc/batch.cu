@@ -26,7 +26,8 @@ void set_btrsv_smem_limit(int bytes);
 void launch_bcouple(const BatchLevel &lv, const double *in, float *work, cudaStream_t st);
 void launch_blowrank(const BatchLevel &lv, float *work, cudaStream_t st);
 void launch_bspmv(int64_t nrows, const int64_t *rp, const int32_t *ci, const double *v, const double *x,
-                  const double *b, double *y, double *zcol, const int32_t *jp, int64_t ld, cudaStream_t st);
+                  const double *b, double *y, double *zcol, const int32_t *jp, int64_t ld, cudaStream_t st,
+                  const int32_t *sys_of = nullptr, const int32_t *live = nullptr);
 void launch_bgs(int pass, const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, double *w,
                 cudaStream_t st);
 void launch_bgs_subnorm(const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, double *w,
@@ -358,7 +359,8 @@ void ensure_batch_krylov(gemslr_batch_ctx *B, int m) {
 void batch_step(gemslr_batch_ctx *B, cudaStream_t st, cudaGraphConditionalHandle h, int use_cond) {
     const int64_t L = B->N * kBatchRhs;
     batch_apply_layout(B, B->vin, B->zout, st, B->K.sys_run);
-    launch_bspmv(B->N, B->A_rp, B->A_ci, B->A_v, B->zout, nullptr, B->w, B->Z, B->K.j, L, st);
+    launch_bspmv(B->N, B->A_rp, B->A_ci, B->A_v, B->zout, nullptr, B->w, B->Z, B->K.j, L, st, B->sys_of,
+                 B->K.sys_run);
     launch_bgs(1, B->S, B->K, B->V, L, B->w, st);
     launch_bgs(2, B->S, B->K, B->V, L, B->w, st);
     launch_bgs_subnorm(B->S, B->K, B->V, L, B->w, st);

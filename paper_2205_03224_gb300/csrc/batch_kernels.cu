@@ -338,10 +338,12 @@ size_t bgs_smem_bytes(int pass, int m) {
 __global__ void __launch_bounds__(256)
 k_bspmv(int64_t nrows, const int64_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ v,
         const double *__restrict__ x, const double *__restrict__ b, double *__restrict__ y, double *__restrict__ zcol,
-        const int32_t *__restrict__ jp, int64_t ld) {
+        const int32_t *__restrict__ jp, int64_t ld, const int32_t *__restrict__ sys_of,
+        const int32_t *__restrict__ live) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= nrows * R8) return;
     const int64_t g = idx / R8;
+    if (live && !live[sys_of[g]]) return;      // every pair of the system has stopped
     const int r = (int)(idx % R8);
     double acc = 0.0;
     for (int64_t p = rp[g]; p < rp[g + 1]; ++p) acc += v[p] * x[(int64_t)ci[p] * R8 + r];
@@ -858,10 +860,11 @@ void launch_blowrank(const BatchLevel &lv, float *work, cudaStream_t st) {
     count_launch();
 }
 void launch_bspmv(int64_t nrows, const int64_t *rp, const int32_t *ci, const double *v, const double *x,
-                  const double *b, double *y, double *zcol, const int32_t *jp, int64_t ld, cudaStream_t st) {
+                  const double *b, double *y, double *zcol, const int32_t *jp, int64_t ld, cudaStream_t st,
+                  const int32_t *sys_of, const int32_t *live) {
     const int64_t n = nrows * R8;
     if (n == 0) return;
-    k_bspmv<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nrows, rp, ci, v, x, b, y, zcol, jp, ld);
+    k_bspmv<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nrows, rp, ci, v, x, b, y, zcol, jp, ld, sys_of, live);
     count_launch();
 }
 void launch_bgs(int pass, const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, double *w,
