@@ -599,6 +599,14 @@ def batch_measure(steps, warmup):
     total_ms = sum(ms)
     st = B.stats()
     B.close()
+    # bytes one level-0 sweep must move (8 rhs); each sweep is a solve with L
+    # and then U: down: the chunks, the FP64 right-hand side in, the FP32 z1
+    # out; up: the chunks, F (values, columns, row offsets), the tail rows F
+    # reads, z1 in and the FP64 result out
+    rows0, tail = st["lev0_rows"], int(sum(A.n for A in As)) - st["lev0_rows"]
+    lu = st["lev0_l_bytes"] + st["lev0_u_bytes"]
+    level0 = {"rows": rows0, "chunk_bytes": lu, "down_bytes": lu + rows0 * (64 + 32),
+              "up_bytes": lu + st["lev0_f_nnz"] * 8 + rows0 * 8 + tail * 32 + rows0 * (32 + 64)}
     return {
         "workload": f"{len(As)} 3-D conv-diff systems, sides U[16,48], beta U[0,0.5], {nrhs} rhs each, "
                     f"{c['nlev']} levels x {c['p']} subdomains, ILUT(1e-3,10), rank {c['rank']}, "
@@ -611,7 +619,7 @@ def batch_measure(steps, warmup):
         "batched_applies_per_s": 1e3 / apply_ms, "rhs_applies_per_s": npairs * 1e3 / apply_ms,
         "setup_s": setup_s, "autotune": {"rows_couple": st["rows_couple"], "rows_krylov": st["rows_krylov"],
                                          "tune_ms": st["tune_ms"]},
-        "gpu_launches": int(launches), "clocks": clk,
+        "level0_sweep_bytes": level0, "gpu_launches": int(launches), "clocks": clk,
     }
 
 

@@ -371,7 +371,10 @@ void gemslr_destroy(gemslr_handle h);
  * right-hand sides a substitution CTA handles (8, 4, 2 or 1: a level whose
  * largest block's vector for 8 right-hand sides does not fit in shared memory
  * splits them over several CTAs; 0: a block too large even for 1 keeps its
- * vector in global memory).
+ * vector in global memory); with nout > 12, out[9..12] = the first level's
+ * block rows (all systems), bytes of its stored L chunks and of its U chunks,
+ * and the nonzeros of its F (what one down and one up sweep of that level
+ * must read).
  */
 #define GEMSLR_BATCH_RHS 8
 typedef struct gemslr_batch_ctx *gemslr_batch;

@@ -425,8 +425,9 @@ class GemslrBatch:
         return x, infos
 
     def stats(self):
-        out = np.zeros(9)
-        L.check(self._lib.gemslr_batch_stats(self._h, L.ptr(out), 9), batch=True)
+        out = np.zeros(13)
+        L.check(self._lib.gemslr_batch_stats(self._h, L.ptr(out), 13), batch=True)
         return dict(nsys=int(out[0]), rows=int(out[1]), nnz_factors=int(out[2]), bytes_per_apply=float(out[3]),
                     setup_ms=float(out[4]), tune_ms=float(out[5]), rows_couple=int(out[6]), rows_krylov=int(out[7]),
-                    rhs_per_cta=int(out[8]))
+                    rhs_per_cta=int(out[8]), lev0_rows=int(out[9]), lev0_l_bytes=int(out[10]),
+                    lev0_u_bytes=int(out[11]), lev0_f_nnz=int(out[12]))

@@ -56,6 +56,9 @@ struct BLevelHost {          // device level plus what the launcher needs
     BatchLevel v{};
     int rpc = 0;              // right-hand sides per substitution CTA (0: vector in global memory)
     size_t smem_bytes = 0;
+    int64_t rows = 0;         // rows of the level's blocks, all systems
+    int64_t l_bytes = 0, u_bytes = 0;   // stored L and U chunks
+    int64_t f_nnz = 0;        // nonzeros of F
 };
 
 struct gemslr_batch_ctx {
@@ -187,6 +190,14 @@ void build_batch_level(gemslr_batch_ctx *B, int l, bool last, int rows_cta, BLev
         }
         frows += hl.e - hl.s;
     }
+    out.rows = out.l_bytes = out.u_bytes = 0;    // the level may be rebuilt (autotuning)
+    for (size_t c = 0; c + 1 < ch.off.size(); ++c) {
+        int32_t upper = 0;
+        std::memcpy(&upper, ch.data.data() + ch.off[c] + 8, 4);
+        (upper ? out.u_bytes : out.l_bytes) += ch.off[c + 1] - ch.off[c];
+    }
+    for (int32_t nr : blk_nr) out.rows += nr;
+    out.f_nnz = (int64_t)F_ci.size();
     if (ch.data.empty()) ch.data.resize(16, 0);
     Arena &a = B->arena;
     BatchLevel &v = out.v;
@@ -202,6 +213,7 @@ void build_batch_level(gemslr_batch_ctx *B, int l, bool last, int rows_cta, BLev
     v.order = a.upload(order);
     v.blk_sys = a.upload(blk_sys);
     v.live = nullptr;
+    v.final_up = (!last && l == 0) ? 1 : 0;
     v.blk_r0 = a.upload(blk_r0);
     v.blk_nr = a.upload(blk_nr);
     v.blk_f0 = a.upload(blk_f0);
@@ -743,6 +755,13 @@ gemslr_status gemslr_batch_stats(gemslr_batch B, double *out, int32_t nout) {
             int rpc = kBatchRhs;
             for (auto &l : B->lev) rpc = std::min(rpc, l.rpc);
             out[8] = rpc;
+        }
+        if (nout > 12 && !B->lev.empty()) {   // the first level's sweeps
+            const BLevelHost &l0 = B->lev[0];
+            out[9] = (double)l0.rows;
+            out[10] = (double)l0.l_bytes;
+            out[11] = (double)l0.u_bytes;
+            out[12] = (double)l0.f_nnz;
         }
     });
 }

@@ -26,6 +26,7 @@ struct BatchLevel {
     // inside a batched solve: nsys flags, 0 when every pair of the system has
     // stopped stepping (its CTAs then return at once); nullptr: apply everything
     const int32_t *live;
+    int32_t final_up;          // the first level: its up sweep's result goes to out only
     const int64_t *blk_r0;     // first batch row of every block
     const int32_t *blk_nr;     // rows of every block
     const int64_t *blk_f0;     // first row of the block in the level's F

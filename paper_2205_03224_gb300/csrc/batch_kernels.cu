@@ -138,7 +138,10 @@ k_btrsv(const BatchLevel lv, const double *__restrict__ in, float *__restrict__ 
         const int64_t g = (int64_t)(idx / RPC) * R8 + rhs0 + idx % RPC;
         float y = xs[idx];
         if (MODE == 1) y = mine[g] - y;
-        if (SMEM || MODE == 1) mine[g] = y;
+        // down: z1 (in place already without SMEM); up: the lower levels' up
+        // sweeps gather this level's result from work, nothing reads the first level's
+        const bool keep = MODE == 0 ? SMEM : !(lv.final_up && out_final);
+        if (keep) mine[g] = y;
         if (out_final) out_final[r0 * R8 + g] = (double)y;
     }
 }

@@ -90,6 +90,8 @@ def test_batch_fgmres_converges_every_pair(torch_cuda, batch, nrhs):
         off += n * nrhs
     st = B.stats()
     assert st["nsys"] == len(sy) and st["rows_couple"] in (64, 128, 256)
+    rows0 = sum(int(p["level_ptr"][1]) for _, p in sy)          # the first level of every system
+    assert st["lev0_rows"] == rows0 and st["lev0_l_bytes"] > 0 and st["lev0_u_bytes"] > 0
 
 
 def test_batch_zero_rhs_and_single_system_iterations(torch_cuda, batch):
