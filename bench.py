@@ -565,6 +565,7 @@ def batch_measure(steps, warmup):
     torch.cuda.synchronize()
     l0 = _lib.kernel_launches()
     ms = []
+    torch.cuda.nvtx.range_push("timed")
     for _ in range(steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -573,6 +574,7 @@ def batch_measure(steps, warmup):
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     launches = _lib.kernel_launches() - l0
     clk = clocks.stop()

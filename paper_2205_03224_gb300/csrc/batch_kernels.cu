@@ -326,15 +326,6 @@ k_blowrank(const BatchLevel lv, float *__restrict__ work) {
 }
 
 // ---- Krylov kernels (FP64, per (system, rhs) pair) ---------------------------------
-constexpr int kGsTile = 16;                  // rows of a Gram-Schmidt tile
-constexpr int kGsThreads = kGsTile * R8;     // one thread per tile element
-
-// Dynamic shared memory of a Gram-Schmidt pass for restart length m.
-size_t bgs_smem_bytes(int pass, int m) {
-    const size_t m1 = (size_t)m + 1;
-    (void)pass;
-    return (R8 * m1 + kGsThreads + std::max<size_t>(m1 * R8, kGsThreads)) * sizeof(double);
-}
 
 // y = A x or y = b - A x over the batch (block-diagonal A, batch columns);
 // zcol: copy x into column *j of zcol (leading dimension ld).
@@ -435,78 +426,44 @@ __device__ void bgivens(const BatchKrylov &K, int p, int j) {
 }
 }  // namespace
 
-// Gram-Schmidt passes over tiles of kGsTile rows x 8 right-hand sides, one
-// element per thread.  Pass 1: h1 = V^T w.  Pass 2: w -= V h1, then h2 = V^T w
-// on the same tile, whose V values the CTA has just read: that second read
-// hits in L1/L2 (the resident tiles of all CTAs take a few tens of MB), so V
-// comes from DRAM once per pass without a shared-memory copy, and the small
-// shared-memory footprint keeps many CTAs resident to hide the latency.  The
-// dot products go to (column, rhs) pairs, split over row classes while there
-// are fewer pairs than threads; every item adds its tile sums in shared
-// memory.  The finisher of pass 1 stores h1; that of pass 2 adds h2 to the
-// Hessenberg column and keeps h2 for the subtraction that follows.
+// The dot products of a Gram-Schmidt pass, h = V^T w: one thread per (column,
+// rhs, row class) item streams over all rows of the CTA with register
+// accumulators (the items of a row share its w through L1), so that no
+// barrier interrupts the loads; the CTA's item sums go to its partials, and
+// the system's last CTA finishes the pass.  Pass 1 stores h1; pass 2 (after
+// w -= V h1 by k_bgs_sub) adds h2 to the Hessenberg column.  Every pass keeps
+// its coefficients in hbuf for the subtraction that follows it.
+constexpr int kGs1Threads = 512;
+
 template <int PASS>
-__global__ void __launch_bounds__(kGsThreads)
-k_bgs(const BatchSegs S, BatchKrylov K, const double *__restrict__ V, int64_t ldv, double *__restrict__ w) {
-    extern __shared__ __align__(16) double gsm[];
-    const int m1 = K.m + 1;
-    double *hs = gsm;                           // R8 x m1: h1 of every rhs (pass 2)
-    double *xs = hs + R8 * m1;                  // the tile of w
-    double *acc = xs + kGsThreads;              // max(m1 * R8, kGsThreads) items
+__global__ void __launch_bounds__(kGs1Threads)
+k_bgs_dots(const BatchSegs S, BatchKrylov K, const double *__restrict__ V, int64_t ldv,
+           const double *__restrict__ w) {
+    extern __shared__ __align__(16) double acc[];   // max(8 (m + 1), kGs1Threads) item sums
     const int c = blockIdx.x, s = S.cta_sys[c];
     if (!K.sys_run[s]) return;                  // every CTA of the system
     const int64_t r0 = S.cta_r0[c], r1 = S.cta_r1[c];
     const int j = *K.j, ncols = j + 1;
     const int t = threadIdx.x;
     const int npairs = ncols * R8;
-    const int rs = npairs >= kGsThreads ? 1 : kGsThreads / npairs;   // row classes per pair
+    const int rs = npairs >= kGs1Threads ? 1 : kGs1Threads / npairs;   // row classes per pair
     const int items = npairs * rs;
-    for (int q = t; q < items; q += kGsThreads) acc[q] = 0.0;
-    if (PASS == 2)
-        for (int idx = t; idx < R8 * ncols; idx += kGsThreads) {
-            const int rr = idx / ncols, cc = idx % ncols;
-            hs[rr * m1 + cc] = K.hbuf[(int64_t)(s * R8 + rr) * kMaxCols + cc];
+    for (int q = t; q < items; q += kGs1Threads) {
+        const int pr = q % npairs, part = q / npairs, rr = pr & 7;
+        const double *vp = V + (int64_t)(pr >> 3) * ldv + rr;
+        const double *wp = w + rr;
+        double a0 = 0.0, a1 = 0.0;
+        int64_t g = r0 + part;
+        for (; g + rs < r1; g += 2 * rs) {
+            a0 += vp[g * R8] * wp[g * R8];
+            a1 += vp[(g + rs) * R8] * wp[(g + rs) * R8];
         }
-    for (int64_t g0 = r0; g0 < r1; g0 += kGsTile) {
-        const int nrow = (int)min((int64_t)kGsTile, r1 - g0);
-        __syncthreads();                        // the previous tile's readers are done
-        const int64_t idx = g0 * R8 + t;
-        if (t < nrow * R8) {
-            if (PASS == 1) {
-                xs[t] = w[idx];
-            } else {
-                const double *h = hs + (t & 7) * m1;
-                double x0 = w[idx], x1 = 0.0;
-                int cc = 0;
-                for (; cc + 1 < ncols; cc += 2) {
-                    x0 -= V[(int64_t)cc * ldv + idx] * h[cc];
-                    x1 -= V[(int64_t)(cc + 1) * ldv + idx] * h[cc + 1];
-                }
-                if (cc < ncols) x0 -= V[(int64_t)cc * ldv + idx] * h[cc];
-                const double x = x0 + x1;
-                w[idx] = x;
-                xs[t] = x;
-            }
-        }
-        __syncthreads();
-        for (int q = t; q < items; q += kGsThreads) {
-            const int pr = q % npairs, part = q / npairs;
-            const int rr = pr & 7;
-            const double *vp = V + (int64_t)(pr >> 3) * ldv + g0 * R8 + rr;
-            double a0 = 0.0, a1 = 0.0;
-            int i = part;
-#pragma unroll 4
-            for (; i + rs < nrow; i += 2 * rs) {
-                a0 += vp[(int64_t)i * R8] * xs[i * R8 + rr];
-                a1 += vp[(int64_t)(i + rs) * R8] * xs[(i + rs) * R8 + rr];
-            }
-            if (i < nrow) a0 += vp[(int64_t)i * R8] * xs[i * R8 + rr];
-            acc[q] += a0 + a1;
-        }
+        if (g < r1) a0 += vp[g * R8] * wp[g * R8];
+        acc[q] = a0 + a1;
     }
     __syncthreads();
     double *part_out = K.partial + (int64_t)c * (kMaxCols + 1) * R8;
-    for (int pr = t; pr < npairs; pr += kGsThreads) {
+    for (int pr = t; pr < npairs; pr += kGs1Threads) {
         double sum = 0.0;
         for (int p2 = 0; p2 < rs; ++p2) sum += acc[pr + p2 * npairs];
         part_out[pr] = sum;
@@ -516,7 +473,7 @@ k_bgs(const BatchSegs S, BatchKrylov K, const double *__restrict__ V, int64_t ld
     double *out = acc;                          // ncols x R8 sums of the system
     bdots_finish(K.partial, ca, cb, ncols, out);
     if (t < R8) {
-        const int p = s * R8 + t;
+        const int p = s * R8 + t, m1 = K.m + 1;
         double *hcol = K.H + (int64_t)p * m1 * K.m + (int64_t)j * m1;
         if (K.run[p]) {
             for (int cc = 0; cc < ncols; ++cc) {
@@ -533,12 +490,38 @@ k_bgs(const BatchSegs S, BatchKrylov K, const double *__restrict__ V, int64_t ld
     if (t == 0) S.sys_counter[s] = 0u;
 }
 
+// w -= V h (h = the coefficients of the pass before, kept per pair in hbuf).
+__global__ void __launch_bounds__(256)
+k_bgs_sub(const BatchSegs S, BatchKrylov K, const double *__restrict__ V, int64_t ldv, double *__restrict__ w) {
+    __shared__ double hs[R8][kMaxCols + 1];      // odd row stride: the 8 rhs of a warp in 8 banks
+    const int c = blockIdx.x, s = S.cta_sys[c];
+    if (!K.sys_run[s]) return;
+    const int64_t r0 = S.cta_r0[c], r1 = S.cta_r1[c];
+    const int ncols = *K.j + 1;
+    for (int idx = threadIdx.x; idx < R8 * ncols; idx += blockDim.x) {
+        const int rr = idx / ncols, cc = idx % ncols;
+        hs[rr][cc] = K.hbuf[(int64_t)(s * R8 + rr) * kMaxCols + cc];
+    }
+    __syncthreads();
+    const int rr = threadIdx.x & 7;             // r0 * 8 and the stride are multiples of 8
+    for (int64_t idx = r0 * R8 + threadIdx.x; idx < r1 * R8; idx += blockDim.x) {
+        double x0 = w[idx], x1 = 0.0;
+        int cc = 0;
+        for (; cc + 1 < ncols; cc += 2) {
+            x0 -= V[(int64_t)cc * ldv + idx] * hs[rr][cc];
+            x1 -= V[(int64_t)(cc + 1) * ldv + idx] * hs[rr][cc + 1];
+        }
+        if (cc < ncols) x0 -= V[(int64_t)cc * ldv + idx] * hs[rr][cc];
+        w[idx] = x0 + x1;
+    }
+}
+
 // w -= V h2 with ||w_p||^2 summed on the way (an explicit norm: Pythagoras
 // would lose all accuracy to cancellation after the second pass); the
 // per-system finisher sets beta_p and the pair's Givens update.
 __global__ void __launch_bounds__(256)
 k_bgs_subnorm(const BatchSegs S, BatchKrylov K, const double *__restrict__ V, int64_t ldv, double *__restrict__ w) {
-    __shared__ double hs[R8][kMaxCols];
+    __shared__ double hs[R8][kMaxCols + 1];      // odd row stride: the 8 rhs of a warp in 8 banks
     __shared__ double red[8][R8];
     __shared__ double out[R8];
     const int c = blockIdx.x, s = S.cta_sys[c];
@@ -736,7 +719,7 @@ __global__ void k_blsq(BatchKrylov K) {
 // x_p += Z_p y_p
 __global__ void __launch_bounds__(256)
 k_bupdate_x(const BatchSegs S, BatchKrylov K, const double *__restrict__ Z, int64_t ldz, double *__restrict__ x) {
-    __shared__ double ys[R8][kMaxCols];
+    __shared__ double ys[R8][kMaxCols + 1];      // odd row stride: the 8 rhs of a warp in 8 banks
     __shared__ int jd[R8];
     const int c = blockIdx.x, s = S.cta_sys[c];
     if (threadIdx.x < R8) {
@@ -872,17 +855,14 @@ void launch_bspmv(int64_t nrows, const int64_t *rp, const int32_t *ci, const dou
 }
 void launch_bgs(int pass, const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, double *w,
                 cudaStream_t st) {
-    static bool attr = false;                   // once: room for the longest restart
-    if (!attr) {
-        GEMSLR_CUDA(cudaFuncSetAttribute(k_bgs<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bgs_smem_bytes(1, kMaxCols - 1)));
-        GEMSLR_CUDA(cudaFuncSetAttribute(k_bgs<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bgs_smem_bytes(2, kMaxCols - 1)));
-        attr = true;
+    const size_t bytes = sizeof(double) * std::max(R8 * (K.m + 1), kGs1Threads);
+    if (pass == 1) {
+        k_bgs_dots<1><<<S.ncta, kGs1Threads, bytes, st>>>(S, K, V, ldv, w);
+    } else {
+        k_bgs_sub<<<S.ncta, 256, 0, st>>>(S, K, V, ldv, w);
+        count_launch();
+        k_bgs_dots<2><<<S.ncta, kGs1Threads, bytes, st>>>(S, K, V, ldv, w);
     }
-    const size_t smem = bgs_smem_bytes(pass, K.m);
-    if (pass == 1) k_bgs<1><<<S.ncta, kGsThreads, smem, st>>>(S, K, V, ldv, w);
-    else k_bgs<2><<<S.ncta, kGsThreads, smem, st>>>(S, K, V, ldv, w);
     count_launch();
 }
 void launch_bgs_subnorm(const BatchSegs &S, const BatchKrylov &K, double *V, int64_t ldv, double *w,
