@@ -365,6 +365,8 @@ void gemslr_destroy(gemslr_handle h);
  * gemslr_setup_batch: A and part are arrays of nsys entries; opt applies to all.
  * gemslr_batch_apply: z = M_s^{-1} r for every system and rhs (captured graph).
  * gemslr_batch_fgmres_solve: info has nsys * nrhs entries (system-major).
+ * Both return ARG when a device other than the one the batch was set up on
+ * is current.
  * gemslr_batch_stats: out[0..7] = nsys, total rows, factor nonzeros, bytes of one
  * application (approximate), setup ms, autotuning ms, tuned rows per CTA of the
  * coupling kernels and of the Krylov kernels; with nout > 8, out[8] = the fewest

@@ -63,6 +63,7 @@ struct BLevelHost {          // device level plus what the launcher needs
 
 struct gemslr_batch_ctx {
     int nsys = 0, nlev = 0;
+    int dev = 0;                            // the device the batch was set up on
     int64_t N = 0;                          // batch rows
     std::vector<Hierarchy> sys;
     std::vector<int64_t> base;              // nsys + 1
@@ -506,6 +507,7 @@ gemslr_status setup_batch(int32_t nsys, const gemslr_csr *A, const gemslr_partit
         if (!out || nsys < 1 || !A || !part) fail(GEMSLR_ERR_ARG, "invalid batch arguments");
         auto t0 = std::chrono::steady_clock::now();
         std::unique_ptr<gemslr_batch_ctx> B(new gemslr_batch_ctx());
+        GEMSLR_CUDA(cudaGetDevice(&B->dev));
         if (opt && (opt->dev_alloc == nullptr) != (opt->dev_free == nullptr))
             fail(GEMSLR_ERR_ARG, "dev_alloc and dev_free must be given together");
         if (opt) B->arena.set_allocator(opt->dev_alloc, opt->dev_free, opt->alloc_ctx);
@@ -650,9 +652,20 @@ static void set_user_layout(gemslr_batch_ctx *B, int nrhs) {
     else B->usr_off = B->arena.upload(off);
 }
 
+// The batch's device memory belongs to the device it was set up on: a call
+// made while another device is current is an argument error, not a fault.
+static void require_batch_device(const gemslr_batch_ctx *B) {
+    int dev = -1;
+    GEMSLR_CUDA(cudaGetDevice(&dev));
+    if (dev != B->dev)
+        fail(GEMSLR_ERR_ARG, "the batch lives on device " + std::to_string(B->dev) + " but device " +
+                                 std::to_string(dev) + " is current");
+}
+
 gemslr_status gemslr_batch_apply(gemslr_batch B, const double *r_dev, double *z_dev, int32_t nrhs, void *stream) {
     return bguard([&] {
         if (!B || nrhs < 1 || nrhs > kBatchRhs || !r_dev || !z_dev) fail(GEMSLR_ERR_ARG, "invalid argument");
+        require_batch_device(B);
         cudaStream_t st = (cudaStream_t)stream;
         set_user_layout(B, nrhs);
         ensure_apply_graph_b(B);
@@ -671,6 +684,7 @@ gemslr_status gemslr_batch_fgmres_solve(gemslr_batch B, const double *b_dev, dou
         if (!B || nrhs < 1 || nrhs > kBatchRhs || !b_dev || !x_dev || !opts || !info)
             fail(GEMSLR_ERR_ARG, "invalid argument");
         if (opts->restart < 1 || opts->maxit < 1 || !(opts->rtol > 0)) fail(GEMSLR_ERR_ARG, "invalid solve options");
+        require_batch_device(B);
         auto t0 = std::chrono::steady_clock::now();
         cudaStream_t st = (cudaStream_t)stream;
         const int m = opts->restart;
