@@ -320,6 +320,9 @@ def krylov_work(n, nnzA, its, m, j=None):
     return out
 
 
+SIDE_STREAM = ("dgs_fix_adots", "dgs_tail")     # kernels overlapped with the critical path
+
+
 def rooflines(prof, ab, kw, hbm, peaks, precision, nkeep=4):
     """Roofline entries of the profiled kernels that have a work model, largest
     total time first: M^-1 kernels against the HBM copy peak (algorithmic
@@ -490,7 +493,10 @@ def run_ours(args):
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
     rl = rooflines(prof, ab, kw, hbm, peaks, args.precision)
-    roofline = rl[0]
+    # the dominant kernel on the solve's critical path: the previous step's
+    # reorthogonalisation (dgs_fix_adots) and the Hessenberg bookkeeping
+    # (dgs_tail) run on a second stream beside M^-1 and the next-direction sweep
+    roofline = next((r for r in rl if r["kernel"] not in SIDE_STREAM), rl[0])
     total_prof = sum(v[0] for v in prof.values())
     kernels = {k: {"ms_total": round(v[0], 4), "launches": v[1], "share": round(v[0] / total_prof, 4)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
