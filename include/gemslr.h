@@ -310,7 +310,11 @@ typedef struct {
  * internal stream of its own (created on first use), forked from and joined
  * back into `stream` within every step, so that the next direction's
  * reorthogonalisation overlaps the application of M^{-1}; the call returns
- * with both idle.  Calls on one handle must not overlap.
+ * with both idle.  Calls on one handle must not overlap.  The whole solve is
+ * one CUDA graph with conditional nodes; with the environment variable
+ * GEMSLR_SOLVE_GRAPH=0 the same kernels run in the same order from a host
+ * loop instead (for profilers, which do not see kernels inside conditional
+ * nodes; the iterates are identical).
  * Returns NOT_CONVERGED (with info filled) when maxit is reached, NAN when b
  * or the iteration is not finite.
  */
@@ -355,7 +359,9 @@ void gemslr_destroy(gemslr_handle h);
  * multilevel partition and setup, Alg. 1) handled together with up to
  * GEMSLR_BATCH_RHS right-hand sides each.  Every stage of M^{-1} (Alg. 2) is
  * one launch over all systems; FGMRES runs for every (system, rhs) pair in
- * lock step, the whole solve being one CUDA graph.  The preconditioner is
+ * lock step, the whole solve being one CUDA graph (GEMSLR_SOLVE_GRAPH=0: a
+ * host loop, as for gemslr_fgmres_solve); a system whose pairs have all
+ * stopped is skipped by the rest of the cycle's steps.  The preconditioner is
  * applied in FP32 (W in BF16, FP32 accumulation); Krylov vectors, the
  * least-squares problems and residuals are FP64.  All systems need the same
  * nlev; ranks up to 64.
