@@ -323,6 +323,13 @@ def krylov_work(n, nnzA, its, m, j=None):
 SIDE_STREAM = ("dgs_fix_adots", "dgs_tail")     # kernels overlapped with the critical path
 
 
+def critical_roofline(rl):
+    """The dominant kernel on the solve's critical path: the previous step's
+    reorthogonalisation (dgs_fix_adots) and the Hessenberg bookkeeping
+    (dgs_tail) run on a second stream beside M^-1 and the next-direction sweep."""
+    return next((r for r in rl if r["kernel"] not in SIDE_STREAM), rl[0])
+
+
 def rooflines(prof, ab, kw, hbm, peaks, precision, nkeep=4):
     """Roofline entries of the profiled kernels that have a work model, largest
     total time first: M^-1 kernels against the HBM copy peak (algorithmic
@@ -493,10 +500,7 @@ def run_ours(args):
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
     rl = rooflines(prof, ab, kw, hbm, peaks, args.precision)
-    # the dominant kernel on the solve's critical path: the previous step's
-    # reorthogonalisation (dgs_fix_adots) and the Hessenberg bookkeeping
-    # (dgs_tail) run on a second stream beside M^-1 and the next-direction sweep
-    roofline = next((r for r in rl if r["kernel"] not in SIDE_STREAM), rl[0])
+    roofline = critical_roofline(rl)
     total_prof = sum(v[0] for v in prof.values())
     kernels = {k: {"ms_total": round(v[0], 4), "launches": v[1], "share": round(v[0] / total_prof, 4)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}

@@ -44,3 +44,18 @@ def test_roofline_picks_the_largest_modelled_kernel():
     k = rl[1]
     assert abs(k["achieved"] - kw["dgs_spmv_dots"][0] / 3.0e-3 / 1e9) < 1e-6
     assert k["peak"] == b.FP64_PEAK_GFLOPS
+
+
+def test_line_roofline_is_on_the_critical_path():
+    """A kernel that runs on the second stream beside M^-1 stays in
+    rooflines_top but is not the line's roofline, even with the largest share."""
+    b = _bench()
+    n, nnz = 262144, 1810432
+    kw = {k: tuple(v) for k, v in b.krylov_work(n, nnz, 42, 50).items()}
+    kw["_step"] = {k: tuple(v) for k, v in b.krylov_work(n, nnz, 42, 50, j=25).items()}
+    prof = {"dgs_fix_adots": (2.8, 42), "trsv_up_L0": (2.7, 42), "dgs_spmv_dots": (2.0, 42)}
+    rl = b.rooflines(prof, {"trsv_up_L0": 44_000_000}, kw, 6800.0, {"hbm_gbs": 6800.0}, "mixed")
+    assert rl[0]["kernel"] == "dgs_fix_adots"
+    assert b.critical_roofline(rl)["kernel"] == "trsv_up_L0"
+    only_side = [r for r in rl if r["kernel"] in b.SIDE_STREAM]
+    assert b.critical_roofline(only_side)["kernel"] == "dgs_fix_adots"   # nothing else measured
