@@ -547,6 +547,20 @@ def run_ours(args):
     return 0
 
 
+def level0_sweep_bytes(st, rows_total):
+    """Bytes one level-0 sweep of the batched M^-1 must move (8 right-hand
+    sides), from the batch's stats.  Each sweep is a solve with L and then U:
+    down: the chunks, the FP64 right-hand side in (64 B/row), the FP32 z1 out
+    (32 B/row); up: the chunks, F (values and columns 8 B per entry, row
+    offsets 8 B per row), the tail rows F reads (32 B/row), z1 in (32 B/row)
+    and the FP64 result out (64 B/row)."""
+    rows0 = st["lev0_rows"]
+    tail = rows_total - rows0
+    lu = st["lev0_l_bytes"] + st["lev0_u_bytes"]
+    return {"rows": rows0, "chunk_bytes": lu, "down_bytes": lu + rows0 * (64 + 32),
+            "up_bytes": lu + st["lev0_f_nnz"] * 8 + rows0 * 8 + tail * 32 + rows0 * (32 + 64)}
+
+
 def batch_measure(steps, warmup):
     """c4: 96 uneven convection-diffusion systems x 8 right-hand sides; batched
     FGMRES solves (CUDA events) and batched M^-1 applications per second."""
@@ -611,14 +625,7 @@ def batch_measure(steps, warmup):
     total_ms = sum(ms)
     st = B.stats()
     B.close()
-    # bytes one level-0 sweep must move (8 rhs); each sweep is a solve with L
-    # and then U: down: the chunks, the FP64 right-hand side in, the FP32 z1
-    # out; up: the chunks, F (values, columns, row offsets), the tail rows F
-    # reads, z1 in and the FP64 result out
-    rows0, tail = st["lev0_rows"], int(sum(A.n for A in As)) - st["lev0_rows"]
-    lu = st["lev0_l_bytes"] + st["lev0_u_bytes"]
-    level0 = {"rows": rows0, "chunk_bytes": lu, "down_bytes": lu + rows0 * (64 + 32),
-              "up_bytes": lu + st["lev0_f_nnz"] * 8 + rows0 * 8 + tail * 32 + rows0 * (32 + 64)}
+    level0 = level0_sweep_bytes(st, int(sum(A.n for A in As)))
     return {
         "workload": f"{len(As)} 3-D conv-diff systems, sides U[16,48], beta U[0,0.5], {nrhs} rhs each, "
                     f"{c['nlev']} levels x {c['p']} subdomains, ILUT(1e-3,10), rank {c['rank']}, "

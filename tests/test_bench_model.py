@@ -59,3 +59,16 @@ def test_line_roofline_is_on_the_critical_path():
     assert b.critical_roofline(rl)["kernel"] == "trsv_up_L0"
     only_side = [r for r in rl if r["kernel"] in b.SIDE_STREAM]
     assert b.critical_roofline(only_side)["kernel"] == "dgs_fix_adots"   # nothing else measured
+
+
+def test_level0_sweep_bytes_of_the_batched_workload():
+    """The batched level-0 sweeps' algorithmic bytes, against the figures the
+    c4 bench entry reported for the 96-system workload (2,685,836 level-0 rows
+    of 2,955,748; 493,891,312 chunk bytes)."""
+    b = _bench()
+    rows, total, lu = 2_685_836, 2_955_748, 493_891_312
+    st = {"lev0_rows": rows, "lev0_l_bytes": lu // 2, "lev0_u_bytes": lu - lu // 2, "lev0_f_nnz": 1000}
+    d = b.level0_sweep_bytes(st, total)
+    assert d["chunk_bytes"] == lu
+    assert d["down_bytes"] == 751_731_568 == lu + 96 * rows
+    assert d["up_bytes"] == lu + 8 * 1000 + 8 * rows + 32 * (total - rows) + 96 * rows
