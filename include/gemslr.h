@@ -374,8 +374,8 @@ void gemslr_destroy(gemslr_handle h);
  * Both return ARG when a device other than the one the batch was set up on
  * is current.
  * gemslr_batch_stats: out[0..7] = nsys, total rows, factor nonzeros, bytes of one
- * application (approximate), setup ms, autotuning ms, tuned rows per CTA of the
- * coupling kernels and of the Krylov kernels; with nout > 8, out[8] = the fewest
+ * application (approximate), setup ms, autotuning ms, rows per CTA of the
+ * coupling kernels (tuned) and of the Krylov kernels (512); with nout > 8, out[8] = the fewest
  * right-hand sides a substitution CTA handles (8, 4, 2 or 1: a level whose
  * largest block's vector for 8 right-hand sides does not fit in shared memory
  * splits them over several CTAs; 0: a block too large even for 1 keeps its

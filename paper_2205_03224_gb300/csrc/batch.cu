@@ -89,7 +89,7 @@ struct gemslr_batch_ctx {
     int solve_m = 0;
     uint64_t k_apply = 0, k_top = 0, k_cycle = 0, k_step = 0;
     // autotuned work-list sizes
-    int rows_couple = 128, rows_krylov = 1024;
+    int rows_couple = 128, rows_krylov = kKrylovRows;
     double setup_ms = 0.0, tune_ms = 0.0;
     std::vector<int32_t> host_ints;
     ~gemslr_batch_ctx() {
@@ -610,15 +610,13 @@ gemslr_status setup_batch(int32_t nsys, const gemslr_csr *A, const gemslr_partit
         }
         B->rows_couple = best_rows;
         for (int l = 0; l + 1 < B->nlev; ++l) build_batch_level(B.get(), l, false, best_rows, B->lev[l]);
-        best = 1e30;
-        int best_k = B->rows_krylov;
-        for (int rows : {256, 512, 1024, 2048, 4096}) {
-            build_segments(B.get(), rows);
-            const double t = time_ms(B->cap, [&] { launch_bnorm2(B->S, B->K.partial, B->vin, B->K.rn2, B->cap); });
-            if (t < best) { best = t; best_k = rows; }
-        }
-        B->rows_krylov = best_k;
-        build_segments(B.get(), best_k);
+        // the Krylov kernels' rows per CTA is not tuned on a proxy: a norm
+        // (one column) prefers long CTAs, while the Gram-Schmidt passes over
+        // tens of basis columns are bound by load latency and want many CTAs
+        // in flight (96 systems x 8 rhs: 2048 rows 173 ms per solve, 1024
+        // rows 159 ms, 512 rows 155 ms)
+        B->rows_krylov = kKrylovRows;
+        build_segments(B.get(), B->rows_krylov);
         GEMSLR_CUDA(cudaStreamSynchronize(B->cap));
         B->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tt).count();
         GEMSLR_CUDA(cudaDeviceSynchronize());

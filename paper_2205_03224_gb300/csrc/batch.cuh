@@ -17,6 +17,7 @@ constexpr int kBatchChunkRows = 4 * kBatchWarps; // 4 rows per warp, 8 lanes (on
 constexpr int kBatchTrsvThreads = 32 * (kBatchWarps + 1);
 constexpr int kBatchMaxRank = 64;              // k_eff per system in the batched correction
 constexpr int kBatchThreads = 256;
+constexpr int kKrylovRows = 512;               // batch rows per CTA of the batched Krylov kernels
 
 // One stage level of the batch: the level-l blocks of every system.
 struct BatchLevel {
