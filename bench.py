@@ -561,7 +561,7 @@ def level0_sweep_bytes(st, rows_total):
             "up_bytes": lu + st["lev0_f_nnz"] * 8 + rows0 * 8 + tail * 32 + rows0 * (32 + 64)}
 
 
-def batch_measure(steps, warmup):
+def batch_measure(steps, warmup, systems=None):
     """c4: 96 uneven convection-diffusion systems x 8 right-hand sides; batched
     FGMRES solves (CUDA events) and batched M^-1 applications per second."""
     import torch
@@ -569,6 +569,8 @@ def batch_measure(steps, warmup):
     from paper_2205_03224_gb300 import _lib
     c = gi.CONFIGS["c4"]
     sy = gi.batch_systems(count=c["count"], seed=c["seed"])
+    if systems is not None:              # the first `systems` of the same batch (small profiling cases)
+        sy = sy[:systems]
     As, parts = [], []
     for dims, beta in sy:
         A, xyz = gi.grid_operator(dims, beta=beta)
@@ -646,7 +648,7 @@ def run_batch(args):
     """c4 alone: one batched solve per step."""
     import __graft_entry__
     __graft_entry__.build()
-    d = batch_measure(args.steps, args.warmup)
+    d = batch_measure(args.steps, args.warmup, args.systems)
     line = {
         "metric": METRIC, "value": d["solves_per_s"], "unit": d["unit"],
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": d["time_to_solution_ms"],
@@ -892,6 +894,8 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "c2z"],
                     help="c2 (default line), c3: 128^3 shifted (mixed), c4: batched systems, c5: learned stage, "
                          "c2z: c2 with the complex shift 0.05 (complex FP64)")
+    ap.add_argument("--systems", type=int, default=None,
+                    help="c4 only: the first N systems of the batch (small profiling cases; default all 96)")
     ap.add_argument("--maxit", type=int, default=1000)
     ap.add_argument("--npairs", type=int, default=20000)
     ap.add_argument("--epochs", type=int, default=8)
